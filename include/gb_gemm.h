@@ -1,0 +1,218 @@
+/*
+ * gb_gemm.h -- C ABI of a GB300 (sm_103a) FP64 GEMM library built on the
+ * grid / block / thread / element work-division model of Alpaka
+ * (arXiv 1602.08477, Section 3.2 "Model of Parallel Abstraction").
+ *
+ * The one operation is the DGEMM of Section 4.2:   C <- alpha * A * B + beta * C
+ * over caller-owned, row-major device buffers with leading dimensions ("pitched"
+ * rows, Section 3.4.4):
+ *     A is m x k, element (i, l) at A[i * lda + l], lda >= max(1, k)
+ *     B is k x n, element (l, j) at B[l * ldb + j], ldb >= max(1, n)
+ *     C is m x n, element (i, j) at C[i * ldc + j], ldc >= max(1, n)
+ * All pointers are device pointers of the queue's device, 8-byte aligned.
+ *
+ * Conventions where the paper is silent (BLAS):
+ *   beta == 0            : C is not read (NaN/Inf in C do not propagate).
+ *   alpha == 0 or k == 0 : C <- beta * C and A, B are not read (may be NULL).
+ *   m == 0 or n == 0     : nothing is enqueued; GB_OK.
+ *
+ * Accuracy contract (both precisions): |C - C*|_ij <= 2 (k + 2) 2^-53
+ * (|alpha| (|A||B|)_ij + |beta| |C_ij|), where C* is the exact result; on integer
+ * inputs whose partial sums are exact in FP64 the result is exact.  The emulated
+ * precision meets it when enough slices are used for the data's dynamic range.
+ *
+ * Ownership: the caller owns every A, B, C and workspace buffer; the library
+ * never frees a caller pointer.  The library owns the opaque handles and frees
+ * them in the matching *_destroy / *_release call.  A queue wraps a caller
+ * cudaStream_t and never destroys it.
+ *
+ * Errors: every call returns gb_status and never aborts or throws across the
+ * ABI.  Argument errors are found on the host before anything is enqueued.
+ * gb_last_error() returns a message for the calling thread's last failure.
+ * Errors found on the device (a bounded device-side wait that gave up; a
+ * non-finite input to the emulated path) are recorded in the queue's status
+ * word and returned by gb_queue_wait().
+ *
+ * Asynchrony (Section 3.4.5, "Streams"): operations on a queue run in order.
+ * On a non-blocking queue every call returns once its work is enqueued; on a
+ * blocking queue it returns after the work has finished, with the device
+ * status of that work.
+ */
+#ifndef GB_GEMM_H
+#define GB_GEMM_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    GB_OK = 0,
+    GB_ERR_INVALID_ARG = 1,      /* a size, pointer, leading dimension or option is invalid */
+    GB_ERR_INVALID_WORKDIV = 2,  /* the work division does not cover C or no variant has it */
+    GB_ERR_UNSUPPORTED = 3,      /* valid request the library does not implement */
+    GB_ERR_NO_DEVICE = 4,        /* no CUDA device, or index out of range */
+    GB_ERR_CUDA = 5,             /* a CUDA runtime call failed (message in gb_last_error) */
+    GB_ERR_OUT_OF_BUDGET = 6,    /* a serving request can never fit the HBM budget */
+    GB_ERR_TIMEOUT = 7,          /* a bounded device-side wait gave up */
+    GB_ERR_NONFINITE = 8,        /* the emulated path saw NaN/Inf input (outputs set to NaN) */
+    GB_ERR_BUSY = 9,             /* the handle is in use (e.g. a server still has requests) */
+    GB_ERR_WORKSPACE = 10        /* workspace missing, too small or misaligned */
+} gb_status;
+
+/* Opaque handles. */
+typedef struct gb_device gb_device;
+typedef struct gb_queue gb_queue;
+typedef struct gb_server gb_server;
+
+/*
+ * Work division (Section 3.4.3, "Work Division and Index Retrieval"): the
+ * extents of the grid (blocks per grid), block (threads per block) and thread
+ * (elements per thread) levels, per dimension.  For the GEMM, dim == 2,
+ * dimension 0 runs over the rows of C (m) and dimension 1 over its columns
+ * (n); linearisation is row-major.  The CUDA mapping of Table 2 applies per
+ * dimension: blocks = N / (B * V), threads = B, elements = V.  For the
+ * tensor-pipe kernel one work-division "thread" is one warp and its elements
+ * are that warp's register tile.  A work division must cover C:
+ * grid_blocks[d] * block_threads[d] * thread_elems[d] >= extent[d].
+ */
+typedef struct {
+    uint32_t dim;
+    uint64_t grid_blocks[3];
+    uint64_t block_threads[3];
+    uint64_t thread_elems[3];
+} gb_workdiv;
+
+typedef enum {
+    GB_PREC_NATIVE = 0,    /* FP64 arithmetic on the FP64 pipes */
+    GB_PREC_EMULATED = 1   /* FP64 result from E4M3 slices on the tcgen05 tensor cores */
+} gb_precision;
+
+typedef enum {
+    GB_KERNEL_AUTO = 0,    /* library choice (native: the fastest compiled variant) */
+    GB_KERNEL_NAIVE = 1,   /* one thread per element of C, operands read from global memory */
+    GB_KERNEL_TILED = 2,   /* square shared-memory tiles, one element per thread */
+    GB_KERNEL_DFMA = 3,    /* hierarchical tiles, V x V elements per thread on the FP64 FMA pipe */
+    GB_KERNEL_DMMA = 4     /* hierarchical tiles, warp tiles on FP64 mma.sync (DMMA) */
+} gb_kernel;
+
+/* Library version as major * 10000 + minor * 100 + patch. */
+int gb_version(void);
+
+/* Message for the calling thread's most recent failed call ("" if none).
+ * The pointer stays valid until the next library call on this thread. */
+const char* gb_last_error(void);
+
+/* ---- Devices (Section 3.4.6, Listing "kernel": DevMan<Acc>::getDevByIdx) ---- */
+
+/* Number of CUDA devices. GB_ERR_NO_DEVICE with *n = 0 when there is none. */
+gb_status gb_device_count(int* n);
+
+/* Handle of device `idx` (0-based). No device becomes implicitly current
+ * (Section 3.1: no default device or stream). Free with gb_device_release. */
+gb_status gb_device_get(int idx, gb_device** out);
+
+/* Streaming multiprocessor count and compute capability of a device. */
+gb_status gb_device_info(const gb_device* dev, int* sm_count, int* cc_major, int* cc_minor);
+
+gb_status gb_device_release(gb_device* dev);
+
+/* ---- Queues (Section 3.4.5, "Streams") ----------------------------------------- */
+
+/* Wrap `cuda_stream` (a cudaStream_t of device `dev`, or NULL for the legacy
+ * default stream) into a queue.  blocking != 0: every call on the queue waits
+ * for its work (a synchronous stream); 0: calls return once enqueued.
+ * The queue owns a small device status word; it never destroys the stream. */
+gb_status gb_queue_create(gb_device* dev, void* cuda_stream, int blocking, gb_queue** out);
+
+/* Wait for all work enqueued so far; return the first device-side error
+ * recorded since the last wait (GB_ERR_TIMEOUT, GB_ERR_NONFINITE) and clear it. */
+gb_status gb_queue_wait(gb_queue* q);
+
+/* The wrapped stream (a cudaStream_t). */
+void* gb_queue_stream(const gb_queue* q);
+
+gb_status gb_queue_destroy(gb_queue* q);
+
+/* ---- Work division ------------------------------------------------------------- */
+
+/* The work division the library would use for `kernel` on an m x n x k GEMM
+ * (the CUDA row of Table 2 with the variant's compiled B and V).  For
+ * GB_KERNEL_AUTO the chosen kernel is returned in *chosen (may be NULL). */
+gb_status gb_workdiv_suggest(const gb_device* dev, gb_kernel kernel, int64_t m, int64_t n,
+                             int64_t k, gb_workdiv* out, gb_kernel* chosen);
+
+/* ---- The GEMM (Section 4.2) --------------------------------------------------- */
+
+/*
+ * C <- alpha * A * B + beta * C, enqueued on q (executor "create + enqueue",
+ * Section 3.4.6).
+ *   wd        work division, or NULL for the library's choice.  Native only;
+ *             the emulated precision takes NULL.
+ *   kernel    native variant (GB_KERNEL_AUTO for the library's choice).
+ *   prec      GB_PREC_NATIVE or GB_PREC_EMULATED.
+ *   slices    emulated only: number s of E4M3 digit slices per operand,
+ *             1 <= s <= 16 (each slice carries 5 bits; 0 selects the default
+ *             of 11); ignored for native.
+ *   workspace device buffer of at least gb_dgemm_workspace_size() bytes,
+ *             256-byte aligned (emulated only; native takes NULL, 0).
+ * Errors: GB_ERR_INVALID_ARG (sizes, pointers, leading dimensions, slices),
+ * GB_ERR_INVALID_WORKDIV, GB_ERR_WORKSPACE, GB_ERR_CUDA; on a blocking queue
+ * also the device status of this call (GB_ERR_NONFINITE, GB_ERR_TIMEOUT).
+ */
+gb_status gb_dgemm(gb_queue* q, const gb_workdiv* wd, gb_kernel kernel, gb_precision prec,
+                   int slices, int64_t m, int64_t n, int64_t k, double alpha,
+                   const double* A, int64_t lda, const double* B, int64_t ldb, double beta,
+                   double* C, int64_t ldc, void* workspace, size_t workspace_bytes);
+
+/* Workspace bytes gb_dgemm needs (0 for native). */
+gb_status gb_dgemm_workspace_size(gb_precision prec, int slices, int64_t m, int64_t n,
+                                  int64_t k, size_t* out);
+
+/*
+ * Layout of the emulated path's workspace (all offsets in bytes from its
+ * start, each 1024-byte aligned), for tests and for callers who run the steps
+ * one at a time:
+ *   a_digits  s planes of m rows x kp bytes: E4M3 digit t of A[i, l] at
+ *             a_digits + (t * m + i) * kp + l, zero for l >= k
+ *   b_digits  s planes of n rows x kp bytes: digit t of B[l, j] at
+ *             b_digits + (t * n + j) * kp + l (B transposed, K-major)
+ *   a_exp     m int32: exponent e_i of max_l |A[i, l]| (frexp convention),
+ *             GB_BAD_LINE if row i holds a NaN or Inf
+ *   b_exp     n int32: exponent f_j of max_l |B[l, j]|, or GB_BAD_LINE
+ * with kp = k rounded up to a multiple of 32.
+ */
+#define GB_BAD_LINE 0x40000000
+typedef struct {
+    int64_t kp;
+    size_t a_digits, b_digits, a_exp, b_exp, total;
+} gb_emulated_layout;
+
+gb_status gb_emulated_layout_get(int slices, int64_t m, int64_t n, int64_t k,
+                                 gb_emulated_layout* out);
+
+/* Emulated step e1+e2 for A: exponents and E4M3 digit planes of the rows of A
+ * (m x k, lda) into a workspace laid out as above. */
+gb_status gb_emulated_split_a(gb_queue* q, int slices, int64_t m, int64_t n, int64_t k,
+                              const double* A, int64_t lda, void* workspace,
+                              size_t workspace_bytes);
+
+/* Emulated step e1+e2 for B: exponents and transposed digit planes of the
+ * columns of B (k x n, ldb). */
+gb_status gb_emulated_split_b(gb_queue* q, int slices, int64_t m, int64_t n, int64_t k,
+                              const double* B, int64_t ldb, void* workspace,
+                              size_t workspace_bytes);
+
+/* Emulated steps e3+e4 from a workspace filled by the two split calls: the
+ * slice-pair products on the tensor cores and the recombination into C. */
+gb_status gb_emulated_products(gb_queue* q, int slices, int64_t m, int64_t n, int64_t k,
+                               double alpha, double beta, double* C, int64_t ldc,
+                               void* workspace, size_t workspace_bytes);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* GB_GEMM_H */

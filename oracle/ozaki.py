@@ -20,10 +20,13 @@ kernels can be compared with it step by step:
       E4M3 digits: b1 = 4, b = 5, |d| <= 16 (every such integer is exact in E4M3).
   e3  level sums: S_g = sum_{p+q=g} DA_p DB_q over 2 <= g <= s+1 (pairs with
       p + q > s + 1 are dropped), exact integers.
-  e4  recombination in FP64: acc = 0; for g = s+1 down to 2 (smallest weight
-      first): acc = acc + S_g * 2^-(2 b1 + b (g - 2)); t = acc * 2^(e_i + f_j);
-      C = alpha * t + beta * C0 (beta = 0: C0 not read).  Each operation is one
-      IEEE double rounding, in this order.
+  e4  recombination: the levels are summed exactly as one integer in units of
+      the smallest level, T = sum_{g=2..s+1} S_g 2^(b (s+1-g)), then rounded once
+      to FP64 (round to nearest, ties to even) and scaled by the exact power of
+      two 2^(e_i + f_j - 2 b1 - b (s-1)):  t = RN(T) * 2^E  (a scaling outside
+      the double range is applied as two multiplications by in-range powers of
+      two).  Then C = alpha * t + beta * C0 with each product and the sum one
+      IEEE rounding (beta = 0: C0 not read; alpha = 1 and beta = 0: C = t).
       Rows of A or columns of B flagged in e1 give NaN outputs.
 
 BLAS conventions as for the FP64 oracle: alpha == 0 or k == 0 gives beta*C0
@@ -57,7 +60,7 @@ def slice_digits(X: np.ndarray, e: np.ndarray, s: int, fmt: str = "e4m3", axis: 
     """e2: signed digits of X scaled by 2^-e along ``axis`` (e per row: axis=1).
 
     Lines flagged ``bad`` (non-finite, from e1) get all-zero digits.
-    Returns (digits int64 of shape (s,) + X.shape, final remainders r_s)."""
+    Returns (digits int8 of shape (s,) + X.shape, final remainders r_s)."""
     b1, b, dmax = FORMATS[fmt]
     X = np.asarray(X, dtype=np.float64)
     eb = e[:, None] if axis == 1 else e[None, :]
@@ -65,48 +68,69 @@ def slice_digits(X: np.ndarray, e: np.ndarray, s: int, fmt: str = "e4m3", axis: 
     if bad is not None:
         Xf = np.where(bad[:, None] if axis == 1 else bad[None, :], 0.0, Xf)
     x = np.ldexp(Xf, -eb)
-    D = np.zeros((s,) + X.shape, dtype=np.int64)
+    D = np.zeros((s,) + X.shape, dtype=np.int8)
     y = x * float(2 ** b1)
     for t in range(s):
         if t > 0:
             y = r * float(2 ** b)
         d = np.rint(y)
         r = y - d
-        D[t] = d.astype(np.int64)
-    assert np.abs(D).max(initial=0) <= dmax
+        assert np.abs(d).max(initial=0) <= dmax
+        D[t] = d.astype(np.int8)
     return D, r
 
 
 def level_sums(DA: np.ndarray, DBt: np.ndarray, s: int) -> np.ndarray:
     """e3: S[g-2] = sum_{p+q=g} DA_p @ DBt_q^T for g = 2..s+1 (exact int64).
 
-    DA: (s, m, k) digits of A's rows; DBt: (s, n, k) digits of B's columns."""
+    DA: (s, m, k) digits of A's rows; DBt: (s, n, k) digits of B's columns.
+    The products are formed by a float64 matrix multiply: every digit product
+    is an integer <= 256 and every partial sum an integer far below 2^53, so the
+    library matmul is exact whatever its summation order."""
     m, n = DA.shape[1], DBt.shape[1]
     S = np.zeros((s, m, n), dtype=np.int64)
-    for p in range(1, s + 1):
-        for q in range(1, s + 2 - p):
-            S[p + q - 2] += DA[p - 1] @ DBt[q - 1].T
+    assert DA.shape[2] * s * 256 < 2 ** 53
+    fa = [DA[p].astype(np.float64) for p in range(s)]
+    for q in range(1, s + 1):
+        fbq = DBt[q - 1].astype(np.float64).T      # one plane at a time (memory)
+        for p in range(1, s + 2 - q):
+            S[p + q - 2] += (fa[p - 1] @ fbq).astype(np.int64)
     return S
+
+
+def pow2_scale(x: np.ndarray, E: np.ndarray) -> np.ndarray:
+    """x * 2^E as IEEE multiplications by powers of two that are normal doubles:
+    one multiplication when -1022 <= E <= 1023, else two with E split in halves."""
+    E = np.asarray(E, dtype=np.int64)
+    one = (E >= -1022) & (E <= 1023)
+    E1 = np.where(one, E, E // 2)
+    E2 = np.where(one, 0, E - E // 2)
+    return (x * np.ldexp(1.0, E1)) * np.ldexp(1.0, E2)
 
 
 def recombine(S: np.ndarray, e: np.ndarray, f: np.ndarray, alpha: float, beta: float = 0.0,
               C0: np.ndarray | None = None, fmt: str = "e4m3",
               bad_rows=None, bad_cols=None) -> np.ndarray:
-    """e4: FP64 recombination, smallest-weight level first, then alpha/beta."""
+    """e4: exact integer sum of the levels, one rounding to FP64, exact scaling,
+    then alpha/beta."""
     b1, b, _ = FORMATS[fmt]
     s = S.shape[0]
-    acc = np.zeros(S.shape[1:], dtype=np.float64)
-    for g in range(s + 1, 1, -1):
-        w = 2.0 ** -(2 * b1 + b * (g - 2))
-        acc = acc + S[g - 2].astype(np.float64) * w
-    t = np.ldexp(acc, e[:, None] + f[None, :])
-    out = alpha * t
-    if beta != 0.0:
-        out = out + beta * C0
+    T = np.zeros(S.shape[1:], dtype=object)
+    for g in range(2, s + 2):                   # Horner form of sum S_g 2^(b(s+1-g))
+        T = T * (2 ** b) + S[g - 2].astype(object)
+    rT = np.vectorize(float, otypes=[np.float64])(T) if T.size else np.zeros(T.shape)
+    E = e[:, None] + f[None, :] - (2 * b1 + b * (s - 1))
+    t = pow2_scale(rT, E)
+    if alpha == 1.0 and beta == 0.0:
+        out = t.copy()
+    else:
+        out = alpha * t
+        if beta != 0.0:
+            out = out + beta * np.asarray(C0, dtype=np.float64)
     if bad_rows is not None:
-        out[np.asarray(bad_rows), :] = np.nan
+        out[np.asarray(bad_rows, dtype=np.int64), :] = np.nan
     if bad_cols is not None:
-        out[:, np.asarray(bad_cols)] = np.nan
+        out[:, np.asarray(bad_cols, dtype=np.int64)] = np.nan
     return out
 
 

@@ -1,0 +1,25 @@
+"""GB300-native FP64 GEMM library on the grid / block / thread / element work
+division of Alpaka (arXiv 1602.08477).
+
+The computation lives in libgbgemm.so (hand-written CUDA for sm_103a, C ABI in
+include/gb_gemm.h); this package only builds it and marshals torch tensors and
+streams into its calls.  Importing the package does not load the library;
+the first call does, and raises if it is not built.
+"""
+from ._lib import GbError, Workdiv, load  # noqa: F401
+from .gemm import (  # noqa: F401
+    Device,
+    Queue,
+    alloc_workspace,
+    default_queue,
+    dgemm,
+    emulated_layout,
+    emulated_steps,
+    workdiv_suggest,
+    workspace_size,
+)
+
+
+def build(verbose: bool = False) -> str:
+    from .build import build as _build
+    return _build(verbose=verbose)

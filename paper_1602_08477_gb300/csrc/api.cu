@@ -1,0 +1,507 @@
+// C ABI of the library (include/gb_gemm.h): devices, queues, work divisions and
+// the FP64 GEMM.  Every argument is validated here, on the host, before anything
+// is enqueued; no call throws or aborts across the ABI.
+#include <cuda_runtime.h>
+
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <new>
+
+#include "gb_gemm.h"
+#include "internal.h"
+
+struct gb_device {
+    int idx;
+    int sm_count;
+    int cc_major, cc_minor;
+};
+
+struct gb_queue {
+    gb_device* dev;
+    cudaStream_t stream;
+    int blocking;
+    unsigned* status;  // device status word (kStatus* bits)
+};
+
+namespace gb {
+
+static thread_local char g_err[512] = "";
+
+void set_error(const char* fmt, ...) {
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(g_err, sizeof(g_err), fmt, ap);
+    va_end(ap);
+}
+
+namespace {
+
+// Makes `dev` current for the scope and restores the caller's device.
+struct DeviceScope {
+    int prev = -1;
+    bool ok = true;
+    explicit DeviceScope(int dev) {
+        if (cudaGetDevice(&prev) != cudaSuccess) prev = -1;
+        if (prev != dev) ok = cudaSetDevice(dev) == cudaSuccess;
+    }
+    ~DeviceScope() {
+        int cur = -1;
+        if (prev >= 0 && cudaGetDevice(&cur) == cudaSuccess && cur != prev) cudaSetDevice(prev);
+    }
+};
+
+gb_status cuda_fail(cudaError_t e, const char* what) {
+    set_error("%s: %s", what, cudaGetErrorString(e));
+    return GB_ERR_CUDA;
+}
+
+gb_status invalid(const char* fmt, ...) {
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(g_err, sizeof(g_err), fmt, ap);
+    va_end(ap);
+    return GB_ERR_INVALID_ARG;
+}
+
+bool aligned(const void* p, size_t a) { return (reinterpret_cast<uintptr_t>(p) % a) == 0; }
+
+// Reads and clears the queue's device status word (after the stream finished).
+gb_status drain_status(gb_queue* q) {
+    unsigned h = 0;
+    cudaError_t e = cudaMemcpyAsync(&h, q->status, sizeof(h), cudaMemcpyDeviceToHost, q->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(q->stream);
+    if (e != cudaSuccess) return cuda_fail(e, "reading the queue status");
+    if (h == 0) return GB_OK;
+    e = cudaMemsetAsync(q->status, 0, sizeof(unsigned), q->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(q->stream);
+    if (e != cudaSuccess) return cuda_fail(e, "clearing the queue status");
+    if (h & kStatusTimeout) {
+        set_error("a device-side wait timed out");
+        return GB_ERR_TIMEOUT;
+    }
+    set_error("the emulated path found NaN/Inf in A or B; affected outputs are NaN");
+    return GB_ERR_NONFINITE;
+}
+
+gb_status finish_call(gb_queue* q, cudaError_t e, const char* what) {
+    if (e != cudaSuccess) return cuda_fail(e, what);
+    if (!q->blocking) return GB_OK;
+    e = cudaStreamSynchronize(q->stream);
+    if (e != cudaSuccess) return cuda_fail(e, what);
+    return drain_status(q);
+}
+
+Launch launch_of(const gb_queue* q) { return Launch{q->stream, q->status, q->dev->sm_count}; }
+
+// ---- work divisions ----------------------------------------------------------------
+struct Variant {
+    gb_kernel kernel;
+    uint64_t bt0, bt1;  // block_threads (rows, cols)
+    uint64_t te0, te1;  // thread_elems (rows, cols)
+};
+
+uint64_t cdiv(int64_t a, uint64_t b) { return (uint64_t)((a + (int64_t)b - 1) / (int64_t)b); }
+
+void fill_workdiv(gb_workdiv* wd, const Variant& v, int64_t m, int64_t n) {
+    std::memset(wd, 0, sizeof(*wd));
+    wd->dim = 2;
+    wd->block_threads[0] = v.bt0;
+    wd->block_threads[1] = v.bt1;
+    wd->thread_elems[0] = v.te0;
+    wd->thread_elems[1] = v.te1;
+    wd->grid_blocks[0] = cdiv(m > 0 ? m : 1, v.bt0 * v.te0);
+    wd->grid_blocks[1] = cdiv(n > 0 ? n : 1, v.bt1 * v.te1);
+    for (int d = 2; d < 3; ++d) wd->grid_blocks[d] = wd->block_threads[d] = wd->thread_elems[d] = 1;
+}
+
+// The library's default variant per kernel family and size.
+Variant default_variant(gb_kernel kernel, int64_t m, int64_t n, int64_t k) {
+    (void)k;
+    const int64_t mn = m < n ? m : n;
+    switch (kernel) {
+        case GB_KERNEL_NAIVE: return {kernel, 16, 16, 1, 1};
+        case GB_KERNEL_TILED: return {kernel, 16, 16, 1, 1};
+        case GB_KERNEL_DFMA: return {kernel, 16, 16, 4, 4};
+        case GB_KERNEL_DMMA:
+        default:
+            // a warp is one "thread"; its 32 x 32 (or 16 x 16) register tile the elements
+            if (mn <= 1024) return {GB_KERNEL_DMMA, 2, 2, 16, 16};
+            return {GB_KERNEL_DMMA, 2, 2, 32, 32};
+    }
+}
+
+gb_status check_workdiv(const gb_workdiv* wd, gb_kernel kernel, int64_t m, int64_t n) {
+    if (wd->dim != 2) {
+        set_error("work division: dim must be 2 (rows, cols), got %u", wd->dim);
+        return GB_ERR_INVALID_WORKDIV;
+    }
+    for (int d = 0; d < 2; ++d) {
+        if (wd->grid_blocks[d] == 0 || wd->block_threads[d] == 0 || wd->thread_elems[d] == 0) {
+            set_error("work division: zero extent in dimension %d", d);
+            return GB_ERR_INVALID_WORKDIV;
+        }
+    }
+    const uint64_t ext[2] = {(uint64_t)m, (uint64_t)n};
+    for (int d = 0; d < 2; ++d) {
+        const uint64_t cover = wd->grid_blocks[d] * wd->block_threads[d] * wd->thread_elems[d];
+        if (cover < ext[d]) {
+            set_error("work division does not cover C: dimension %d covers %llu < %llu", d,
+                      (unsigned long long)cover, (unsigned long long)ext[d]);
+            return GB_ERR_INVALID_WORKDIV;
+        }
+    }
+    const uint64_t by = wd->block_threads[0], bx = wd->block_threads[1];
+    const uint64_t ey = wd->thread_elems[0], ex = wd->thread_elems[1];
+    bool ok = false;
+    switch (kernel) {
+        case GB_KERNEL_NAIVE:
+            ok = ey == 1 && ex == 1 && by * bx <= 1024 && bx <= 1024 && by <= 1024 &&
+                 wd->grid_blocks[0] <= 65535;
+            break;
+        case GB_KERNEL_TILED:
+            ok = ey == 1 && ex == 1 && by == bx && (bx == 8 || bx == 16 || bx == 32) &&
+                 wd->grid_blocks[0] <= 65535;
+            break;
+        case GB_KERNEL_DFMA:
+            ok = by == 16 && bx == 16 && ey == ex && (ex == 2 || ex == 4 || ex == 8) &&
+                 wd->grid_blocks[0] <= 65535;
+            break;
+        case GB_KERNEL_DMMA:
+            ok = dmma_variant_exists((int)by, (int)bx, (int)ey, (int)ex) &&
+                 wd->grid_blocks[0] <= 65535;
+            break;
+        default: break;
+    }
+    if (!ok) {
+        set_error("no compiled variant of kernel %d has block (%llu, %llu) x elements (%llu, %llu)",
+                  (int)kernel, (unsigned long long)by, (unsigned long long)bx,
+                  (unsigned long long)ey, (unsigned long long)ex);
+        return GB_ERR_INVALID_WORKDIV;
+    }
+    return GB_OK;
+}
+
+gb_status check_gemm_args(int64_t m, int64_t n, int64_t k, double alpha, const double* A,
+                          int64_t lda, const double* B, int64_t ldb, double beta,
+                          const double* C, int64_t ldc) {
+    if (m < 0 || n < 0 || k < 0) return invalid("m, n, k must be >= 0 (got %lld, %lld, %lld)",
+                                                 (long long)m, (long long)n, (long long)k);
+    if (lda < (k > 1 ? k : 1)) return invalid("lda = %lld < max(1, k = %lld)", (long long)lda, (long long)k);
+    if (ldb < (n > 1 ? n : 1)) return invalid("ldb = %lld < max(1, n = %lld)", (long long)ldb, (long long)n);
+    if (ldc < (n > 1 ? n : 1)) return invalid("ldc = %lld < max(1, n = %lld)", (long long)ldc, (long long)n);
+    if (m == 0 || n == 0) return GB_OK;
+    if (!C) return invalid("C is NULL");
+    if (!aligned(C, 8)) return invalid("C is not 8-byte aligned");
+    const bool reads_ab = alpha != 0.0 && k > 0;
+    if (reads_ab && (!A || !B)) return invalid("A or B is NULL while alpha != 0 and k > 0");
+    if (reads_ab && (!aligned(A, 8) || !aligned(B, 8))) return invalid("A or B is not 8-byte aligned");
+    if (!(alpha == alpha) || !(beta == beta)) return invalid("alpha or beta is NaN");
+    (void)beta;
+    return GB_OK;
+}
+
+int resolve_slices(int slices) { return slices == 0 ? 11 : slices; }
+
+}  // namespace
+
+EmuLayout emu_layout(int s, int64_t m, int64_t n, int64_t k) {
+    EmuLayout L{};
+    L.kp = ((k + 31) / 32) * 32;
+    if (L.kp == 0) L.kp = 32;
+    auto up = [](size_t x) { return (x + 1023) & ~(size_t)1023; };
+    size_t off = 0;
+    L.a_digits = off;
+    off = up(off + (size_t)s * (size_t)m * (size_t)L.kp);
+    L.b_digits = off;
+    off = up(off + (size_t)s * (size_t)n * (size_t)L.kp);
+    L.a_exp = off;
+    off = up(off + sizeof(int32_t) * (size_t)m);
+    L.b_exp = off;
+    off = up(off + sizeof(int32_t) * (size_t)n);
+    L.total = off;
+    return L;
+}
+
+}  // namespace gb
+
+using namespace gb;
+
+extern "C" {
+
+int gb_version(void) { return 100; }
+
+const char* gb_last_error(void) { return gb::g_err; }
+
+gb_status gb_device_count(int* n) {
+    if (!n) return invalid("n is NULL");
+    int c = 0;
+    cudaError_t e = cudaGetDeviceCount(&c);
+    if (e != cudaSuccess || c == 0) {
+        *n = 0;
+        set_error("no CUDA device: %s", cudaGetErrorString(e));
+        return GB_ERR_NO_DEVICE;
+    }
+    *n = c;
+    return GB_OK;
+}
+
+gb_status gb_device_get(int idx, gb_device** out) {
+    if (!out) return invalid("out is NULL");
+    *out = nullptr;
+    int c = 0;
+    if (cudaGetDeviceCount(&c) != cudaSuccess || idx < 0 || idx >= c) {
+        set_error("device index %d out of range (count %d)", idx, c);
+        return GB_ERR_NO_DEVICE;
+    }
+    cudaDeviceProp p;
+    cudaError_t e = cudaGetDeviceProperties(&p, idx);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaGetDeviceProperties");
+    gb_device* d = new (std::nothrow) gb_device{idx, p.multiProcessorCount, p.major, p.minor};
+    if (!d) return invalid("out of host memory");
+    *out = d;
+    return GB_OK;
+}
+
+gb_status gb_device_info(const gb_device* dev, int* sm_count, int* cc_major, int* cc_minor) {
+    if (!dev) return invalid("dev is NULL");
+    if (sm_count) *sm_count = dev->sm_count;
+    if (cc_major) *cc_major = dev->cc_major;
+    if (cc_minor) *cc_minor = dev->cc_minor;
+    return GB_OK;
+}
+
+gb_status gb_device_release(gb_device* dev) {
+    delete dev;
+    return GB_OK;
+}
+
+gb_status gb_queue_create(gb_device* dev, void* cuda_stream, int blocking, gb_queue** out) {
+    if (!dev || !out) return invalid("dev or out is NULL");
+    *out = nullptr;
+    DeviceScope scope(dev->idx);
+    if (!scope.ok) return cuda_fail(cudaGetLastError(), "cudaSetDevice");
+    unsigned* st = nullptr;
+    cudaError_t e = cudaMalloc(&st, sizeof(unsigned));
+    if (e != cudaSuccess) return cuda_fail(e, "allocating the queue status word");
+    e = cudaMemset(st, 0, sizeof(unsigned));
+    if (e != cudaSuccess) {
+        cudaFree(st);
+        return cuda_fail(e, "clearing the queue status word");
+    }
+    gb_queue* q = new (std::nothrow) gb_queue{dev, (cudaStream_t)cuda_stream, blocking, st};
+    if (!q) {
+        cudaFree(st);
+        return invalid("out of host memory");
+    }
+    *out = q;
+    return GB_OK;
+}
+
+gb_status gb_queue_wait(gb_queue* q) {
+    if (!q) return invalid("q is NULL");
+    DeviceScope scope(q->dev->idx);
+    cudaError_t e = cudaStreamSynchronize(q->stream);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaStreamSynchronize");
+    return drain_status(q);
+}
+
+void* gb_queue_stream(const gb_queue* q) { return q ? (void*)q->stream : nullptr; }
+
+gb_status gb_queue_destroy(gb_queue* q) {
+    if (!q) return GB_OK;
+    DeviceScope scope(q->dev->idx);
+    cudaStreamSynchronize(q->stream);
+    cudaFree(q->status);
+    delete q;
+    return GB_OK;
+}
+
+gb_status gb_workdiv_suggest(const gb_device* dev, gb_kernel kernel, int64_t m, int64_t n,
+                             int64_t k, gb_workdiv* out, gb_kernel* chosen) {
+    if (!out) return invalid("out is NULL");
+    (void)dev;
+    if (m < 0 || n < 0 || k < 0) return invalid("m, n, k must be >= 0");
+    if (kernel < GB_KERNEL_AUTO || kernel > GB_KERNEL_DMMA) return invalid("unknown kernel %d", (int)kernel);
+    const Variant v = default_variant(kernel, m, n, k);
+    fill_workdiv(out, v, m, n);
+    if (chosen) *chosen = v.kernel;
+    return GB_OK;
+}
+
+gb_status gb_dgemm_workspace_size(gb_precision prec, int slices, int64_t m, int64_t n,
+                                  int64_t k, size_t* out) {
+    if (!out) return invalid("out is NULL");
+    if (m < 0 || n < 0 || k < 0) return invalid("m, n, k must be >= 0");
+    if (prec == GB_PREC_NATIVE) {
+        *out = 0;
+        return GB_OK;
+    }
+    if (prec != GB_PREC_EMULATED) return invalid("unknown precision %d", (int)prec);
+    const int s = resolve_slices(slices);
+    if (s < 1 || s > 16) return invalid("slices must be in [1, 16] (or 0 for the default), got %d", slices);
+    *out = emu_layout(s, m, n, k).total;
+    return GB_OK;
+}
+
+gb_status gb_emulated_layout_get(int slices, int64_t m, int64_t n, int64_t k,
+                                 gb_emulated_layout* out) {
+    if (!out) return invalid("out is NULL");
+    if (m < 0 || n < 0 || k < 0) return invalid("m, n, k must be >= 0");
+    const int s = resolve_slices(slices);
+    if (s < 1 || s > 16) return invalid("slices must be in [1, 16], got %d", slices);
+    const EmuLayout L = emu_layout(s, m, n, k);
+    out->kp = L.kp;
+    out->a_digits = L.a_digits;
+    out->b_digits = L.b_digits;
+    out->a_exp = L.a_exp;
+    out->b_exp = L.b_exp;
+    out->total = L.total;
+    return GB_OK;
+}
+
+static gb_status check_workspace(int s, int64_t m, int64_t n, int64_t k, void* ws, size_t bytes) {
+    const EmuLayout L = emu_layout(s, m, n, k);
+    if (!ws) {
+        set_error("the emulated path needs a workspace of %zu bytes", L.total);
+        return GB_ERR_WORKSPACE;
+    }
+    if (!aligned(ws, 256)) {
+        set_error("workspace must be 256-byte aligned");
+        return GB_ERR_WORKSPACE;
+    }
+    if (bytes < L.total) {
+        set_error("workspace of %zu bytes < required %zu", bytes, L.total);
+        return GB_ERR_WORKSPACE;
+    }
+    return GB_OK;
+}
+
+gb_status gb_emulated_split_a(gb_queue* q, int slices, int64_t m, int64_t n, int64_t k,
+                              const double* A, int64_t lda, void* workspace,
+                              size_t workspace_bytes) {
+    if (!q) return invalid("q is NULL");
+    const int s = resolve_slices(slices);
+    if (s < 1 || s > 16) return invalid("slices must be in [1, 16], got %d", slices);
+    if (m < 0 || n < 0 || k < 0) return invalid("m, n, k must be >= 0");
+    if (lda < (k > 1 ? k : 1)) return invalid("lda < max(1, k)");
+    if (m > 0 && k > 0 && (!A || !aligned(A, 8))) return invalid("A is NULL or misaligned");
+    gb_status st = check_workspace(s, m, n, k, workspace, workspace_bytes);
+    if (st != GB_OK) return st;
+    DeviceScope scope(q->dev->idx);
+    const EmuLayout L = emu_layout(s, m, n, k);
+    uint8_t* ws = static_cast<uint8_t*>(workspace);
+    cudaError_t e = launch_split_rows(launch_of(q), s, m, k, A, lda, ws + L.a_digits, L.kp,
+                                      reinterpret_cast<int32_t*>(ws + L.a_exp));
+    return finish_call(q, e, "split of A");
+}
+
+gb_status gb_emulated_split_b(gb_queue* q, int slices, int64_t m, int64_t n, int64_t k,
+                              const double* B, int64_t ldb, void* workspace,
+                              size_t workspace_bytes) {
+    if (!q) return invalid("q is NULL");
+    const int s = resolve_slices(slices);
+    if (s < 1 || s > 16) return invalid("slices must be in [1, 16], got %d", slices);
+    if (m < 0 || n < 0 || k < 0) return invalid("m, n, k must be >= 0");
+    if (ldb < (n > 1 ? n : 1)) return invalid("ldb < max(1, n)");
+    if (n > 0 && k > 0 && (!B || !aligned(B, 8))) return invalid("B is NULL or misaligned");
+    gb_status st = check_workspace(s, m, n, k, workspace, workspace_bytes);
+    if (st != GB_OK) return st;
+    DeviceScope scope(q->dev->idx);
+    const EmuLayout L = emu_layout(s, m, n, k);
+    uint8_t* ws = static_cast<uint8_t*>(workspace);
+    cudaError_t e = launch_split_cols(launch_of(q), s, n, k, B, ldb, ws + L.b_digits, L.kp,
+                                      reinterpret_cast<int32_t*>(ws + L.b_exp));
+    return finish_call(q, e, "split of B");
+}
+
+gb_status gb_emulated_products(gb_queue* q, int slices, int64_t m, int64_t n, int64_t k,
+                               double alpha, double beta, double* C, int64_t ldc,
+                               void* workspace, size_t workspace_bytes) {
+    if (!q) return invalid("q is NULL");
+    const int s = resolve_slices(slices);
+    if (s < 1 || s > 16) return invalid("slices must be in [1, 16], got %d", slices);
+    if (m < 0 || n < 0 || k < 0) return invalid("m, n, k must be >= 0");
+    if (ldc < (n > 1 ? n : 1)) return invalid("ldc < max(1, n)");
+    if (m > 0 && n > 0 && (!C || !aligned(C, 8))) return invalid("C is NULL or misaligned");
+    gb_status st = check_workspace(s, m, n, k, workspace, workspace_bytes);
+    if (st != GB_OK) return st;
+    DeviceScope scope(q->dev->idx);
+    const EmuLayout L = emu_layout(s, m, n, k);
+    uint8_t* ws = static_cast<uint8_t*>(workspace);
+    cudaError_t e = launch_emu_products(launch_of(q), s, m, n, k, alpha, beta, C, ldc,
+                                        ws + L.a_digits, ws + L.b_digits, L.kp,
+                                        reinterpret_cast<int32_t*>(ws + L.a_exp),
+                                        reinterpret_cast<int32_t*>(ws + L.b_exp));
+    return finish_call(q, e, "emulated products");
+}
+
+gb_status gb_dgemm(gb_queue* q, const gb_workdiv* wd, gb_kernel kernel, gb_precision prec,
+                   int slices, int64_t m, int64_t n, int64_t k, double alpha, const double* A,
+                   int64_t lda, const double* B, int64_t ldb, double beta, double* C,
+                   int64_t ldc, void* workspace, size_t workspace_bytes) {
+    if (!q) return invalid("q is NULL");
+    gb_status st = check_gemm_args(m, n, k, alpha, A, lda, B, ldb, beta, C, ldc);
+    if (st != GB_OK) return st;
+    if (prec != GB_PREC_NATIVE && prec != GB_PREC_EMULATED) return invalid("unknown precision %d", (int)prec);
+    if (kernel < GB_KERNEL_AUTO || kernel > GB_KERNEL_DMMA) return invalid("unknown kernel %d", (int)kernel);
+    int s = 0;
+    if (prec == GB_PREC_EMULATED) {
+        s = resolve_slices(slices);
+        if (s < 1 || s > 16) return invalid("slices must be in [1, 16] (or 0), got %d", slices);
+        if (wd) {
+            set_error("the emulated precision takes no work division (pass NULL)");
+            return GB_ERR_INVALID_WORKDIV;
+        }
+    }
+    Variant v{};
+    gb_workdiv resolved;
+    if (prec == GB_PREC_NATIVE) {
+        if (wd) {
+            const gb_kernel kk = kernel == GB_KERNEL_AUTO ? GB_KERNEL_DMMA : kernel;
+            st = check_workdiv(wd, kk, m, n);
+            if (st != GB_OK) return st;
+            resolved = *wd;
+            v = Variant{kk, wd->block_threads[0], wd->block_threads[1], wd->thread_elems[0],
+                        wd->thread_elems[1]};
+        } else {
+            v = default_variant(kernel, m, n, k);
+            fill_workdiv(&resolved, v, m, n);
+            st = check_workdiv(&resolved, v.kernel, m, n);
+            if (st != GB_OK) return st;
+        }
+    }
+    if (m == 0 || n == 0) return GB_OK;
+    DeviceScope scope(q->dev->idx);
+    if (!scope.ok) return cuda_fail(cudaGetLastError(), "cudaSetDevice");
+    const Launch L = launch_of(q);
+    const Gemm g{m, n, k, alpha, beta, A, lda, B, ldb, C, ldc};
+    if (alpha == 0.0 || k == 0) return finish_call(q, launch_scale(L, g), "C <- beta C");
+
+    if (prec == GB_PREC_EMULATED) {
+        st = check_workspace(s, m, n, k, workspace, workspace_bytes);
+        if (st != GB_OK) return st;
+        const EmuLayout lay = emu_layout(s, m, n, k);
+        uint8_t* ws = static_cast<uint8_t*>(workspace);
+        int32_t* ea = reinterpret_cast<int32_t*>(ws + lay.a_exp);
+        int32_t* fb = reinterpret_cast<int32_t*>(ws + lay.b_exp);
+        cudaError_t e = launch_split_rows(L, s, m, k, A, lda, ws + lay.a_digits, lay.kp, ea);
+        if (e == cudaSuccess) e = launch_split_cols(L, s, n, k, B, ldb, ws + lay.b_digits, lay.kp, fb);
+        if (e == cudaSuccess)
+            e = launch_emu_products(L, s, m, n, k, alpha, beta, C, ldc, ws + lay.a_digits,
+                                    ws + lay.b_digits, lay.kp, ea, fb);
+        return finish_call(q, e, "emulated dgemm");
+    }
+
+    cudaError_t e = cudaSuccess;
+    switch (v.kernel) {
+        case GB_KERNEL_NAIVE: e = launch_naive(L, g, (int)v.bt0, (int)v.bt1); break;
+        case GB_KERNEL_TILED: e = launch_tiled(L, g, (int)v.bt0); break;
+        case GB_KERNEL_DFMA: e = launch_dfma(L, g, (int)v.te0); break;
+        case GB_KERNEL_DMMA:
+        default: e = launch_dmma(L, g, (int)v.bt0, (int)v.bt1, (int)v.te0, (int)v.te1); break;
+    }
+    return finish_call(q, e, "native dgemm");
+}
+
+}  // extern "C"

@@ -1,0 +1,390 @@
+// Native FP64 GEMM kernels for sm_103a: C <- alpha*A*B + beta*C (Section 4.2).
+//
+// Three work divisions of the grid / block / thread / element hierarchy
+// (Section 3.2, Table 2 CUDA row: blocks = N/(B*V), threads = B, elements = V):
+//   naive  - one thread per element of C, operands straight from global memory
+//            (the nested-loop kernel of Section 4.2.1 mapped to CUDA);
+//   tiled  - square T x T shared-memory tiles, one element per thread (the
+//            block-parallel tiling kernel of Section 4.2.1);
+//   dfma   - hierarchical tiling with V x V elements per thread in registers
+//            (Section 4.2.2, Fig. "tiling_kernel"), FP64 FMA pipe;
+//   dmma   - the same hierarchy with a warp as the thread level and the warp's
+//            register tile as the element level, on FP64 mma.sync (DMMA).
+// Row-major operands with leading dimensions; beta == 0 never reads C.
+#include <cuda_runtime.h>
+#include <cstdint>
+
+#include "internal.h"
+
+namespace gb {
+namespace {
+
+template <bool kBeta0>
+__device__ __forceinline__ void store_out(double* C, int64_t idx, double alpha, double acc,
+                                          double beta) {
+    if (kBeta0) {
+        C[idx] = alpha * acc;
+    } else {
+        C[idx] = alpha * acc + beta * C[idx];
+    }
+}
+
+// ---- C <- beta * C ---------------------------------------------------------------
+__global__ void scale_kernel(int64_t m, int64_t n, double beta, double* __restrict__ C,
+                             int64_t ldc) {
+    const int64_t total = m * n;
+    for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < total;
+         t += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t i = t / n, j = t - i * n;
+        double* c = &C[i * ldc + j];
+        *c = (beta == 0.0) ? 0.0 : beta * (*c);
+    }
+}
+
+// ---- naive: one element per thread ---------------------------------------------------
+template <bool kBeta0>
+__global__ void naive_kernel(int64_t m, int64_t n, int64_t k, double alpha,
+                             const double* __restrict__ A, int64_t lda,
+                             const double* __restrict__ B, int64_t ldb, double beta,
+                             double* __restrict__ C, int64_t ldc) {
+    const int64_t i = blockIdx.y * (int64_t)blockDim.y + threadIdx.y;
+    const int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i >= m || j >= n) return;
+    const double* a = A + i * lda;
+    const double* b = B + j;
+    double s = 0.0;
+    for (int64_t l = 0; l < k; ++l) s = fma(a[l], b[l * ldb], s);
+    store_out<kBeta0>(C, i * ldc + j, alpha, s, beta);
+}
+
+// ---- tiled: T x T shared-memory tiles, one element per thread ------------------------
+template <int T, bool kBeta0>
+__global__ void tiled_kernel(int64_t m, int64_t n, int64_t k, double alpha,
+                             const double* __restrict__ A, int64_t lda,
+                             const double* __restrict__ B, int64_t ldb, double beta,
+                             double* __restrict__ C, int64_t ldc) {
+    __shared__ double As[T][T];
+    __shared__ double Bs[T][T];
+    const int tx = threadIdx.x, ty = threadIdx.y;
+    const int64_t i = blockIdx.y * (int64_t)T + ty;
+    const int64_t j = blockIdx.x * (int64_t)T + tx;
+    double s = 0.0;
+    for (int64_t l0 = 0; l0 < k; l0 += T) {
+        As[ty][tx] = (i < m && l0 + tx < k) ? A[i * lda + l0 + tx] : 0.0;
+        Bs[ty][tx] = (l0 + ty < k && j < n) ? B[(l0 + ty) * ldb + j] : 0.0;
+        __syncthreads();
+#pragma unroll
+        for (int e = 0; e < T; ++e) s = fma(As[ty][e], Bs[e][tx], s);
+        __syncthreads();
+    }
+    if (i < m && j < n) store_out<kBeta0>(C, i * ldc + j, alpha, s, beta);
+}
+
+// ---- dfma: 16 x 16 threads, V x V elements per thread --------------------------------
+// Block tile (16V) x (16V); thread (ty, tx) owns rows ty + 16r and columns tx + 16c
+// (r, c < V), so shared-memory reads are broadcasts / consecutive and the global
+// stores of a half-warp are 128 contiguous bytes.  K advances in steps of 16
+// through a register-prefetched, double-buffered shared-memory stage.
+template <int V, bool kBeta0>
+__global__ void __launch_bounds__(256) dfma_kernel(int64_t m, int64_t n, int64_t k,
+                                                   double alpha, const double* __restrict__ A,
+                                                   int64_t lda, const double* __restrict__ B,
+                                                   int64_t ldb, double beta,
+                                                   double* __restrict__ C, int64_t ldc) {
+    constexpr int BM = 16 * V, BN = 16 * V, BK = (V == 8) ? 8 : 16;  // <= 48 KB static smem
+    constexpr int A_PER_T = BM * BK / 256;  // elements of the A tile each thread loads
+    constexpr int B_PER_T = BK * BN / 256;
+    __shared__ double As[2][BK][BM + 1];  // transposed: As[l][row]
+    __shared__ double Bs[2][BK][BN];
+    const int tid = threadIdx.x;
+    const int tx = tid & 15, ty = tid >> 4;
+    const int64_t row0 = blockIdx.y * (int64_t)BM, col0 = blockIdx.x * (int64_t)BN;
+
+    double acc[V][V];
+#pragma unroll
+    for (int r = 0; r < V; ++r)
+#pragma unroll
+        for (int c = 0; c < V; ++c) acc[r][c] = 0.0;
+
+    double ra[A_PER_T], rb[B_PER_T];
+    auto load_regs = [&](int64_t l0) {
+#pragma unroll
+        for (int u = 0; u < A_PER_T; ++u) {
+            const int e = tid + 256 * u;          // e in [0, BM*BK)
+            const int r = e / BK, l = e % BK;     // consecutive threads along l
+            const int64_t gi = row0 + r, gl = l0 + l;
+            ra[u] = (gi < m && gl < k) ? A[gi * lda + gl] : 0.0;
+        }
+#pragma unroll
+        for (int u = 0; u < B_PER_T; ++u) {
+            const int e = tid + 256 * u;
+            const int l = e / BN, c = e % BN;     // consecutive threads along columns
+            const int64_t gl = l0 + l, gj = col0 + c;
+            rb[u] = (gl < k && gj < n) ? B[gl * ldb + gj] : 0.0;
+        }
+    };
+    auto store_smem = [&](int buf) {
+#pragma unroll
+        for (int u = 0; u < A_PER_T; ++u) {
+            const int e = tid + 256 * u;
+            As[buf][e % BK][e / BK] = ra[u];
+        }
+#pragma unroll
+        for (int u = 0; u < B_PER_T; ++u) {
+            const int e = tid + 256 * u;
+            Bs[buf][e / BN][e % BN] = rb[u];
+        }
+    };
+
+    const int64_t nk = (k + BK - 1) / BK;
+    if (nk > 0) {
+        load_regs(0);
+        store_smem(0);
+    }
+    __syncthreads();
+    for (int64_t kt = 0; kt < nk; ++kt) {
+        const int buf = (int)(kt & 1);
+        if (kt + 1 < nk) load_regs((kt + 1) * BK);
+#pragma unroll
+        for (int l = 0; l < BK; ++l) {
+            double a[V], b[V];
+#pragma unroll
+            for (int r = 0; r < V; ++r) a[r] = As[buf][l][ty + 16 * r];
+#pragma unroll
+            for (int c = 0; c < V; ++c) b[c] = Bs[buf][l][tx + 16 * c];
+#pragma unroll
+            for (int r = 0; r < V; ++r)
+#pragma unroll
+                for (int c = 0; c < V; ++c) acc[r][c] = fma(a[r], b[c], acc[r][c]);
+        }
+        if (kt + 1 < nk) store_smem(buf ^ 1);
+        __syncthreads();
+    }
+#pragma unroll
+    for (int r = 0; r < V; ++r) {
+        const int64_t gi = row0 + ty + 16 * r;
+        if (gi >= m) continue;
+#pragma unroll
+        for (int c = 0; c < V; ++c) {
+            const int64_t gj = col0 + tx + 16 * c;
+            if (gj < n) store_out<kBeta0>(C, gi * ldc + gj, alpha, acc[r][c], beta);
+        }
+    }
+}
+
+// ---- dmma: FP64 mma.sync.m16n8k4 warp tiles ----------------------------------------
+// Fragment layout of mma.m16n8k4 .f64 (PTX ISA, "Matrix fragments for mma.m16n8k4"):
+// with g = lane / 4 and t = lane % 4,
+//   A (16x4, row): a0 = A[g][t], a1 = A[g+8][t]
+//   B (4x8, col):  b0 = B[t][g]
+//   C (16x8):      c0, c1 = C[g][2t], C[g][2t+1];  c2, c3 = C[g+8][2t], C[g+8][2t+1]
+__device__ __forceinline__ void dmma_16x8x4(double (&c)[4], double a0, double a1, double b0) {
+    asm volatile(
+        "mma.sync.aligned.m16n8k4.row.col.f64.f64.f64.f64 {%0,%1,%2,%3}, {%4,%5}, {%6}, "
+        "{%0,%1,%2,%3};\n"
+        : "+d"(c[0]), "+d"(c[1]), "+d"(c[2]), "+d"(c[3])
+        : "d"(a0), "d"(a1), "d"(b0));
+}
+
+__device__ __forceinline__ void cp_async8(void* smem, const void* gmem, bool valid) {
+    const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
+    const int src_bytes = valid ? 8 : 0;  // 0: zero-fill, global not read
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 8, %2;\n" ::"r"(s), "l"(gmem),
+                 "r"(src_bytes));
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n"); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait() {
+    asm volatile("cp.async.wait_group %0;\n" ::"n"(N));
+}
+
+template <int WARPS_M, int WARPS_N, int WT_M, int WT_N, bool kBeta0>
+__global__ void __launch_bounds__(32 * WARPS_M * WARPS_N)
+    dmma_kernel(int64_t m, int64_t n, int64_t k, double alpha, const double* __restrict__ A,
+                int64_t lda, const double* __restrict__ B, int64_t ldb, double beta,
+                double* __restrict__ C, int64_t ldc) {
+    constexpr int NT = 32 * WARPS_M * WARPS_N;
+    constexpr int BM = WARPS_M * WT_M, BN = WARPS_N * WT_N, BK = 8;
+    constexpr int MT = WT_M / 16, NTILE = WT_N / 8;
+    // Row pitches chosen so each half-warp's fragment reads hit distinct banks.
+    constexpr int LDA_S = BK + 4;
+    constexpr int LDB_S = BN + 4;
+    constexpr int STAGES = (BM >= 128) ? 2 : 3;  // <= 48 KB static smem
+    __shared__ __align__(16) double As[STAGES][BM * LDA_S];
+    __shared__ __align__(16) double Bs[STAGES][BK * LDB_S];
+
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int wm = warp / WARPS_N, wn = warp % WARPS_N;
+    const int g = lane >> 2, t = lane & 3;
+    const int64_t row0 = blockIdx.y * (int64_t)BM, col0 = blockIdx.x * (int64_t)BN;
+    const int64_t nk = (k + BK - 1) / BK;
+
+    auto issue = [&](int stage, int64_t kt) {
+        const int64_t l0 = kt * BK;
+        for (int e = tid; e < BM * BK; e += NT) {
+            const int r = e / BK, l = e % BK;
+            const int64_t gi = row0 + r, gl = l0 + l;
+            const bool ok = gi < m && gl < k;
+            cp_async8(&As[stage][r * LDA_S + l], ok ? &A[gi * lda + gl] : A, ok);
+        }
+        for (int e = tid; e < BK * BN; e += NT) {
+            const int l = e / BN, c = e % BN;
+            const int64_t gl = l0 + l, gj = col0 + c;
+            const bool ok = gl < k && gj < n;
+            cp_async8(&Bs[stage][l * LDB_S + c], ok ? &B[gl * ldb + gj] : B, ok);
+        }
+    };
+
+    double acc[MT][NTILE][4];
+#pragma unroll
+    for (int i = 0; i < MT; ++i)
+#pragma unroll
+        for (int j = 0; j < NTILE; ++j)
+#pragma unroll
+            for (int q = 0; q < 4; ++q) acc[i][j][q] = 0.0;
+
+    // prologue: STAGES-1 tiles in flight
+#pragma unroll
+    for (int s = 0; s < STAGES - 1; ++s) {
+        if (s < nk) issue(s, s);
+        cp_async_commit();
+    }
+    for (int64_t kt = 0; kt < nk; ++kt) {
+        cp_async_wait<STAGES - 2>();
+        __syncthreads();
+        const int64_t nxt = kt + STAGES - 1;
+        if (nxt < nk) issue((int)(nxt % STAGES), nxt);
+        cp_async_commit();
+        const double* as = As[kt % STAGES];
+        const double* bs = Bs[kt % STAGES];
+#pragma unroll
+        for (int kk = 0; kk < BK; kk += 4) {
+            double af[MT][2], bf[NTILE];
+#pragma unroll
+            for (int i = 0; i < MT; ++i) {
+                const int r = wm * WT_M + i * 16 + g;
+                af[i][0] = as[r * LDA_S + kk + t];
+                af[i][1] = as[(r + 8) * LDA_S + kk + t];
+            }
+#pragma unroll
+            for (int j = 0; j < NTILE; ++j) bf[j] = bs[(kk + t) * LDB_S + wn * WT_N + j * 8 + g];
+#pragma unroll
+            for (int i = 0; i < MT; ++i)
+#pragma unroll
+                for (int j = 0; j < NTILE; ++j) dmma_16x8x4(acc[i][j], af[i][0], af[i][1], bf[j]);
+        }
+    }
+    cp_async_wait<0>();
+
+#pragma unroll
+    for (int i = 0; i < MT; ++i) {
+#pragma unroll
+        for (int j = 0; j < NTILE; ++j) {
+#pragma unroll
+            for (int h = 0; h < 2; ++h) {
+                const int64_t gi = row0 + wm * WT_M + i * 16 + g + 8 * h;
+                if (gi >= m) continue;
+#pragma unroll
+                for (int q = 0; q < 2; ++q) {
+                    const int64_t gj = col0 + wn * WT_N + j * 8 + 2 * t + q;
+                    if (gj < n) store_out<kBeta0>(C, gi * ldc + gj, alpha, acc[i][j][2 * h + q], beta);
+                }
+            }
+        }
+    }
+}
+
+template <typename K>
+cudaError_t finish(K) {
+    return cudaGetLastError();
+}
+
+}  // namespace
+
+cudaError_t launch_scale(const Launch& L, const Gemm& g) {
+    if (g.m == 0 || g.n == 0) return cudaSuccess;
+    const int64_t total = g.m * g.n;
+    int64_t blocks = (total + 255) / 256;
+    const int64_t cap = (int64_t)L.sm_count * 8;
+    if (blocks > cap) blocks = cap;
+    scale_kernel<<<(unsigned)blocks, 256, 0, L.stream>>>(g.m, g.n, g.beta, g.C, g.ldc);
+    return cudaGetLastError();
+}
+
+#define GB_ARGS g.m, g.n, g.k, g.alpha, g.A, g.lda, g.B, g.ldb, g.beta, g.C, g.ldc
+
+cudaError_t launch_naive(const Launch& L, const Gemm& g, int by, int bx) {
+    const dim3 block(bx, by);
+    const dim3 grid((unsigned)((g.n + bx - 1) / bx), (unsigned)((g.m + by - 1) / by));
+    if (g.beta == 0.0)
+        naive_kernel<true><<<grid, block, 0, L.stream>>>(GB_ARGS);
+    else
+        naive_kernel<false><<<grid, block, 0, L.stream>>>(GB_ARGS);
+    return cudaGetLastError();
+}
+
+template <int T>
+static cudaError_t launch_tiled_t(const Launch& L, const Gemm& g) {
+    const dim3 block(T, T);
+    const dim3 grid((unsigned)((g.n + T - 1) / T), (unsigned)((g.m + T - 1) / T));
+    if (g.beta == 0.0)
+        tiled_kernel<T, true><<<grid, block, 0, L.stream>>>(GB_ARGS);
+    else
+        tiled_kernel<T, false><<<grid, block, 0, L.stream>>>(GB_ARGS);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_tiled(const Launch& L, const Gemm& g, int T) {
+    switch (T) {
+        case 8: return launch_tiled_t<8>(L, g);
+        case 16: return launch_tiled_t<16>(L, g);
+        case 32: return launch_tiled_t<32>(L, g);
+        default: return cudaErrorInvalidValue;
+    }
+}
+
+template <int V>
+static cudaError_t launch_dfma_t(const Launch& L, const Gemm& g) {
+    const int B = 16 * V;
+    const dim3 grid((unsigned)((g.n + B - 1) / B), (unsigned)((g.m + B - 1) / B));
+    if (g.beta == 0.0)
+        dfma_kernel<V, true><<<grid, 256, 0, L.stream>>>(GB_ARGS);
+    else
+        dfma_kernel<V, false><<<grid, 256, 0, L.stream>>>(GB_ARGS);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_dfma(const Launch& L, const Gemm& g, int V) {
+    switch (V) {
+        case 2: return launch_dfma_t<2>(L, g);
+        case 4: return launch_dfma_t<4>(L, g);
+        case 8: return launch_dfma_t<8>(L, g);
+        default: return cudaErrorInvalidValue;
+    }
+}
+
+template <int WM, int WN, int TM, int TN>
+static cudaError_t launch_dmma_t(const Launch& L, const Gemm& g) {
+    const int BM = WM * TM, BN = WN * TN;
+    const dim3 grid((unsigned)((g.n + BN - 1) / BN), (unsigned)((g.m + BM - 1) / BM));
+    if (g.beta == 0.0)
+        dmma_kernel<WM, WN, TM, TN, true><<<grid, 32 * WM * WN, 0, L.stream>>>(GB_ARGS);
+    else
+        dmma_kernel<WM, WN, TM, TN, false><<<grid, 32 * WM * WN, 0, L.stream>>>(GB_ARGS);
+    return cudaGetLastError();
+}
+
+bool dmma_variant_exists(int wm, int wn, int tm, int tn) {
+    return (wm == 2 && wn == 2 && tm == 32 && tn == 32) ||
+           (wm == 2 && wn == 2 && tm == 16 && tn == 16) ||
+           (wm == 4 && wn == 2 && tm == 32 && tn == 32);
+}
+
+cudaError_t launch_dmma(const Launch& L, const Gemm& g, int wm, int wn, int tm, int tn) {
+    if (wm == 2 && wn == 2 && tm == 32 && tn == 32) return launch_dmma_t<2, 2, 32, 32>(L, g);
+    if (wm == 2 && wn == 2 && tm == 16 && tn == 16) return launch_dmma_t<2, 2, 16, 16>(L, g);
+    if (wm == 4 && wn == 2 && tm == 32 && tn == 32) return launch_dmma_t<4, 2, 32, 32>(L, g);
+    return cudaErrorInvalidValue;
+}
+
+}  // namespace gb

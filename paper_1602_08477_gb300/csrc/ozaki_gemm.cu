@@ -1,0 +1,369 @@
+// Emulated FP64 GEMM, steps e3 + e4 on the tcgen05 tensor cores.
+//
+// e3: for an output tile of 128 rows x BN columns, the level sums
+//       S_g = sum_{p + q = g} DA_p DB_q^T,  g = 2 .. s+1,
+//     of the E4M3 digit planes (|digit| <= 16) are accumulated in tensor memory,
+//     one FP32 accumulator of 128 lanes x BN columns per level (s * BN <= 512
+//     columns).  Every digit product is an integer <= 256, so each partial sum is
+//     an exact integer in FP32 while it stays below 2^24 (k * pairs * 256).
+// e4: the epilogue reads the levels back, forms the exact integer
+//       T = sum_g S_g 2^(5 (s+1-g))
+//     in 128-bit integer arithmetic, rounds it once to FP64 (nearest, ties to
+//     even), scales by the power of two 2^(e_i + f_j - 8 - 5 (s-1)) and writes
+//     C = alpha t + beta C.  GB300 runs FP64 at a small fraction of its integer
+//     rate, so only the alpha / beta step uses the FP64 pipe.
+//
+// Pipeline per CTA (one output tile, 192 threads):
+//   warp 0 lane 0 : TMA producer.  Stage = one 32-byte K block of all s digit
+//                   planes of A (128 x 32 B each) and B (BN x 32 B each),
+//                   fetched by two 3-D tensor loads into the 32-byte-swizzled
+//                   K-major layout the tensor core reads.
+//   warp 1        : allocates 512 TMEM columns; lane 0 issues the s(s+1)/2
+//                   pair MMAs per stage (M = 128, N = BN, K = 32) and commits
+//                   each stage back to the producer.
+//   warps 2 - 5   : epilogue; warp w reads TMEM lanes 32 (w % 4) .. + 31.
+// Every wait on an mbarrier is bounded (wall-clock); on a timeout the CTA records
+// the timeout bit in the status word, skips its output and still frees TMEM.
+#include <cuda.h>
+#include <cuda_runtime.h>
+#include <cudaTypedefs.h>
+#include <cstdint>
+#include <cstring>
+
+#include "internal.h"
+#include "tc_ptx.cuh"
+
+#define GB_BAD_LINE_DEV 0x40000000
+
+namespace gb {
+namespace {
+
+constexpr int kBM = 128;
+constexpr int kBKBytes = 32;
+constexpr int kThreads = 192;
+constexpr uint32_t kTmemCols = 512;
+constexpr uint64_t kWaitTimeoutNs = 4000000000ull;  // 4 s
+constexpr int kSmemLimit = 227 * 1024;
+
+struct SmemTail {
+    uint64_t bars[2 * 8 + 1];
+    uint32_t tmem_holder;
+    int abort;
+};
+
+// exact integer value of an FP32 that holds an integer (|v| < 2^63)
+__device__ __forceinline__ int64_t f32_int_value(uint32_t b) {
+    const uint32_t a = b & 0x7FFFFFFFu;
+    if (a == 0) return 0;
+    const int ex = (int)(a >> 23) - 127;
+    if (ex < 0) return 0;  // not an integer: cannot occur for digit products
+    const int64_t mant = (int64_t)((a & 0x7FFFFFu) | 0x800000u);
+    const int64_t v = ex >= 23 ? (mant << (ex - 23)) : (mant >> (23 - ex));
+    return (b >> 31) ? -v : v;
+}
+
+struct I128 {
+    int64_t hi;
+    uint64_t lo;
+};
+
+__device__ __forceinline__ void i128_horner(I128& x, int sh, int64_t v) {
+    // x = x * 2^sh + v
+    x.hi = (int64_t)(((uint64_t)x.hi << sh) | (x.lo >> (64 - sh)));
+    x.lo <<= sh;
+    const uint64_t vlo = (uint64_t)v;
+    const int64_t vhi = v < 0 ? -1 : 0;
+    const uint64_t nlo = x.lo + vlo;
+    x.hi += vhi + (nlo < x.lo ? 1 : 0);
+    x.lo = nlo;
+}
+
+__device__ __forceinline__ double pow2(int e) {  // exact for -1022 <= e <= 1023
+    return __longlong_as_double((long long)(e + 1023) << 52);
+}
+
+// RN(T) * 2^E as an FP64 (T a signed 128-bit integer).  The scaling is exact
+// when the result is a normal double; otherwise RN(T) is multiplied by powers
+// of two in the normal range (one multiplication, or two when E is out of it).
+__device__ __forceinline__ double i128_to_double_scaled(I128 x, int E) {
+    const bool neg = x.hi < 0;
+    uint64_t hi = (uint64_t)x.hi, lo = x.lo;
+    if (neg) {
+        lo = ~lo + 1;
+        hi = ~hi + (lo == 0 ? 1 : 0);
+    }
+    if (hi == 0 && lo == 0) return 0.0;
+    int p = hi ? 64 + 63 - __clzll((long long)hi) : 63 - __clzll((long long)lo);
+    uint64_t M;
+    if (p <= 52) {
+        M = lo << (52 - p);
+    } else {
+        const int sh = p - 52;  // 1 .. 74
+        uint64_t rem_hi, rem_lo, half_hi, half_lo;
+        if (sh < 64) {
+            M = (lo >> sh) | (sh ? (hi << (64 - sh)) : 0);
+            rem_hi = 0;
+            rem_lo = lo & ((1ull << sh) - 1);
+            half_hi = 0;
+            half_lo = 1ull << (sh - 1);
+        } else {
+            const int s2 = sh - 64;
+            M = hi >> s2;
+            rem_hi = s2 ? (hi & ((1ull << s2) - 1)) : 0;
+            rem_lo = lo;
+            half_hi = s2 ? (1ull << (s2 - 1)) : 0;
+            half_lo = s2 ? 0 : (1ull << 63);
+        }
+        const bool gt = rem_hi > half_hi || (rem_hi == half_hi && rem_lo > half_lo);
+        const bool eq = rem_hi == half_hi && rem_lo == half_lo;
+        if (gt || (eq && (M & 1))) {
+            M += 1;
+            if (M == (1ull << 53)) {
+                M >>= 1;
+                p += 1;
+            }
+        }
+    }
+    const int biased = p + E + 1023;
+    double r;
+    if (biased >= 1 && biased <= 2046) {
+        r = __longlong_as_double((long long)(((uint64_t)biased << 52) | (M & 0xFFFFFFFFFFFFFull)));
+    } else {
+        double t = __longlong_as_double(
+            (long long)(((uint64_t)(p + 1023) << 52) | (M & 0xFFFFFFFFFFFFFull)));
+        if (E >= -1022 && E <= 1023) {
+            t = __dmul_rn(t, pow2(E));
+        } else {
+            const int E1 = (E >= 0) ? E / 2 : -((-E + 1) / 2);  // floor(E / 2)
+            t = __dmul_rn(__dmul_rn(t, pow2(E1)), pow2(E - E1));
+        }
+        r = t;
+    }
+    return neg ? -r : r;
+}
+
+template <int BN>
+__global__ void __launch_bounds__(kThreads, 1)
+    emu_products_kernel(const __grid_constant__ CUtensorMap tmA,
+                        const __grid_constant__ CUtensorMap tmB, int s, int64_t m, int64_t n,
+                        int nkb, double alpha, double beta, double* __restrict__ C, int64_t ldc,
+                        const int32_t* __restrict__ eA, const int32_t* __restrict__ fB,
+                        int tiles_m, int tiles_n, int stages, uint32_t stage_bytes,
+                        unsigned* status) {
+    extern __shared__ uint8_t smem_raw[];
+    uint8_t* smem = reinterpret_cast<uint8_t*>(
+        (reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~(uintptr_t)1023);
+    SmemTail* tail = reinterpret_cast<SmemTail*>(smem + (size_t)stages * stage_bytes);
+    uint64_t* full = tail->bars;
+    uint64_t* empty = tail->bars + stages;
+    uint64_t* tmem_full = tail->bars + 2 * stages;
+    volatile int* abort = &tail->abort;
+
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+
+    // tile rasterisation: groups of 8 tile rows sweep the tile columns
+    const int bid = blockIdx.x;
+    const int group_size = 8 * tiles_n;
+    const int first_m = (bid / group_size) * 8;
+    const int gm = min(tiles_m - first_m, 8);
+    const int tm = first_m + (bid % group_size) % gm;
+    const int tn = (bid % group_size) / gm;
+
+    if (threadIdx.x == 0) {
+        for (int i = 0; i < stages; ++i) {
+            ptx::mbar_init(&full[i], 1);
+            ptx::mbar_init(&empty[i], 1);
+        }
+        ptx::mbar_init(tmem_full, 1);
+        tail->abort = 0;
+        ptx::mbar_init_fence();
+        ptx::tma_prefetch_desc(&tmA);
+        ptx::tma_prefetch_desc(&tmB);
+    }
+    if (warp == 1) {
+        ptx::tmem_alloc(&tail->tmem_holder, kTmemCols);
+        ptx::tmem_relinquish();
+    }
+    ptx::tc_fence_before();
+    __syncthreads();
+    ptx::tc_fence_after();
+    const uint32_t tmem_base = tail->tmem_holder;
+    const uint32_t a_bytes = (uint32_t)s * kBM * kBKBytes;
+
+    if (warp == 0 && lane == 0) {
+        // ---- TMA producer ----
+        for (int kb = 0; kb < nkb; ++kb) {
+            const int st = kb % stages;
+            const uint32_t ph = (uint32_t)(kb / stages) & 1u;
+            if (!ptx::mbar_wait_bounded(&empty[st], ph ^ 1u, abort, status, kStatusTimeout,
+                                        kWaitTimeoutNs))
+                break;
+            uint8_t* sa = smem + (size_t)st * stage_bytes;
+            ptx::mbar_arrive_expect_tx(&full[st], stage_bytes);
+            ptx::tma_load_3d(sa, &tmA, kb * kBKBytes, tm * kBM, 0, &full[st]);
+            ptx::tma_load_3d(sa + a_bytes, &tmB, kb * kBKBytes, tn * BN, 0, &full[st]);
+        }
+    } else if (warp == 1 && lane == 0) {
+        // ---- MMA issuer ----
+        constexpr uint32_t idesc = ptx::idesc_e4m3_f32(kBM, BN);
+        for (int kb = 0; kb < nkb; ++kb) {
+            const int st = kb % stages;
+            const uint32_t ph = (uint32_t)(kb / stages) & 1u;
+            if (!ptx::mbar_wait_bounded(&full[st], ph, abort, status, kStatusTimeout,
+                                        kWaitTimeoutNs))
+                break;
+            ptx::tc_fence_after();
+            const uint32_t a0 = ptx::smem_u32(smem + (size_t)st * stage_bytes);
+            const uint32_t b0 = a0 + a_bytes;
+            for (int p = 1; p <= s; ++p) {
+                const uint64_t ad = ptx::umma_desc_sw32(a0 + (uint32_t)(p - 1) * kBM * kBKBytes);
+                for (int q = 1; q <= s + 1 - p; ++q) {
+                    const uint64_t bd = ptx::umma_desc_sw32(b0 + (uint32_t)(q - 1) * BN * kBKBytes);
+                    const uint32_t acc = (kb > 0 || p > 1) ? 1u : 0u;
+                    ptx::mma_e4m3(tmem_base + (uint32_t)(p + q - 2) * BN, ad, bd, idesc, acc);
+                }
+            }
+            ptx::mma_commit(&empty[st]);
+        }
+        ptx::mma_commit(tmem_full);
+    } else if (warp >= 2) {
+        // ---- epilogue ----
+        const int quarter = warp & 3;
+        const int64_t row = (int64_t)tm * kBM + quarter * 32 + lane;
+        const bool ok = ptx::mbar_wait_bounded(tmem_full, 0, abort, status, kStatusTimeout,
+                                               kWaitTimeoutNs);
+        ptx::tc_fence_after();
+        if (ok && !*abort) {
+            const int32_t ei = row < m ? eA[row] : 0;
+            const bool bad_row = ei == GB_BAD_LINE_DEV;
+            const int Ebase = -8 - 5 * (s - 1);
+            const bool plain = (alpha == 1.0 && beta == 0.0);
+            const uint32_t lane_addr = tmem_base + ((uint32_t)(quarter * 32) << 16);
+#pragma unroll 1
+            for (int cb = 0; cb < BN; cb += 32) {
+                I128 T[32];
+#pragma unroll
+                for (int j = 0; j < 32; ++j) T[j] = I128{0, 0};
+#pragma unroll 1
+                for (int g = 2; g <= s + 1; ++g) {
+                    uint32_t v[32];
+                    ptx::tmem_ld_32x32b_x32(lane_addr + (uint32_t)(g - 2) * BN + cb, v);
+                    ptx::tmem_ld_wait();
+#pragma unroll
+                    for (int j = 0; j < 32; ++j) i128_horner(T[j], 5, f32_int_value(v[j]));
+                }
+                if (row < m) {
+                    double* crow = C + row * ldc;
+#pragma unroll
+                    for (int j = 0; j < 32; ++j) {
+                        const int64_t col = (int64_t)tn * BN + cb + j;
+                        if (col < n) {
+                            const int32_t fj = fB[col];
+                            double out;
+                            if (bad_row || fj == GB_BAD_LINE_DEV) {
+                                out = __longlong_as_double(0x7FF8000000000000ll);
+                            } else {
+                                const double t = i128_to_double_scaled(T[j], ei + fj + Ebase);
+                                if (plain) {
+                                    out = t;
+                                } else {
+                                    out = __dmul_rn(alpha, t);
+                                    if (beta != 0.0)
+                                        out = __dadd_rn(out, __dmul_rn(beta, crow[col]));
+                                }
+                            }
+                            crow[col] = out;
+                        }
+                    }
+                }
+            }
+        }
+    }
+    ptx::tc_fence_before();
+    __syncthreads();
+    if (warp == 1) {
+        ptx::tc_fence_after();
+        if (lane == 0 && *abort) {
+            // make sure no MMA is still writing the accumulators before freeing them
+            volatile int dummy = 0;
+            ptx::mbar_wait_bounded(tmem_full, 0, &dummy, nullptr, 0, kWaitTimeoutNs);
+        }
+        __syncwarp();
+        ptx::tmem_dealloc(tmem_base, kTmemCols);
+    }
+}
+
+PFN_cuTensorMapEncodeTiled_v12000 get_encoder() {
+    static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+    if (!fn) {
+        void* p = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000,
+                                             cudaEnableDefault, &q) == cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(p);
+    }
+    return fn;
+}
+
+// 3-D map over s digit planes of `rows` x kp bytes, box 32 B x box_rows x s.
+bool make_digit_map(CUtensorMap* map, const uint8_t* base, int s, int64_t rows, int64_t kp,
+                    int box_rows) {
+    auto enc = get_encoder();
+    if (!enc) return false;
+    const cuuint64_t dims[3] = {(cuuint64_t)kp, (cuuint64_t)rows, (cuuint64_t)s};
+    const cuuint64_t strides[2] = {(cuuint64_t)kp, (cuuint64_t)(rows * kp)};
+    const cuuint32_t box[3] = {(cuuint32_t)kBKBytes, (cuuint32_t)box_rows, (cuuint32_t)s};
+    const cuuint32_t estr[3] = {1, 1, 1};
+    return enc(map, CU_TENSOR_MAP_DATA_TYPE_UINT8, 3, const_cast<uint8_t*>(base), dims, strides,
+               box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_32B,
+               CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) ==
+           CUDA_SUCCESS;
+}
+
+template <int BN>
+cudaError_t launch_bn(const Launch& L, int s, int64_t m, int64_t n, int64_t kp, double alpha,
+                      double beta, double* C, int64_t ldc, const uint8_t* ad, const uint8_t* bd,
+                      const int32_t* ea, const int32_t* fb) {
+    CUtensorMap tma, tmb;
+    if (!make_digit_map(&tma, ad, s, m, kp, kBM) || !make_digit_map(&tmb, bd, s, n, kp, BN)) {
+        set_error("cuTensorMapEncodeTiled failed (s=%d m=%lld n=%lld kp=%lld)", s, (long long)m,
+                  (long long)n, (long long)kp);
+        return cudaErrorInvalidValue;
+    }
+    const uint32_t stage_bytes = (uint32_t)s * (kBM + BN) * kBKBytes;
+    const int fixed = 1024 + (int)sizeof(SmemTail) + 64;
+    int stages = (kSmemLimit - fixed) / (int)stage_bytes;
+    if (stages > 8) stages = 8;
+    if (stages < 2) return cudaErrorInvalidValue;
+    const size_t smem = (size_t)stages * stage_bytes + fixed;
+    static bool attr_set = false;
+    if (!attr_set) {
+        cudaError_t e = cudaFuncSetAttribute(emu_products_kernel<BN>,
+                                             cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             kSmemLimit);
+        if (e != cudaSuccess) return e;
+        attr_set = true;
+    }
+    const int tiles_m = (int)((m + kBM - 1) / kBM), tiles_n = (int)((n + BN - 1) / BN);
+    const int nkb = (int)(kp / kBKBytes);
+    emu_products_kernel<BN><<<tiles_m * tiles_n, kThreads, smem, L.stream>>>(
+        tma, tmb, s, m, n, nkb, alpha, beta, C, ldc, ea, fb, tiles_m, tiles_n, stages,
+        stage_bytes, L.status);
+    return cudaGetLastError();
+}
+
+}  // namespace
+
+cudaError_t launch_emu_products(const Launch& L, int s, int64_t m, int64_t n, int64_t k,
+                                double alpha, double beta, double* C, int64_t ldc,
+                                const uint8_t* a_digits, const uint8_t* b_digits, int64_t kp,
+                                const int32_t* a_exp, const int32_t* b_exp) {
+    (void)k;
+    if (m == 0 || n == 0) return cudaSuccess;
+    if (s <= 8)
+        return launch_bn<64>(L, s, m, n, kp, alpha, beta, C, ldc, a_digits, b_digits, a_exp, b_exp);
+    return launch_bn<32>(L, s, m, n, kp, alpha, beta, C, ldc, a_digits, b_digits, a_exp, b_exp);
+}
+
+}  // namespace gb

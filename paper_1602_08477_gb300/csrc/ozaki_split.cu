@@ -1,0 +1,250 @@
+// Emulated FP64 GEMM, steps e1 + e2: exponent extraction and E4M3 digit slicing.
+//
+// For a line (row of A, column of B) with max |value| = mu, e = frexp exponent of
+// mu (mu < 2^e).  Each value a = 2^e (sum_t d_t 2^-(4 + 5(t-1)) + remainder) with
+// signed digits d_t in [-16, 16] taken by round-to-nearest-even:
+//   d_1 = rint(a 2^(4-e)),  r = a 2^(4-e) - d_1,  d_t = rint(32 r),  r = 32 r - d_t.
+//
+// GB300 executes FP64 at a small fraction of its integer rate, so every step here
+// is integer arithmetic on the IEEE-754 bit pattern: a = M 2^E2 with an integer
+// significand M, and "r scaled by 2^-sh" is kept as the exact integer R with an
+// explicit shift sh.  Rounding R / 2^sh to nearest-even with integer shifts gives
+// the same digits as the FP64 recurrence, which is exact at every step.
+//
+// Output layout (K-major, the operand layout of the tensor-core products):
+//   digits[(t * lines + line) * kp + l], one E4M3 byte each, zero for l >= k;
+//   exps[line] = e, or GB_BAD_LINE when the line holds a NaN or Inf (its digits
+//   are all zero and the products mark its outputs NaN).
+#include <cuda_runtime.h>
+#include <cstdint>
+
+#include "internal.h"
+
+#define GB_BAD_LINE_DEV 0x40000000
+
+namespace gb {
+namespace {
+
+constexpr int kB1 = 4;   // bits of the first digit
+constexpr int kB = 5;    // bits of every further digit
+
+// E4M3 encodings of the integers 0..16 (sign bit 7, exponent bias 7, 3 mantissa bits).
+__device__ __forceinline__ uint32_t e4m3_of_int(int d) {
+    const uint32_t a = (uint32_t)(d < 0 ? -d : d);
+    uint32_t code;
+    if (a == 0) {
+        code = 0;
+    } else {
+        const int E = 31 - __clz(a);                     // 0..4
+        const uint32_t mant = ((a << 3) >> E) & 7u;      // exact for a <= 16
+        code = ((uint32_t)(E + 7) << 3) | mant;
+    }
+    return (d < 0 ? 0x80u : 0u) | code;
+}
+
+// frexp exponent of a finite non-negative double given by its bits (0 -> 0).
+__device__ __forceinline__ int frexp_exp_bits(uint64_t absbits) {
+    if (absbits == 0) return 0;
+    const int ef = (int)(absbits >> 52);
+    if (ef != 0) return ef - 1022;
+    const int p = 63 - __clzll((long long)absbits);  // subnormal: value = mant * 2^-1074
+    return p - 1073;
+}
+
+// The s digits of one finite double x relative to line exponent e, packed as
+// E4M3 bytes into out[t] (byte lane `lane` of a 64-bit word).
+template <int S_MAX>
+__device__ __forceinline__ void digits_of(uint64_t bits, int e, int s, int lane,
+                                          uint64_t (&out)[S_MAX]) {
+    const int ef = (int)((bits >> 52) & 0x7FF);
+    int64_t M = (int64_t)(bits & 0xFFFFFFFFFFFFFull);
+    int E2;
+    if (ef == 0) {
+        E2 = -1074;
+    } else {
+        M |= (int64_t)1 << 52;
+        E2 = ef - 1075;
+    }
+    int64_t R = (bits >> 63) ? -M : M;
+    int sh = e - kB1 - E2;  // y_1 = R / 2^sh
+#pragma unroll
+    for (int t = 0; t < S_MAX; ++t) {
+        if (t >= s) break;
+        int64_t d;
+        if (R == 0 || sh >= 55) {
+            d = 0;                         // |R| < 2^53 <= 2^(sh-2): |y| < 1/2
+        } else if (sh <= 0) {
+            d = R << (-sh);                // y is an integer
+            R = 0;
+        } else {
+            int64_t q = R >> sh;           // floor
+            const int64_t fr = R - (q << sh);
+            const int64_t half = (int64_t)1 << (sh - 1);
+            if (fr > half || (fr == half && (q & 1))) q += 1;
+            d = q;
+            R -= q << sh;
+        }
+        out[t] |= (uint64_t)e4m3_of_int((int)d) << (8 * lane);
+        sh -= kB;
+    }
+}
+
+constexpr int kSMax = 16;
+
+// One block per row (grid-stride): pass 1 max |a| and finiteness, pass 2 digits.
+__global__ void __launch_bounds__(128) split_rows_kernel(int64_t m, int64_t k,
+                                                         const double* __restrict__ A,
+                                                         int64_t lda, int s,
+                                                         uint8_t* __restrict__ digits,
+                                                         int64_t kp, int32_t* __restrict__ exps,
+                                                         unsigned* status) {
+    __shared__ uint64_t red[4];
+    __shared__ int bad_sh;
+    const int tid = threadIdx.x;
+    for (int64_t i = blockIdx.x; i < m; i += gridDim.x) {
+        const uint64_t* row = reinterpret_cast<const uint64_t*>(A + i * lda);
+        uint64_t mx = 0;
+        int bad = 0;
+        for (int64_t l = tid; l < k; l += blockDim.x) {
+            const uint64_t a = row[l] & 0x7FFFFFFFFFFFFFFFull;
+            if (a >= 0x7FF0000000000000ull) bad = 1;
+            else if (a > mx) mx = a;
+        }
+        for (int o = 16; o > 0; o >>= 1) {
+            const uint64_t v = __shfl_xor_sync(0xffffffffu, mx, o);
+            mx = v > mx ? v : mx;
+        }
+        bad = __syncthreads_or(bad);
+        if ((tid & 31) == 0) red[tid >> 5] = mx;
+        __syncthreads();
+        if (tid == 0) {
+            uint64_t v = red[0];
+            for (int w = 1; w < (int)(blockDim.x >> 5); ++w) v = red[w] > v ? red[w] : v;
+            red[0] = v;
+            bad_sh = bad;
+        }
+        __syncthreads();
+        const int e = frexp_exp_bits(red[0]);
+        const bool is_bad = bad_sh != 0;
+        if (tid == 0) {
+            exps[i] = is_bad ? GB_BAD_LINE_DEV : e;
+            if (is_bad && status) atomicOr(status, kStatusNonfinite);
+        }
+        // pass 2: 8 consecutive elements per thread -> one 8-byte word per plane
+        for (int64_t l0 = (int64_t)tid * 8; l0 < kp; l0 += (int64_t)blockDim.x * 8) {
+            uint64_t w[kSMax];
+#pragma unroll
+            for (int t = 0; t < kSMax; ++t) w[t] = 0;
+            if (!is_bad) {
+#pragma unroll
+                for (int u = 0; u < 8; ++u) {
+                    const int64_t l = l0 + u;
+                    if (l < k) digits_of<kSMax>(row[l], e, s, u, w);
+                }
+            }
+#pragma unroll
+            for (int t = 0; t < kSMax; ++t) {
+                if (t >= s) break;
+                *reinterpret_cast<uint64_t*>(digits + ((int64_t)t * m + i) * kp + l0) = w[t];
+            }
+        }
+        __syncthreads();
+    }
+}
+
+// Column max of B (k x n): block of 32 columns x 8 row groups.
+__global__ void __launch_bounds__(256) colmax_kernel(int64_t n, int64_t k,
+                                                     const double* __restrict__ B, int64_t ldb,
+                                                     int32_t* __restrict__ exps,
+                                                     unsigned* status) {
+    __shared__ uint64_t mx_sh[8][32];
+    __shared__ int bad_sh[8][32];
+    const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
+    const int64_t j = blockIdx.x * 32ll + tx;
+    uint64_t mx = 0;
+    int bad = 0;
+    if (j < n) {
+        const uint64_t* col = reinterpret_cast<const uint64_t*>(B) + j;
+        for (int64_t l = ty; l < k; l += 8) {
+            const uint64_t a = col[l * ldb] & 0x7FFFFFFFFFFFFFFFull;
+            if (a >= 0x7FF0000000000000ull) bad = 1;
+            else if (a > mx) mx = a;
+        }
+    }
+    mx_sh[ty][tx] = mx;
+    bad_sh[ty][tx] = bad;
+    __syncthreads();
+    if (ty == 0 && j < n) {
+        for (int r = 1; r < 8; ++r) {
+            mx = mx_sh[r][tx] > mx ? mx_sh[r][tx] : mx;
+            bad |= bad_sh[r][tx];
+        }
+        exps[j] = bad ? GB_BAD_LINE_DEV : frexp_exp_bits(mx);
+        if (bad && status) atomicOr(status, kStatusNonfinite);
+    }
+}
+
+// Transposing digit pass for B: tile of 64 rows (l) x 32 columns (j).
+__global__ void __launch_bounds__(256) split_cols_kernel(int64_t n, int64_t k,
+                                                         const double* __restrict__ B,
+                                                         int64_t ldb, int s,
+                                                         uint8_t* __restrict__ digits,
+                                                         int64_t kp,
+                                                         const int32_t* __restrict__ exps) {
+    __shared__ uint64_t T[64][33];
+    const int tid = threadIdx.x;
+    const int tx = tid & 31, ty = tid >> 5;
+    const int64_t j0 = blockIdx.x * 32ll, l0 = blockIdx.y * 64ll;
+    const uint64_t* Bb = reinterpret_cast<const uint64_t*>(B);
+#pragma unroll
+    for (int r = 0; r < 8; ++r) {
+        const int64_t l = l0 + ty + 8 * r, j = j0 + tx;
+        T[ty + 8 * r][tx] = (l < k && j < n) ? Bb[l * ldb + j] : 0ull;
+    }
+    __syncthreads();
+    const int jj = tid >> 3, lsub = (tid & 7) * 8;
+    const int64_t j = j0 + jj, lbase = l0 + lsub;
+    if (j >= n || lbase >= kp) return;
+    const int e = exps[j];
+    uint64_t w[kSMax];
+#pragma unroll
+    for (int t = 0; t < kSMax; ++t) w[t] = 0;
+    if (e != GB_BAD_LINE_DEV) {
+#pragma unroll
+        for (int u = 0; u < 8; ++u) {
+            if (lbase + u < k) digits_of<kSMax>(T[lsub + u][jj], e, s, u, w);
+        }
+    }
+#pragma unroll
+    for (int t = 0; t < kSMax; ++t) {
+        if (t >= s) break;
+        *reinterpret_cast<uint64_t*>(digits + ((int64_t)t * n + j) * kp + lbase) = w[t];
+    }
+}
+
+}  // namespace
+
+cudaError_t launch_split_rows(const Launch& L, int s, int64_t m, int64_t k, const double* A,
+                              int64_t lda, uint8_t* digits, int64_t kp, int32_t* exps) {
+    if (m == 0) return cudaSuccess;
+    int64_t blocks = m;
+    const int64_t cap = (int64_t)L.sm_count * 16;
+    if (blocks > cap) blocks = cap;
+    split_rows_kernel<<<(unsigned)blocks, 128, 0, L.stream>>>(m, k, A, lda, s, digits, kp, exps,
+                                                              L.status);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_split_cols(const Launch& L, int s, int64_t n, int64_t k, const double* B,
+                              int64_t ldb, uint8_t* digits, int64_t kp, int32_t* exps) {
+    if (n == 0) return cudaSuccess;
+    const unsigned gx = (unsigned)((n + 31) / 32);
+    colmax_kernel<<<gx, 256, 0, L.stream>>>(n, k, B, ldb, exps, L.status);
+    cudaError_t err = cudaGetLastError();
+    if (err != cudaSuccess) return err;
+    const dim3 grid(gx, (unsigned)((kp + 63) / 64));
+    split_cols_kernel<<<grid, 256, 0, L.stream>>>(n, k, B, ldb, s, digits, kp, exps);
+    return cudaGetLastError();
+}
+
+}  // namespace gb

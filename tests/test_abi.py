@@ -1,0 +1,109 @@
+"""The C-ABI library: builds, loads, exports every declared symbol, and rejects bad
+arguments on the host before any device work (no compute calls here)."""
+import ctypes
+import glob
+import os
+import re
+
+import pytest
+
+from paper_1602_08477_gb300 import _lib, build
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    build()
+    return _lib.load()
+
+
+def declared_functions():
+    names = set()
+    pat = re.compile(r"^\s*(?:gb_status|int|const char\s*\*|void\s*\*)\s*(gb_\w+)\s*\(", re.M)
+    for h in glob.glob(os.path.join(ROOT, "include", "*.h")):
+        names.update(pat.findall(open(h).read()))
+    return sorted(names)
+
+
+def test_headers_declare_the_boundary():
+    names = declared_functions()
+    for must in ("gb_dgemm", "gb_queue_create", "gb_device_get", "gb_workdiv_suggest",
+                 "gb_dgemm_workspace_size", "gb_last_error"):
+        assert must in names
+
+
+def test_every_declared_symbol_is_exported(lib):
+    missing = [n for n in declared_functions() if not hasattr(lib, n)]
+    assert not missing, missing
+
+
+def test_every_declared_symbol_has_a_binding_signature(lib):
+    missing = [n for n in declared_functions() if n not in _lib.SIGNATURES]
+    assert not missing, missing
+
+
+def test_version_and_error_string(lib):
+    assert lib.gb_version() >= 100
+    assert isinstance(lib.gb_last_error(), bytes)
+
+
+def test_null_queue_rejected_on_host(lib):
+    st = lib.gb_dgemm(None, None, 0, 0, 0, 4, 4, 4, 1.0, None, 4, None, 4, 0.0, None, 4, None, 0)
+    assert st == 1  # GB_ERR_INVALID_ARG
+    assert b"NULL" in lib.gb_last_error()
+
+
+def test_workspace_size_and_layout(lib):
+    out = ctypes.c_size_t()
+    assert lib.gb_dgemm_workspace_size(0, 0, 100, 100, 100, ctypes.byref(out)) == 0
+    assert out.value == 0
+    assert lib.gb_dgemm_workspace_size(1, 11, 100, 70, 45, ctypes.byref(out)) == 0
+    lay = _lib.EmulatedLayout()
+    assert lib.gb_emulated_layout_get(11, 100, 70, 45, ctypes.byref(lay)) == 0
+    assert lay.kp == 64
+    assert lay.a_digits == 0 and lay.b_digits >= 11 * 100 * 64
+    assert lay.a_exp >= lay.b_digits + 11 * 70 * 64 and lay.b_exp >= lay.a_exp + 400
+    assert all(x % 1024 == 0 for x in (lay.b_digits, lay.a_exp, lay.b_exp))
+    assert out.value == lay.total
+    # slices out of range
+    assert lib.gb_dgemm_workspace_size(1, 17, 8, 8, 8, ctypes.byref(out)) == 1
+    assert lib.gb_dgemm_workspace_size(1, -1, 8, 8, 8, ctypes.byref(out)) == 1
+    assert lib.gb_dgemm_workspace_size(0, 0, -1, 8, 8, ctypes.byref(out)) == 1
+
+
+def test_workdiv_suggest_follows_table2_cuda_row(lib):
+    # blocks = N / (B * V) per dimension (Table 2, CUDA row)
+    wd = _lib.Workdiv()
+    chosen = ctypes.c_int()
+    for kernel, (B, V) in {1: (16, 1), 2: (16, 1), 3: (16, 4)}.items():
+        assert lib.gb_workdiv_suggest(None, kernel, 1000, 700, 64, ctypes.byref(wd),
+                                      ctypes.byref(chosen)) == 0
+        assert chosen.value == kernel
+        assert wd.dim == 2
+        assert tuple(wd.block_threads[:2]) == (B, B)
+        assert tuple(wd.thread_elems[:2]) == (V, V)
+        assert wd.grid_blocks[0] == -(-1000 // (B * V))
+        assert wd.grid_blocks[1] == -(-700 // (B * V))
+    assert lib.gb_workdiv_suggest(None, 0, 4096, 4096, 4096, ctypes.byref(wd),
+                                  ctypes.byref(chosen)) == 0
+    assert chosen.value == 4  # DMMA: 2 x 2 warps, 32 x 32 elements per warp
+    assert tuple(wd.block_threads[:2]) == (2, 2) and tuple(wd.thread_elems[:2]) == (32, 32)
+    assert lib.gb_workdiv_suggest(None, 9, 8, 8, 8, ctypes.byref(wd), None) == 1
+
+
+def test_device_count_without_gpu_is_an_error_not_a_crash(lib):
+    n = ctypes.c_int(-1)
+    st = lib.gb_device_count(ctypes.byref(n))
+    if st == 0:
+        pytest.skip("a CUDA device is present")
+    assert st == 4 and n.value == 0  # GB_ERR_NO_DEVICE
+    h = ctypes.c_void_p()
+    assert lib.gb_device_get(0, ctypes.byref(h)) == 4
+
+
+def test_missing_library_raises(monkeypatch, tmp_path):
+    monkeypatch.setattr(_lib, "_lib", None)
+    monkeypatch.setattr(_lib, "LIB_PATH", str(tmp_path / "absent.so"))
+    with pytest.raises(RuntimeError, match="not built"):
+        _lib.load()

@@ -1,0 +1,156 @@
+"""GPU parity of the split-precision (emulated FP64) path against the CPU model of
+steps e1..e4 and the FP64 oracle.
+
+Step by step: exponents and E4M3 digit bytes of the split kernels bit-exact
+against the model; the tensor-core products + recombination bit-exact against
+the model (every level sum below 2^24 is exact in FP32 tensor memory); the full
+result within the FP64 bound against the double-double reference; integer
+inputs exact; an adversarial input with the largest level-2 sums; NaN/Inf
+handling and its queue status.
+"""
+import numpy as np
+import pytest
+
+from oracle import cgemm, ozaki
+from synth import generators as g
+
+from gpu_util import e4m3_decode, inputs, to_dev, within_bound
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def gb():
+    import torch
+    import paper_1602_08477_gb300 as gb
+    gb.build()
+    assert torch.cuda.is_available()
+    return gb
+
+
+def emulate(gb, A, B, C0, alpha, beta, s):
+    import torch
+    dA, dB = to_dev(A), to_dev(B)
+    dC = to_dev(C0) if C0 is not None else torch.zeros((A.shape[0], B.shape[1]),
+                                                         dtype=torch.float64, device="cuda")
+    gb.dgemm(dA, dB, dC, alpha, beta if C0 is not None else 0.0, precision="emulated", slices=s)
+    torch.cuda.synchronize()
+    return dC.cpu().numpy()
+
+
+def split_on_gpu(gb, A, B, s):
+    import torch
+    m, k = A.shape
+    n = B.shape[1]
+    lay = gb.emulated_layout(s, m, n, k)
+    ws = gb.alloc_workspace(lay.total)
+    ws.fill_(0xAB)  # poison: every byte the layout defines must be written
+    dA, dB = to_dev(A), to_dev(B)
+    dC = torch.zeros((m, n), dtype=torch.float64, device="cuda")
+    gb.emulated_steps(dA, dB, dC, 1.0, 0.0, s, ws, steps=("split_a", "split_b"))
+    torch.cuda.synchronize()
+    raw = ws.cpu().numpy()
+    kp = lay.kp
+    da = raw[lay.a_digits:lay.a_digits + s * m * kp].reshape(s, m, kp)
+    db = raw[lay.b_digits:lay.b_digits + s * n * kp].reshape(s, n, kp)
+    ea = raw[lay.a_exp:lay.a_exp + 4 * m].view(np.int32)
+    fb = raw[lay.b_exp:lay.b_exp + 4 * n].view(np.int32)
+    return da, db, ea, fb, kp
+
+
+@pytest.mark.parametrize("kind", ["uniform", "hard"])
+@pytest.mark.parametrize("m,n,k,s", [(37, 45, 70, 11), (128, 64, 256, 16), (5, 300, 33, 1),
+                                     (200, 3, 129, 7)])
+def test_split_digits_and_exponents_bit_exact(gb, kind, m, n, k, s):
+    A, B, _ = inputs(kind, m, n, k, 31, with_c=False)
+    da, db, ea, fb, kp = split_on_gpu(gb, A, B, s)
+    e, _ = ozaki.exponents(A, axis=1)
+    f, _ = ozaki.exponents(B, axis=0)
+    assert np.array_equal(ea, e) and np.array_equal(fb, f)
+    DA, _ = ozaki.slice_digits(A, e, s, axis=1)
+    DB, _ = ozaki.slice_digits(B, f, s, axis=0)
+    vals_a = e4m3_decode(da)
+    vals_b = e4m3_decode(db)
+    assert np.array_equal(vals_a[:, :, :k], DA.astype(np.float64))
+    assert np.array_equal(vals_b[:, :, :k], DB.transpose(0, 2, 1).astype(np.float64))
+    assert np.all(vals_a[:, :, k:] == 0) and np.all(vals_b[:, :, k:] == 0)
+
+
+@pytest.mark.parametrize("s", [1, 2, 4, 8, 9, 11, 13, 16])
+def test_products_bit_exact_against_model(gb, s):
+    m, n, k = 300, 200, 129
+    A, B, C0 = inputs("uniform", m, n, k, 32)
+    want = ozaki.emulated_gemm(1.5, A, B, 0.5, C0, s=s)
+    got = emulate(gb, A, B, C0, 1.5, 0.5, s)
+    assert np.array_equal(got, want)
+
+
+@pytest.mark.parametrize("kind,s", [("uniform", 11), ("hard", 13)])
+def test_config0_within_fp64_bound(gb, kind, s):
+    # C = 1.5 A B + 0.5 C at n = 256: the emulated result meets the FP64 contract
+    A, B, C0 = inputs(kind, 256, 256, 256, g.BASE_SEED + (0 if kind == "uniform" else 3))
+    got = emulate(gb, A, B, C0, 1.5, 0.5, s)
+    assert np.array_equal(got, ozaki.emulated_gemm(1.5, A, B, 0.5, C0, s=s))
+    assert within_bound(got, 1.5, A, B, 0.5, C0) <= 1.0
+
+
+@pytest.mark.parametrize("s", [1, 2, 11])
+def test_integer_variant_bit_exact(gb, s):
+    A, B, C0 = inputs("int8", 256, 256, 256, g.BASE_SEED + 100)
+    want = cgemm.dgemm(1.5, A, B, 0.5, C0.copy())
+    assert np.array_equal(emulate(gb, A, B, C0, 1.5, 0.5, s), want)
+
+
+def test_largest_level_sums_exact_in_tensor_memory(gb):
+    # every digit of A and B is (16, 0, 0, 0, -16): S_2 = 256 k = 2^21 at k = 8192,
+    # the largest exact level-2 sum; the result k (1 - 2^-20)^2 is exact (s = 9).
+    k = 8192
+    v = 1.0 - 2.0 ** -20
+    A = np.full((130, k), v)
+    B = np.full((k, 70), v)
+    got = emulate(gb, A, B, None, 1.0, 0.0, 9)
+    assert np.all(got == k * (1.0 - 2.0 ** -19 + 2.0 ** -40))
+    got5 = emulate(gb, A, B, None, 1.0, 0.0, 5)
+    assert np.all(got5 == k * (1.0 - 2.0 ** -19))
+
+
+def test_nonfinite_rows_and_columns(gb):
+    import torch
+    A, B, _ = inputs("uniform", 70, 50, 40, 33, with_c=False)
+    A[4, 7] = np.inf
+    B[9, 13] = np.nan
+    q = gb.Queue(gb.Device(0), torch.cuda.current_stream())
+    dA, dB = to_dev(A), to_dev(B)
+    dC = torch.zeros((70, 50), dtype=torch.float64, device="cuda")
+    gb.dgemm(dA, dB, dC, 1.0, 0.0, precision="emulated", slices=8, queue=q)
+    with pytest.raises(gb.GbError, match="GB_ERR_NONFINITE"):
+        q.wait()
+    q.wait()  # the status was cleared by the first wait
+    got = dC.cpu().numpy()
+    want = ozaki.emulated_gemm(1.0, A, B, s=8)
+    assert np.array_equal(np.isnan(got), np.isnan(want))
+    fin = ~np.isnan(want)
+    assert np.array_equal(got[fin], want[fin])
+
+
+def test_workspace_errors(gb):
+    import torch
+    A, B, C0 = inputs("uniform", 16, 16, 16, 34)
+    dA, dB, dC = to_dev(A), to_dev(B), to_dev(C0)
+    with pytest.raises(gb.GbError, match="GB_ERR_WORKSPACE"):
+        gb.dgemm(dA, dB, dC, precision="emulated", slices=8,
+                 workspace=torch.empty(64, dtype=torch.uint8, device="cuda"))
+    with pytest.raises(gb.GbError, match="GB_ERR_INVALID_ARG"):
+        gb.dgemm(dA, dB, dC, precision="emulated", slices=17)
+
+
+@pytest.mark.parametrize("n,s", [(4096, 10), (8192, 11)])
+def test_full_size_sampled_rows(gb, n, s):
+    # square sizes of the emulated workload: 8 sampled rows against the model
+    # (bit-exact) and against the double-double reference (FP64 bound)
+    A, B, _ = inputs("uniform", n, n, n, g.BASE_SEED + 2, with_c=False)
+    got = emulate(gb, A, B, None, 1.0, 0.0, s)
+    rows = np.random.default_rng(n + s).choice(n, 8, replace=False)
+    want = ozaki.emulated_gemm(1.0, A, B, s=s, rows=rows)
+    assert np.array_equal(got[rows], want)
+    assert within_bound(got[rows], 1.0, A, B, 0.0, None, rows=rows) <= 1.0
