@@ -21,5 +21,5 @@ from .gemm import (  # noqa: F401
 
 
 def build(verbose: bool = False) -> str:
-    from .build import build as _build
+    from .compile_lib import build as _build
     return _build(verbose=verbose)

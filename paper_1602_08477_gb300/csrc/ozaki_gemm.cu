@@ -18,9 +18,10 @@
 //                   planes of A (128 x 32 B each) and B (BN x 32 B each),
 //                   fetched by two 3-D tensor loads into the 32-byte-swizzled
 //                   K-major layout the tensor core reads.
-//   warp 1        : allocates 512 TMEM columns; lane 0 issues the s(s+1)/2
-//                   pair MMAs per stage (M = 128, N = BN, K = 32) and commits
-//                   each stage back to the producer.
+//   warp 1        : allocates 512 TMEM columns; lane 0 issues the pair
+//                   products of a stage (M = 128, K = 32, N up to 256; all pairs
+//                   sharing an A slice go into one MMA) and commits each stage
+//                   back to the producer.
 //   warps 2 - 5   : epilogue; warp w reads TMEM lanes 32 (w % 4) .. + 31.
 // Every wait on an mbarrier is bounded (wall-clock); on a timeout the CTA records
 // the timeout bit in the status word, skips its output and still frees TMEM.
@@ -205,7 +206,11 @@ __global__ void __launch_bounds__(kThreads, 1)
         }
     } else if (warp == 1 && lane == 0) {
         // ---- MMA issuer ----
-        constexpr uint32_t idesc = ptx::idesc_e4m3_f32(kBM, BN);
+        // For a fixed A slice p the pairs (p, q), q = 1 .. s+1-p, land in the
+        // consecutive levels p-1 .. s-1, whose accumulators are consecutive TMEM
+        // column blocks, and the B slices q are consecutive in shared memory.  So
+        // one MMA with N = BN (s+1-p) (split at the 256-column limit) covers them
+        // all, reading the A tile once instead of once per pair.
         for (int kb = 0; kb < nkb; ++kb) {
             const int st = kb % stages;
             const uint32_t ph = (uint32_t)(kb / stages) & 1u;
@@ -217,10 +222,13 @@ __global__ void __launch_bounds__(kThreads, 1)
             const uint32_t b0 = a0 + a_bytes;
             for (int p = 1; p <= s; ++p) {
                 const uint64_t ad = ptx::umma_desc_sw32(a0 + (uint32_t)(p - 1) * kBM * kBKBytes);
-                for (int q = 1; q <= s + 1 - p; ++q) {
-                    const uint64_t bd = ptx::umma_desc_sw32(b0 + (uint32_t)(q - 1) * BN * kBKBytes);
-                    const uint32_t acc = (kb > 0 || p > 1) ? 1u : 0u;
-                    ptx::mma_e4m3(tmem_base + (uint32_t)(p + q - 2) * BN, ad, bd, idesc, acc);
+                const uint32_t acc = (kb > 0 || p > 1) ? 1u : 0u;
+                const int rows = BN * (s + 1 - p);
+                for (int r0 = 0; r0 < rows; r0 += 256) {
+                    const int nn = min(256, rows - r0);
+                    const uint64_t bd = ptx::umma_desc_sw32(b0 + (uint32_t)r0 * kBKBytes);
+                    ptx::mma_e4m3(tmem_base + (uint32_t)((p - 1) * BN + r0), ad, bd,
+                                  ptx::idesc_e4m3_f32(kBM, nn), acc);
                 }
             }
             ptx::mma_commit(&empty[st]);

@@ -125,7 +125,7 @@ def test_nonfinite_propagates_in_place(gb, kernel):
 
 
 @pytest.mark.parametrize("grid_block_elem,kernel", [
-    (((3, 10), (32, 8), (1, 1)), "naive"),
+    (((4, 10), (32, 8), (1, 1)), "naive"),
     (((13, 3), (8, 32), (1, 1)), "naive"),
     (((13, 10), (8, 8), (1, 1)), "tiled"),
     (((4, 3), (32, 32), (1, 1)), "tiled"),
