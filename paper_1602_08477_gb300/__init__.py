@@ -23,3 +23,13 @@ from .gemm import (  # noqa: F401
 def build(verbose: bool = False) -> str:
     from .compile_lib import build as _build
     return _build(verbose=verbose)
+
+
+from .grouped import (  # noqa: E402,F401
+    GroupedPlan,
+    dgemm_grouped,
+    tune_get,
+    tune_lookup,
+    tune_set,
+)
+from .serve import Server, fill_uniform  # noqa: E402,F401

@@ -9,20 +9,8 @@
 #include <new>
 
 #include "gb_gemm.h"
+#include "handles.h"
 #include "internal.h"
-
-struct gb_device {
-    int idx;
-    int sm_count;
-    int cc_major, cc_minor;
-};
-
-struct gb_queue {
-    gb_device* dev;
-    cudaStream_t stream;
-    int blocking;
-    unsigned* status;  // device status word (kStatus* bits)
-};
 
 namespace gb {
 
@@ -35,26 +23,12 @@ void set_error(const char* fmt, ...) {
     va_end(ap);
 }
 
-namespace {
-
-// Makes `dev` current for the scope and restores the caller's device.
-struct DeviceScope {
-    int prev = -1;
-    bool ok = true;
-    explicit DeviceScope(int dev) {
-        if (cudaGetDevice(&prev) != cudaSuccess) prev = -1;
-        if (prev != dev) ok = cudaSetDevice(dev) == cudaSuccess;
-    }
-    ~DeviceScope() {
-        int cur = -1;
-        if (prev >= 0 && cudaGetDevice(&cur) == cudaSuccess && cur != prev) cudaSetDevice(prev);
-    }
-};
-
 gb_status cuda_fail(cudaError_t e, const char* what) {
     set_error("%s: %s", what, cudaGetErrorString(e));
     return GB_ERR_CUDA;
 }
+
+namespace {
 
 gb_status invalid(const char* fmt, ...) {
     va_list ap;
@@ -65,6 +39,8 @@ gb_status invalid(const char* fmt, ...) {
 }
 
 bool aligned(const void* p, size_t a) { return (reinterpret_cast<uintptr_t>(p) % a) == 0; }
+
+}  // namespace
 
 // Reads and clears the queue's device status word (after the stream finished).
 gb_status drain_status(gb_queue* q) {
@@ -91,6 +67,8 @@ gb_status finish_call(gb_queue* q, cudaError_t e, const char* what) {
     if (e != cudaSuccess) return cuda_fail(e, what);
     return drain_status(q);
 }
+
+namespace {
 
 Launch launch_of(const gb_queue* q) { return Launch{q->stream, q->status, q->dev->sm_count}; }
 
@@ -205,16 +183,23 @@ int resolve_slices(int slices) { return slices == 0 ? 11 : slices; }
 
 }  // namespace
 
+int validate_gemm(int64_t m, int64_t n, int64_t k, double alpha, const double* A, int64_t lda,
+                  const double* B, int64_t ldb, double beta, const double* C, int64_t ldc) {
+    return (int)check_gemm_args(m, n, k, alpha, A, lda, B, ldb, beta, C, ldc);
+}
+
 EmuLayout emu_layout(int s, int64_t m, int64_t n, int64_t k) {
     EmuLayout L{};
     L.kp = ((k + 31) / 32) * 32;
     if (L.kp == 0) L.kp = 32;
     auto up = [](size_t x) { return (x + 1023) & ~(size_t)1023; };
     size_t off = 0;
+    const size_t mp = (size_t)((m + kEmuBM - 1) / kEmuBM) * kEmuBM;
+    const size_t np = (size_t)((n + kEmuGroupBN - 1) / kEmuGroupBN) * kEmuGroupBN;
     L.a_digits = off;
-    off = up(off + (size_t)s * (size_t)m * (size_t)L.kp);
+    off = up(off + (size_t)s * mp * (size_t)L.kp);
     L.b_digits = off;
-    off = up(off + (size_t)s * (size_t)n * (size_t)L.kp);
+    off = up(off + (size_t)s * np * (size_t)L.kp);
     L.a_exp = off;
     off = up(off + sizeof(int32_t) * (size_t)m);
     L.b_exp = off;

@@ -198,40 +198,54 @@ __device__ __forceinline__ void cp_async_wait() {
     asm volatile("cp.async.wait_group %0;\n" ::"n"(N));
 }
 
-template <int WARPS_M, int WARPS_N, int WT_M, int WT_N, bool kBeta0>
-__global__ void __launch_bounds__(32 * WARPS_M * WARPS_N)
-    dmma_kernel(int64_t m, int64_t n, int64_t k, double alpha, const double* __restrict__ A,
-                int64_t lda, const double* __restrict__ B, int64_t ldb, double beta,
-                double* __restrict__ C, int64_t ldc) {
-    constexpr int NT = 32 * WARPS_M * WARPS_N;
-    constexpr int BM = WARPS_M * WT_M, BN = WARPS_N * WT_N, BK = 8;
-    constexpr int MT = WT_M / 16, NTILE = WT_N / 8;
+// Shared-memory footprint (doubles) of one DMMA tile variant.
+template <int WARPS_M, int WARPS_N, int WT_M, int WT_N>
+struct DmmaShape {
+    static constexpr int NT = 32 * WARPS_M * WARPS_N;
+    static constexpr int BM = WARPS_M * WT_M, BN = WARPS_N * WT_N, BK = 8;
     // Row pitches chosen so each half-warp's fragment reads hit distinct banks.
-    constexpr int LDA_S = BK + 4;
-    constexpr int LDB_S = BN + 4;
-    constexpr int STAGES = (BM >= 128) ? 2 : 3;  // <= 48 KB static smem
-    __shared__ __align__(16) double As[STAGES][BM * LDA_S];
-    __shared__ __align__(16) double Bs[STAGES][BK * LDB_S];
+    static constexpr int LDA_S = BK + 4;
+    static constexpr int LDB_S = BN + 4;
+    static constexpr int STAGES = (BM >= 128) ? 2 : 3;  // <= 48 KB static smem
+    static constexpr int A_STAGE = BM * LDA_S, B_STAGE = BK * LDB_S;
+    static constexpr int SMEM_DOUBLES = STAGES * (A_STAGE + B_STAGE);
+};
+
+// One BM x BN tile of C at (row0, col0) on the FP64 tensor pipe; `smem` holds
+// DmmaShape::SMEM_DOUBLES doubles (16-byte aligned).  All threads of the block call it.
+template <int WARPS_M, int WARPS_N, int WT_M, int WT_N>
+__device__ __forceinline__ void dmma_tile(int64_t m, int64_t n, int64_t k, double alpha,
+                                          const double* __restrict__ A, int64_t lda,
+                                          const double* __restrict__ B, int64_t ldb,
+                                          double beta, double* __restrict__ C, int64_t ldc,
+                                          int64_t row0, int64_t col0, double* smem) {
+    using S = DmmaShape<WARPS_M, WARPS_N, WT_M, WT_N>;
+    constexpr int NT = S::NT, BM = S::BM, BN = S::BN, BK = S::BK;
+    constexpr int MT = WT_M / 16, NTILE = WT_N / 8;
+    constexpr int LDA_S = S::LDA_S, LDB_S = S::LDB_S, STAGES = S::STAGES;
+    double* As = smem;
+    double* Bs = smem + STAGES * S::A_STAGE;
 
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int wm = warp / WARPS_N, wn = warp % WARPS_N;
     const int g = lane >> 2, t = lane & 3;
-    const int64_t row0 = blockIdx.y * (int64_t)BM, col0 = blockIdx.x * (int64_t)BN;
     const int64_t nk = (k + BK - 1) / BK;
 
     auto issue = [&](int stage, int64_t kt) {
         const int64_t l0 = kt * BK;
+        double* as = As + stage * S::A_STAGE;
+        double* bs = Bs + stage * S::B_STAGE;
         for (int e = tid; e < BM * BK; e += NT) {
             const int r = e / BK, l = e % BK;
             const int64_t gi = row0 + r, gl = l0 + l;
             const bool ok = gi < m && gl < k;
-            cp_async8(&As[stage][r * LDA_S + l], ok ? &A[gi * lda + gl] : A, ok);
+            cp_async8(&as[r * LDA_S + l], ok ? &A[gi * lda + gl] : A, ok);
         }
         for (int e = tid; e < BK * BN; e += NT) {
             const int l = e / BN, c = e % BN;
             const int64_t gl = l0 + l, gj = col0 + c;
             const bool ok = gl < k && gj < n;
-            cp_async8(&Bs[stage][l * LDB_S + c], ok ? &B[gl * ldb + gj] : B, ok);
+            cp_async8(&bs[l * LDB_S + c], ok ? &B[gl * ldb + gj] : B, ok);
         }
     };
 
@@ -245,8 +259,8 @@ __global__ void __launch_bounds__(32 * WARPS_M * WARPS_N)
 
     // prologue: STAGES-1 tiles in flight
 #pragma unroll
-    for (int s = 0; s < STAGES - 1; ++s) {
-        if (s < nk) issue(s, s);
+    for (int st = 0; st < STAGES - 1; ++st) {
+        if (st < nk) issue(st, st);
         cp_async_commit();
     }
     for (int64_t kt = 0; kt < nk; ++kt) {
@@ -255,8 +269,8 @@ __global__ void __launch_bounds__(32 * WARPS_M * WARPS_N)
         const int64_t nxt = kt + STAGES - 1;
         if (nxt < nk) issue((int)(nxt % STAGES), nxt);
         cp_async_commit();
-        const double* as = As[kt % STAGES];
-        const double* bs = Bs[kt % STAGES];
+        const double* as = As + (kt % STAGES) * S::A_STAGE;
+        const double* bs = Bs + (kt % STAGES) * S::B_STAGE;
 #pragma unroll
         for (int kk = 0; kk < BK; kk += 4) {
             double af[MT][2], bf[NTILE];
@@ -275,7 +289,9 @@ __global__ void __launch_bounds__(32 * WARPS_M * WARPS_N)
         }
     }
     cp_async_wait<0>();
+    __syncthreads();  // the shared-memory stages may be reused by the caller's next tile
 
+    const bool beta0 = beta == 0.0;
 #pragma unroll
     for (int i = 0; i < MT; ++i) {
 #pragma unroll
@@ -287,9 +303,74 @@ __global__ void __launch_bounds__(32 * WARPS_M * WARPS_N)
 #pragma unroll
                 for (int q = 0; q < 2; ++q) {
                     const int64_t gj = col0 + wn * WT_N + j * 8 + 2 * t + q;
-                    if (gj < n) store_out<kBeta0>(C, gi * ldc + gj, alpha, acc[i][j][2 * h + q], beta);
+                    if (gj >= n) continue;
+                    double* c = &C[gi * ldc + gj];
+                    const double v = acc[i][j][2 * h + q];
+                    *c = beta0 ? alpha * v : alpha * v + beta * (*c);
                 }
             }
+        }
+    }
+}
+
+template <int WARPS_M, int WARPS_N, int WT_M, int WT_N>
+__global__ void __launch_bounds__(32 * WARPS_M * WARPS_N)
+    dmma_kernel(int64_t m, int64_t n, int64_t k, double alpha, const double* __restrict__ A,
+                int64_t lda, const double* __restrict__ B, int64_t ldb, double beta,
+                double* __restrict__ C, int64_t ldc) {
+    using S = DmmaShape<WARPS_M, WARPS_N, WT_M, WT_N>;
+    __shared__ __align__(16) double smem[S::SMEM_DOUBLES];
+    dmma_tile<WARPS_M, WARPS_N, WT_M, WT_N>(m, n, k, alpha, A, lda, B, ldb, beta, C, ldc,
+                                            blockIdx.y * (int64_t)S::BM,
+                                            blockIdx.x * (int64_t)S::BN, smem);
+}
+
+// ---- grouped: persistent CTAs over the tiles of many problems ----------------------
+// Each CTA repeatedly takes the next tile index from a global counter (so tiles
+// of expensive problems, placed first in the table, start first), finds its
+// problem by binary search over the tile prefix, and runs that problem's tile
+// variant.  One shared buffer serves every variant.
+constexpr int kGroupedSmemDoubles = DmmaShape<2, 2, 32, 32>::SMEM_DOUBLES;
+static_assert(DmmaShape<2, 2, 16, 16>::SMEM_DOUBLES <= kGroupedSmemDoubles, "smem");
+static_assert(DmmaShape<2, 2, 32, 16>::SMEM_DOUBLES <= kGroupedSmemDoubles, "smem");
+static_assert(DmmaShape<2, 2, 16, 32>::SMEM_DOUBLES <= kGroupedSmemDoubles, "smem");
+
+__global__ void __launch_bounds__(128) grouped_native_kernel(const GroupProb* __restrict__ probs,
+                                                             int nprob, int64_t total_tiles,
+                                                             unsigned long long* counter) {
+    __shared__ __align__(16) double smem[kGroupedSmemDoubles];
+    __shared__ long long next_tile;
+    for (;;) {
+        if (threadIdx.x == 0) next_tile = (long long)atomicAdd(counter, 1ull);
+        __syncthreads();
+        const long long t = next_tile;
+        __syncthreads();
+        if (t >= total_tiles) break;
+        int lo = 0, hi = nprob - 1;
+        while (lo < hi) {
+            const int mid = (lo + hi + 1) >> 1;
+            if (probs[mid].first_tile <= t) lo = mid; else hi = mid - 1;
+        }
+        const GroupProb& P = probs[lo];
+        const int64_t local = t - P.first_tile;
+        const int64_t tm = local / P.tiles_n, tn = local % P.tiles_n;
+        switch (P.tile) {
+            case kTile64x64:
+                dmma_tile<2, 2, 32, 32>(P.m, P.n, P.k, P.alpha, P.A, P.lda, P.B, P.ldb, P.beta,
+                                        P.C, P.ldc, tm * 64, tn * 64, smem);
+                break;
+            case kTile32x32:
+                dmma_tile<2, 2, 16, 16>(P.m, P.n, P.k, P.alpha, P.A, P.lda, P.B, P.ldb, P.beta,
+                                        P.C, P.ldc, tm * 32, tn * 32, smem);
+                break;
+            case kTile64x32:
+                dmma_tile<2, 2, 32, 16>(P.m, P.n, P.k, P.alpha, P.A, P.lda, P.B, P.ldb, P.beta,
+                                        P.C, P.ldc, tm * 64, tn * 32, smem);
+                break;
+            default:
+                dmma_tile<2, 2, 16, 32>(P.m, P.n, P.k, P.alpha, P.A, P.lda, P.B, P.ldb, P.beta,
+                                        P.C, P.ldc, tm * 32, tn * 64, smem);
+                break;
         }
     }
 }
@@ -367,10 +448,7 @@ template <int WM, int WN, int TM, int TN>
 static cudaError_t launch_dmma_t(const Launch& L, const Gemm& g) {
     const int BM = WM * TM, BN = WN * TN;
     const dim3 grid((unsigned)((g.n + BN - 1) / BN), (unsigned)((g.m + BM - 1) / BM));
-    if (g.beta == 0.0)
-        dmma_kernel<WM, WN, TM, TN, true><<<grid, 32 * WM * WN, 0, L.stream>>>(GB_ARGS);
-    else
-        dmma_kernel<WM, WN, TM, TN, false><<<grid, 32 * WM * WN, 0, L.stream>>>(GB_ARGS);
+    dmma_kernel<WM, WN, TM, TN><<<grid, 32 * WM * WN, 0, L.stream>>>(GB_ARGS);
     return cudaGetLastError();
 }
 
@@ -385,6 +463,22 @@ cudaError_t launch_dmma(const Launch& L, const Gemm& g, int wm, int wn, int tm, 
     if (wm == 2 && wn == 2 && tm == 16 && tn == 16) return launch_dmma_t<2, 2, 16, 16>(L, g);
     if (wm == 4 && wn == 2 && tm == 32 && tn == 32) return launch_dmma_t<4, 2, 32, 32>(L, g);
     return cudaErrorInvalidValue;
+}
+
+int grouped_native_occupancy() {
+    int blocks = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks, grouped_native_kernel, 128, 0) !=
+            cudaSuccess ||
+        blocks < 1)
+        blocks = 1;
+    return blocks;
+}
+
+cudaError_t launch_grouped_native(const Launch& L, const GroupProb* probs, int nprob,
+                                  int64_t total_tiles, unsigned long long* counter, int grid) {
+    if (nprob == 0 || total_tiles == 0) return cudaSuccess;
+    grouped_native_kernel<<<grid, 128, 0, L.stream>>>(probs, nprob, total_tiles, counter);
+    return cudaGetLastError();
 }
 
 }  // namespace gb

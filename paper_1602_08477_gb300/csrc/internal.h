@@ -46,12 +46,72 @@ cudaError_t launch_dmma(const Launch& L, const Gemm& g, int warps_m, int warps_n
                         int wt_n);
 bool dmma_variant_exists(int warps_m, int warps_n, int wt_m, int wt_n);
 
+// ---- grouped native FP64 (dgemm_native.cu) ----
+// Tile variants of the grouped kernel (4 warps of DMMA each): BM x BN.
+enum : int { kTile64x64 = 1, kTile32x32 = 2, kTile64x32 = 3, kTile32x64 = 4 };
+inline int tile_bm(int v) { return (v == kTile64x64 || v == kTile64x32) ? 64 : 32; }
+inline int tile_bn(int v) { return (v == kTile64x64 || v == kTile32x64) ? 64 : 32; }
+
+// One problem of a grouped launch, as the device reads it.
+struct GroupProb {
+    int64_t m, n, k, lda, ldb, ldc;
+    const double* A;
+    const double* B;
+    double* C;
+    double alpha, beta;
+    int32_t tile, tiles_n;
+    int64_t first_tile;  // exclusive prefix of tile counts over the table
+};
+
+// Persistent kernel over `total_tiles` tiles of `nprob` problems; CTAs take
+// tiles from *counter (zeroed by the caller) in table order.  `grid` CTAs.
+cudaError_t launch_grouped_native(const Launch& L, const GroupProb* probs, int nprob,
+                                  int64_t total_tiles, unsigned long long* counter, int grid);
+// Resident 128-thread CTAs per SM of the grouped native kernel.
+int grouped_native_occupancy();
+
 // ---- emulated FP64 (ozaki_split.cu, ozaki_gemm.cu) ----
+// Workspace of the emulated path.  Digits are stored pre-tiled: for each tile of
+// R rows (R = 128 for A's rows, 32 for B's columns) and each 32-byte K block,
+// the s slices follow one another, each an R x 32-byte K-major block in the
+// 32-byte swizzle (16-byte chunk c of row r stored at chunk c ^ ((r / 4) & 1)),
+// i.e. exactly the shared-memory image the tensor core reads:
+//   byte of digit t of line x at column l:
+//     ((x / R) * nkb + l / 32) * s + t) * (R * 32) + (x % R) * 32
+//     + (((l % 32) / 16) ^ (((x % R) / 4) & 1)) * 16 + l % 16,   nkb = kp / 32.
+// Lines are padded to multiples of R (zero digits); columns to kp (zero digits).
 struct EmuLayout {
     int64_t kp;
     size_t a_digits, b_digits, a_exp, b_exp, total;
 };
 EmuLayout emu_layout(int s, int64_t m, int64_t n, int64_t k);
+
+// One emulated problem of a grouped launch, as the device reads it.
+struct EmuProb {
+    int64_t m, n, k, lda, ldb, ldc, kp;
+    const double* A;
+    const double* B;
+    double* C;
+    double alpha, beta;
+    uint8_t* a_digits;
+    uint8_t* b_digits;
+    int32_t* a_exp;
+    int32_t* b_exp;
+    int32_t s, tiles_n;
+    int64_t first_row;     // exclusive prefixes over the table of: rows of A padded to 128,
+    int64_t first_colblk;  // 32-column blocks of B,
+    int64_t first_tblk;    // (32-column x 64-row) blocks of B,
+    int64_t first_tile;    // 128 x 32 output tiles
+};
+
+// Grouped e1 + e2 over a table of emulated problems (three launches).
+cudaError_t launch_grouped_split(const Launch& L, const EmuProb* probs, int np,
+                                 int64_t total_rows, int64_t total_colblks, int64_t total_tblks);
+// Grouped e3 + e4: one CTA per 128 x 32 output tile.  max_s: largest s.
+cudaError_t launch_grouped_products(const Launch& L, const EmuProb* probs, int np,
+                                    int64_t total_tiles, int max_s);
+constexpr int kEmuBM = 128;      // output tile rows of the products kernel (A digit tile rows)
+constexpr int kEmuGroupBN = 32;  // output tile columns (B digit tile rows)
 
 cudaError_t launch_split_rows(const Launch& L, int s, int64_t m, int64_t k, const double* A,
                               int64_t lda, uint8_t* digits, int64_t kp, int32_t* exps);
@@ -62,7 +122,12 @@ cudaError_t launch_emu_products(const Launch& L, int s, int64_t m, int64_t n, in
                                 const uint8_t* a_digits, const uint8_t* b_digits, int64_t kp,
                                 const int32_t* a_exp, const int32_t* b_exp);
 
-// Last error text helper used by launchers (thread-local in api.cpp).
+// Last error text helper used by launchers (thread-local in api.cu).
 void set_error(const char* fmt, ...);
+
+// Host-side validation of a GEMM's sizes, leading dimensions and pointers;
+// returns a gb_status value (0 = OK) and sets the error text.
+int validate_gemm(int64_t m, int64_t n, int64_t k, double alpha, const double* A, int64_t lda,
+                  const double* B, int64_t ldb, double beta, const double* C, int64_t ldc);
 
 }  // namespace gb

@@ -14,10 +14,12 @@
 //     rate, so only the alpha / beta step uses the FP64 pipe.
 //
 // Pipeline per CTA (one output tile, 192 threads):
-//   warp 0 lane 0 : TMA producer.  Stage = one 32-byte K block of all s digit
-//                   planes of A (128 x 32 B each) and B (BN x 32 B each),
-//                   fetched by two 3-D tensor loads into the 32-byte-swizzled
-//                   K-major layout the tensor core reads.
+//   warp 0 lane 0 : producer.  Stage = one 32-byte K block of all s digit planes
+//                   of A (128 x 32 B each) and B (BN x 32 B each).  The split
+//                   kernels store each such block pre-tiled and pre-swizzled
+//                   (the 32-byte-swizzled K-major image the tensor core reads),
+//                   so a stage is two contiguous 1-D bulk copies (s * 4 KiB and
+//                   s * 1 KiB) instead of thousands of 32-byte row requests.
 //   warp 1        : allocates 512 TMEM columns; lane 0 issues the pair
 //                   products of a stage (M = 128, K = 32, N up to 256; all pairs
 //                   sharing an A slice go into one MMA) and commits each stage
@@ -25,9 +27,7 @@
 //   warps 2 - 5   : epilogue; warp w reads TMEM lanes 32 (w % 4) .. + 31.
 // Every wait on an mbarrier is bounded (wall-clock); on a timeout the CTA records
 // the timeout bit in the status word, skips its output and still frees TMEM.
-#include <cuda.h>
 #include <cuda_runtime.h>
-#include <cudaTypedefs.h>
 #include <cstdint>
 #include <cstring>
 
@@ -39,7 +39,8 @@
 namespace gb {
 namespace {
 
-constexpr int kBM = 128;
+constexpr int kBM = kEmuBM;
+constexpr int kBN = kEmuGroupBN;
 constexpr int kBKBytes = 32;
 constexpr int kThreads = 192;
 constexpr uint32_t kTmemCols = 512;
@@ -143,32 +144,31 @@ __device__ __forceinline__ double i128_to_double_scaled(I128 x, int E) {
     return neg ? -r : r;
 }
 
+// Arguments of one output tile (row0, col0) of one problem.
+struct TileArgs {
+    const uint8_t* a_src;  // A digit tiles of this tile row, K block 0 (s * 4 KiB per block)
+    const uint8_t* b_src;  // B digit tiles of this tile column, K block 0 (s * 1 KiB per block)
+    int s, nkb;
+    int64_t m, n, ldc, row0, col0;
+    double alpha, beta;
+    double* C;
+    const int32_t* eA;  // row exponents (indexed by row)
+    const int32_t* fB;  // column exponents (indexed by column)
+};
+
+// One 128 x BN output tile: level sums on the tensor cores, recombination into
+// C.  All 192 threads call it; `smem` is 1024-byte aligned and holds `stages`
+// ring slots of `slot_bytes` plus a SmemTail.
 template <int BN>
-__global__ void __launch_bounds__(kThreads, 1)
-    emu_products_kernel(const __grid_constant__ CUtensorMap tmA,
-                        const __grid_constant__ CUtensorMap tmB, int s, int64_t m, int64_t n,
-                        int nkb, double alpha, double beta, double* __restrict__ C, int64_t ldc,
-                        const int32_t* __restrict__ eA, const int32_t* __restrict__ fB,
-                        int tiles_m, int tiles_n, int stages, uint32_t stage_bytes,
-                        unsigned* status) {
-    extern __shared__ uint8_t smem_raw[];
-    uint8_t* smem = reinterpret_cast<uint8_t*>(
-        (reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~(uintptr_t)1023);
-    SmemTail* tail = reinterpret_cast<SmemTail*>(smem + (size_t)stages * stage_bytes);
+__device__ __forceinline__ void products_tile(const TileArgs& a, uint8_t* smem, int stages,
+                                              uint32_t slot_bytes, unsigned* status) {
+    SmemTail* tail = reinterpret_cast<SmemTail*>(smem + (size_t)stages * slot_bytes);
     uint64_t* full = tail->bars;
     uint64_t* empty = tail->bars + stages;
     uint64_t* tmem_full = tail->bars + 2 * stages;
     volatile int* abort = &tail->abort;
-
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-
-    // tile rasterisation: groups of 8 tile rows sweep the tile columns
-    const int bid = blockIdx.x;
-    const int group_size = 8 * tiles_n;
-    const int first_m = (bid / group_size) * 8;
-    const int gm = min(tiles_m - first_m, 8);
-    const int tm = first_m + (bid % group_size) % gm;
-    const int tn = (bid % group_size) / gm;
+    const int s = a.s, nkb = a.nkb;
 
     if (threadIdx.x == 0) {
         for (int i = 0; i < stages; ++i) {
@@ -178,8 +178,6 @@ __global__ void __launch_bounds__(kThreads, 1)
         ptx::mbar_init(tmem_full, 1);
         tail->abort = 0;
         ptx::mbar_init_fence();
-        ptx::tma_prefetch_desc(&tmA);
-        ptx::tma_prefetch_desc(&tmB);
     }
     if (warp == 1) {
         ptx::tmem_alloc(&tail->tmem_holder, kTmemCols);
@@ -190,19 +188,20 @@ __global__ void __launch_bounds__(kThreads, 1)
     ptx::tc_fence_after();
     const uint32_t tmem_base = tail->tmem_holder;
     const uint32_t a_bytes = (uint32_t)s * kBM * kBKBytes;
+    const uint32_t b_bytes = (uint32_t)s * BN * kBKBytes;
 
     if (warp == 0 && lane == 0) {
-        // ---- TMA producer ----
+        // ---- producer: two contiguous bulk copies per stage ----
         for (int kb = 0; kb < nkb; ++kb) {
             const int st = kb % stages;
             const uint32_t ph = (uint32_t)(kb / stages) & 1u;
             if (!ptx::mbar_wait_bounded(&empty[st], ph ^ 1u, abort, status, kStatusTimeout,
                                         kWaitTimeoutNs))
                 break;
-            uint8_t* sa = smem + (size_t)st * stage_bytes;
-            ptx::mbar_arrive_expect_tx(&full[st], stage_bytes);
-            ptx::tma_load_3d(sa, &tmA, kb * kBKBytes, tm * kBM, 0, &full[st]);
-            ptx::tma_load_3d(sa + a_bytes, &tmB, kb * kBKBytes, tn * BN, 0, &full[st]);
+            uint8_t* sa = smem + (size_t)st * slot_bytes;
+            ptx::mbar_arrive_expect_tx(&full[st], a_bytes + b_bytes);
+            ptx::bulk_load(sa, a.a_src + (size_t)kb * a_bytes, a_bytes, &full[st]);
+            ptx::bulk_load(sa + a_bytes, a.b_src + (size_t)kb * b_bytes, b_bytes, &full[st]);
         }
     } else if (warp == 1 && lane == 0) {
         // ---- MMA issuer ----
@@ -218,7 +217,7 @@ __global__ void __launch_bounds__(kThreads, 1)
                                         kWaitTimeoutNs))
                 break;
             ptx::tc_fence_after();
-            const uint32_t a0 = ptx::smem_u32(smem + (size_t)st * stage_bytes);
+            const uint32_t a0 = ptx::smem_u32(smem + (size_t)st * slot_bytes);
             const uint32_t b0 = a0 + a_bytes;
             for (int p = 1; p <= s; ++p) {
                 const uint64_t ad = ptx::umma_desc_sw32(a0 + (uint32_t)(p - 1) * kBM * kBKBytes);
@@ -237,15 +236,15 @@ __global__ void __launch_bounds__(kThreads, 1)
     } else if (warp >= 2) {
         // ---- epilogue ----
         const int quarter = warp & 3;
-        const int64_t row = (int64_t)tm * kBM + quarter * 32 + lane;
+        const int64_t row = a.row0 + quarter * 32 + lane;
         const bool ok = ptx::mbar_wait_bounded(tmem_full, 0, abort, status, kStatusTimeout,
                                                kWaitTimeoutNs);
         ptx::tc_fence_after();
         if (ok && !*abort) {
-            const int32_t ei = row < m ? eA[row] : 0;
+            const int32_t ei = row < a.m ? a.eA[row] : 0;
             const bool bad_row = ei == GB_BAD_LINE_DEV;
             const int Ebase = -8 - 5 * (s - 1);
-            const bool plain = (alpha == 1.0 && beta == 0.0);
+            const bool plain = (a.alpha == 1.0 && a.beta == 0.0);
             const uint32_t lane_addr = tmem_base + ((uint32_t)(quarter * 32) << 16);
 #pragma unroll 1
             for (int cb = 0; cb < BN; cb += 32) {
@@ -260,13 +259,13 @@ __global__ void __launch_bounds__(kThreads, 1)
 #pragma unroll
                     for (int j = 0; j < 32; ++j) i128_horner(T[j], 5, f32_int_value(v[j]));
                 }
-                if (row < m) {
-                    double* crow = C + row * ldc;
+                if (row < a.m) {
+                    double* crow = a.C + row * a.ldc;
 #pragma unroll
                     for (int j = 0; j < 32; ++j) {
-                        const int64_t col = (int64_t)tn * BN + cb + j;
-                        if (col < n) {
-                            const int32_t fj = fB[col];
+                        const int64_t col = a.col0 + cb + j;
+                        if (col < a.n) {
+                            const int32_t fj = a.fB[col];
                             double out;
                             if (bad_row || fj == GB_BAD_LINE_DEV) {
                                 out = __longlong_as_double(0x7FF8000000000000ll);
@@ -275,9 +274,9 @@ __global__ void __launch_bounds__(kThreads, 1)
                                 if (plain) {
                                     out = t;
                                 } else {
-                                    out = __dmul_rn(alpha, t);
-                                    if (beta != 0.0)
-                                        out = __dadd_rn(out, __dmul_rn(beta, crow[col]));
+                                    out = __dmul_rn(a.alpha, t);
+                                    if (a.beta != 0.0)
+                                        out = __dadd_rn(out, __dmul_rn(a.beta, crow[col]));
                                 }
                             }
                             crow[col] = out;
@@ -299,66 +298,99 @@ __global__ void __launch_bounds__(kThreads, 1)
         __syncwarp();
         ptx::tmem_dealloc(tmem_base, kTmemCols);
     }
+    __syncthreads();  // the shared memory may be reused by a following tile
 }
 
-PFN_cuTensorMapEncodeTiled_v12000 get_encoder() {
-    static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
-    if (!fn) {
-        void* p = nullptr;
-        cudaDriverEntryPointQueryResult q;
-        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000,
-                                             cudaEnableDefault, &q) == cudaSuccess &&
-            q == cudaDriverEntryPointSuccess)
-            fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(p);
+__device__ __forceinline__ uint8_t* aligned_smem(uint8_t* raw) {
+    return reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(raw) + 1023) & ~(uintptr_t)1023);
+}
+
+__global__ void __launch_bounds__(kThreads, 1)
+    emu_products_kernel(const uint8_t* __restrict__ ad, const uint8_t* __restrict__ bd, int s,
+                        int64_t m, int64_t n, int nkb, double alpha, double beta,
+                        double* __restrict__ C, int64_t ldc, const int32_t* __restrict__ eA,
+                        const int32_t* __restrict__ fB, int tiles_m, int tiles_n, int stages,
+                        uint32_t slot_bytes, unsigned* status) {
+    extern __shared__ uint8_t smem_raw[];
+    uint8_t* smem = aligned_smem(smem_raw);
+    // tile rasterisation: groups of 8 tile rows sweep the tile columns
+    const int bid = blockIdx.x;
+    const int group_size = 8 * tiles_n;
+    const int first_m = (bid / group_size) * 8;
+    const int gm = min(tiles_m - first_m, 8);
+    const int tm = first_m + (bid % group_size) % gm;
+    const int tn = (bid % group_size) / gm;
+    TileArgs a;
+    a.a_src = ad + (size_t)tm * nkb * s * kBM * kBKBytes;
+    a.b_src = bd + (size_t)tn * nkb * s * kBN * kBKBytes;
+    a.s = s;
+    a.nkb = nkb;
+    a.m = m;
+    a.n = n;
+    a.ldc = ldc;
+    a.row0 = (int64_t)tm * kBM;
+    a.col0 = (int64_t)tn * kBN;
+    a.alpha = alpha;
+    a.beta = beta;
+    a.C = C;
+    a.eA = eA;
+    a.fB = fB;
+    products_tile<kBN>(a, smem, stages, slot_bytes, status);
+}
+
+// Grouped: one CTA per output tile of any problem of the table.
+__global__ void __launch_bounds__(kThreads, 1)
+    grouped_products_kernel(const EmuProb* __restrict__ P, int np, int stages,
+                            uint32_t slot_bytes, unsigned* status) {
+    extern __shared__ uint8_t smem_raw[];
+    uint8_t* smem = aligned_smem(smem_raw);
+    const int64_t t = blockIdx.x;
+    int lo = 0, hi = np - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (P[mid].first_tile <= t) lo = mid; else hi = mid - 1;
     }
-    return fn;
+    const EmuProb& q = P[lo];
+    const int64_t local = t - q.first_tile;
+    const int64_t tm = local / q.tiles_n, tn = local % q.tiles_n;
+    const int nkb = (int)(q.kp / kBKBytes);
+    TileArgs a;
+    a.a_src = q.a_digits + (size_t)tm * nkb * q.s * kBM * kBKBytes;
+    a.b_src = q.b_digits + (size_t)tn * nkb * q.s * kBN * kBKBytes;
+    a.s = q.s;
+    a.nkb = nkb;
+    a.m = q.m;
+    a.n = q.n;
+    a.ldc = q.ldc;
+    a.row0 = tm * kBM;
+    a.col0 = tn * kBN;
+    a.alpha = q.alpha;
+    a.beta = q.beta;
+    a.C = q.C;
+    a.eA = q.a_exp;
+    a.fB = q.b_exp;
+    products_tile<kBN>(a, smem, stages, slot_bytes, status);
 }
 
-// 3-D map over s digit planes of `rows` x kp bytes, box 32 B x box_rows x s.
-bool make_digit_map(CUtensorMap* map, const uint8_t* base, int s, int64_t rows, int64_t kp,
-                    int box_rows) {
-    auto enc = get_encoder();
-    if (!enc) return false;
-    const cuuint64_t dims[3] = {(cuuint64_t)kp, (cuuint64_t)rows, (cuuint64_t)s};
-    const cuuint64_t strides[2] = {(cuuint64_t)kp, (cuuint64_t)(rows * kp)};
-    const cuuint32_t box[3] = {(cuuint32_t)kBKBytes, (cuuint32_t)box_rows, (cuuint32_t)s};
-    const cuuint32_t estr[3] = {1, 1, 1};
-    return enc(map, CU_TENSOR_MAP_DATA_TYPE_UINT8, 3, const_cast<uint8_t*>(base), dims, strides,
-               box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_32B,
-               CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) ==
-           CUDA_SUCCESS;
-}
+struct RingShape {
+    int stages;
+    uint32_t slot_bytes;
+    size_t smem;
+};
 
-template <int BN>
-cudaError_t launch_bn(const Launch& L, int s, int64_t m, int64_t n, int64_t kp, double alpha,
-                      double beta, double* C, int64_t ldc, const uint8_t* ad, const uint8_t* bd,
-                      const int32_t* ea, const int32_t* fb) {
-    CUtensorMap tma, tmb;
-    if (!make_digit_map(&tma, ad, s, m, kp, kBM) || !make_digit_map(&tmb, bd, s, n, kp, BN)) {
-        set_error("cuTensorMapEncodeTiled failed (s=%d m=%lld n=%lld kp=%lld)", s, (long long)m,
-                  (long long)n, (long long)kp);
-        return cudaErrorInvalidValue;
-    }
-    const uint32_t stage_bytes = (uint32_t)s * (kBM + BN) * kBKBytes;
+RingShape ring_for(int max_s) {
+    RingShape r{};
+    r.slot_bytes = (uint32_t)max_s * (kBM + kBN) * kBKBytes;
     const int fixed = 1024 + (int)sizeof(SmemTail) + 64;
-    int stages = (kSmemLimit - fixed) / (int)stage_bytes;
-    if (stages > 8) stages = 8;
-    if (stages < 2) return cudaErrorInvalidValue;
-    const size_t smem = (size_t)stages * stage_bytes + fixed;
-    static bool attr_set = false;
-    if (!attr_set) {
-        cudaError_t e = cudaFuncSetAttribute(emu_products_kernel<BN>,
-                                             cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                             kSmemLimit);
-        if (e != cudaSuccess) return e;
-        attr_set = true;
-    }
-    const int tiles_m = (int)((m + kBM - 1) / kBM), tiles_n = (int)((n + BN - 1) / BN);
-    const int nkb = (int)(kp / kBKBytes);
-    emu_products_kernel<BN><<<tiles_m * tiles_n, kThreads, smem, L.stream>>>(
-        tma, tmb, s, m, n, nkb, alpha, beta, C, ldc, ea, fb, tiles_m, tiles_n, stages,
-        stage_bytes, L.status);
-    return cudaGetLastError();
+    r.stages = (kSmemLimit - fixed) / (int)r.slot_bytes;
+    if (r.stages > 8) r.stages = 8;
+    r.smem = (size_t)r.stages * r.slot_bytes + fixed;
+    return r;
+}
+
+template <typename K>
+cudaError_t allow_smem(K kernel) {
+    return cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemLimit);
 }
 
 }  // namespace
@@ -369,9 +401,28 @@ cudaError_t launch_emu_products(const Launch& L, int s, int64_t m, int64_t n, in
                                 const int32_t* a_exp, const int32_t* b_exp) {
     (void)k;
     if (m == 0 || n == 0) return cudaSuccess;
-    if (s <= 8)
-        return launch_bn<64>(L, s, m, n, kp, alpha, beta, C, ldc, a_digits, b_digits, a_exp, b_exp);
-    return launch_bn<32>(L, s, m, n, kp, alpha, beta, C, ldc, a_digits, b_digits, a_exp, b_exp);
+    const RingShape r = ring_for(s);
+    if (r.stages < 2) return cudaErrorInvalidValue;
+    cudaError_t e = allow_smem(emu_products_kernel);
+    if (e != cudaSuccess) return e;
+    const int tiles_m = (int)((m + kBM - 1) / kBM), tiles_n = (int)((n + kBN - 1) / kBN);
+    const int nkb = (int)(kp / kBKBytes);
+    emu_products_kernel<<<tiles_m * tiles_n, kThreads, r.smem, L.stream>>>(
+        a_digits, b_digits, s, m, n, nkb, alpha, beta, C, ldc, a_exp, b_exp, tiles_m, tiles_n,
+        r.stages, r.slot_bytes, L.status);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_grouped_products(const Launch& L, const EmuProb* probs, int np,
+                                    int64_t total_tiles, int max_s) {
+    if (np == 0 || total_tiles == 0) return cudaSuccess;
+    const RingShape r = ring_for(max_s);
+    if (r.stages < 2) return cudaErrorInvalidValue;
+    cudaError_t e = allow_smem(grouped_products_kernel);
+    if (e != cudaSuccess) return e;
+    grouped_products_kernel<<<(unsigned)total_tiles, kThreads, r.smem, L.stream>>>(
+        probs, np, r.stages, r.slot_bytes, L.status);
+    return cudaGetLastError();
 }
 
 }  // namespace gb

@@ -11,8 +11,9 @@
 // explicit shift sh.  Rounding R / 2^sh to nearest-even with integer shifts gives
 // the same digits as the FP64 recurrence, which is exact at every step.
 //
-// Output layout (K-major, the operand layout of the tensor-core products):
-//   digits[(t * lines + line) * kp + l], one E4M3 byte each, zero for l >= k;
+// Output layout: one E4M3 byte per digit, pre-tiled for the tensor-core
+// products (tiles of R lines x 32 bytes, R = 128 for A and 32 for B, in the
+// 32-byte swizzle; see tiled_offset), zero for l >= k and for padding lines;
 //   exps[line] = e, or GB_BAD_LINE when the line holds a NaN or Inf (its digits
 //   are all zero and the products mark its outputs NaN).
 #include <cuda_runtime.h>
@@ -74,7 +75,7 @@ __device__ __forceinline__ void digits_of(uint64_t bits, int e, int s, int lane,
         if (R == 0 || sh >= 55) {
             d = 0;                         // |R| < 2^53 <= 2^(sh-2): |y| < 1/2
         } else if (sh <= 0) {
-            d = R << (-sh);                // y is an integer
+            d = R * ((int64_t)1 << (-sh));  // y is an integer
             R = 0;
         } else {
             int64_t q = R >> sh;           // floor
@@ -91,76 +92,89 @@ __device__ __forceinline__ void digits_of(uint64_t bits, int e, int s, int lane,
 
 constexpr int kSMax = 16;
 
-// One block per row (grid-stride): pass 1 max |a| and finiteness, pass 2 digits.
-__global__ void __launch_bounds__(128) split_rows_kernel(int64_t m, int64_t k,
-                                                         const double* __restrict__ A,
-                                                         int64_t lda, int s,
-                                                         uint8_t* __restrict__ digits,
-                                                         int64_t kp, int32_t* __restrict__ exps,
-                                                         unsigned* status) {
-    __shared__ uint64_t red[4];
-    __shared__ int bad_sh;
-    const int tid = threadIdx.x;
-    for (int64_t i = blockIdx.x; i < m; i += gridDim.x) {
-        const uint64_t* row = reinterpret_cast<const uint64_t*>(A + i * lda);
-        uint64_t mx = 0;
-        int bad = 0;
-        for (int64_t l = tid; l < k; l += blockDim.x) {
-            const uint64_t a = row[l] & 0x7FFFFFFFFFFFFFFFull;
-            if (a >= 0x7FF0000000000000ull) bad = 1;
-            else if (a > mx) mx = a;
-        }
-        for (int o = 16; o > 0; o >>= 1) {
-            const uint64_t v = __shfl_xor_sync(0xffffffffu, mx, o);
-            mx = v > mx ? v : mx;
-        }
-        bad = __syncthreads_or(bad);
-        if ((tid & 31) == 0) red[tid >> 5] = mx;
-        __syncthreads();
-        if (tid == 0) {
-            uint64_t v = red[0];
-            for (int w = 1; w < (int)(blockDim.x >> 5); ++w) v = red[w] > v ? red[w] : v;
-            red[0] = v;
-            bad_sh = bad;
-        }
-        __syncthreads();
-        const int e = frexp_exp_bits(red[0]);
-        const bool is_bad = bad_sh != 0;
-        if (tid == 0) {
-            exps[i] = is_bad ? GB_BAD_LINE_DEV : e;
-            if (is_bad && status) atomicOr(status, kStatusNonfinite);
-        }
-        // pass 2: 8 consecutive elements per thread -> one 8-byte word per plane
-        for (int64_t l0 = (int64_t)tid * 8; l0 < kp; l0 += (int64_t)blockDim.x * 8) {
-            uint64_t w[kSMax];
-#pragma unroll
-            for (int t = 0; t < kSMax; ++t) w[t] = 0;
-            if (!is_bad) {
-#pragma unroll
-                for (int u = 0; u < 8; ++u) {
-                    const int64_t l = l0 + u;
-                    if (l < k) digits_of<kSMax>(row[l], e, s, u, w);
-                }
-            }
-#pragma unroll
-            for (int t = 0; t < kSMax; ++t) {
-                if (t >= s) break;
-                *reinterpret_cast<uint64_t*>(digits + ((int64_t)t * m + i) * kp + l0) = w[t];
-            }
-        }
-        __syncthreads();
-    }
+// Byte offset of digit t of line x at K index l0 (l0 % 8 == 0; the 8 bytes
+// l0 .. l0+7 are contiguous) in the tiled layout with R-line tiles.
+__device__ __forceinline__ int64_t tiled_offset(int64_t x, int64_t l0, int t, int s, int64_t nkb,
+                                                int R) {
+    const int64_t tile = x / R;
+    const int r = (int)(x - tile * R);
+    const int64_t kb = l0 >> 5;
+    const int c = (int)(l0 & 31);
+    const int chunk = (c >> 4) ^ ((r >> 2) & 1);
+    return ((tile * nkb + kb) * s + t) * (int64_t)(R * 32) + r * 32 + (chunk << 4) + (c & 15);
 }
 
-// Column max of B (k x n): block of 32 columns x 8 row groups.
-__global__ void __launch_bounds__(256) colmax_kernel(int64_t n, int64_t k,
-                                                     const double* __restrict__ B, int64_t ldb,
-                                                     int32_t* __restrict__ exps,
-                                                     unsigned* status) {
-    __shared__ uint64_t mx_sh[8][32];
-    __shared__ int bad_sh[8][32];
+// Row i of A: pass 1 max |a| and finiteness, pass 2 digits (all threads call it).
+// Rows m <= i < (tile padding) get zero digits.
+__device__ __forceinline__ void split_one_row(int64_t i, int64_t m, int64_t k,
+                                              const double* __restrict__ A, int64_t lda, int s,
+                                              uint8_t* __restrict__ digits, int64_t kp,
+                                              int32_t* __restrict__ exps, unsigned* status,
+                                              uint64_t* red, int* bad_sh) {
+    const int tid = threadIdx.x;
+    const int64_t nkb = kp >> 5;
+    if (i >= m) {
+        for (int64_t l0 = (int64_t)tid * 8; l0 < kp; l0 += (int64_t)blockDim.x * 8)
+            for (int t = 0; t < s; ++t)
+                *reinterpret_cast<uint64_t*>(digits + tiled_offset(i, l0, t, s, nkb, kEmuBM)) = 0;
+        return;
+    }
+    const uint64_t* row = reinterpret_cast<const uint64_t*>(A + i * lda);
+    uint64_t mx = 0;
+    int bad = 0;
+    for (int64_t l = tid; l < k; l += blockDim.x) {
+        const uint64_t a = row[l] & 0x7FFFFFFFFFFFFFFFull;
+        if (a >= 0x7FF0000000000000ull) bad = 1;
+        else if (a > mx) mx = a;
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+        const uint64_t v = __shfl_xor_sync(0xffffffffu, mx, o);
+        mx = v > mx ? v : mx;
+    }
+    bad = __syncthreads_or(bad);
+    if ((tid & 31) == 0) red[tid >> 5] = mx;
+    __syncthreads();
+    if (tid == 0) {
+        uint64_t v = red[0];
+        for (int w = 1; w < (int)(blockDim.x >> 5); ++w) v = red[w] > v ? red[w] : v;
+        red[0] = v;
+        *bad_sh = bad;
+    }
+    __syncthreads();
+    const int e = frexp_exp_bits(red[0]);
+    const bool is_bad = *bad_sh != 0;
+    if (tid == 0) {
+        exps[i] = is_bad ? GB_BAD_LINE_DEV : e;
+        if (is_bad && status) atomicOr(status, kStatusNonfinite);
+    }
+    // pass 2: 8 consecutive elements per thread -> one 8-byte word per plane
+    for (int64_t l0 = (int64_t)tid * 8; l0 < kp; l0 += (int64_t)blockDim.x * 8) {
+        uint64_t w[kSMax];
+#pragma unroll
+        for (int t = 0; t < kSMax; ++t) w[t] = 0;
+        if (!is_bad) {
+#pragma unroll
+            for (int u = 0; u < 8; ++u) {
+                const int64_t l = l0 + u;
+                if (l < k) digits_of<kSMax>(row[l], e, s, u, w);
+            }
+        }
+#pragma unroll
+        for (int t = 0; t < kSMax; ++t) {
+            if (t >= s) break;
+            *reinterpret_cast<uint64_t*>(digits + tiled_offset(i, l0, t, s, nkb, kEmuBM)) = w[t];
+        }
+    }
+    __syncthreads();
+}
+
+// Column block jb (32 columns) of B: max |b| over all rows, per column.
+__device__ __forceinline__ void colmax_block(int64_t jb, int64_t n, int64_t k,
+                                             const double* __restrict__ B, int64_t ldb,
+                                             int32_t* __restrict__ exps, unsigned* status,
+                                             uint64_t (*mx_sh)[32], int (*bad_sh)[32]) {
     const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
-    const int64_t j = blockIdx.x * 32ll + tx;
+    const int64_t j = jb * 32 + tx;
     uint64_t mx = 0;
     int bad = 0;
     if (j < n) {
@@ -182,19 +196,19 @@ __global__ void __launch_bounds__(256) colmax_kernel(int64_t n, int64_t k,
         exps[j] = bad ? GB_BAD_LINE_DEV : frexp_exp_bits(mx);
         if (bad && status) atomicOr(status, kStatusNonfinite);
     }
+    __syncthreads();
 }
 
-// Transposing digit pass for B: tile of 64 rows (l) x 32 columns (j).
-__global__ void __launch_bounds__(256) split_cols_kernel(int64_t n, int64_t k,
-                                                         const double* __restrict__ B,
-                                                         int64_t ldb, int s,
-                                                         uint8_t* __restrict__ digits,
-                                                         int64_t kp,
-                                                         const int32_t* __restrict__ exps) {
-    __shared__ uint64_t T[64][33];
+// Transposing digit pass for B over the tile of 64 rows (l) x 32 columns (j)
+// at (lb, jb).
+__device__ __forceinline__ void split_cols_tile(int64_t jb, int64_t lb, int64_t n, int64_t k,
+                                                const double* __restrict__ B, int64_t ldb,
+                                                int s, uint8_t* __restrict__ digits, int64_t kp,
+                                                const int32_t* __restrict__ exps,
+                                                uint64_t (*T)[33]) {
     const int tid = threadIdx.x;
     const int tx = tid & 31, ty = tid >> 5;
-    const int64_t j0 = blockIdx.x * 32ll, l0 = blockIdx.y * 64ll;
+    const int64_t j0 = jb * 32, l0 = lb * 64;
     const uint64_t* Bb = reinterpret_cast<const uint64_t*>(B);
 #pragma unroll
     for (int r = 0; r < 8; ++r) {
@@ -204,21 +218,102 @@ __global__ void __launch_bounds__(256) split_cols_kernel(int64_t n, int64_t k,
     __syncthreads();
     const int jj = tid >> 3, lsub = (tid & 7) * 8;
     const int64_t j = j0 + jj, lbase = l0 + lsub;
-    if (j >= n || lbase >= kp) return;
-    const int e = exps[j];
-    uint64_t w[kSMax];
+    if (lbase < kp) {  // columns n <= j < (tile padding) get zero digits
+        const int e = j < n ? exps[j] : GB_BAD_LINE_DEV;
+        uint64_t w[kSMax];
 #pragma unroll
-    for (int t = 0; t < kSMax; ++t) w[t] = 0;
-    if (e != GB_BAD_LINE_DEV) {
+        for (int t = 0; t < kSMax; ++t) w[t] = 0;
+        if (e != GB_BAD_LINE_DEV) {
 #pragma unroll
-        for (int u = 0; u < 8; ++u) {
-            if (lbase + u < k) digits_of<kSMax>(T[lsub + u][jj], e, s, u, w);
+            for (int u = 0; u < 8; ++u) {
+                if (lbase + u < k) digits_of<kSMax>(T[lsub + u][jj], e, s, u, w);
+            }
+        }
+#pragma unroll
+        for (int t = 0; t < kSMax; ++t) {
+            if (t >= s) break;
+            *reinterpret_cast<uint64_t*>(digits + tiled_offset(j, lbase, t, s, kp >> 5,
+                                                               kEmuGroupBN)) = w[t];
         }
     }
-#pragma unroll
-    for (int t = 0; t < kSMax; ++t) {
-        if (t >= s) break;
-        *reinterpret_cast<uint64_t*>(digits + ((int64_t)t * n + j) * kp + lbase) = w[t];
+    __syncthreads();
+}
+
+__global__ void __launch_bounds__(128) split_rows_kernel(int64_t m, int64_t k,
+                                                         const double* __restrict__ A,
+                                                         int64_t lda, int s,
+                                                         uint8_t* __restrict__ digits,
+                                                         int64_t kp, int32_t* __restrict__ exps,
+                                                         unsigned* status) {
+    __shared__ uint64_t red[4];
+    __shared__ int bad_sh;
+    const int64_t mp = (m + kEmuBM - 1) / kEmuBM * kEmuBM;
+    for (int64_t i = blockIdx.x; i < mp; i += gridDim.x)
+        split_one_row(i, m, k, A, lda, s, digits, kp, exps, status, red, &bad_sh);
+}
+
+__global__ void __launch_bounds__(256) colmax_kernel(int64_t n, int64_t k,
+                                                     const double* __restrict__ B, int64_t ldb,
+                                                     int32_t* __restrict__ exps,
+                                                     unsigned* status) {
+    __shared__ uint64_t mx_sh[8][32];
+    __shared__ int bad_sh[8][32];
+    colmax_block(blockIdx.x, n, k, B, ldb, exps, status, mx_sh, bad_sh);
+}
+
+__global__ void __launch_bounds__(256) split_cols_kernel(int64_t n, int64_t k,
+                                                         const double* __restrict__ B,
+                                                         int64_t ldb, int s,
+                                                         uint8_t* __restrict__ digits,
+                                                         int64_t kp,
+                                                         const int32_t* __restrict__ exps) {
+    __shared__ uint64_t T[64][33];
+    split_cols_tile(blockIdx.x, blockIdx.y, n, k, B, ldb, s, digits, kp, exps, T);
+}
+
+// ---- grouped: one launch per step over the problems of a table ---------------------
+__device__ __forceinline__ int find_prob(const EmuProb* __restrict__ P, int np,
+                                         int64_t EmuProb::*field, int64_t x) {
+    int lo = 0, hi = np - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (P[mid].*field <= x) lo = mid; else hi = mid - 1;
+    }
+    return lo;
+}
+
+__global__ void __launch_bounds__(128) grouped_split_rows_kernel(const EmuProb* __restrict__ P,
+                                                                 int np, int64_t total_rows,
+                                                                 unsigned* status) {
+    __shared__ uint64_t red[4];
+    __shared__ int bad_sh;
+    for (int64_t r = blockIdx.x; r < total_rows; r += gridDim.x) {
+        const EmuProb& q = P[find_prob(P, np, &EmuProb::first_row, r)];
+        split_one_row(r - q.first_row, q.m, q.k, q.A, q.lda, q.s, q.a_digits, q.kp, q.a_exp,
+                      status, red, &bad_sh);
+    }
+}
+
+__global__ void __launch_bounds__(256) grouped_colmax_kernel(const EmuProb* __restrict__ P,
+                                                             int np, int64_t total_blocks,
+                                                             unsigned* status) {
+    __shared__ uint64_t mx_sh[8][32];
+    __shared__ int bad_sh[8][32];
+    for (int64_t b = blockIdx.x; b < total_blocks; b += gridDim.x) {
+        const EmuProb& q = P[find_prob(P, np, &EmuProb::first_colblk, b)];
+        colmax_block(b - q.first_colblk, q.n, q.k, q.B, q.ldb, q.b_exp, status, mx_sh, bad_sh);
+    }
+}
+
+__global__ void __launch_bounds__(256) grouped_split_cols_kernel(const EmuProb* __restrict__ P,
+                                                                 int np, int64_t total_tiles) {
+    __shared__ uint64_t T[64][33];
+    for (int64_t b = blockIdx.x; b < total_tiles; b += gridDim.x) {
+        const EmuProb& q = P[find_prob(P, np, &EmuProb::first_tblk, b)];
+        const int64_t local = b - q.first_tblk;
+        const int64_t ncb = (q.n + 31) / 32;
+        split_cols_tile(local % ncb, local / ncb, q.n, q.k, q.B, q.ldb, q.s, q.b_digits, q.kp,
+                        q.b_exp, T);
     }
 }
 
@@ -227,11 +322,26 @@ __global__ void __launch_bounds__(256) split_cols_kernel(int64_t n, int64_t k,
 cudaError_t launch_split_rows(const Launch& L, int s, int64_t m, int64_t k, const double* A,
                               int64_t lda, uint8_t* digits, int64_t kp, int32_t* exps) {
     if (m == 0) return cudaSuccess;
-    int64_t blocks = m;
+    int64_t blocks = (m + kEmuBM - 1) / kEmuBM * kEmuBM;
     const int64_t cap = (int64_t)L.sm_count * 16;
     if (blocks > cap) blocks = cap;
     split_rows_kernel<<<(unsigned)blocks, 128, 0, L.stream>>>(m, k, A, lda, s, digits, kp, exps,
                                                               L.status);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_grouped_split(const Launch& L, const EmuProb* probs, int np,
+                                 int64_t total_rows, int64_t total_colblks, int64_t total_tblks) {
+    if (np == 0) return cudaSuccess;
+    const int64_t cap = (int64_t)L.sm_count * 16;
+    auto g = [&](int64_t x) { return (unsigned)(x < cap ? (x > 0 ? x : 1) : cap); };
+    grouped_split_rows_kernel<<<g(total_rows), 128, 0, L.stream>>>(probs, np, total_rows, L.status);
+    cudaError_t err = cudaGetLastError();
+    if (err != cudaSuccess) return err;
+    grouped_colmax_kernel<<<g(total_colblks), 256, 0, L.stream>>>(probs, np, total_colblks, L.status);
+    err = cudaGetLastError();
+    if (err != cudaSuccess) return err;
+    grouped_split_cols_kernel<<<g(total_tblks), 256, 0, L.stream>>>(probs, np, total_tblks);
     return cudaGetLastError();
 }
 

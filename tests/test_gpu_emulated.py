@@ -38,6 +38,20 @@ def emulate(gb, A, B, C0, alpha, beta, s):
     return dC.cpu().numpy()
 
 
+def untile(raw, base, s, lines, kp, R):
+    """Digit planes (s, lines_padded, kp) from the tiled workspace layout: tiles of R
+    lines x 32 bytes, slices consecutive per K block, 16-byte chunk c of row r
+    stored at chunk c ^ ((r // 4) & 1)."""
+    lp = -(-lines // R) * R
+    nkb = kp // 32
+    buf = raw[base:base + s * lp * kp].reshape(lp // R, nkb, s, R, 2, 16)
+    swz = (np.arange(R) // 4) & 1
+    logical = np.empty_like(buf)
+    logical[:, :, :, swz == 0] = buf[:, :, :, swz == 0]
+    logical[:, :, :, swz == 1] = buf[:, :, :, swz == 1][:, :, :, :, ::-1]
+    return logical.transpose(2, 0, 3, 1, 4, 5).reshape(s, lp, kp)
+
+
 def split_on_gpu(gb, A, B, s):
     import torch
     m, k = A.shape
@@ -51,8 +65,8 @@ def split_on_gpu(gb, A, B, s):
     torch.cuda.synchronize()
     raw = ws.cpu().numpy()
     kp = lay.kp
-    da = raw[lay.a_digits:lay.a_digits + s * m * kp].reshape(s, m, kp)
-    db = raw[lay.b_digits:lay.b_digits + s * n * kp].reshape(s, n, kp)
+    da = untile(raw, lay.a_digits, s, m, kp, 128)
+    db = untile(raw, lay.b_digits, s, n, kp, 32)
     ea = raw[lay.a_exp:lay.a_exp + 4 * m].view(np.int32)
     fb = raw[lay.b_exp:lay.b_exp + 4 * n].view(np.int32)
     return da, db, ea, fb, kp
@@ -71,9 +85,11 @@ def test_split_digits_and_exponents_bit_exact(gb, kind, m, n, k, s):
     DB, _ = ozaki.slice_digits(B, f, s, axis=0)
     vals_a = e4m3_decode(da)
     vals_b = e4m3_decode(db)
-    assert np.array_equal(vals_a[:, :, :k], DA.astype(np.float64))
-    assert np.array_equal(vals_b[:, :, :k], DB.transpose(0, 2, 1).astype(np.float64))
+    assert np.array_equal(vals_a[:, :m, :k], DA.astype(np.float64))
+    assert np.array_equal(vals_b[:, :n, :k], DB.transpose(0, 2, 1).astype(np.float64))
+    # K padding and line padding hold zero digits
     assert np.all(vals_a[:, :, k:] == 0) and np.all(vals_b[:, :, k:] == 0)
+    assert np.all(vals_a[:, m:, :] == 0) and np.all(vals_b[:, n:, :] == 0)
 
 
 @pytest.mark.parametrize("s", [1, 2, 4, 8, 9, 11, 13, 16])

@@ -1,0 +1,143 @@
+"""GPU parity of the grouped (persistent, graph-captured) GEMMs.
+
+The grouped result of each problem equals the single-launch result bit for bit
+(same per-element summation order in every native tile variant; same digits and
+products in the emulated path), and each is within the FP64 bound of the
+oracle.  Problem sizes follow the grouped workload's recipe (m, n, k
+log-uniform in [16, 512]) at a reduced count, plus edge cases.
+"""
+import numpy as np
+import pytest
+
+from oracle import cgemm, exact
+from synth import generators as g
+
+from gpu_util import to_dev
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def gb():
+    import torch
+    import paper_1602_08477_gb300 as gb
+    gb.build()
+    assert torch.cuda.is_available()
+    return gb
+
+
+def make_group(count, seed, precision="native", tile="auto", emulated_every=0):
+    ms, ns, ks = g.grouped_problems(seed, count)
+    probs, host = [], []
+    for i, (m, n, k) in enumerate(zip(ms, ns, ks)):
+        A = g.matrix("uniform", int(m), int(k), seed + i, 0)
+        B = g.matrix("uniform", int(k), int(n), seed + i, 1)
+        C0 = g.matrix("uniform", int(m), int(n), seed + i, 2)
+        prec = precision
+        if emulated_every and i % emulated_every == 0:
+            prec = "emulated"
+        probs.append(dict(A=to_dev(A), B=to_dev(B), C=to_dev(C0), alpha=1.0, beta=0.5,
+                          precision=prec, slices=12, tile=tile))
+        host.append((A, B, C0))
+    return probs, host
+
+
+def check_bound(probs, host):
+    worst = 0.0
+    for p, (A, B, C0) in zip(probs, host):
+        got = p["C"].cpu().numpy()
+        k = A.shape[1]
+        ref = cgemm.dgemm(p["alpha"], A, B, p["beta"], C0.copy())
+        bound = exact.error_bound(k, p["alpha"], cgemm.dgemm(1.0, np.abs(A), np.abs(B)),
+                                  p["beta"], C0)
+        # the oracle is itself within the bound of C*, so |got - ref| <= 2 bound
+        worst = max(worst, float(np.max(np.abs(got - ref) / bound)))
+    return worst
+
+
+@pytest.mark.parametrize("tile", ["auto", "64x64", "32x32", "64x32", "32x64"])
+def test_native_group_matches_single_launches_bit_exact(gb, tile):
+    import torch
+    probs, host = make_group(96, 4401, tile=tile)
+    plan = gb.GroupedPlan(probs, use_graph=True)
+    plan.run()
+    torch.cuda.synchronize()
+    info = plan.info()
+    assert info["launches"] == 1 and info["emulated_tiles"] == 0
+    for p, (A, B, C0) in zip(probs, host):
+        single = to_dev(C0)
+        gb.dgemm(to_dev(A), to_dev(B), single, p["alpha"], p["beta"], kernel="dmma")
+        torch.cuda.synchronize()
+        assert torch.equal(p["C"], single)
+    assert check_bound(probs, host) <= 2.0
+    plan.close()
+
+
+def test_graph_replay_recomputes(gb):
+    import torch
+    probs, host = make_group(64, 4402)
+    plan = gb.GroupedPlan(probs, use_graph=True)
+    plan.run()
+    torch.cuda.synchronize()
+    first = [p["C"].clone() for p in probs]
+    for p, (_, _, C0) in zip(probs, host):
+        p["C"].copy_(to_dev(C0))
+    plan.run()
+    plan.run()  # beta = 0.5: the second replay updates C again
+    torch.cuda.synchronize()
+    for p, f, (A, B, C0) in zip(probs, first, host):
+        again = f.clone()
+        gb.dgemm(to_dev(A), to_dev(B), again, p["alpha"], p["beta"], kernel="dmma")
+        torch.cuda.synchronize()
+        assert torch.equal(p["C"], again)
+    plan.close()
+
+
+def test_emulated_and_mixed_group(gb):
+    import torch
+    probs, host = make_group(60, 4403, emulated_every=3)
+    plan = gb.GroupedPlan(probs, use_graph=True)
+    plan.run()
+    torch.cuda.synchronize()
+    info = plan.info()
+    assert info["emulated_tiles"] > 0 and info["native_tiles"] > 0 and info["launches"] == 5
+    for p, (A, B, C0) in zip(probs, host):
+        single = to_dev(C0)
+        if p["precision"] == "emulated":
+            gb.dgemm(to_dev(A), to_dev(B), single, p["alpha"], p["beta"], precision="emulated",
+                     slices=p["slices"])
+        else:
+            gb.dgemm(to_dev(A), to_dev(B), single, p["alpha"], p["beta"], kernel="dmma")
+        torch.cuda.synchronize()
+        assert torch.equal(p["C"], single)
+    assert check_bound(probs, host) <= 2.0
+    plan.close()
+
+
+def test_edge_problems_in_a_group(gb):
+    import torch
+    A, B, C0 = (g.matrix("uniform", 40, 30, 9, 0), g.matrix("uniform", 30, 20, 9, 1),
+                g.matrix("uniform", 40, 20, 9, 2))
+    e = torch.empty((0, 5), dtype=torch.float64, device="cuda")
+    probs = [
+        dict(A=to_dev(A), B=to_dev(B), C=to_dev(C0), alpha=0.0, beta=0.25),           # beta C
+        dict(A=to_dev(A), B=to_dev(B), C=torch.full((40, 20), float("nan"), dtype=torch.float64,
+                                                      device="cuda"), alpha=1.0, beta=0.0),
+        dict(A=e, B=torch.empty((5, 7), dtype=torch.float64, device="cuda"),
+             C=torch.empty((0, 7), dtype=torch.float64, device="cuda")),               # m = 0
+        dict(A=to_dev(A), B=to_dev(B), C=to_dev(C0), alpha=1.0, beta=1.0,
+             precision="emulated", slices=0),
+    ]
+    gb.dgemm_grouped(probs)
+    torch.cuda.synchronize()
+    assert np.array_equal(probs[0]["C"].cpu().numpy(), 0.25 * C0)
+    assert np.isfinite(probs[1]["C"].cpu().numpy()).all()
+    bound = exact.error_bound(30, 1.0, cgemm.dgemm(1.0, np.abs(A), np.abs(B)), 1.0, C0)
+    ref = cgemm.dgemm(1.0, A, B, 1.0, C0.copy())
+    assert np.all(np.abs(probs[3]["C"].cpu().numpy() - ref) <= 2 * bound)
+
+
+def test_invalid_descriptor_rejected(gb):
+    A = to_dev(g.matrix("uniform", 8, 8, 1, 0))
+    with pytest.raises(gb.GbError, match="INVALID_ARG"):
+        gb.dgemm_grouped([dict(A=A, B=A, C=A.clone(), precision="emulated", slices=40)])

@@ -1,0 +1,108 @@
+"""GPU tests of the request server: each result is the same alone and in the mix
+(bit for bit), budget admission, the device operand generator, host-side
+rejection of a request that can never fit."""
+import numpy as np
+import pytest
+
+from oracle import cgemm, exact
+from synth import generators as g
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def gb():
+    import torch
+    import paper_1602_08477_gb300 as gb
+    gb.build()
+    assert torch.cuda.is_available()
+    return gb
+
+
+def test_device_generator_matches_host_generator(gb):
+    import torch
+    t = torch.empty((37, 53), dtype=torch.float64, device="cuda")
+    gb.fill_uniform(t, 1234, 1)
+    torch.cuda.synchronize()
+    assert np.array_equal(t.cpu().numpy(), g.matrix("uniform", 37, 53, 1234, 1))
+
+
+def _requests(count, seed):
+    sizes = g.log_uniform_ints(seed, 30, count, 16, 700)
+    prec = (g.raw_stream(seed, 31, count) % np.uint64(5)) == 0  # ~20% emulated
+    reqs = []
+    for i in range(count):
+        n = int(sizes[i])
+        m = max(1, n // 2 + i % 7)
+        k = max(1, n - i % 5)
+        A = g.matrix("uniform", m, k, seed + i, 0)
+        B = g.matrix("uniform", k, n, seed + i, 1)
+        C0 = g.matrix("uniform", m, n, seed + i, 2)
+        reqs.append(dict(m=m, n=n, k=k, A=A, B=B, C=C0, alpha=1.0, beta=0.5,
+                         precision="emulated" if prec[i] else "native", slices=12))
+    return reqs
+
+
+def test_results_alone_equal_results_in_the_mix(gb):
+    reqs = _requests(48, 5500)
+    # in the mix: all submitted at once to a server with small batches and a
+    # budget that forces admission waits
+    mix = gb.Server(hbm_budget_bytes=64 << 20, n_streams=3, max_batch=8)
+    outs, ids = [], []
+    for r in reqs:
+        out = np.empty((r["m"], r["n"]))
+        outs.append(out)
+        ids.append(mix.submit(r["m"], r["n"], r["k"], r["alpha"], r["beta"], r["precision"],
+                              r["slices"], A=r["A"], B=r["B"], C=r["C"], out=out))
+    mix.drain(600)
+    st = mix.stats()
+    assert st["completed"] == len(reqs) and st["peak_bytes"] <= 64 << 20
+    assert st["batches"] > 1
+    for rid in ids:
+        done, status, lat = mix.poll(rid)
+        assert done and status == 0 and lat >= 0
+    mix.close()
+    # alone: one request per server
+    for r, out in zip(reqs, outs):
+        solo = gb.Server(hbm_budget_bytes=64 << 20, n_streams=1, max_batch=1)
+        alone = np.empty((r["m"], r["n"]))
+        solo.submit(r["m"], r["n"], r["k"], r["alpha"], r["beta"], r["precision"], r["slices"],
+                    A=r["A"], B=r["B"], C=r["C"], out=alone)
+        solo.drain(600)
+        solo.close()
+        assert np.array_equal(alone, out)
+        # and within the FP64 bound of the oracle
+        ref = cgemm.dgemm(r["alpha"], r["A"], r["B"], r["beta"], r["C"].copy())
+        bound = exact.error_bound(r["k"], r["alpha"], cgemm.dgemm(1.0, np.abs(r["A"]),
+                                                                   np.abs(r["B"])),
+                                  r["beta"], r["C"])
+        assert np.all(np.abs(out - ref) <= 2 * bound)
+
+
+def test_device_generated_operands(gb):
+    import torch
+    srv = gb.Server(hbm_budget_bytes=256 << 20, n_streams=2, max_batch=16)
+    m, n, k = 300, 200, 150
+    out = np.empty((m, n))
+    rid = srv.submit(m, n, k, 1.5, 0.5, "native", 0, out=out, seed=777)
+    srv.drain(120)
+    assert srv.poll(rid)[0]
+    A = g.matrix("uniform", m, k, 777, 0)
+    B = g.matrix("uniform", k, n, 777, 1)
+    C0 = g.matrix("uniform", m, n, 777, 2)
+    ref = cgemm.dgemm(1.5, A, B, 0.5, C0.copy())
+    bound = exact.error_bound(k, 1.5, cgemm.dgemm(1.0, np.abs(A), np.abs(B)), 0.5, C0)
+    assert np.all(np.abs(out - ref) <= 2 * bound)
+    srv.close()
+    torch.cuda.synchronize()
+
+
+def test_request_that_never_fits_is_rejected_on_the_host(gb):
+    srv = gb.Server(hbm_budget_bytes=8 << 20, n_streams=1, max_batch=4)
+    with pytest.raises(gb.GbError, match="OUT_OF_BUDGET"):
+        srv.submit(1024, 1024, 1024)   # 24 MiB of operands > 8 MiB
+    ok = srv.submit(64, 64, 64)
+    srv.drain(60)
+    assert srv.poll(ok)[0]
+    assert srv.stats()["rejected"] == 1
+    srv.close()
