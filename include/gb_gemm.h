@@ -211,6 +211,34 @@ gb_status gb_emulated_products(gb_queue* q, int slices, int64_t m, int64_t n, in
                                double alpha, double beta, double* C, int64_t ldc,
                                void* workspace, size_t workspace_bytes);
 
+/*
+ * The emulated GEMM without any allocation or workspace argument.  The paper
+ * has no counterpart: this entry point exists for callers that cannot allocate
+ * device memory when they need the product -- code inside a CUDA stream
+ * capture that forbids allocation, programs whose memory pool owns the whole
+ * device, or plug-ins handed only their input and output buffers.
+ *
+ * Same operation, arguments and result as gb_dgemm(prec = GB_PREC_EMULATED,
+ * slices) with C <- alpha A B + beta C, enqueued on `cuda_stream` (a
+ * cudaStream_t of the current device, or NULL).  Its scratch (digit planes and
+ * exponents) is a 64 MiB array in the library's device memory, reserved on every
+ * GPU that loads the library until the process exits; a GEMM whose
+ * gb_dgemm_workspace_size() exceeds 64 MiB is rejected with
+ * GB_ERR_UNSUPPORTED.  No cudaMalloc, cudaFree or other allocating call is made.
+ * The first call on a device looks up the scratch's device address (make that
+ * first call before any stream capture).  Every call uses the same scratch: two
+ * calls that can run at the same time on the GPU (different streams, no
+ * ordering between them) race and corrupt each other's result.  Device-side
+ * status (NaN/Inf input, a timed-out wait) is not reported: rows of A and
+ * columns of B with NaN/Inf give NaN outputs as in gb_dgemm.
+ * Errors: those of gb_dgemm's argument checks, GB_ERR_UNSUPPORTED,
+ * GB_ERR_NO_DEVICE, GB_ERR_CUDA.
+ */
+gb_status gb_dgemm_emulated_noalloc(void* cuda_stream, int slices, int64_t m, int64_t n,
+                                    int64_t k, double alpha, const double* A, int64_t lda,
+                                    const double* B, int64_t ldb, double beta, double* C,
+                                    int64_t ldc);
+
 #ifdef __cplusplus
 }
 #endif
