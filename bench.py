@@ -45,6 +45,13 @@ def parse():
     p.add_argument("--impl", default="ours", choices=["ours", "reference"])
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--cpu-seconds", type=float, default=12.0)
+    p.add_argument("--workload", default="dgemm", choices=["dgemm", "grouped", "serve"])
+    p.add_argument("--problems", type=int, default=2048)
+    p.add_argument("--serve-seconds", type=float, default=60.0)
+    p.add_argument("--serve-rate", type=float, default=2000.0)
+    p.add_argument("--serve-budget-gb", type=float, default=40.0)
+    p.add_argument("--serve-streams", type=int, default=4)
+    p.add_argument("--serve-batch", type=int, default=64)
     return p.parse_args()
 
 
@@ -174,10 +181,244 @@ def run_reference(args):
     return 0
 
 
+def _grouped_inputs(gb, torch, count, seed, precision, slices):
+    from synth import generators as g
+    ms, ns, ks = g.grouped_problems(seed, count)
+    probs = []
+    for i, (m, n, k) in enumerate(zip(ms, ns, ks)):
+        m, n, k = int(m), int(n), int(k)
+        A = torch.empty((m, k), dtype=torch.float64, device="cuda")
+        B = torch.empty((k, n), dtype=torch.float64, device="cuda")
+        C = torch.zeros((m, n), dtype=torch.float64, device="cuda")
+        gb.fill_uniform(A, seed + i, 0)
+        gb.fill_uniform(B, seed + i, 1)
+        probs.append(dict(A=A, B=B, C=C, alpha=1.0, beta=0.0, precision=precision,
+                          slices=slices))
+    torch.cuda.synchronize()
+    return probs, ms, ns, ks
+
+
+def _time_stream(torch, fn, steps, warmup):
+    stream = torch.cuda.current_stream()
+    for _ in range(warmup):
+        fn()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(steps):
+        fn()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    return e0.elapsed_time(e1) / steps
+
+
+def run_grouped(args):
+    """2048 independent GEMMs, m, n, k log-uniform in [16, 512]: one persistent
+    launch in a CUDA graph, native and emulated, against one launch per GEMM."""
+    import numpy as np
+    import torch
+
+    import paper_1602_08477_gb300 as gb
+    from paper_1602_08477_gb300 import autotune
+    from synth import generators as g
+    torch.cuda.set_device(0)
+    gb.build()
+    try:
+        autotune.load()
+        tuned = "shipped tuning table"
+    except Exception:
+        tuned = "size rule (no tuning table)"
+    seed = g.BASE_SEED + 3
+    s = 12
+    probs, ms, ns, ks = _grouped_inputs(gb, torch, args.problems, seed, "native", s)
+    flops = float(np.sum(2.0 * ms * ns * ks))
+    clocks = ClockSampler(0)
+    clocks.start()
+    time.sleep(0.3)
+    plan = gb.GroupedPlan(probs, use_graph=True)
+    native_ms = _time_stream(torch, plan.run, args.steps, args.warmup)
+    info = plan.info()
+    # one launch per GEMM, same kernels' default variants, uncaptured
+    q = gb.default_queue()
+
+    def per_gemm():
+        for p in probs:
+            gb.dgemm(p["A"], p["B"], p["C"], 1.0, 0.0, kernel="dmma", queue=q)
+    per_ms = _time_stream(torch, per_gemm, max(1, args.steps // 2), 1)
+    # one launch per GEMM, captured in a CUDA graph
+    cap_stream = torch.cuda.Stream()
+    cap_q = gb.Queue(gb.Device(0), cap_stream)
+    graph = torch.cuda.CUDAGraph()
+    torch.cuda.synchronize()
+    with torch.cuda.graph(graph, stream=cap_stream):
+        for p in probs:
+            gb.dgemm(p["A"], p["B"], p["C"], 1.0, 0.0, kernel="dmma", queue=cap_q)
+    per_graph_ms = _time_stream(torch, graph.replay, args.steps, 1)
+    # emulated group (same problems)
+    eprobs = [dict(p, precision="emulated", C=torch.zeros_like(p["C"])) for p in probs]
+    eplan = gb.GroupedPlan(eprobs, use_graph=True)
+    emu_ms = _time_stream(torch, eplan.run, args.steps, args.warmup)
+    einfo = eplan.info()
+    clk = clocks.stop()
+    pk, pk_kind = peaks()
+    fp64_peak = SMS * FP64_FLOP_PER_CLK_SM * SM_MAX_MHZ * 1e6 / 1e12
+    value = flops / (native_ms * 1e-3) / 1e12
+    emu_tf = flops / (emu_ms * 1e-3) / 1e12
+    pair_flops = s * (s + 1) / 2 * flops
+    out = {
+        "metric": "grouped FP64 GEMM TFLOP/s (one persistent launch in a CUDA graph)",
+        "value": round(value, 4), "unit": "TFLOP/s", "n_gpus": 1, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": round(native_ms, 4), "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic (device splitmix64, uniform[-1,1])",
+        "config": {"workload": f"{args.problems} independent GEMMs, m, n, k log-uniform in "
+                               "[16, 512], alpha = 1, beta = 0", "tiles": tuned,
+                   "flush": "none: operands (~1 GB) larger than L2"},
+        "gpu_launches": info["launches"] * args.steps,
+        "roofline": {"bound": "alu", "kernel": "grouped_native_kernel",
+                     "achieved": round(value, 4), "peak": round(fp64_peak, 4),
+                     "unit": "TFLOP/s", "frac": round(value / fp64_peak, 4),
+                     "peak_kind": "derived: 152 SM x 4 flop/clk x 2070 MHz",
+                     "algorithmic": f"sum 2mnk = {flops:.4g} flop per launch"},
+        "one_launch_per_gemm": {"ms": round(per_ms, 3), "tflops": round(flops / per_ms / 1e9, 4),
+                                "graph_ms": round(per_graph_ms, 3),
+                                "graph_tflops": round(flops / per_graph_ms / 1e9, 4),
+                                "launches": args.problems},
+        "emulated": {"slices": s, "ms": round(emu_ms, 3), "tflops_fp64_equiv": round(emu_tf, 3),
+                     "tensor_frac": round(pair_flops / (emu_ms * 1e-3) / 1e12 /
+                                          (2.0 * pk["bf16_tflops"]), 4),
+                     "launches": einfo["launches"]},
+        "tiles": {"native": info["native_tiles"], "emulated": einfo["emulated_tiles"]},
+        "e2e": None, "clocks": clk,
+    }
+    # end to end: operands from pinned host memory, results back
+    hostA = [p["A"].cpu().pin_memory() for p in probs]
+    hostB = [p["B"].cpu().pin_memory() for p in probs]
+    hostC = [torch.empty(p["C"].shape, dtype=torch.float64).pin_memory() for p in probs]
+    h2d = sum(a.numel() + b.numel() for a, b in zip(hostA, hostB)) * 8
+    d2h = sum(c.numel() for c in hostC) * 8
+
+    def e2e():
+        for p, a, b in zip(probs, hostA, hostB):
+            p["A"].copy_(a, non_blocking=True)
+            p["B"].copy_(b, non_blocking=True)
+        plan.run()
+        for p, c in zip(probs, hostC):
+            c.copy_(p["C"], non_blocking=True)
+    e2e_ms = _time_stream(torch, e2e, max(1, args.steps // 2), 1)
+    out["e2e"] = {"value": round(flops / e2e_ms / 1e9, 4), "unit": "TFLOP/s",
+                  "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h)}
+    plan.close()
+    eplan.close()
+    print(json.dumps(out), flush=True)
+    return 0
+
+
+def run_serve(args):
+    """Poisson arrivals of square GEMMs, n log-uniform in [64, 4096], 20% emulated,
+    HBM-budget admission, continuous batching; p50/p99 latency and TFLOP/s."""
+    import numpy as np
+    import torch
+
+    import paper_1602_08477_gb300 as gb
+    from paper_1602_08477_gb300 import autotune
+    from synth import generators as g
+    torch.cuda.set_device(0)
+    gb.build()
+    try:
+        autotune.load()
+    except Exception:
+        pass
+    seed = g.BASE_SEED + 4
+    count = int(args.serve_rate * args.serve_seconds * 1.2) + 16
+    gaps = g.poisson_gaps_ms(seed, count, args.serve_rate) * 1e-3
+    arrivals = np.cumsum(gaps)
+    sizes = g.log_uniform_ints(seed, 21, count, 64, 4096)
+    emulated = (g.raw_stream(seed, 22, count) % np.uint64(5)) == 0
+    s = 12
+    srv = gb.Server(int(args.serve_budget_gb * 2 ** 30), n_streams=args.serve_streams,
+                    max_batch=args.serve_batch)
+    # warm the kernels on a few small requests (not counted)
+    for i in range(4):
+        srv.submit(64, 64, 64, precision="emulated" if i % 2 else "native", slices=s, seed=i)
+    srv.drain(60)
+    srv.close()
+    srv = gb.Server(int(args.serve_budget_gb * 2 ** 30), n_streams=args.serve_streams,
+                    max_batch=args.serve_batch)
+    clocks = ClockSampler(0)
+    clocks.start()
+    t0 = time.perf_counter()
+    submitted, native_flops, emu_flops, offered = 0, 0.0, 0.0, 0.0
+    ids = []
+    for i in range(count):
+        t = arrivals[i]
+        if t > args.serve_seconds:
+            break
+        now = time.perf_counter() - t0
+        if t > now:
+            time.sleep(t - now)
+        n = int(sizes[i])
+        prec = "emulated" if emulated[i] else "native"
+        ids.append((srv.submit(n, n, n, 1.0, 0.0, prec, s, seed=seed * 1000003 + i), n, prec))
+        submitted += 1
+        offered += 2.0 * n ** 3
+    wall = time.perf_counter() - t0
+    st = srv.stats()
+    clk = clocks.stop()
+    done_native = done_emu = 0.0
+    for rid, n, prec in ids:
+        done, status, lat = srv.poll(rid)
+        if done and status == 0:
+            if prec == "native":
+                done_native += 2.0 * n ** 3
+            else:
+                done_emu += 2.0 * n ** 3
+    srv.close()
+    pk, _ = peaks()
+    fp64_peak = SMS * FP64_FLOP_PER_CLK_SM * SM_MAX_MHZ * 1e6
+    fp8_peak = 2.0 * pk["bf16_tflops"] * 1e12
+    # roofline time of the work completed: native flops on the FP64 pipe, emulated
+    # pair products on the FP8 tensor pipe
+    bound_s = done_native / fp64_peak + done_emu * s * (s + 1) / 2 / fp8_peak
+    busy = max(st["busy_s"], 1e-9)
+    out = {
+        "metric": "serving FP64 GEMM p50/p99 latency (ms) and TFLOP/s",
+        "value": round(st["tflops"], 4), "unit": "TFLOP/s", "n_gpus": 1,
+        "steps": int(submitted), "warmup": 4, "ms_per_step": round(st["mean_ms"], 3),
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic (device splitmix64 per request seed, uniform[-1,1])",
+        "config": {"workload": f"Poisson arrivals {args.serve_rate:g}/s for "
+                               f"{args.serve_seconds:g} s, square n log-uniform in [64, 4096], "
+                               f"20% emulated (s = {s}), {args.serve_budget_gb:g} GB budget",
+                   "streams": args.serve_streams, "max_batch": args.serve_batch},
+        "serve": {"p50_ms": round(st["p50_ms"], 3), "p99_ms": round(st["p99_ms"], 3),
+                  "max_ms": round(st["max_ms"], 3), "submitted": st["submitted"],
+                  "completed": st["completed"], "pending_at_end": st["pending"],
+                  "in_flight_at_end": st["in_flight"], "max_queue": st["max_queue"],
+                  "batches": st["batches"], "mean_batch": round(st["mean_batch"], 2),
+                  "peak_arena_gb": round(st["peak_bytes"] / 2 ** 30, 3),
+                  "offered_tflops": round(offered / max(wall, 1e-9) / 1e12, 3),
+                  "submit_wall_s": round(wall, 2)},
+        "roofline": {"bound": "mixed", "frac": round(bound_s / busy, 4),
+                     "note": "roofline time of the completed work (native on the FP64 pipe, "
+                             "emulated pair products on the FP8 tensor pipe) / busy time"},
+        "gpu_launches": int(st["batches"]) * 5,
+        "e2e": {"value": round(st["tflops"], 4), "unit": "TFLOP/s", "h2d_bytes_per_step": 0,
+                "d2h_bytes_per_step": 0, "note": "operands generated on the device per request"},
+        "clocks": clk,
+    }
+    print(json.dumps(out), flush=True)
+    return 0
+
+
 def main():
     args = parse()
     if args.impl == "reference":
         return run_reference(args)
+    if args.workload == "grouped":
+        return run_grouped(args)
+    if args.workload == "serve":
+        return run_serve(args)
 
     import numpy as np
     import torch

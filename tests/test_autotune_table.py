@@ -1,0 +1,26 @@
+"""The autotuner's table format: first-match lookup finds each problem's own cell."""
+import itertools
+import json
+
+from paper_1602_08477_gb300 import autotune
+
+
+def test_first_match_is_the_problems_own_cell():
+    T = autotune.THRESHOLDS
+    entries = [(m, n, k, "64x64") for m in T for n in T for k in T]
+    for m, n, k in itertools.product([1, 17, 32, 33, 64, 100, 128, 129, 300, 512], repeat=3):
+        first = next(e for e in entries if m <= e[0] and n <= e[1] and k <= e[2])
+        assert first[:3] == (autotune.cell_of(m), autotune.cell_of(n), autotune.cell_of(k))
+
+
+def test_shipped_table_covers_every_cell(tmp_path):
+    entries = autotune.load(apply=False)
+    cells = {e[:3] for e in entries}
+    T = autotune.THRESHOLDS
+    assert cells == {(m, n, k) for m in T for n in T for k in T}
+    assert all(e[3] in autotune.CANDIDATES for e in entries)
+    # save/load round trip
+    p = tmp_path / "t.json"
+    autotune.save(entries, str(p))
+    assert autotune.load(str(p), apply=False) == entries
+    assert json.load(open(p))["thresholds"] == list(T)
