@@ -119,6 +119,23 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
+def max_over_ranks(x: float, world: int, device: str = "cuda") -> float:
+    """Largest value of x over all ranks (the slowest replica's time)."""
+    if world == 1:
+        return float(x)
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def replica_value(units_per_rank: float, world: int, slowest_ms: float) -> float:
+    """Whole-job throughput of independent replicas (weak scaling): the units all
+    ranks processed divided by the slowest rank's time."""
+    return world * units_per_rank / (slowest_ms * 1e-3)
+
+
 def cpu_baseline(n, seed, seconds, A=None, B=None):
     """The CPU oracle (plain C, OpenMP over rows) on a bounded sample of rows of
     the same GEMM; returns the baseline record and the computed rows."""
@@ -442,12 +459,8 @@ def main():
         if world > 1:
             dist.barrier()
 
-    def max_over_ranks(x):
-        if world == 1:
-            return x
-        t = torch.tensor([x], dtype=torch.float64, device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        return float(t.item())
+    def slowest(x):
+        return max_over_ranks(x, world)
 
     n, s = args.n, args.slices
     seed = g.BASE_SEED + 1
@@ -487,7 +500,7 @@ def main():
     t1.record(stream)
     torch.cuda.synchronize()
     barrier()
-    ms_total = max_over_ranks(t0.elapsed_time(t1))
+    ms_total = slowest(t0.elapsed_time(t1))
     prod_ms = statistics.mean(a.elapsed_time(b) for a, b in evs)
     q.wait()
     emu_C = C.clone()
@@ -503,7 +516,7 @@ def main():
         gb.dgemm(A, B, Cn, 1.0, 0.0, kernel="dmma", queue=q)
     n1.record(stream)
     torch.cuda.synchronize()
-    native_ms = max_over_ranks(n0.elapsed_time(n1)) / args.native_steps
+    native_ms = slowest(n0.elapsed_time(n1)) / args.native_steps
     clk = clocks.stop()
 
     # end to end through the public API with pinned host buffers
@@ -528,11 +541,11 @@ def main():
         e2e_step()
     e1.record(stream)
     torch.cuda.synchronize()
-    e2e_ms = max_over_ranks(e0.elapsed_time(e1)) / e2e_steps
+    e2e_ms = slowest(e0.elapsed_time(e1)) / e2e_steps
     q.wait()
 
     ms_step = ms_total / args.steps
-    value = world * flops / (ms_step * 1e-3) / 1e12
+    value = replica_value(flops, world, ms_step) / 1e12
     pk, pk_kind = peaks()
     fp8_peak = 2.0 * pk["bf16_tflops"]
     achieved = pair_flops / (prod_ms * 1e-3) / 1e12
@@ -564,7 +577,7 @@ def main():
                                 "peak": round(fp64_peak, 4), "unit": "TFLOP/s",
                                 "frac": round(native_tflops / fp64_peak, 4),
                                 "peak_kind": "derived: 152 SM x 4 flop/clk x 2070 MHz"}},
-        "e2e": {"value": round(world * flops / (e2e_ms * 1e-3) / 1e12, 3), "unit": "TFLOP/s",
+        "e2e": {"value": round(replica_value(flops, world, e2e_ms) / 1e12, 3), "unit": "TFLOP/s",
                 "h2d_bytes_per_step": 2 * 8 * n * n, "d2h_bytes_per_step": 8 * n * n},
         "clocks": clk,
     }

@@ -24,7 +24,8 @@
 //                   products of a stage (M = 128, K = 32, N up to 256; all pairs
 //                   sharing an A slice go into one MMA) and commits each stage
 //                   back to the producer.
-//   warps 2 - 5   : epilogue; warp w reads TMEM lanes 32 (w % 4) .. + 31.
+//   warps 2 - 17  : epilogue; warp w reads TMEM lanes 32 (w % 4) .. + 31 and
+//                   the 8 columns of group (w - 2) / 4 of every level.
 // Every wait on an mbarrier is bounded (wall-clock); on a timeout the CTA records
 // the timeout bit in the status word, skips its output and still frees TMEM.
 #include <cuda_runtime.h>
@@ -42,7 +43,8 @@ namespace {
 constexpr int kBM = kEmuBM;
 constexpr int kBN = kEmuGroupBN;
 constexpr int kBKBytes = 32;
-constexpr int kThreads = 192;
+constexpr int kEpiWarps = 16;    // 4 TMEM lane quarters x 4 column groups of 8
+constexpr int kThreads = 32 * (2 + kEpiWarps);
 constexpr uint32_t kTmemCols = 512;
 constexpr uint64_t kWaitTimeoutNs = 4000000000ull;  // 4 s
 constexpr int kSmemLimit = 227 * 1024;
@@ -70,7 +72,7 @@ struct I128 {
 };
 
 __device__ __forceinline__ void i128_horner(I128& x, int sh, int64_t v) {
-    // x = x * 2^sh + v
+    // x = x * 2^sh + v   (1 <= sh <= 63)
     x.hi = (int64_t)(((uint64_t)x.hi << sh) | (x.lo >> (64 - sh)));
     x.lo <<= sh;
     const uint64_t vlo = (uint64_t)v;
@@ -235,7 +237,11 @@ __device__ __forceinline__ void products_tile(const TileArgs& a, uint8_t* smem, 
         ptx::mma_commit(tmem_full);
     } else if (warp >= 2) {
         // ---- epilogue ----
+        // T = sum_g S_g 2^(5 (s+1-g)) exactly: Horner in int64 over groups of at
+        // most 6 levels (each group stays below 2^53 for k * pairs * 256 < 2^28),
+        // folded into a 128-bit integer at group ends; one rounding to FP64.
         const int quarter = warp & 3;
+        const int cgroup = (warp - 2) >> 2;
         const int64_t row = a.row0 + quarter * 32 + lane;
         const bool ok = ptx::mbar_wait_bounded(tmem_full, 0, abort, status, kStatusTimeout,
                                                kWaitTimeoutNs);
@@ -245,42 +251,52 @@ __device__ __forceinline__ void products_tile(const TileArgs& a, uint8_t* smem, 
             const bool bad_row = ei == GB_BAD_LINE_DEV;
             const int Ebase = -8 - 5 * (s - 1);
             const bool plain = (a.alpha == 1.0 && a.beta == 0.0);
-            const uint32_t lane_addr = tmem_base + ((uint32_t)(quarter * 32) << 16);
-#pragma unroll 1
-            for (int cb = 0; cb < BN; cb += 32) {
-                I128 T[32];
+            const uint32_t col_addr = tmem_base + ((uint32_t)(quarter * 32) << 16) + cgroup * 8;
+            I128 T[8];
+            int64_t G[8];
 #pragma unroll
-                for (int j = 0; j < 32; ++j) T[j] = I128{0, 0};
+            for (int j = 0; j < 8; ++j) {
+                T[j] = I128{0, 0};
+                G[j] = 0;
+            }
+            int in_group = 0;
 #pragma unroll 1
-                for (int g = 2; g <= s + 1; ++g) {
-                    uint32_t v[32];
-                    ptx::tmem_ld_32x32b_x32(lane_addr + (uint32_t)(g - 2) * BN + cb, v);
-                    ptx::tmem_ld_wait();
+            for (int g = 2; g <= s + 1; ++g) {
+                uint32_t v[8];
+                ptx::tmem_ld_32x32b_x8(col_addr + (uint32_t)(g - 2) * BN, v);
+                ptx::tmem_ld_wait();
 #pragma unroll
-                    for (int j = 0; j < 32; ++j) i128_horner(T[j], 5, f32_int_value(v[j]));
+                for (int j = 0; j < 8; ++j) G[j] = G[j] * 32 + f32_int_value(v[j]);
+                ++in_group;
+                if (in_group == 6 || g == s + 1) {
+#pragma unroll
+                    for (int j = 0; j < 8; ++j) {
+                        i128_horner(T[j], 5 * in_group, G[j]);
+                        G[j] = 0;
+                    }
+                    in_group = 0;
                 }
-                if (row < a.m) {
-                    double* crow = a.C + row * a.ldc;
+            }
+            if (row < a.m) {
+                double* crow = a.C + row * a.ldc;
 #pragma unroll
-                    for (int j = 0; j < 32; ++j) {
-                        const int64_t col = a.col0 + cb + j;
-                        if (col < a.n) {
-                            const int32_t fj = a.fB[col];
-                            double out;
-                            if (bad_row || fj == GB_BAD_LINE_DEV) {
-                                out = __longlong_as_double(0x7FF8000000000000ll);
+                for (int j = 0; j < 8; ++j) {
+                    const int64_t col = a.col0 + cgroup * 8 + j;
+                    if (col < a.n) {
+                        const int32_t fj = a.fB[col];
+                        double out;
+                        if (bad_row || fj == GB_BAD_LINE_DEV) {
+                            out = __longlong_as_double(0x7FF8000000000000ll);
+                        } else {
+                            const double t = i128_to_double_scaled(T[j], ei + fj + Ebase);
+                            if (plain) {
+                                out = t;
                             } else {
-                                const double t = i128_to_double_scaled(T[j], ei + fj + Ebase);
-                                if (plain) {
-                                    out = t;
-                                } else {
-                                    out = __dmul_rn(a.alpha, t);
-                                    if (a.beta != 0.0)
-                                        out = __dadd_rn(out, __dmul_rn(a.beta, crow[col]));
-                                }
+                                out = __dmul_rn(a.alpha, t);
+                                if (a.beta != 0.0) out = __dadd_rn(out, __dmul_rn(a.beta, crow[col]));
                             }
-                            crow[col] = out;
                         }
+                        crow[col] = out;
                     }
                 }
             }
