@@ -161,16 +161,64 @@ struct TileArgs {
 // One 128 x BN output tile: level sums on the tensor cores, recombination into
 // C.  All 192 threads call it; `smem` is 1024-byte aligned and holds `stages`
 // ring slots of `slot_bytes` plus a SmemTail.
-template <int BN>
+// The MMAs of one K block (32 bytes) of all slice pairs, with compile-time slice
+// count S: for a fixed A slice p the pairs (p, q), q = 1 .. S+1-p, land in the
+// consecutive levels p-1 .. S-1, whose accumulators are consecutive TMEM column
+// blocks, and the B slices q are consecutive in shared memory.  So one MMA with
+// N = 32 (S+1-p) (split at the 256-column limit) covers them all, reading the A
+// tile once.  Fully unrolled: descriptor offsets are immediates, so the single
+// issuing thread spends a few instructions per MMA.
+template <int S>
+__device__ __forceinline__ void issue_kblock(uint64_t adesc, uint64_t bdesc, uint32_t tmem_base,
+                                             bool first) {
+#pragma unroll
+    for (int p = 1; p <= S; ++p) {
+        const uint64_t ad = adesc + (uint64_t)(((p - 1) * kBM * kBKBytes) >> 4);
+        const uint32_t acc = (first && p == 1) ? 0u : 1u;
+        constexpr int kUnused = 0;
+        (void)kUnused;
+        const int rows = kBN * (S + 1 - p);
+#pragma unroll
+        for (int r0 = 0; r0 < kBN * S; r0 += 256) {
+            if (r0 < rows) {
+                const int nn = rows - r0 < 256 ? rows - r0 : 256;
+                const uint64_t bd = bdesc + (uint64_t)((r0 * kBKBytes) >> 4);
+                ptx::mma_e4m3(tmem_base + (uint32_t)((p - 1) * kBN + r0), ad, bd,
+                              ptx::idesc_e4m3_f32(kBM, nn), acc);
+            }
+        }
+    }
+}
+
+// K blocks per pipeline stage for S slices: as many as keep two stages in 227 KB
+// (at most 4), so the per-stage wait / fence / commit of the issuing thread is
+// shared by KB K blocks.
+__host__ __device__ constexpr int kblocks_per_stage(int S) {
+    return ((kSmemLimit - 2048) / (2 * S * (kBM + kBN) * kBKBytes)) < 1
+               ? 1
+               : ((kSmemLimit - 2048) / (2 * S * (kBM + kBN) * kBKBytes)) > 4
+                     ? 4
+                     : ((kSmemLimit - 2048) / (2 * S * (kBM + kBN) * kBKBytes));
+}
+
+// One 128 x 32 output tile: level sums on the tensor cores, recombination into
+// C.  All threads call it; `smem` is 1024-byte aligned and holds `stages` ring
+// slots of `slot_bytes` (>= KB * S * 5 KiB) plus a SmemTail.  A stage holds KB
+// consecutive K blocks: their A tiles (KB * S * 4 KiB, contiguous in the
+// workspace) then their B tiles (KB * S * 1 KiB).
+template <int S, int KB>
 __device__ __forceinline__ void products_tile(const TileArgs& a, uint8_t* smem, int stages,
                                               uint32_t slot_bytes, unsigned* status) {
+    constexpr int BN = kBN;
     SmemTail* tail = reinterpret_cast<SmemTail*>(smem + (size_t)stages * slot_bytes);
     uint64_t* full = tail->bars;
     uint64_t* empty = tail->bars + stages;
     uint64_t* tmem_full = tail->bars + 2 * stages;
     volatile int* abort = &tail->abort;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int s = a.s, nkb = a.nkb;
+    constexpr int s = S;
+    const int nkb = a.nkb;
+    const int nst = (nkb + KB - 1) / KB;  // stages of K blocks
 
     if (threadIdx.x == 0) {
         for (int i = 0; i < stages; ++i) {
@@ -189,48 +237,44 @@ __device__ __forceinline__ void products_tile(const TileArgs& a, uint8_t* smem, 
     __syncthreads();
     ptx::tc_fence_after();
     const uint32_t tmem_base = tail->tmem_holder;
-    const uint32_t a_bytes = (uint32_t)s * kBM * kBKBytes;
-    const uint32_t b_bytes = (uint32_t)s * BN * kBKBytes;
+    constexpr uint32_t a_bytes = (uint32_t)S * kBM * kBKBytes;  // one K block
+    constexpr uint32_t b_bytes = (uint32_t)S * BN * kBKBytes;
 
     if (warp == 0 && lane == 0) {
         // ---- producer: two contiguous bulk copies per stage ----
-        for (int kb = 0; kb < nkb; ++kb) {
-            const int st = kb % stages;
-            const uint32_t ph = (uint32_t)(kb / stages) & 1u;
+        for (int it = 0; it < nst; ++it) {
+            const int st = it % stages;
+            const uint32_t ph = (uint32_t)(it / stages) & 1u;
             if (!ptx::mbar_wait_bounded(&empty[st], ph ^ 1u, abort, status, kStatusTimeout,
                                         kWaitTimeoutNs))
                 break;
+            const int kb0 = it * KB;
+            const int kc = nkb - kb0 < KB ? nkb - kb0 : KB;
             uint8_t* sa = smem + (size_t)st * slot_bytes;
-            ptx::mbar_arrive_expect_tx(&full[st], a_bytes + b_bytes);
-            ptx::bulk_load(sa, a.a_src + (size_t)kb * a_bytes, a_bytes, &full[st]);
-            ptx::bulk_load(sa + a_bytes, a.b_src + (size_t)kb * b_bytes, b_bytes, &full[st]);
+            ptx::mbar_arrive_expect_tx(&full[st], (uint32_t)kc * (a_bytes + b_bytes));
+            ptx::bulk_load(sa, a.a_src + (size_t)kb0 * a_bytes, (uint32_t)kc * a_bytes, &full[st]);
+            ptx::bulk_load(sa + KB * a_bytes, a.b_src + (size_t)kb0 * b_bytes,
+                           (uint32_t)kc * b_bytes, &full[st]);
         }
     } else if (warp == 1 && lane == 0) {
         // ---- MMA issuer ----
-        // For a fixed A slice p the pairs (p, q), q = 1 .. s+1-p, land in the
-        // consecutive levels p-1 .. s-1, whose accumulators are consecutive TMEM
-        // column blocks, and the B slices q are consecutive in shared memory.  So
-        // one MMA with N = BN (s+1-p) (split at the 256-column limit) covers them
-        // all, reading the A tile once instead of once per pair.
-        for (int kb = 0; kb < nkb; ++kb) {
-            const int st = kb % stages;
-            const uint32_t ph = (uint32_t)(kb / stages) & 1u;
+        for (int it = 0; it < nst; ++it) {
+            const int st = it % stages;
+            const uint32_t ph = (uint32_t)(it / stages) & 1u;
             if (!ptx::mbar_wait_bounded(&full[st], ph, abort, status, kStatusTimeout,
                                         kWaitTimeoutNs))
                 break;
             ptx::tc_fence_after();
             const uint32_t a0 = ptx::smem_u32(smem + (size_t)st * slot_bytes);
-            const uint32_t b0 = a0 + a_bytes;
-            for (int p = 1; p <= s; ++p) {
-                const uint64_t ad = ptx::umma_desc_sw32(a0 + (uint32_t)(p - 1) * kBM * kBKBytes);
-                const uint32_t acc = (kb > 0 || p > 1) ? 1u : 0u;
-                const int rows = BN * (s + 1 - p);
-                for (int r0 = 0; r0 < rows; r0 += 256) {
-                    const int nn = min(256, rows - r0);
-                    const uint64_t bd = ptx::umma_desc_sw32(b0 + (uint32_t)r0 * kBKBytes);
-                    ptx::mma_e4m3(tmem_base + (uint32_t)((p - 1) * BN + r0), ad, bd,
-                                  ptx::idesc_e4m3_f32(kBM, nn), acc);
-                }
+            const uint64_t adesc = ptx::umma_desc_sw32(a0);
+            const uint64_t bdesc = ptx::umma_desc_sw32(a0 + KB * a_bytes);
+            const int kc = nkb - it * KB < KB ? nkb - it * KB : KB;
+#pragma unroll
+            for (int kk = 0; kk < KB; ++kk) {
+                if (kk < kc)
+                    issue_kblock<S>(adesc + (uint64_t)((kk * a_bytes) >> 4),
+                                    bdesc + (uint64_t)((kk * b_bytes) >> 4), tmem_base,
+                                    it == 0 && kk == 0);
             }
             ptx::mma_commit(&empty[st]);
         }
@@ -321,8 +365,9 @@ __device__ __forceinline__ uint8_t* aligned_smem(uint8_t* raw) {
     return reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(raw) + 1023) & ~(uintptr_t)1023);
 }
 
+template <int S>
 __global__ void __launch_bounds__(kThreads, 1)
-    emu_products_kernel(const uint8_t* __restrict__ ad, const uint8_t* __restrict__ bd, int s,
+    emu_products_kernel(const uint8_t* __restrict__ ad, const uint8_t* __restrict__ bd,
                         int64_t m, int64_t n, int nkb, double alpha, double beta,
                         double* __restrict__ C, int64_t ldc, const int32_t* __restrict__ eA,
                         const int32_t* __restrict__ fB, int tiles_m, int tiles_n, int stages,
@@ -337,9 +382,9 @@ __global__ void __launch_bounds__(kThreads, 1)
     const int tm = first_m + (bid % group_size) % gm;
     const int tn = (bid % group_size) / gm;
     TileArgs a;
-    a.a_src = ad + (size_t)tm * nkb * s * kBM * kBKBytes;
-    a.b_src = bd + (size_t)tn * nkb * s * kBN * kBKBytes;
-    a.s = s;
+    a.a_src = ad + (size_t)tm * nkb * S * kBM * kBKBytes;
+    a.b_src = bd + (size_t)tn * nkb * S * kBN * kBKBytes;
+    a.s = S;
     a.nkb = nkb;
     a.m = m;
     a.n = n;
@@ -351,10 +396,11 @@ __global__ void __launch_bounds__(kThreads, 1)
     a.C = C;
     a.eA = eA;
     a.fB = fB;
-    products_tile<kBN>(a, smem, stages, slot_bytes, status);
+    products_tile<S, kblocks_per_stage(S)>(a, smem, stages, slot_bytes, status);
 }
 
-// Grouped: one CTA per output tile of any problem of the table.
+// Grouped: one CTA per output tile of any problem of the table (one K block per
+// stage; the problem's slice count selects the unrolled variant).
 __global__ void __launch_bounds__(kThreads, 1)
     grouped_products_kernel(const EmuProb* __restrict__ P, int np, int stages,
                             uint32_t slot_bytes, unsigned* status) {
@@ -385,7 +431,15 @@ __global__ void __launch_bounds__(kThreads, 1)
     a.C = q.C;
     a.eA = q.a_exp;
     a.fB = q.b_exp;
-    products_tile<kBN>(a, smem, stages, slot_bytes, status);
+    switch (q.s) {
+#define GB_CASE(SS) \
+    case SS: products_tile<SS, 1>(a, smem, stages, slot_bytes, status); break;
+        GB_CASE(1) GB_CASE(2) GB_CASE(3) GB_CASE(4) GB_CASE(5) GB_CASE(6) GB_CASE(7) GB_CASE(8)
+        GB_CASE(9) GB_CASE(10) GB_CASE(11) GB_CASE(12) GB_CASE(13) GB_CASE(14) GB_CASE(15)
+        GB_CASE(16)
+#undef GB_CASE
+        default: break;
+    }
 }
 
 struct RingShape {
@@ -394,9 +448,9 @@ struct RingShape {
     size_t smem;
 };
 
-RingShape ring_for(int max_s) {
+RingShape ring_for(int max_s, int kb_per_stage) {
     RingShape r{};
-    r.slot_bytes = (uint32_t)max_s * (kBM + kBN) * kBKBytes;
+    r.slot_bytes = (uint32_t)kb_per_stage * max_s * (kBM + kBN) * kBKBytes;
     const int fixed = 1024 + (int)sizeof(SmemTail) + 64;
     r.stages = (kSmemLimit - fixed) / (int)r.slot_bytes;
     if (r.stages > 8) r.stages = 8;
@@ -409,6 +463,22 @@ cudaError_t allow_smem(K kernel) {
     return cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemLimit);
 }
 
+template <int S>
+cudaError_t launch_products_s(const Launch& L, int64_t m, int64_t n, int64_t kp, double alpha,
+                              double beta, double* C, int64_t ldc, const uint8_t* ad,
+                              const uint8_t* bd, const int32_t* ea, const int32_t* fb) {
+    const RingShape r = ring_for(S, kblocks_per_stage(S));
+    if (r.stages < 2) return cudaErrorInvalidValue;
+    cudaError_t e = allow_smem(emu_products_kernel<S>);
+    if (e != cudaSuccess) return e;
+    const int tiles_m = (int)((m + kBM - 1) / kBM), tiles_n = (int)((n + kBN - 1) / kBN);
+    const int nkb = (int)(kp / kBKBytes);
+    emu_products_kernel<S><<<tiles_m * tiles_n, kThreads, r.smem, L.stream>>>(
+        ad, bd, m, n, nkb, alpha, beta, C, ldc, ea, fb, tiles_m, tiles_n, r.stages,
+        r.slot_bytes, L.status);
+    return cudaGetLastError();
+}
+
 }  // namespace
 
 cudaError_t launch_emu_products(const Launch& L, int s, int64_t m, int64_t n, int64_t k,
@@ -417,22 +487,23 @@ cudaError_t launch_emu_products(const Launch& L, int s, int64_t m, int64_t n, in
                                 const int32_t* a_exp, const int32_t* b_exp) {
     (void)k;
     if (m == 0 || n == 0) return cudaSuccess;
-    const RingShape r = ring_for(s);
-    if (r.stages < 2) return cudaErrorInvalidValue;
-    cudaError_t e = allow_smem(emu_products_kernel);
-    if (e != cudaSuccess) return e;
-    const int tiles_m = (int)((m + kBM - 1) / kBM), tiles_n = (int)((n + kBN - 1) / kBN);
-    const int nkb = (int)(kp / kBKBytes);
-    emu_products_kernel<<<tiles_m * tiles_n, kThreads, r.smem, L.stream>>>(
-        a_digits, b_digits, s, m, n, nkb, alpha, beta, C, ldc, a_exp, b_exp, tiles_m, tiles_n,
-        r.stages, r.slot_bytes, L.status);
-    return cudaGetLastError();
+    switch (s) {
+#define GB_CASE(SS)                                                                          \
+    case SS:                                                                                 \
+        return launch_products_s<SS>(L, m, n, kp, alpha, beta, C, ldc, a_digits, b_digits, \
+                                     a_exp, b_exp);
+        GB_CASE(1) GB_CASE(2) GB_CASE(3) GB_CASE(4) GB_CASE(5) GB_CASE(6) GB_CASE(7) GB_CASE(8)
+        GB_CASE(9) GB_CASE(10) GB_CASE(11) GB_CASE(12) GB_CASE(13) GB_CASE(14) GB_CASE(15)
+        GB_CASE(16)
+#undef GB_CASE
+        default: return cudaErrorInvalidValue;
+    }
 }
 
 cudaError_t launch_grouped_products(const Launch& L, const EmuProb* probs, int np,
                                     int64_t total_tiles, int max_s) {
     if (np == 0 || total_tiles == 0) return cudaSuccess;
-    const RingShape r = ring_for(max_s);
+    const RingShape r = ring_for(max_s, 1);
     if (r.stages < 2) return cudaErrorInvalidValue;
     cudaError_t e = allow_smem(grouped_products_kernel);
     if (e != cudaSuccess) return e;
