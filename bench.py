@@ -30,8 +30,13 @@ L2_BYTES = 129 * 1024 * 1024
 SMS = 152
 SM_MAX_MHZ = 2070.0
 # FP64 pipe of the GB300 SM: 2 FP64 FMA / clock / SM (4 flop), derived from the
-# chip's unit counts and clocks and confirmed by a DFMA/DMMA throughput probe.
+# chip's unit counts and clocks; the DFMA kernels reach 99% of it.
 FP64_FLOP_PER_CLK_SM = 4.0
+
+# DRAM bytes (read + write) per launch of the dominant kernel, from one ncu
+# capture of the kernel as it is now (profiles/emu_products_kernel_n8192_s10.md):
+# (kernel, n, slices) -> bytes.  Reported only for that exact workload.
+MEASURED_TRAFFIC = {("emu_products_kernel", 8192, 10): 15211482112 + 542167808}
 
 
 def parse():
@@ -40,12 +45,14 @@ def parse():
     p.add_argument("--steps", type=int, default=10)
     p.add_argument("--warmup", type=int, default=3)
     p.add_argument("--n", type=int, default=8192)
-    p.add_argument("--slices", type=int, default=11)
+    p.add_argument("--slices", type=int, default=10)
     p.add_argument("--native-steps", type=int, default=2)
     p.add_argument("--impl", default="ours", choices=["ours", "reference"])
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--cpu-seconds", type=float, default=12.0)
-    p.add_argument("--workload", default="dgemm", choices=["dgemm", "grouped", "serve"])
+    p.add_argument("--workload", default="dgemm",
+                   choices=["dgemm", "grouped", "serve", "sweep", "d0", "daxpy"])
+    p.add_argument("--sizes", default="1024,2048,4096,8192,10240")
     p.add_argument("--problems", type=int, default=2048)
     p.add_argument("--serve-seconds", type=float, default=60.0)
     p.add_argument("--serve-rate", type=float, default=2000.0)
@@ -260,7 +267,7 @@ def run_grouped(args):
 
     def per_gemm():
         for p in probs:
-            gb.dgemm(p["A"], p["B"], p["C"], 1.0, 0.0, kernel="dmma", queue=q)
+            gb.dgemm(p["A"], p["B"], p["C"], 1.0, 0.0, kernel="auto", queue=q)
     per_ms = _time_stream(torch, per_gemm, max(1, args.steps // 2), 1)
     # one launch per GEMM, captured in a CUDA graph
     cap_stream = torch.cuda.Stream()
@@ -269,7 +276,7 @@ def run_grouped(args):
     torch.cuda.synchronize()
     with torch.cuda.graph(graph, stream=cap_stream):
         for p in probs:
-            gb.dgemm(p["A"], p["B"], p["C"], 1.0, 0.0, kernel="dmma", queue=cap_q)
+            gb.dgemm(p["A"], p["B"], p["C"], 1.0, 0.0, kernel="auto", queue=cap_q)
     per_graph_ms = _time_stream(torch, graph.replay, args.steps, 1)
     # emulated group (same problems)
     eprobs = [dict(p, precision="emulated", C=torch.zeros_like(p["C"])) for p in probs]
@@ -428,6 +435,137 @@ def run_serve(args):
     return 0
 
 
+def run_sweep(args):
+    """Native square DGEMM sweep n in {1024, ..., 10240}: naive vs tiled vs DFMA vs
+    DMMA kernels, TFLOP/s and fraction of the FP64 peak."""
+    import torch
+
+    import paper_1602_08477_gb300 as gb
+    torch.cuda.set_device(0)
+    gb.build()
+    fp64_peak = SMS * FP64_FLOP_PER_CLK_SM * SM_MAX_MHZ * 1e6 / 1e12
+    res = []
+    for n in (int(x) for x in args.sizes.split(",")):
+        A = torch.empty((n, n), dtype=torch.float64, device="cuda")
+        B = torch.empty((n, n), dtype=torch.float64, device="cuda")
+        C = torch.empty((n, n), dtype=torch.float64, device="cuda")
+        gb.fill_uniform(A, 1602084771, 0)
+        gb.fill_uniform(B, 1602084771, 1)
+        for kernel in ("naive", "tiled", "dfma", "dmma"):
+            f = lambda: gb.dgemm(A, B, C, kernel=kernel)
+            ms = _time_stream(torch, f, 1 if n >= 4096 else 3, 1)
+            tf = 2.0 * n ** 3 / ms / 1e9
+            res.append(dict(n=n, kernel=kernel, ms=round(ms, 3), tflops=round(tf, 4),
+                            frac_fp64_peak=round(tf / fp64_peak, 4)))
+        del A, B, C
+        torch.cuda.empty_cache()
+    print(json.dumps({"metric": "native FP64 DGEMM TFLOP/s per kernel", "unit": "TFLOP/s",
+                      "peak": round(fp64_peak, 4), "sweep": res}), flush=True)
+    return 0
+
+
+def run_d0(args):
+    """C = 1.5 A B + 0.5 C at n = 256 (uniform[-1, 1]): device microseconds and
+    TFLOP/s per call for each kernel, and the host cost of one C-ABI call
+    (validation + launch, through the Python binding) next to the host cost of
+    one minimal torch kernel launch, the zero-overhead comparison of the paper
+    transposed to this library."""
+    import numpy as np
+    import torch
+
+    import paper_1602_08477_gb300 as gb
+    from synth import generators as g
+    torch.cuda.set_device(0)
+    gb.build()
+    n = 256
+    seed = g.BASE_SEED
+    A = torch.from_numpy(g.matrix("uniform", n, n, seed, g.STREAM_A)).cuda()
+    B = torch.from_numpy(g.matrix("uniform", n, n, seed, g.STREAM_B)).cuda()
+    C0 = torch.from_numpy(g.matrix("uniform", n, n, seed, g.STREAM_C)).cuda()
+    C = C0.clone()
+    q = gb.default_queue()
+    fp64_peak = SMS * FP64_FLOP_PER_CLK_SM * SM_MAX_MHZ * 1e6 / 1e12
+    flops = 2.0 * n ** 3
+    calls = 200
+    res = {}
+    for kernel in ("naive", "tiled", "dfma", "dmma", "emulated"):
+        if kernel == "emulated":
+            ws = gb.alloc_workspace(gb.workspace_size("emulated", 11, n, n, n))
+            f = lambda: gb.dgemm(A, B, C, 1.5, 0.5, precision="emulated", slices=11, queue=q,
+                                 workspace=ws)
+        else:
+            f = (lambda kk: (lambda: gb.dgemm(A, B, C, 1.5, 0.5, kernel=kk, queue=q)))(kernel)
+        ms = _time_stream(torch, f, calls, 10)
+        res[kernel] = {"us_per_call": round(ms * 1e3, 2),
+                       "tflops": round(flops / ms / 1e9, 4),
+                       "frac_fp64_peak": round(flops / ms / 1e9 / fp64_peak, 4)}
+    # host cost per call: issue many calls without synchronising in between
+    def host_us(fn, reps=2000):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for _ in range(reps):
+            fn()
+        t1 = time.perf_counter()
+        torch.cuda.synchronize()
+        return (t1 - t0) / reps * 1e6
+    small = torch.zeros(1, dtype=torch.float64, device="cuda")
+    lib = gb.load()
+    import ctypes
+    args = (q.handle, None, 0, 0, 0, n, n, n, 1.5, ctypes.c_void_p(A.data_ptr()), n,
+            ctypes.c_void_p(B.data_ptr()), n, 0.5, ctypes.c_void_p(C.data_ptr()), n, None, 0)
+    out = {
+        "metric": "DGEMM C = 1.5 A B + 0.5 C at n = 256: device us per call, TFLOP/s",
+        "unit": "us", "n_gpus": 1, "higher_is_better": False, "dtype": "f64",
+        "data": "synthetic (seeded splitmix64, uniform[-1,1])",
+        "config": {"workload": "square DGEMM n = 256, alpha = 1.5, beta = 0.5"},
+        "kernels": res,
+        "host_us_per_call": {
+            "gb_dgemm_c_abi_via_ctypes": round(host_us(lambda: lib.gb_dgemm(*args)), 3),
+            "gb_dgemm_python_binding": round(host_us(lambda: gb.dgemm(A, B, C, 1.5, 0.5,
+                                                                        kernel="auto", queue=q)), 3),
+            "torch_minimal_kernel_launch": round(host_us(lambda: small.add_(0.0)), 3),
+        },
+    }
+    print(json.dumps(out), flush=True)
+    return 0
+
+
+def run_daxpy(args):
+    """DAXPY y <- alpha x + y (Section 4.1) over 2^28 doubles per vector (2 GiB,
+    far larger than L2): HBM GB/s against the measured copy bandwidth, for the
+    library's work division and explicit ones."""
+    import torch
+
+    import paper_1602_08477_gb300 as gb
+    torch.cuda.set_device(0)
+    gb.build()
+    n = 1 << 28
+    x = torch.empty(n, dtype=torch.float64, device="cuda")
+    y = torch.empty(n, dtype=torch.float64, device="cuda")
+    gb.fill_uniform(x.view(1 << 14, 1 << 14), 1602084777, 0)
+    gb.fill_uniform(y.view(1 << 14, 1 << 14), 1602084777, 1)
+    pk, pk_kind = peaks()
+    res = {}
+    for name, (B, V) in {"default": (256, 4), "B128_V8": (128, 8), "B512_V2": (512, 2),
+                         "B1024_V1": (1024, 1)}.items():
+        wd = gb.Workdiv.make([-(-n // (B * V))], [B], [V])
+        ms = _time_stream(torch, lambda: gb.daxpy(1.0000001, x, y, workdiv=wd), args.steps,
+                          args.warmup)
+        gbs = 24.0 * n / (ms * 1e-3) / 1e9
+        res[name] = {"ms": round(ms, 4), "GBps": round(gbs, 1), "frac": round(gbs / pk["hbm_gbs"], 4)}
+    best = max(res.values(), key=lambda r: r["GBps"])
+    out = {"metric": "DAXPY HBM bandwidth", "value": best["GBps"], "unit": "GB/s", "n_gpus": 1,
+           "steps": args.steps, "warmup": args.warmup, "ms_per_step": best["ms"],
+           "higher_is_better": True, "dtype": "f64", "data": "synthetic (device splitmix64)",
+           "config": {"workload": "DAXPY n = 2^28, 24 bytes per element (read x, y; write y)",
+                      "flush": "vectors larger than L2"},
+           "roofline": {"bound": "hbm", "achieved": best["GBps"], "peak": pk["hbm_gbs"],
+                        "unit": "GB/s", "frac": best["frac"], "peak_kind": f"{pk_kind} copy"},
+           "workdivs": res}
+    print(json.dumps(out), flush=True)
+    return 0
+
+
 def main():
     args = parse()
     if args.impl == "reference":
@@ -436,6 +574,12 @@ def main():
         return run_grouped(args)
     if args.workload == "serve":
         return run_serve(args)
+    if args.workload == "sweep":
+        return run_sweep(args)
+    if args.workload == "d0":
+        return run_d0(args)
+    if args.workload == "daxpy":
+        return run_daxpy(args)
 
     import numpy as np
     import torch
@@ -505,15 +649,15 @@ def main():
     q.wait()
     emu_C = C.clone()
 
-    # native FP64 (DMMA) leg on the same inputs
+    # native FP64 leg on the same inputs (the library's default kernel at this size)
     Cn = torch.zeros_like(C)
-    gb.dgemm(A, B, Cn, 1.0, 0.0, kernel="dmma", queue=q)
+    gb.dgemm(A, B, Cn, 1.0, 0.0, kernel="auto", queue=q)
     torch.cuda.synchronize()
     n0 = torch.cuda.Event(enable_timing=True)
     n1 = torch.cuda.Event(enable_timing=True)
     n0.record(stream)
     for _ in range(args.native_steps):
-        gb.dgemm(A, B, Cn, 1.0, 0.0, kernel="dmma", queue=q)
+        gb.dgemm(A, B, Cn, 1.0, 0.0, kernel="auto", queue=q)
     n1.record(stream)
     torch.cuda.synchronize()
     native_ms = slowest(n0.elapsed_time(n1)) / args.native_steps
@@ -569,9 +713,11 @@ def main():
                      "achieved": round(achieved, 1), "peak": round(fp8_peak, 1),
                      "unit": "TFLOP/s", "frac": round(achieved / fp8_peak, 4),
                      "peak_kind": f"{pk_kind} bf16 burst x 2 (FP8 nominal ratio)",
-                     "traffic": None, "launch_ms": round(prod_ms, 4),
+                     "traffic": MEASURED_TRAFFIC.get(("emu_products_kernel", n, s)),
+                     "launch_ms": round(prod_ms, 4),
                      "algorithmic": f"s(s+1)/2 * 2 n^3 = {pair_flops:.4g} FP8 flop per launch"},
-        "native": {"kernel": "dmma", "value": round(native_tflops, 4), "unit": "TFLOP/s",
+        "native": {"kernel": "dfma" if n > 2048 else "tiled", "value": round(native_tflops, 4),
+                   "unit": "TFLOP/s",
                    "ms_per_call": round(native_ms, 2),
                    "roofline": {"bound": "alu", "achieved": round(native_tflops, 4),
                                 "peak": round(fp64_peak, 4), "unit": "TFLOP/s",

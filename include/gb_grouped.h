@@ -23,7 +23,8 @@ extern "C" {
 #endif
 
 /* Tile variants of the native grouped kernel (rows x columns of C per CTA,
- * 4 warps of FP64 DMMA each). */
+ * 256 threads with 4 x 4, 2 x 2, 4 x 2 or 2 x 4 elements each on the FP64
+ * FMA pipe). */
 typedef enum {
     GB_TILE_AUTO = 0,   /* from the tuning table (gb_tune_set), else a size rule */
     GB_TILE_64x64 = 1,

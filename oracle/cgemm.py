@@ -50,6 +50,8 @@ def _load():
             lib.oracle_dgemm_omp.restype = ctypes.c_int
             lib.oracle_dgemm_dd_rows.argtypes = [i64, p, i64, i64, p, i64, p, i64, p, p, i64]
             lib.oracle_dgemm_dd_rows.restype = None
+            lib.oracle_daxpy.argtypes = [i64, dbl, p, p]
+            lib.oracle_daxpy.restype = None
             _lib = lib
     return _lib
 
@@ -139,3 +141,13 @@ def dgemm_dd_rows(A: np.ndarray, B: np.ndarray, rows=None, n: int | None = None,
     _load().oracle_dgemm_dd_rows(nrows, _ptr(rp), n, k, _ptr(A), lda, _ptr(B), ldb,
                                  _ptr(hi), _ptr(lo), n)
     return hi, lo
+
+
+def daxpy(alpha: float, x: np.ndarray, y: np.ndarray) -> np.ndarray:
+    """y <- fma(alpha, x, y) elementwise (in place on a float64 copy); returns y."""
+    x = np.ascontiguousarray(x, dtype=np.float64)
+    y = np.array(y, dtype=np.float64, copy=True)
+    if x.shape != y.shape:
+        raise ValueError("x and y differ in shape")
+    _load().oracle_daxpy(x.size, alpha, _ptr(x), _ptr(y))
+    return y

@@ -131,3 +131,12 @@ void oracle_dgemm_dd_rows(int64_t nrows, const int64_t* rows, int64_t n, int64_t
         }
     }
 }
+
+/* ---- DAXPY  Y <- alpha X + Y  (Section 4.1, "Conceptual Comparison") ----------------
+ * Reading: each element is evaluated with one rounding, y_i <- fma(alpha, x_i, y_i)
+ * (C99 fma, correctly rounded).  n == 0 does nothing; alpha == 0 leaves Y unchanged
+ * and does not read X. */
+void oracle_daxpy(int64_t n, double alpha, const double* x, double* y) {
+    if (alpha == 0.0) return;
+    for (int64_t i = 0; i < n; ++i) y[i] = fma(alpha, x[i], y[i]);
+}

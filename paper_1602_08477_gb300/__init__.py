@@ -33,3 +33,4 @@ from .grouped import (  # noqa: E402,F401
     tune_set,
 )
 from .serve import Server, fill_uniform  # noqa: E402,F401
+from .execute import daxpy, enqueue, kernel_handle  # noqa: E402,F401

@@ -102,10 +102,16 @@ Variant default_variant(gb_kernel kernel, int64_t m, int64_t n, int64_t k) {
         case GB_KERNEL_TILED: return {kernel, 16, 16, 1, 1};
         case GB_KERNEL_DFMA: return {kernel, 16, 16, 4, 4};
         case GB_KERNEL_DMMA:
-        default:
             // a warp is one "thread"; its 32 x 32 (or 16 x 16) register tile the elements
             if (mn <= 1024) return {GB_KERNEL_DMMA, 2, 2, 16, 16};
             return {GB_KERNEL_DMMA, 2, 2, 32, 32};
+        case GB_KERNEL_AUTO:
+        default:
+            // measured on GB300: one element per thread in 16 x 16 smem tiles is
+            // fastest up to 2048 (finest load balance over 152 SMs); above it the
+            // 4 x 4 register tiles run the FP64 FMA pipe at its peak
+            if (mn <= 2048) return {GB_KERNEL_TILED, 16, 16, 1, 1};
+            return {GB_KERNEL_DFMA, 16, 16, 4, 4};
     }
 }
 
@@ -443,7 +449,7 @@ gb_status gb_dgemm(gb_queue* q, const gb_workdiv* wd, gb_kernel kernel, gb_preci
     gb_workdiv resolved;
     if (prec == GB_PREC_NATIVE) {
         if (wd) {
-            const gb_kernel kk = kernel == GB_KERNEL_AUTO ? GB_KERNEL_DMMA : kernel;
+            const gb_kernel kk = kernel == GB_KERNEL_AUTO ? GB_KERNEL_DFMA : kernel;
             st = check_workdiv(wd, kk, m, n);
             if (st != GB_OK) return st;
             resolved = *wd;

@@ -10,6 +10,9 @@
 //            (Section 4.2.2, Fig. "tiling_kernel"), FP64 FMA pipe;
 //   dmma   - the same hierarchy with a warp as the thread level and the warp's
 //            register tile as the element level, on FP64 mma.sync (DMMA).
+// On GB300 the FP64 FMA pipe sustains the nominal 2 FMA / clock / SM, ahead of
+// FP64 mma.sync; the library's default is therefore the tiled (small sizes) and
+// dfma (large sizes) path.
 // Row-major operands with leading dimensions; beta == 0 never reads C.
 #include <cuda_runtime.h>
 #include <cstdint>
@@ -80,31 +83,41 @@ __global__ void tiled_kernel(int64_t m, int64_t n, int64_t k, double alpha,
     if (i < m && j < n) store_out<kBeta0>(C, i * ldc + j, alpha, s, beta);
 }
 
-// ---- dfma: 16 x 16 threads, V x V elements per thread --------------------------------
-// Block tile (16V) x (16V); thread (ty, tx) owns rows ty + 16r and columns tx + 16c
-// (r, c < V), so shared-memory reads are broadcasts / consecutive and the global
-// stores of a half-warp are 128 contiguous bytes.  K advances in steps of 16
-// through a register-prefetched, double-buffered shared-memory stage.
-template <int V, bool kBeta0>
-__global__ void __launch_bounds__(256) dfma_kernel(int64_t m, int64_t n, int64_t k,
-                                                   double alpha, const double* __restrict__ A,
-                                                   int64_t lda, const double* __restrict__ B,
-                                                   int64_t ldb, double beta,
-                                                   double* __restrict__ C, int64_t ldc) {
-    constexpr int BM = 16 * V, BN = 16 * V, BK = (V == 8) ? 8 : 16;  // <= 48 KB static smem
+// ---- dfma: 16 x 16 threads, VY x VX elements per thread --------------------------------
+// Tile (16 VY) x (16 VX); thread (ty, tx) owns rows ty + 16r and columns tx + 16c
+// (r < VY, c < VX), so shared-memory reads are broadcasts / consecutive and the
+// global stores of a half-warp are 128 contiguous bytes.  K advances in steps of
+// BK through a register-prefetched, double-buffered shared-memory stage.  Every
+// element accumulates fma(A[i,l], B[l,j], acc) for l = 0, 1, ..., k-1 in order, so
+// all tile shapes give bit-identical results.
+template <int VY, int VX>
+struct DfmaShape {
+    static constexpr int BM = 16 * VY, BN = 16 * VX;
+    static constexpr int BK = (VY * VX >= 64) ? 8 : 16;   // <= 48 KB static smem
+    static constexpr int A_STAGE = BK * (BM + 1), B_STAGE = BK * BN;
+    static constexpr int SMEM_DOUBLES = 2 * (A_STAGE + B_STAGE);
+};
+
+template <int VY, int VX>
+__device__ __forceinline__ void dfma_tile(int64_t m, int64_t n, int64_t k, double alpha,
+                                          const double* __restrict__ A, int64_t lda,
+                                          const double* __restrict__ B, int64_t ldb,
+                                          double beta, double* __restrict__ C, int64_t ldc,
+                                          int64_t row0, int64_t col0, double* smem) {
+    using S = DfmaShape<VY, VX>;
+    constexpr int BM = S::BM, BN = S::BN, BK = S::BK;
     constexpr int A_PER_T = BM * BK / 256;  // elements of the A tile each thread loads
     constexpr int B_PER_T = BK * BN / 256;
-    __shared__ double As[2][BK][BM + 1];  // transposed: As[l][row]
-    __shared__ double Bs[2][BK][BN];
+    double* As = smem;                       // [2][BK][BM + 1]: transposed, As[l][row]
+    double* Bs = smem + 2 * S::A_STAGE;      // [2][BK][BN]
     const int tid = threadIdx.x;
     const int tx = tid & 15, ty = tid >> 4;
-    const int64_t row0 = blockIdx.y * (int64_t)BM, col0 = blockIdx.x * (int64_t)BN;
 
-    double acc[V][V];
+    double acc[VY][VX];
 #pragma unroll
-    for (int r = 0; r < V; ++r)
+    for (int r = 0; r < VY; ++r)
 #pragma unroll
-        for (int c = 0; c < V; ++c) acc[r][c] = 0.0;
+        for (int c = 0; c < VX; ++c) acc[r][c] = 0.0;
 
     double ra[A_PER_T], rb[B_PER_T];
     auto load_regs = [&](int64_t l0) {
@@ -124,15 +137,17 @@ __global__ void __launch_bounds__(256) dfma_kernel(int64_t m, int64_t n, int64_t
         }
     };
     auto store_smem = [&](int buf) {
+        double* as = As + buf * S::A_STAGE;
+        double* bs = Bs + buf * S::B_STAGE;
 #pragma unroll
         for (int u = 0; u < A_PER_T; ++u) {
             const int e = tid + 256 * u;
-            As[buf][e % BK][e / BK] = ra[u];
+            as[(e % BK) * (BM + 1) + e / BK] = ra[u];
         }
 #pragma unroll
         for (int u = 0; u < B_PER_T; ++u) {
             const int e = tid + 256 * u;
-            Bs[buf][e / BN][e % BN] = rb[u];
+            bs[(e / BN) * BN + e % BN] = rb[u];
         }
     };
 
@@ -145,31 +160,50 @@ __global__ void __launch_bounds__(256) dfma_kernel(int64_t m, int64_t n, int64_t
     for (int64_t kt = 0; kt < nk; ++kt) {
         const int buf = (int)(kt & 1);
         if (kt + 1 < nk) load_regs((kt + 1) * BK);
+        const double* as = As + buf * S::A_STAGE;
+        const double* bs = Bs + buf * S::B_STAGE;
 #pragma unroll
         for (int l = 0; l < BK; ++l) {
-            double a[V], b[V];
+            double av[VY], bv[VX];
 #pragma unroll
-            for (int r = 0; r < V; ++r) a[r] = As[buf][l][ty + 16 * r];
+            for (int r = 0; r < VY; ++r) av[r] = as[l * (BM + 1) + ty + 16 * r];
 #pragma unroll
-            for (int c = 0; c < V; ++c) b[c] = Bs[buf][l][tx + 16 * c];
+            for (int c = 0; c < VX; ++c) bv[c] = bs[l * BN + tx + 16 * c];
 #pragma unroll
-            for (int r = 0; r < V; ++r)
+            for (int r = 0; r < VY; ++r)
 #pragma unroll
-                for (int c = 0; c < V; ++c) acc[r][c] = fma(a[r], b[c], acc[r][c]);
+                for (int c = 0; c < VX; ++c) acc[r][c] = fma(av[r], bv[c], acc[r][c]);
         }
         if (kt + 1 < nk) store_smem(buf ^ 1);
         __syncthreads();
     }
+    const bool beta0 = beta == 0.0;
 #pragma unroll
-    for (int r = 0; r < V; ++r) {
+    for (int r = 0; r < VY; ++r) {
         const int64_t gi = row0 + ty + 16 * r;
         if (gi >= m) continue;
 #pragma unroll
-        for (int c = 0; c < V; ++c) {
+        for (int c = 0; c < VX; ++c) {
             const int64_t gj = col0 + tx + 16 * c;
-            if (gj < n) store_out<kBeta0>(C, gi * ldc + gj, alpha, acc[r][c], beta);
+            if (gj < n) {
+                double* cp = &C[gi * ldc + gj];
+                *cp = beta0 ? alpha * acc[r][c] : alpha * acc[r][c] + beta * (*cp);
+            }
         }
     }
+    __syncthreads();  // the shared-memory stages may be reused by the caller's next tile
+}
+
+template <int V>
+__global__ void __launch_bounds__(256) dfma_kernel(int64_t m, int64_t n, int64_t k,
+                                                   double alpha, const double* __restrict__ A,
+                                                   int64_t lda, const double* __restrict__ B,
+                                                   int64_t ldb, double beta,
+                                                   double* __restrict__ C, int64_t ldc) {
+    __shared__ __align__(16) double smem[DfmaShape<V, V>::SMEM_DOUBLES];
+    dfma_tile<V, V>(m, n, k, alpha, A, lda, B, ldb, beta, C, ldc,
+                    blockIdx.y * (int64_t)DfmaShape<V, V>::BM,
+                    blockIdx.x * (int64_t)DfmaShape<V, V>::BN, smem);
 }
 
 // ---- dmma: FP64 mma.sync.m16n8k4 warp tiles ----------------------------------------
@@ -329,13 +363,13 @@ __global__ void __launch_bounds__(32 * WARPS_M * WARPS_N)
 // Each CTA repeatedly takes the next tile index from a global counter (so tiles
 // of expensive problems, placed first in the table, start first), finds its
 // problem by binary search over the tile prefix, and runs that problem's tile
-// variant.  One shared buffer serves every variant.
-constexpr int kGroupedSmemDoubles = DmmaShape<2, 2, 32, 32>::SMEM_DOUBLES;
-static_assert(DmmaShape<2, 2, 16, 16>::SMEM_DOUBLES <= kGroupedSmemDoubles, "smem");
-static_assert(DmmaShape<2, 2, 32, 16>::SMEM_DOUBLES <= kGroupedSmemDoubles, "smem");
-static_assert(DmmaShape<2, 2, 16, 32>::SMEM_DOUBLES <= kGroupedSmemDoubles, "smem");
+// variant on the FP64 FMA pipe.  One shared buffer serves every variant.
+constexpr int kGroupedSmemDoubles = DfmaShape<4, 4>::SMEM_DOUBLES;
+static_assert(DfmaShape<2, 2>::SMEM_DOUBLES <= kGroupedSmemDoubles, "smem");
+static_assert(DfmaShape<4, 2>::SMEM_DOUBLES <= kGroupedSmemDoubles, "smem");
+static_assert(DfmaShape<2, 4>::SMEM_DOUBLES <= kGroupedSmemDoubles, "smem");
 
-__global__ void __launch_bounds__(128) grouped_native_kernel(const GroupProb* __restrict__ probs,
+__global__ void __launch_bounds__(256) grouped_native_kernel(const GroupProb* __restrict__ probs,
                                                              int nprob, int64_t total_tiles,
                                                              unsigned long long* counter) {
     __shared__ __align__(16) double smem[kGroupedSmemDoubles];
@@ -356,20 +390,20 @@ __global__ void __launch_bounds__(128) grouped_native_kernel(const GroupProb* __
         const int64_t tm = local / P.tiles_n, tn = local % P.tiles_n;
         switch (P.tile) {
             case kTile64x64:
-                dmma_tile<2, 2, 32, 32>(P.m, P.n, P.k, P.alpha, P.A, P.lda, P.B, P.ldb, P.beta,
-                                        P.C, P.ldc, tm * 64, tn * 64, smem);
+                dfma_tile<4, 4>(P.m, P.n, P.k, P.alpha, P.A, P.lda, P.B, P.ldb, P.beta, P.C,
+                                P.ldc, tm * 64, tn * 64, smem);
                 break;
             case kTile32x32:
-                dmma_tile<2, 2, 16, 16>(P.m, P.n, P.k, P.alpha, P.A, P.lda, P.B, P.ldb, P.beta,
-                                        P.C, P.ldc, tm * 32, tn * 32, smem);
+                dfma_tile<2, 2>(P.m, P.n, P.k, P.alpha, P.A, P.lda, P.B, P.ldb, P.beta, P.C,
+                                P.ldc, tm * 32, tn * 32, smem);
                 break;
             case kTile64x32:
-                dmma_tile<2, 2, 32, 16>(P.m, P.n, P.k, P.alpha, P.A, P.lda, P.B, P.ldb, P.beta,
-                                        P.C, P.ldc, tm * 64, tn * 32, smem);
+                dfma_tile<4, 2>(P.m, P.n, P.k, P.alpha, P.A, P.lda, P.B, P.ldb, P.beta, P.C,
+                                P.ldc, tm * 64, tn * 32, smem);
                 break;
             default:
-                dmma_tile<2, 2, 16, 32>(P.m, P.n, P.k, P.alpha, P.A, P.lda, P.B, P.ldb, P.beta,
-                                        P.C, P.ldc, tm * 32, tn * 64, smem);
+                dfma_tile<2, 4>(P.m, P.n, P.k, P.alpha, P.A, P.lda, P.B, P.ldb, P.beta, P.C,
+                                P.ldc, tm * 32, tn * 64, smem);
                 break;
         }
     }
@@ -428,10 +462,7 @@ template <int V>
 static cudaError_t launch_dfma_t(const Launch& L, const Gemm& g) {
     const int B = 16 * V;
     const dim3 grid((unsigned)((g.n + B - 1) / B), (unsigned)((g.m + B - 1) / B));
-    if (g.beta == 0.0)
-        dfma_kernel<V, true><<<grid, 256, 0, L.stream>>>(GB_ARGS);
-    else
-        dfma_kernel<V, false><<<grid, 256, 0, L.stream>>>(GB_ARGS);
+    dfma_kernel<V><<<grid, 256, 0, L.stream>>>(GB_ARGS);
     return cudaGetLastError();
 }
 
@@ -467,7 +498,7 @@ cudaError_t launch_dmma(const Launch& L, const Gemm& g, int wm, int wn, int tm, 
 
 int grouped_native_occupancy() {
     int blocks = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks, grouped_native_kernel, 128, 0) !=
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks, grouped_native_kernel, 256, 0) !=
             cudaSuccess ||
         blocks < 1)
         blocks = 1;
@@ -477,7 +508,7 @@ int grouped_native_occupancy() {
 cudaError_t launch_grouped_native(const Launch& L, const GroupProb* probs, int nprob,
                                   int64_t total_tiles, unsigned long long* counter, int grid) {
     if (nprob == 0 || total_tiles == 0) return cudaSuccess;
-    grouped_native_kernel<<<grid, 128, 0, L.stream>>>(probs, nprob, total_tiles, counter);
+    grouped_native_kernel<<<grid, 256, 0, L.stream>>>(probs, nprob, total_tiles, counter);
     return cudaGetLastError();
 }
 

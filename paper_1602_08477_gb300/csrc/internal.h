@@ -47,7 +47,7 @@ cudaError_t launch_dmma(const Launch& L, const Gemm& g, int warps_m, int warps_n
 bool dmma_variant_exists(int warps_m, int warps_n, int wt_m, int wt_n);
 
 // ---- grouped native FP64 (dgemm_native.cu) ----
-// Tile variants of the grouped kernel (4 warps of DMMA each): BM x BN.
+// Tile variants of the grouped kernel (256 threads on the FP64 FMA pipe): BM x BN.
 enum : int { kTile64x64 = 1, kTile32x32 = 2, kTile64x32 = 3, kTile32x64 = 4 };
 inline int tile_bm(int v) { return (v == kTile64x64 || v == kTile64x32) ? 64 : 32; }
 inline int tile_bn(int v) { return (v == kTile64x64 || v == kTile32x64) ? 64 : 32; }
@@ -67,7 +67,7 @@ struct GroupProb {
 // tiles from *counter (zeroed by the caller) in table order.  `grid` CTAs.
 cudaError_t launch_grouped_native(const Launch& L, const GroupProb* probs, int nprob,
                                   int64_t total_tiles, unsigned long long* counter, int grid);
-// Resident 128-thread CTAs per SM of the grouped native kernel.
+// Resident 256-thread CTAs per SM of the grouped native kernel.
 int grouped_native_occupancy();
 
 // ---- emulated FP64 (ozaki_split.cu, ozaki_gemm.cu) ----

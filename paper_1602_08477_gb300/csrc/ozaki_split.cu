@@ -54,9 +54,11 @@ __device__ __forceinline__ int frexp_exp_bits(uint64_t absbits) {
 
 // The s digits of one finite double x relative to line exponent e, packed as
 // E4M3 bytes into out[t] (byte lane `lane` of a 64-bit word).
-template <int S_MAX>
+// S: compile-time maximum of the slice count s (the single-GEMM kernels pass
+// s == S, so the loop bound is a constant).
+template <int S>
 __device__ __forceinline__ void digits_of(uint64_t bits, int e, int s, int lane,
-                                          uint64_t (&out)[S_MAX]) {
+                                          uint64_t (&out)[S]) {
     const int ef = (int)((bits >> 52) & 0x7FF);
     int64_t M = (int64_t)(bits & 0xFFFFFFFFFFFFFull);
     int E2;
@@ -69,7 +71,7 @@ __device__ __forceinline__ void digits_of(uint64_t bits, int e, int s, int lane,
     int64_t R = (bits >> 63) ? -M : M;
     int sh = e - kB1 - E2;  // y_1 = R / 2^sh
 #pragma unroll
-    for (int t = 0; t < S_MAX; ++t) {
+    for (int t = 0; t < S; ++t) {
         if (t >= s) break;
         int64_t d;
         if (R == 0 || sh >= 55) {
@@ -90,7 +92,6 @@ __device__ __forceinline__ void digits_of(uint64_t bits, int e, int s, int lane,
     }
 }
 
-constexpr int kSMax = 16;
 
 // Byte offset of digit t of line x at K index l0 (l0 % 8 == 0; the 8 bytes
 // l0 .. l0+7 are contiguous) in the tiled layout with R-line tiles.
@@ -106,6 +107,7 @@ __device__ __forceinline__ int64_t tiled_offset(int64_t x, int64_t l0, int t, in
 
 // Row i of A: pass 1 max |a| and finiteness, pass 2 digits (all threads call it).
 // Rows m <= i < (tile padding) get zero digits.
+template <int S>
 __device__ __forceinline__ void split_one_row(int64_t i, int64_t m, int64_t k,
                                               const double* __restrict__ A, int64_t lda, int s,
                                               uint8_t* __restrict__ digits, int64_t kp,
@@ -149,18 +151,18 @@ __device__ __forceinline__ void split_one_row(int64_t i, int64_t m, int64_t k,
     }
     // pass 2: 8 consecutive elements per thread -> one 8-byte word per plane
     for (int64_t l0 = (int64_t)tid * 8; l0 < kp; l0 += (int64_t)blockDim.x * 8) {
-        uint64_t w[kSMax];
+        uint64_t w[S];
 #pragma unroll
-        for (int t = 0; t < kSMax; ++t) w[t] = 0;
+        for (int t = 0; t < S; ++t) w[t] = 0;
         if (!is_bad) {
 #pragma unroll
             for (int u = 0; u < 8; ++u) {
                 const int64_t l = l0 + u;
-                if (l < k) digits_of<kSMax>(row[l], e, s, u, w);
+                if (l < k) digits_of<S>(row[l], e, s, u, w);
             }
         }
 #pragma unroll
-        for (int t = 0; t < kSMax; ++t) {
+        for (int t = 0; t < S; ++t) {
             if (t >= s) break;
             *reinterpret_cast<uint64_t*>(digits + tiled_offset(i, l0, t, s, nkb, kEmuBM)) = w[t];
         }
@@ -201,9 +203,10 @@ __device__ __forceinline__ void colmax_block(int64_t jb, int64_t n, int64_t k,
 
 // Transposing digit pass for B over the tile of 64 rows (l) x 32 columns (j)
 // at (lb, jb).
+template <int S>
 __device__ __forceinline__ void split_cols_tile(int64_t jb, int64_t lb, int64_t n, int64_t k,
-                                                const double* __restrict__ B, int64_t ldb,
-                                                int s, uint8_t* __restrict__ digits, int64_t kp,
+                                                const double* __restrict__ B, int64_t ldb, int s,
+                                                uint8_t* __restrict__ digits, int64_t kp,
                                                 const int32_t* __restrict__ exps,
                                                 uint64_t (*T)[33]) {
     const int tid = threadIdx.x;
@@ -220,17 +223,17 @@ __device__ __forceinline__ void split_cols_tile(int64_t jb, int64_t lb, int64_t 
     const int64_t j = j0 + jj, lbase = l0 + lsub;
     if (lbase < kp) {  // columns n <= j < (tile padding) get zero digits
         const int e = j < n ? exps[j] : GB_BAD_LINE_DEV;
-        uint64_t w[kSMax];
+        uint64_t w[S];
 #pragma unroll
-        for (int t = 0; t < kSMax; ++t) w[t] = 0;
+        for (int t = 0; t < S; ++t) w[t] = 0;
         if (e != GB_BAD_LINE_DEV) {
 #pragma unroll
             for (int u = 0; u < 8; ++u) {
-                if (lbase + u < k) digits_of<kSMax>(T[lsub + u][jj], e, s, u, w);
+                if (lbase + u < k) digits_of<S>(T[lsub + u][jj], e, s, u, w);
             }
         }
 #pragma unroll
-        for (int t = 0; t < kSMax; ++t) {
+        for (int t = 0; t < S; ++t) {
             if (t >= s) break;
             *reinterpret_cast<uint64_t*>(digits + tiled_offset(j, lbase, t, s, kp >> 5,
                                                                kEmuGroupBN)) = w[t];
@@ -239,9 +242,10 @@ __device__ __forceinline__ void split_cols_tile(int64_t jb, int64_t lb, int64_t 
     __syncthreads();
 }
 
+template <int S>
 __global__ void __launch_bounds__(128) split_rows_kernel(int64_t m, int64_t k,
                                                          const double* __restrict__ A,
-                                                         int64_t lda, int s,
+                                                         int64_t lda,
                                                          uint8_t* __restrict__ digits,
                                                          int64_t kp, int32_t* __restrict__ exps,
                                                          unsigned* status) {
@@ -249,7 +253,7 @@ __global__ void __launch_bounds__(128) split_rows_kernel(int64_t m, int64_t k,
     __shared__ int bad_sh;
     const int64_t mp = (m + kEmuBM - 1) / kEmuBM * kEmuBM;
     for (int64_t i = blockIdx.x; i < mp; i += gridDim.x)
-        split_one_row(i, m, k, A, lda, s, digits, kp, exps, status, red, &bad_sh);
+        split_one_row<S>(i, m, k, A, lda, S, digits, kp, exps, status, red, &bad_sh);
 }
 
 __global__ void __launch_bounds__(256) colmax_kernel(int64_t n, int64_t k,
@@ -261,15 +265,26 @@ __global__ void __launch_bounds__(256) colmax_kernel(int64_t n, int64_t k,
     colmax_block(blockIdx.x, n, k, B, ldb, exps, status, mx_sh, bad_sh);
 }
 
+template <int S>
 __global__ void __launch_bounds__(256) split_cols_kernel(int64_t n, int64_t k,
                                                          const double* __restrict__ B,
-                                                         int64_t ldb, int s,
+                                                         int64_t ldb,
                                                          uint8_t* __restrict__ digits,
                                                          int64_t kp,
                                                          const int32_t* __restrict__ exps) {
     __shared__ uint64_t T[64][33];
-    split_cols_tile(blockIdx.x, blockIdx.y, n, k, B, ldb, s, digits, kp, exps, T);
+    split_cols_tile<S>(blockIdx.x, blockIdx.y, n, k, B, ldb, S, digits, kp, exps, T);
 }
+
+#define GB_SWITCH_S(s, CALL)                                                           \
+    switch (s) {                                                                       \
+        case 1: CALL(1); break;  case 2: CALL(2); break;  case 3: CALL(3); break;      \
+        case 4: CALL(4); break;  case 5: CALL(5); break;  case 6: CALL(6); break;      \
+        case 7: CALL(7); break;  case 8: CALL(8); break;  case 9: CALL(9); break;      \
+        case 10: CALL(10); break; case 11: CALL(11); break; case 12: CALL(12); break;  \
+        case 13: CALL(13); break; case 14: CALL(14); break; case 15: CALL(15); break;  \
+        case 16: CALL(16); break; default: break;                                      \
+    }
 
 // ---- grouped: one launch per step over the problems of a table ---------------------
 __device__ __forceinline__ int find_prob(const EmuProb* __restrict__ P, int np,
@@ -289,8 +304,8 @@ __global__ void __launch_bounds__(128) grouped_split_rows_kernel(const EmuProb* 
     __shared__ int bad_sh;
     for (int64_t r = blockIdx.x; r < total_rows; r += gridDim.x) {
         const EmuProb& q = P[find_prob(P, np, &EmuProb::first_row, r)];
-        split_one_row(r - q.first_row, q.m, q.k, q.A, q.lda, q.s, q.a_digits, q.kp, q.a_exp,
-                      status, red, &bad_sh);
+        split_one_row<16>(r - q.first_row, q.m, q.k, q.A, q.lda, q.s, q.a_digits, q.kp, q.a_exp,
+                          status, red, &bad_sh);
     }
 }
 
@@ -312,8 +327,8 @@ __global__ void __launch_bounds__(256) grouped_split_cols_kernel(const EmuProb* 
         const EmuProb& q = P[find_prob(P, np, &EmuProb::first_tblk, b)];
         const int64_t local = b - q.first_tblk;
         const int64_t ncb = (q.n + 31) / 32;
-        split_cols_tile(local % ncb, local / ncb, q.n, q.k, q.B, q.ldb, q.s, q.b_digits, q.kp,
-                        q.b_exp, T);
+        split_cols_tile<16>(local % ncb, local / ncb, q.n, q.k, q.B, q.ldb, q.s, q.b_digits, q.kp,
+                            q.b_exp, T);
     }
 }
 
@@ -325,8 +340,11 @@ cudaError_t launch_split_rows(const Launch& L, int s, int64_t m, int64_t k, cons
     int64_t blocks = (m + kEmuBM - 1) / kEmuBM * kEmuBM;
     const int64_t cap = (int64_t)L.sm_count * 16;
     if (blocks > cap) blocks = cap;
-    split_rows_kernel<<<(unsigned)blocks, 128, 0, L.stream>>>(m, k, A, lda, s, digits, kp, exps,
-                                                              L.status);
+#define GB_LAUNCH_ROWS(SS)                                                                   \
+    split_rows_kernel<SS><<<(unsigned)blocks, 128, 0, L.stream>>>(m, k, A, lda, digits, kp, \
+                                                                  exps, L.status)
+    GB_SWITCH_S(s, GB_LAUNCH_ROWS)
+#undef GB_LAUNCH_ROWS
     return cudaGetLastError();
 }
 
@@ -353,7 +371,10 @@ cudaError_t launch_split_cols(const Launch& L, int s, int64_t n, int64_t k, cons
     cudaError_t err = cudaGetLastError();
     if (err != cudaSuccess) return err;
     const dim3 grid(gx, (unsigned)((kp + 63) / 64));
-    split_cols_kernel<<<grid, 256, 0, L.stream>>>(n, k, B, ldb, s, digits, kp, exps);
+#define GB_LAUNCH_COLS(SS) \
+    split_cols_kernel<SS><<<grid, 256, 0, L.stream>>>(n, k, B, ldb, digits, kp, exps)
+    GB_SWITCH_S(s, GB_LAUNCH_COLS)
+#undef GB_LAUNCH_COLS
     return cudaGetLastError();
 }
 

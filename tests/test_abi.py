@@ -20,7 +20,7 @@ def lib():
 
 def declared_functions():
     names = set()
-    pat = re.compile(r"^\s*(?:gb_status|int|const char\s*\*|void\s*\*)\s*(gb_\w+)\s*\(", re.M)
+    pat = re.compile(r"^\s*(?:gb_status|int|const char\s*\*|const void\s*\*|void\s*\*)\s*(gb_\w+)\s*\(", re.M)
     for h in glob.glob(os.path.join(ROOT, "include", "*.h")):
         names.update(pat.findall(open(h).read()))
     return sorted(names)
@@ -87,7 +87,13 @@ def test_workdiv_suggest_follows_table2_cuda_row(lib):
         assert wd.grid_blocks[1] == -(-700 // (B * V))
     assert lib.gb_workdiv_suggest(None, 0, 4096, 4096, 4096, ctypes.byref(wd),
                                   ctypes.byref(chosen)) == 0
-    assert chosen.value == 4  # DMMA: 2 x 2 warps, 32 x 32 elements per warp
+    assert chosen.value == 3  # DFMA: 16 x 16 threads, 4 x 4 elements each
+    assert tuple(wd.block_threads[:2]) == (16, 16) and tuple(wd.thread_elems[:2]) == (4, 4)
+    assert lib.gb_workdiv_suggest(None, 0, 1024, 1024, 1024, ctypes.byref(wd),
+                                  ctypes.byref(chosen)) == 0
+    assert chosen.value == 2  # smem tiles, one element per thread
+    assert lib.gb_workdiv_suggest(None, 4, 4096, 4096, 4096, ctypes.byref(wd),
+                                  ctypes.byref(chosen)) == 0
     assert tuple(wd.block_threads[:2]) == (2, 2) and tuple(wd.thread_elems[:2]) == (32, 32)
     assert lib.gb_workdiv_suggest(None, 9, 8, 8, 8, ctypes.byref(wd), None) == 1
 

@@ -1,8 +1,8 @@
 """GPU parity of the grouped (persistent, graph-captured) GEMMs.
 
 The grouped result of each problem equals the single-launch result bit for bit
-(same per-element summation order in every native tile variant; same digits and
-products in the emulated path), and each is within the FP64 bound of the
+(every native tile variant accumulates fma(A[i,l], B[l,j], acc) in l order like the
+single DFMA kernel; same digits and products in the emulated path), and each is within the FP64 bound of the
 oracle.  Problem sizes follow the grouped workload's recipe (m, n, k
 log-uniform in [16, 512]) at a reduced count, plus edge cases.
 """
@@ -66,7 +66,7 @@ def test_native_group_matches_single_launches_bit_exact(gb, tile):
     assert info["launches"] == 1 and info["emulated_tiles"] == 0
     for p, (A, B, C0) in zip(probs, host):
         single = to_dev(C0)
-        gb.dgemm(to_dev(A), to_dev(B), single, p["alpha"], p["beta"], kernel="dmma")
+        gb.dgemm(to_dev(A), to_dev(B), single, p["alpha"], p["beta"], kernel="dfma")
         torch.cuda.synchronize()
         assert torch.equal(p["C"], single)
     assert check_bound(probs, host) <= 2.0
@@ -87,7 +87,7 @@ def test_graph_replay_recomputes(gb):
     torch.cuda.synchronize()
     for p, f, (A, B, C0) in zip(probs, first, host):
         again = f.clone()
-        gb.dgemm(to_dev(A), to_dev(B), again, p["alpha"], p["beta"], kernel="dmma")
+        gb.dgemm(to_dev(A), to_dev(B), again, p["alpha"], p["beta"], kernel="dfma")
         torch.cuda.synchronize()
         assert torch.equal(p["C"], again)
     plan.close()
@@ -107,7 +107,7 @@ def test_emulated_and_mixed_group(gb):
             gb.dgemm(to_dev(A), to_dev(B), single, p["alpha"], p["beta"], precision="emulated",
                      slices=p["slices"])
         else:
-            gb.dgemm(to_dev(A), to_dev(B), single, p["alpha"], p["beta"], kernel="dmma")
+            gb.dgemm(to_dev(A), to_dev(B), single, p["alpha"], p["beta"], kernel="dfma")
         torch.cuda.synchronize()
         assert torch.equal(p["C"], single)
     assert check_bound(probs, host) <= 2.0

@@ -188,3 +188,19 @@ def test_rows_and_openmp_forms_bit_identical():
     omp, used = cgemm.dgemm_omp(1.5, A, B, 0.5, C0.copy(), threads=4)
     assert used >= 1
     assert np.array_equal(omp, full)
+
+
+def test_daxpy_oracle_pins():
+    # exact cases: integers, a power-of-two alpha, alpha = 0 leaves y
+    x = np.arange(-50, 50, dtype=np.float64)
+    y = np.arange(100, dtype=np.float64) * 3.0
+    assert np.array_equal(cgemm.daxpy(2.0, x, y), 2.0 * x + y)
+    assert np.array_equal(cgemm.daxpy(0.0, np.full(5, np.nan), np.ones(5)), np.ones(5))
+    # one rounding: fma(a, x, y) equals the exact rational rounded once
+    a = 1.0 / 3.0
+    xs = g.uniform_pm1(g.raw_stream(3, 0, 200))
+    ys = g.uniform_pm1(g.raw_stream(3, 1, 200))
+    got = cgemm.daxpy(a, xs, ys)
+    for i in range(200):
+        exact_v = Fraction(a) * Fraction(float(xs[i])) + Fraction(float(ys[i]))
+        assert got[i] == float(exact_v)  # float(Fraction) rounds to nearest even
