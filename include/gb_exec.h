@@ -37,7 +37,12 @@ gb_status gb_enqueue(gb_queue* q, const gb_workdiv* wd, const void* kernel, void
 /* Host-side handle of one of the library's own kernels usable with gb_enqueue,
  * or NULL.  Names: "daxpy_v1", "daxpy_v2", "daxpy_v4", "daxpy_v8" -- the DAXPY
  * kernel with V elements per thread, parameters
- * (int64_t n, double alpha, const double* x, double* y). */
+ * (int64_t n, double alpha, const double* x, double* y);  "dgemm_naive"
+ * (16 x 16 threads, 1 element each), "dgemm_tiled16" (16 x 16 threads, 16 x 16
+ * shared-memory tiles), "dgemm_dfma4" (16 x 16 threads, 4 x 4 elements each) --
+ * the native DGEMM kernels, parameters (int64_t m, n, k, double alpha,
+ * const double* A, int64_t lda, const double* B, int64_t ldb, double beta,
+ * double* C, int64_t ldc), grid (ceil(n / tile), ceil(m / tile)) on x, y. */
 const void* gb_kernel_handle(const char* name);
 
 /*

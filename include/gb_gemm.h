@@ -211,6 +211,13 @@ gb_status gb_emulated_products(gb_queue* q, int slices, int64_t m, int64_t n, in
                                double alpha, double beta, double* C, int64_t ldc,
                                void* workspace, size_t workspace_bytes);
 
+/* Diagnostic of the failure path (the paper has no failure model; this library
+ * bounds every device-side wait): enqueues a kernel that waits on a barrier
+ * nothing will ever complete, gives up after timeout_us microseconds (1 .. 2e6),
+ * records the timeout in the queue's status word and exits normally.  The next
+ * gb_queue_wait returns GB_ERR_TIMEOUT and the queue stays usable. */
+gb_status gb_selftest_wait_timeout(gb_queue* q, uint32_t timeout_us);
+
 /*
  * The emulated GEMM without any allocation or workspace argument.  The paper
  * has no counterpart: this entry point exists for callers that cannot allocate

@@ -92,7 +92,7 @@ const void* gb_kernel_handle(const char* name) {
     if (!std::strcmp(name, "daxpy_v2")) return daxpy_handle(2);
     if (!std::strcmp(name, "daxpy_v4")) return daxpy_handle(4);
     if (!std::strcmp(name, "daxpy_v8")) return daxpy_handle(8);
-    return nullptr;
+    return native_kernel_handle(name);
 }
 
 gb_status gb_enqueue(gb_queue* q, const gb_workdiv* wd, const void* kernel, void** args,

@@ -16,6 +16,7 @@
 // Row-major operands with leading dimensions; beta == 0 never reads C.
 #include <cuda_runtime.h>
 #include <cstdint>
+#include <cstring>
 
 #include "internal.h"
 
@@ -494,6 +495,21 @@ cudaError_t launch_dmma(const Launch& L, const Gemm& g, int wm, int wn, int tm, 
     if (wm == 2 && wn == 2 && tm == 16 && tn == 16) return launch_dmma_t<2, 2, 16, 16>(L, g);
     if (wm == 4 && wn == 2 && tm == 32 && tn == 32) return launch_dmma_t<4, 2, 32, 32>(L, g);
     return cudaErrorInvalidValue;
+}
+
+const void* native_kernel_handle(const char* name) {
+    struct Entry {
+        const char* name;
+        const void* fn;
+    };
+    static const Entry table[] = {
+        {"dgemm_naive", reinterpret_cast<const void*>(&naive_kernel<false>)},
+        {"dgemm_tiled16", reinterpret_cast<const void*>(&tiled_kernel<16, false>)},
+        {"dgemm_dfma4", reinterpret_cast<const void*>(&dfma_kernel<4>)},
+    };
+    for (const Entry& e : table)
+        if (name && !std::strcmp(name, e.name)) return e.fn;
+    return nullptr;
 }
 
 int grouped_native_occupancy() {

@@ -27,6 +27,7 @@ struct gb_grouped_plan {
     int n_emu;
     int64_t emu_rows, emu_colblks, emu_tblks, emu_tiles;
     int max_s;
+    std::vector<int64_t> s_ranges;  // (s, t_begin, t_end) triples of the emulated tiles
     int launches;
     double flops;
 };
@@ -63,6 +64,8 @@ struct Layout {
     std::vector<GroupProb> native;
     std::vector<EmuProb> emu;
     std::vector<EmuLayout> emu_ws;
+    std::vector<int64_t> emu_idx;   // descriptor index of each emulated problem
+    std::vector<int64_t> s_ranges;  // (s, t_begin, t_end) per distinct slice count
     size_t off_counter = 0, off_native = 0, off_emu = 0, off_data = 0, total = 0;
     int max_s = 0;
     double flops = 0;
@@ -123,6 +126,7 @@ gb_status build_layout(const gb_gemm_desc* d, int64_t count, Layout& L) {
             e.tiles_n = (int32_t)((x.n + kEmuGroupBN - 1) / kEmuGroupBN);
             L.emu.push_back(e);
             L.emu_ws.push_back(emu_layout(s, x.m, x.n, x.k));
+            L.emu_idx.push_back(i);
             L.max_s = std::max(L.max_s, s);
         }
     }
@@ -136,6 +140,24 @@ gb_status build_layout(const gb_gemm_desc* d, int64_t count, Layout& L) {
     for (auto& p : L.native) {
         p.first_tile = t;
         t += ((p.m + tile_bm(p.tile) - 1) / tile_bm(p.tile)) * p.tiles_n;
+    }
+    // emulated problems of equal slice count together: one persistent launch each
+    {
+        std::vector<size_t> perm(L.emu.size());
+        for (size_t i = 0; i < perm.size(); ++i) perm[i] = i;
+        std::stable_sort(perm.begin(), perm.end(),
+                         [&](size_t a, size_t b) { return L.emu[a].s < L.emu[b].s; });
+        std::vector<EmuProb> e2;
+        std::vector<EmuLayout> w2;
+        std::vector<int64_t> i2;
+        for (size_t i : perm) {
+            e2.push_back(L.emu[i]);
+            w2.push_back(L.emu_ws[i]);
+            i2.push_back(L.emu_idx[i]);
+        }
+        L.emu.swap(e2);
+        L.emu_ws.swap(w2);
+        L.emu_idx.swap(i2);
     }
     L.off_counter = 0;
     L.off_native = 256;
@@ -156,7 +178,15 @@ gb_status build_layout(const gb_gemm_desc* d, int64_t count, Layout& L) {
         rows += (e.m + kEmuBM - 1) / kEmuBM * kEmuBM;
         colblks += ncb;
         tblks += ncb * ((w.kp + 63) / 64);
-        tiles += ((e.m + kEmuBM - 1) / kEmuBM) * e.tiles_n;
+        const int64_t t_new = tiles + ((e.m + kEmuBM - 1) / kEmuBM) * e.tiles_n;
+        if (L.s_ranges.empty() || L.s_ranges[L.s_ranges.size() - 3] != e.s) {
+            L.s_ranges.push_back(e.s);
+            L.s_ranges.push_back(tiles);
+            L.s_ranges.push_back(t_new);
+        } else {
+            L.s_ranges.back() = t_new;
+        }
+        tiles = t_new;
         off += w.total;
     }
     L.total = off;
@@ -179,20 +209,15 @@ gb_status grouped_enqueue_async(const Launch& L, const gb_gemm_desc* descs, int6
         set_error("grouped table space %zu < %zu", table_bytes, lay.off_data);
         return GB_ERR_WORKSPACE;
     }
-    // emulated problems in the order build_layout kept them (descriptor order)
-    size_t ei = 0;
-    for (int64_t i = 0; i < count && ei < lay.emu.size(); ++i) {
-        const gb_gemm_desc& x = descs[i];
-        if (x.precision != GB_PREC_EMULATED || x.m == 0 || x.n == 0 || x.alpha == 0.0 || x.k == 0)
-            continue;
-        uint8_t* w = static_cast<uint8_t*>(emu_ws[i]);
+    // each emulated problem uses the workspace of its own descriptor
+    for (size_t ei = 0; ei < lay.emu.size(); ++ei) {
+        uint8_t* w = static_cast<uint8_t*>(emu_ws[lay.emu_idx[ei]]);
         EmuProb& e = lay.emu[ei];
         const EmuLayout& wl = lay.emu_ws[ei];
         e.a_digits = w + wl.a_digits;
         e.b_digits = w + wl.b_digits;
         e.a_exp = reinterpret_cast<int32_t*>(w + wl.a_exp);
         e.b_exp = reinterpret_cast<int32_t*>(w + wl.b_exp);
-        ++ei;
     }
     uint8_t* stg = static_cast<uint8_t*>(staging);
     uint8_t* dev = static_cast<uint8_t*>(tables);
@@ -221,11 +246,12 @@ gb_status grouped_enqueue_async(const Launch& L, const gb_gemm_desc* descs, int6
         e = launch_grouped_split(L, d, (int)lay.emu.size(),
                                  l.first_row + (l.m + kEmuBM - 1) / kEmuBM * kEmuBM,
                                  l.first_colblk + ncb, l.first_tblk + ncb * ((l.kp + 63) / 64));
-        if (e == cudaSuccess)
-            e = launch_grouped_products(L, d, (int)lay.emu.size(),
-                                        l.first_tile + ((l.m + kEmuBM - 1) / kEmuBM) * l.tiles_n,
-                                        lay.max_s);
-        nl += 4;
+        nl += 3;
+        for (size_t r = 0; r + 2 < lay.s_ranges.size() && e == cudaSuccess; r += 3) {
+            e = launch_grouped_products(L, d, (int)lay.emu.size(), lay.s_ranges[r + 1],
+                                        lay.s_ranges[r + 2], (int)lay.s_ranges[r]);
+            ++nl;
+        }
     }
     if (launches) *launches = nl;
     if (e != cudaSuccess) return cuda_fail(e, "grouped enqueue");
@@ -297,8 +323,9 @@ static gb_status enqueue_plan(gb_grouped_plan* p, cudaStream_t stream) {
     }
     if (e == cudaSuccess && p->n_emu > 0) {
         e = launch_grouped_split(L, p->d_emu, p->n_emu, p->emu_rows, p->emu_colblks, p->emu_tblks);
-        if (e == cudaSuccess)
-            e = launch_grouped_products(L, p->d_emu, p->n_emu, p->emu_tiles, p->max_s);
+        for (size_t r = 0; r + 2 < p->s_ranges.size() && e == cudaSuccess; r += 3)
+            e = launch_grouped_products(L, p->d_emu, p->n_emu, p->s_ranges[r + 1],
+                                        p->s_ranges[r + 2], (int)p->s_ranges[r]);
     }
     if (e != cudaSuccess) return cuda_fail(e, "grouped launch");
     return GB_OK;
@@ -331,7 +358,7 @@ gb_status gb_grouped_plan_create(gb_queue* q, const gb_gemm_desc* descs, int64_t
         e.b_exp = reinterpret_cast<int32_t*>(ws + off + w.b_exp);
         off += w.total;
     }
-    gb_grouped_plan* p = new (std::nothrow) gb_grouped_plan{};
+    gb_grouped_plan* p = new (std::nothrow) gb_grouped_plan();
     if (!p) {
         set_error("out of host memory");
         return GB_ERR_INVALID_ARG;
@@ -358,12 +385,14 @@ gb_status gb_grouped_plan_create(gb_queue* q, const gb_gemm_desc* descs, int64_t
         p->emu_tiles = e.first_tile + ((e.m + kEmuBM - 1) / kEmuBM) * e.tiles_n;
     }
     p->max_s = L.max_s;
+    p->s_ranges = L.s_ranges;
     p->flops = L.flops;
     const int occ = grouped_native_occupancy();
     int64_t grid = (int64_t)q->dev->sm_count * occ;
     if (grid > p->native_tiles) grid = p->native_tiles;
     p->grid_native = (int)(grid > 0 ? grid : 1);
-    p->launches = (p->native_tiles > 0 ? 1 : 0) + (p->n_emu > 0 ? 4 : 0);
+    p->launches = (p->native_tiles > 0 ? 1 : 0) +
+                  (p->n_emu > 0 ? 3 + (int)(L.s_ranges.size() / 3) : 0);
 
     cudaError_t e = cudaSuccess;
     if (!L.native.empty())

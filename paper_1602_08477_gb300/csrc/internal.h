@@ -67,6 +67,9 @@ struct GroupProb {
 // tiles from *counter (zeroed by the caller) in table order.  `grid` CTAs.
 cudaError_t launch_grouped_native(const Launch& L, const GroupProb* probs, int nprob,
                                   int64_t total_tiles, unsigned long long* counter, int grid);
+// Host handle of a native DGEMM kernel by name ("dgemm_naive", "dgemm_tiled16",
+// "dgemm_dfma4"; parameters m, n, k, alpha, A, lda, B, ldb, beta, C, ldc), or null.
+const void* native_kernel_handle(const char* name);
 // Resident 256-thread CTAs per SM of the grouped native kernel.
 int grouped_native_occupancy();
 
@@ -107,9 +110,10 @@ struct EmuProb {
 // Grouped e1 + e2 over a table of emulated problems (three launches).
 cudaError_t launch_grouped_split(const Launch& L, const EmuProb* probs, int np,
                                  int64_t total_rows, int64_t total_colblks, int64_t total_tblks);
-// Grouped e3 + e4: one CTA per 128 x 32 output tile.  max_s: largest s.
+// Grouped e3 + e4: persistent CTAs over the 128 x 32 output tiles
+// [t_begin, t_end) of the table, all of whose problems use s slices.
 cudaError_t launch_grouped_products(const Launch& L, const EmuProb* probs, int np,
-                                    int64_t total_tiles, int max_s);
+                                    int64_t t_begin, int64_t t_end, int s);
 constexpr int kEmuBM = 128;      // output tile rows of the products kernel (A digit tile rows)
 constexpr int kEmuGroupBN = 32;  // output tile columns (B digit tile rows)
 

@@ -50,7 +50,7 @@ constexpr uint64_t kWaitTimeoutNs = 4000000000ull;  // 4 s
 constexpr int kSmemLimit = 227 * 1024;
 
 struct SmemTail {
-    uint64_t bars[2 * 8 + 1];
+    uint64_t bars[2 * 8 + 3];
     uint32_t tmem_holder;
     int abort;
 };
@@ -201,24 +201,29 @@ __host__ __device__ constexpr int kblocks_per_stage(int S) {
                      : ((kSmemLimit - 2048) / (2 * S * (kBM + kBN) * kBKBytes));
 }
 
-// One 128 x 32 output tile: level sums on the tensor cores, recombination into
-// C.  All threads call it; `smem` is 1024-byte aligned and holds `stages` ring
-// slots of `slot_bytes` (>= KB * S * 5 KiB) plus a SmemTail.  A stage holds KB
+// Persistent CTA over output tiles t = blockIdx.x, blockIdx.x + gridDim.x, ...
+// (tile_of(t) gives a tile's arguments; every role walks the same sequence).
+// Barriers and the TMEM allocation live for the whole CTA: the producer runs
+// ahead into the next tile's stages, and the epilogue hands TMEM back (tmem_empty)
+// as soon as it has read the level sums, so the next tile's MMAs overlap its
+// rounding and stores.  `smem` is 1024-byte aligned and holds `stages` ring slots
+// of `slot_bytes` (>= KB * S * 5 KiB) plus a SmemTail.  A stage holds KB
 // consecutive K blocks: their A tiles (KB * S * 4 KiB, contiguous in the
 // workspace) then their B tiles (KB * S * 1 KiB).
-template <int S, int KB>
-__device__ __forceinline__ void products_tile(const TileArgs& a, uint8_t* smem, int stages,
-                                              uint32_t slot_bytes, unsigned* status) {
+template <int S, int KB, class TileFn>
+__device__ __forceinline__ void products_persistent(const TileFn& tile_of, int64_t t_begin,
+                                                    int64_t t_end, uint8_t* smem, int stages,
+                                                    uint32_t slot_bytes, unsigned* status) {
     constexpr int BN = kBN;
     SmemTail* tail = reinterpret_cast<SmemTail*>(smem + (size_t)stages * slot_bytes);
     uint64_t* full = tail->bars;
     uint64_t* empty = tail->bars + stages;
     uint64_t* tmem_full = tail->bars + 2 * stages;
+    uint64_t* tmem_empty = tail->bars + 2 * stages + 1;
+    uint64_t* drain = tail->bars + 2 * stages + 2;
     volatile int* abort = &tail->abort;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    constexpr int s = S;
-    const int nkb = a.nkb;
-    const int nst = (nkb + KB - 1) / KB;  // stages of K blocks
+    const int64_t t0 = t_begin + blockIdx.x, dt = gridDim.x;
 
     if (threadIdx.x == 0) {
         for (int i = 0; i < stages; ++i) {
@@ -226,6 +231,8 @@ __device__ __forceinline__ void products_tile(const TileArgs& a, uint8_t* smem, 
             ptx::mbar_init(&empty[i], 1);
         }
         ptx::mbar_init(tmem_full, 1);
+        ptx::mbar_init(tmem_empty, kEpiWarps);
+        ptx::mbar_init(drain, 1);
         tail->abort = 0;
         ptx::mbar_init_fence();
     }
@@ -241,44 +248,62 @@ __device__ __forceinline__ void products_tile(const TileArgs& a, uint8_t* smem, 
     constexpr uint32_t b_bytes = (uint32_t)S * BN * kBKBytes;
 
     if (warp == 0 && lane == 0) {
-        // ---- producer: two contiguous bulk copies per stage ----
-        for (int it = 0; it < nst; ++it) {
-            const int st = it % stages;
-            const uint32_t ph = (uint32_t)(it / stages) & 1u;
-            if (!ptx::mbar_wait_bounded(&empty[st], ph ^ 1u, abort, status, kStatusTimeout,
-                                        kWaitTimeoutNs))
-                break;
-            const int kb0 = it * KB;
-            const int kc = nkb - kb0 < KB ? nkb - kb0 : KB;
-            uint8_t* sa = smem + (size_t)st * slot_bytes;
-            ptx::mbar_arrive_expect_tx(&full[st], (uint32_t)kc * (a_bytes + b_bytes));
-            ptx::bulk_load(sa, a.a_src + (size_t)kb0 * a_bytes, (uint32_t)kc * a_bytes, &full[st]);
-            ptx::bulk_load(sa + KB * a_bytes, a.b_src + (size_t)kb0 * b_bytes,
-                           (uint32_t)kc * b_bytes, &full[st]);
+        // ---- producer: two contiguous bulk copies per stage, across tiles ----
+        uint32_t it = 0;
+        for (int64_t t = t0; t < t_end && !*abort; t += dt) {
+            const TileArgs a = tile_of(t);
+            const int nst = (a.nkb + KB - 1) / KB;
+            for (int j = 0; j < nst; ++j, ++it) {
+                const int st = (int)(it % (uint32_t)stages);
+                const uint32_t ph = (it / (uint32_t)stages) & 1u;
+                if (!ptx::mbar_wait_bounded(&empty[st], ph ^ 1u, abort, status, kStatusTimeout,
+                                            kWaitTimeoutNs))
+                    break;
+                const int kb0 = j * KB;
+                const int kc = a.nkb - kb0 < KB ? a.nkb - kb0 : KB;
+                uint8_t* sa = smem + (size_t)st * slot_bytes;
+                ptx::mbar_arrive_expect_tx(&full[st], (uint32_t)kc * (a_bytes + b_bytes));
+                ptx::bulk_load(sa, a.a_src + (size_t)kb0 * a_bytes, (uint32_t)kc * a_bytes,
+                               &full[st]);
+                ptx::bulk_load(sa + KB * a_bytes, a.b_src + (size_t)kb0 * b_bytes,
+                               (uint32_t)kc * b_bytes, &full[st]);
+            }
         }
     } else if (warp == 1 && lane == 0) {
         // ---- MMA issuer ----
-        for (int it = 0; it < nst; ++it) {
-            const int st = it % stages;
-            const uint32_t ph = (uint32_t)(it / stages) & 1u;
-            if (!ptx::mbar_wait_bounded(&full[st], ph, abort, status, kStatusTimeout,
-                                        kWaitTimeoutNs))
-                break;
-            ptx::tc_fence_after();
-            const uint32_t a0 = ptx::smem_u32(smem + (size_t)st * slot_bytes);
-            const uint64_t adesc = ptx::umma_desc_sw32(a0);
-            const uint64_t bdesc = ptx::umma_desc_sw32(a0 + KB * a_bytes);
-            const int kc = nkb - it * KB < KB ? nkb - it * KB : KB;
-#pragma unroll
-            for (int kk = 0; kk < KB; ++kk) {
-                if (kk < kc)
-                    issue_kblock<S>(adesc + (uint64_t)((kk * a_bytes) >> 4),
-                                    bdesc + (uint64_t)((kk * b_bytes) >> 4), tmem_base,
-                                    it == 0 && kk == 0);
+        uint32_t it = 0, tile_iter = 0;
+        for (int64_t t = t0; t < t_end && !*abort; t += dt, ++tile_iter) {
+            const TileArgs a = tile_of(t);
+            const int nst = (a.nkb + KB - 1) / KB;
+            if (tile_iter > 0) {
+                // the epilogue has read the previous tile's accumulators
+                if (!ptx::mbar_wait_bounded(tmem_empty, (tile_iter - 1) & 1u, abort, status,
+                                            kStatusTimeout, kWaitTimeoutNs))
+                    break;
+                ptx::tc_fence_after();
             }
-            ptx::mma_commit(&empty[st]);
+            for (int j = 0; j < nst; ++j, ++it) {
+                const int st = (int)(it % (uint32_t)stages);
+                const uint32_t ph = (it / (uint32_t)stages) & 1u;
+                if (!ptx::mbar_wait_bounded(&full[st], ph, abort, status, kStatusTimeout,
+                                            kWaitTimeoutNs))
+                    break;
+                ptx::tc_fence_after();
+                const uint32_t a0 = ptx::smem_u32(smem + (size_t)st * slot_bytes);
+                const uint64_t adesc = ptx::umma_desc_sw32(a0);
+                const uint64_t bdesc = ptx::umma_desc_sw32(a0 + KB * a_bytes);
+                const int kc = a.nkb - j * KB < KB ? a.nkb - j * KB : KB;
+#pragma unroll
+                for (int kk = 0; kk < KB; ++kk) {
+                    if (kk < kc)
+                        issue_kblock<S>(adesc + (uint64_t)((kk * a_bytes) >> 4),
+                                        bdesc + (uint64_t)((kk * b_bytes) >> 4), tmem_base,
+                                        j == 0 && kk == 0);
+                }
+                ptx::mma_commit(&empty[st]);
+            }
+            ptx::mma_commit(tmem_full);
         }
-        ptx::mma_commit(tmem_full);
     } else if (warp >= 2) {
         // ---- epilogue ----
         // T = sum_g S_g 2^(5 (s+1-g)) exactly: Horner in int64 over groups of at
@@ -286,16 +311,14 @@ __device__ __forceinline__ void products_tile(const TileArgs& a, uint8_t* smem, 
         // folded into a 128-bit integer at group ends; one rounding to FP64.
         const int quarter = warp & 3;
         const int cgroup = (warp - 2) >> 2;
-        const int64_t row = a.row0 + quarter * 32 + lane;
-        const bool ok = ptx::mbar_wait_bounded(tmem_full, 0, abort, status, kStatusTimeout,
-                                               kWaitTimeoutNs);
-        ptx::tc_fence_after();
-        if (ok && !*abort) {
-            const int32_t ei = row < a.m ? a.eA[row] : 0;
-            const bool bad_row = ei == GB_BAD_LINE_DEV;
-            const int Ebase = -8 - 5 * (s - 1);
-            const bool plain = (a.alpha == 1.0 && a.beta == 0.0);
-            const uint32_t col_addr = tmem_base + ((uint32_t)(quarter * 32) << 16) + cgroup * 8;
+        const uint32_t col_addr = tmem_base + ((uint32_t)(quarter * 32) << 16) + cgroup * 8;
+        uint32_t tile_iter = 0;
+        for (int64_t t = t0; t < t_end; t += dt, ++tile_iter) {
+            const TileArgs a = tile_of(t);
+            const bool ok = ptx::mbar_wait_bounded(tmem_full, tile_iter & 1u, abort, status,
+                                                   kStatusTimeout, kWaitTimeoutNs);
+            ptx::tc_fence_after();
+            if (!ok || *abort) break;
             I128 T[8];
             int64_t G[8];
 #pragma unroll
@@ -305,14 +328,14 @@ __device__ __forceinline__ void products_tile(const TileArgs& a, uint8_t* smem, 
             }
             int in_group = 0;
 #pragma unroll 1
-            for (int g = 2; g <= s + 1; ++g) {
+            for (int g = 2; g <= S + 1; ++g) {
                 uint32_t v[8];
                 ptx::tmem_ld_32x32b_x8(col_addr + (uint32_t)(g - 2) * BN, v);
                 ptx::tmem_ld_wait();
 #pragma unroll
                 for (int j = 0; j < 8; ++j) G[j] = G[j] * 32 + f32_int_value(v[j]);
                 ++in_group;
-                if (in_group == 6 || g == s + 1) {
+                if (in_group == 6 || g == S + 1) {
 #pragma unroll
                     for (int j = 0; j < 8; ++j) {
                         i128_horner(T[j], 5 * in_group, G[j]);
@@ -321,7 +344,16 @@ __device__ __forceinline__ void products_tile(const TileArgs& a, uint8_t* smem, 
                     in_group = 0;
                 }
             }
+            // accumulators read: hand TMEM to the next tile's MMAs
+            ptx::tc_fence_before();
+            __syncwarp();
+            if (lane == 0) ptx::mbar_arrive(tmem_empty);
+            const int64_t row = a.row0 + quarter * 32 + lane;
             if (row < a.m) {
+                const int32_t ei = a.eA[row];
+                const bool bad_row = ei == GB_BAD_LINE_DEV;
+                const int Ebase = -8 - 5 * (S - 1);
+                const bool plain = (a.alpha == 1.0 && a.beta == 0.0);
                 double* crow = a.C + row * a.ldc;
 #pragma unroll
                 for (int j = 0; j < 8; ++j) {
@@ -332,11 +364,11 @@ __device__ __forceinline__ void products_tile(const TileArgs& a, uint8_t* smem, 
                         if (bad_row || fj == GB_BAD_LINE_DEV) {
                             out = __longlong_as_double(0x7FF8000000000000ll);
                         } else {
-                            const double t = i128_to_double_scaled(T[j], ei + fj + Ebase);
+                            const double tv = i128_to_double_scaled(T[j], ei + fj + Ebase);
                             if (plain) {
-                                out = t;
+                                out = tv;
                             } else {
-                                out = __dmul_rn(a.alpha, t);
+                                out = __dmul_rn(a.alpha, tv);
                                 if (a.beta != 0.0) out = __dadd_rn(out, __dmul_rn(a.beta, crow[col]));
                             }
                         }
@@ -353,18 +385,20 @@ __device__ __forceinline__ void products_tile(const TileArgs& a, uint8_t* smem, 
         if (lane == 0 && *abort) {
             // make sure no MMA is still writing the accumulators before freeing them
             volatile int dummy = 0;
-            ptx::mbar_wait_bounded(tmem_full, 0, &dummy, nullptr, 0, kWaitTimeoutNs);
+            ptx::mma_commit(drain);
+            ptx::mbar_wait_bounded(drain, 0, &dummy, nullptr, 0, kWaitTimeoutNs);
         }
         __syncwarp();
         ptx::tmem_dealloc(tmem_base, kTmemCols);
     }
-    __syncthreads();  // the shared memory may be reused by a following tile
 }
 
 __device__ __forceinline__ uint8_t* aligned_smem(uint8_t* raw) {
     return reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(raw) + 1023) & ~(uintptr_t)1023);
 }
 
+// One GEMM: persistent CTAs over its tiles in the rasterised order (groups of 8
+// tile rows sweep the tile columns, so concurrent CTAs share A and B strips in L2).
 template <int S>
 __global__ void __launch_bounds__(kThreads, 1)
     emu_products_kernel(const uint8_t* __restrict__ ad, const uint8_t* __restrict__ bd,
@@ -374,72 +408,71 @@ __global__ void __launch_bounds__(kThreads, 1)
                         uint32_t slot_bytes, unsigned* status) {
     extern __shared__ uint8_t smem_raw[];
     uint8_t* smem = aligned_smem(smem_raw);
-    // tile rasterisation: groups of 8 tile rows sweep the tile columns
-    const int bid = blockIdx.x;
-    const int group_size = 8 * tiles_n;
-    const int first_m = (bid / group_size) * 8;
-    const int gm = min(tiles_m - first_m, 8);
-    const int tm = first_m + (bid % group_size) % gm;
-    const int tn = (bid % group_size) / gm;
-    TileArgs a;
-    a.a_src = ad + (size_t)tm * nkb * S * kBM * kBKBytes;
-    a.b_src = bd + (size_t)tn * nkb * S * kBN * kBKBytes;
-    a.s = S;
-    a.nkb = nkb;
-    a.m = m;
-    a.n = n;
-    a.ldc = ldc;
-    a.row0 = (int64_t)tm * kBM;
-    a.col0 = (int64_t)tn * kBN;
-    a.alpha = alpha;
-    a.beta = beta;
-    a.C = C;
-    a.eA = eA;
-    a.fB = fB;
-    products_tile<S, kblocks_per_stage(S)>(a, smem, stages, slot_bytes, status);
+    auto tile_of = [&](int64_t t) {
+        const int bid = (int)t;
+        const int group_size = 8 * tiles_n;
+        const int first_m = (bid / group_size) * 8;
+        const int gm = min(tiles_m - first_m, 8);
+        const int tm = first_m + (bid % group_size) % gm;
+        const int tn = (bid % group_size) / gm;
+        TileArgs a;
+        a.a_src = ad + (size_t)tm * nkb * S * kBM * kBKBytes;
+        a.b_src = bd + (size_t)tn * nkb * S * kBN * kBKBytes;
+        a.s = S;
+        a.nkb = nkb;
+        a.m = m;
+        a.n = n;
+        a.ldc = ldc;
+        a.row0 = (int64_t)tm * kBM;
+        a.col0 = (int64_t)tn * kBN;
+        a.alpha = alpha;
+        a.beta = beta;
+        a.C = C;
+        a.eA = eA;
+        a.fB = fB;
+        return a;
+    };
+    products_persistent<S, kblocks_per_stage(S)>(tile_of, 0, (int64_t)tiles_m * tiles_n, smem,
+                                                  stages, slot_bytes, status);
 }
 
-// Grouped: one CTA per output tile of any problem of the table (one K block per
-// stage; the problem's slice count selects the unrolled variant).
+// Grouped: persistent CTAs over the tiles [t_begin, t_end) of the problems of one
+// slice count S (the table keeps problems of equal s together).
+template <int S>
 __global__ void __launch_bounds__(kThreads, 1)
-    grouped_products_kernel(const EmuProb* __restrict__ P, int np, int stages,
-                            uint32_t slot_bytes, unsigned* status) {
+    grouped_products_kernel(const EmuProb* __restrict__ P, int np, int64_t t_begin,
+                            int64_t t_end, int stages, uint32_t slot_bytes, unsigned* status) {
     extern __shared__ uint8_t smem_raw[];
     uint8_t* smem = aligned_smem(smem_raw);
-    const int64_t t = blockIdx.x;
-    int lo = 0, hi = np - 1;
-    while (lo < hi) {
-        const int mid = (lo + hi + 1) >> 1;
-        if (P[mid].first_tile <= t) lo = mid; else hi = mid - 1;
-    }
-    const EmuProb& q = P[lo];
-    const int64_t local = t - q.first_tile;
-    const int64_t tm = local / q.tiles_n, tn = local % q.tiles_n;
-    const int nkb = (int)(q.kp / kBKBytes);
-    TileArgs a;
-    a.a_src = q.a_digits + (size_t)tm * nkb * q.s * kBM * kBKBytes;
-    a.b_src = q.b_digits + (size_t)tn * nkb * q.s * kBN * kBKBytes;
-    a.s = q.s;
-    a.nkb = nkb;
-    a.m = q.m;
-    a.n = q.n;
-    a.ldc = q.ldc;
-    a.row0 = tm * kBM;
-    a.col0 = tn * kBN;
-    a.alpha = q.alpha;
-    a.beta = q.beta;
-    a.C = q.C;
-    a.eA = q.a_exp;
-    a.fB = q.b_exp;
-    switch (q.s) {
-#define GB_CASE(SS) \
-    case SS: products_tile<SS, 1>(a, smem, stages, slot_bytes, status); break;
-        GB_CASE(1) GB_CASE(2) GB_CASE(3) GB_CASE(4) GB_CASE(5) GB_CASE(6) GB_CASE(7) GB_CASE(8)
-        GB_CASE(9) GB_CASE(10) GB_CASE(11) GB_CASE(12) GB_CASE(13) GB_CASE(14) GB_CASE(15)
-        GB_CASE(16)
-#undef GB_CASE
-        default: break;
-    }
+    auto tile_of = [&](int64_t t) {
+        int lo = 0, hi = np - 1;
+        while (lo < hi) {
+            const int mid = (lo + hi + 1) >> 1;
+            if (P[mid].first_tile <= t) lo = mid; else hi = mid - 1;
+        }
+        const EmuProb& q = P[lo];
+        const int64_t local = t - q.first_tile;
+        const int64_t tm = local / q.tiles_n, tn = local % q.tiles_n;
+        const int nkb = (int)(q.kp / kBKBytes);
+        TileArgs a;
+        a.a_src = q.a_digits + (size_t)tm * nkb * S * kBM * kBKBytes;
+        a.b_src = q.b_digits + (size_t)tn * nkb * S * kBN * kBKBytes;
+        a.s = S;
+        a.nkb = nkb;
+        a.m = q.m;
+        a.n = q.n;
+        a.ldc = q.ldc;
+        a.row0 = tm * kBM;
+        a.col0 = tn * kBN;
+        a.alpha = q.alpha;
+        a.beta = q.beta;
+        a.C = q.C;
+        a.eA = q.a_exp;
+        a.fB = q.b_exp;
+        return a;
+    };
+    products_persistent<S, kblocks_per_stage(S)>(tile_of, t_begin, t_end, smem, stages,
+                                                  slot_bytes, status);
 }
 
 struct RingShape {
@@ -473,13 +506,34 @@ cudaError_t launch_products_s(const Launch& L, int64_t m, int64_t n, int64_t kp,
     if (e != cudaSuccess) return e;
     const int tiles_m = (int)((m + kBM - 1) / kBM), tiles_n = (int)((n + kBN - 1) / kBN);
     const int nkb = (int)(kp / kBKBytes);
-    emu_products_kernel<S><<<tiles_m * tiles_n, kThreads, r.smem, L.stream>>>(
+    const int64_t tiles = (int64_t)tiles_m * tiles_n;
+    const int grid = (int)(tiles < L.sm_count ? tiles : L.sm_count);
+    emu_products_kernel<S><<<grid, kThreads, r.smem, L.stream>>>(
         ad, bd, m, n, nkb, alpha, beta, C, ldc, ea, fb, tiles_m, tiles_n, r.stages,
         r.slot_bytes, L.status);
     return cudaGetLastError();
 }
 
+template <int S>
+cudaError_t launch_grouped_s(const Launch& L, const EmuProb* probs, int np, int64_t t_begin,
+                             int64_t t_end) {
+    const RingShape r = ring_for(S, kblocks_per_stage(S));
+    if (r.stages < 2) return cudaErrorInvalidValue;
+    cudaError_t e = allow_smem(grouped_products_kernel<S>);
+    if (e != cudaSuccess) return e;
+    const int64_t tiles = t_end - t_begin;
+    const int grid = (int)(tiles < L.sm_count ? tiles : L.sm_count);
+    grouped_products_kernel<S><<<grid, kThreads, r.smem, L.stream>>>(probs, np, t_begin, t_end,
+                                                                     r.stages, r.slot_bytes,
+                                                                     L.status);
+    return cudaGetLastError();
+}
+
 }  // namespace
+
+#define GB_CASES(CALL)                                                                     \
+    CALL(1) CALL(2) CALL(3) CALL(4) CALL(5) CALL(6) CALL(7) CALL(8) CALL(9) CALL(10)       \
+        CALL(11) CALL(12) CALL(13) CALL(14) CALL(15) CALL(16)
 
 cudaError_t launch_emu_products(const Launch& L, int s, int64_t m, int64_t n, int64_t k,
                                 double alpha, double beta, double* C, int64_t ldc,
@@ -492,24 +546,22 @@ cudaError_t launch_emu_products(const Launch& L, int s, int64_t m, int64_t n, in
     case SS:                                                                                 \
         return launch_products_s<SS>(L, m, n, kp, alpha, beta, C, ldc, a_digits, b_digits, \
                                      a_exp, b_exp);
-        GB_CASE(1) GB_CASE(2) GB_CASE(3) GB_CASE(4) GB_CASE(5) GB_CASE(6) GB_CASE(7) GB_CASE(8)
-        GB_CASE(9) GB_CASE(10) GB_CASE(11) GB_CASE(12) GB_CASE(13) GB_CASE(14) GB_CASE(15)
-        GB_CASE(16)
+        GB_CASES(GB_CASE)
 #undef GB_CASE
         default: return cudaErrorInvalidValue;
     }
 }
 
 cudaError_t launch_grouped_products(const Launch& L, const EmuProb* probs, int np,
-                                    int64_t total_tiles, int max_s) {
-    if (np == 0 || total_tiles == 0) return cudaSuccess;
-    const RingShape r = ring_for(max_s, 1);
-    if (r.stages < 2) return cudaErrorInvalidValue;
-    cudaError_t e = allow_smem(grouped_products_kernel);
-    if (e != cudaSuccess) return e;
-    grouped_products_kernel<<<(unsigned)total_tiles, kThreads, r.smem, L.stream>>>(
-        probs, np, r.stages, r.slot_bytes, L.status);
-    return cudaGetLastError();
+                                    int64_t t_begin, int64_t t_end, int s) {
+    if (np == 0 || t_end <= t_begin) return cudaSuccess;
+    switch (s) {
+#define GB_CASE(SS) \
+    case SS: return launch_grouped_s<SS>(L, probs, np, t_begin, t_end);
+        GB_CASES(GB_CASE)
+#undef GB_CASE
+        default: return cudaErrorInvalidValue;
+    }
 }
 
 }  // namespace gb
