@@ -5,9 +5,9 @@
  * with the conventions and accuracy contract of gb_gemm.h.  The grid level of
  * the work division (Section 3.2) becomes persistent: a fixed grid of CTAs
  * (SM count x resident CTAs per SM) takes tiles of all problems from a device
- * counter, expensive tiles first; emulated problems run the split-precision
- * steps for all of them in one launch each.  A plan records the launches in a
- * CUDA graph once and replays it.
+ * counter, expensive tiles first; emulated problems run each split-precision
+ * step in one launch per distinct slice count (four launches per slice count).
+ * A plan records the launches in a CUDA graph once and replays it.
  *
  * Ownership: descriptors are read during the call only; A, B, C and the
  * workspace are the caller's device buffers and must stay valid while a plan

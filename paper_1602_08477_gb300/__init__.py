@@ -34,3 +34,4 @@ from .grouped import (  # noqa: E402,F401
 )
 from .serve import Server, fill_uniform  # noqa: E402,F401
 from .execute import daxpy, enqueue, kernel_handle  # noqa: E402,F401
+from .mem import Buffer, OwnedQueue, copy, dgemm_buffers  # noqa: E402,F401

@@ -280,7 +280,7 @@ gb_status gb_queue_create(gb_device* dev, void* cuda_stream, int blocking, gb_qu
         cudaFree(st);
         return cuda_fail(e, "clearing the queue status word");
     }
-    gb_queue* q = new (std::nothrow) gb_queue{dev, (cudaStream_t)cuda_stream, blocking, st};
+    gb_queue* q = new (std::nothrow) gb_queue{dev, (cudaStream_t)cuda_stream, blocking, st, false};
     if (!q) {
         cudaFree(st);
         return invalid("out of host memory");
@@ -304,6 +304,7 @@ gb_status gb_queue_destroy(gb_queue* q) {
     DeviceScope scope(q->dev->idx);
     cudaStreamSynchronize(q->stream);
     cudaFree(q->status);
+    if (q->owns_stream) cudaStreamDestroy(q->stream);
     delete q;
     return GB_OK;
 }

@@ -25,9 +25,9 @@ struct gb_grouped_plan {
     int grid_native;
     gb::EmuProb* d_emu;
     int n_emu;
-    int64_t emu_rows, emu_colblks, emu_tblks, emu_tiles;
+    int64_t emu_tiles;
     int max_s;
-    std::vector<int64_t> s_ranges;  // (s, t_begin, t_end) triples of the emulated tiles
+    std::vector<gb::EmuSRange> s_ranges;  // one per distinct slice count
     int launches;
     double flops;
 };
@@ -65,7 +65,7 @@ struct Layout {
     std::vector<EmuProb> emu;
     std::vector<EmuLayout> emu_ws;
     std::vector<int64_t> emu_idx;   // descriptor index of each emulated problem
-    std::vector<int64_t> s_ranges;  // (s, t_begin, t_end) per distinct slice count
+    std::vector<EmuSRange> s_ranges;  // one per distinct slice count
     size_t off_counter = 0, off_native = 0, off_emu = 0, off_data = 0, total = 0;
     int max_s = 0;
     double flops = 0;
@@ -178,15 +178,15 @@ gb_status build_layout(const gb_gemm_desc* d, int64_t count, Layout& L) {
         rows += (e.m + kEmuBM - 1) / kEmuBM * kEmuBM;
         colblks += ncb;
         tblks += ncb * ((w.kp + 63) / 64);
-        const int64_t t_new = tiles + ((e.m + kEmuBM - 1) / kEmuBM) * e.tiles_n;
-        if (L.s_ranges.empty() || L.s_ranges[L.s_ranges.size() - 3] != e.s) {
-            L.s_ranges.push_back(e.s);
-            L.s_ranges.push_back(tiles);
-            L.s_ranges.push_back(t_new);
-        } else {
-            L.s_ranges.back() = t_new;
-        }
-        tiles = t_new;
+        tiles += ((e.m + kEmuBM - 1) / kEmuBM) * e.tiles_n;
+        if (L.s_ranges.empty() || L.s_ranges.back().s != e.s)
+            L.s_ranges.push_back(EmuSRange{e.s, e.first_row, 0, e.first_colblk, 0, e.first_tblk,
+                                           0, e.first_tile, 0});
+        EmuSRange& r = L.s_ranges.back();
+        r.row_end = rows;
+        r.cb_end = colblks;
+        r.tb_end = tblks;
+        r.t_end = tiles;
         off += w.total;
     }
     L.total = off;
@@ -240,17 +240,13 @@ gb_status grouped_enqueue_async(const Launch& L, const gb_gemm_desc* descs, int6
         ++nl;
     }
     if (e == cudaSuccess && !lay.emu.empty()) {
-        const EmuProb& l = lay.emu.back();
-        const int64_t ncb = (l.n + 31) / 32;
         EmuProb* d = reinterpret_cast<EmuProb*>(dev + lay.off_emu);
-        e = launch_grouped_split(L, d, (int)lay.emu.size(),
-                                 l.first_row + (l.m + kEmuBM - 1) / kEmuBM * kEmuBM,
-                                 l.first_colblk + ncb, l.first_tblk + ncb * ((l.kp + 63) / 64));
-        nl += 3;
-        for (size_t r = 0; r + 2 < lay.s_ranges.size() && e == cudaSuccess; r += 3) {
-            e = launch_grouped_products(L, d, (int)lay.emu.size(), lay.s_ranges[r + 1],
-                                        lay.s_ranges[r + 2], (int)lay.s_ranges[r]);
-            ++nl;
+        for (size_t r = 0; r < lay.s_ranges.size() && e == cudaSuccess; ++r) {
+            e = launch_grouped_split(L, d, (int)lay.emu.size(), lay.s_ranges[r]);
+            if (e == cudaSuccess)
+                e = launch_grouped_products(L, d, (int)lay.emu.size(), lay.s_ranges[r].t_begin,
+                                            lay.s_ranges[r].t_end, lay.s_ranges[r].s);
+            nl += 4;
         }
     }
     if (launches) *launches = nl;
@@ -321,11 +317,11 @@ static gb_status enqueue_plan(gb_grouped_plan* p, cudaStream_t stream) {
             e = launch_grouped_native(L, p->d_native, p->n_native, p->native_tiles, p->d_counter,
                                       p->grid_native);
     }
-    if (e == cudaSuccess && p->n_emu > 0) {
-        e = launch_grouped_split(L, p->d_emu, p->n_emu, p->emu_rows, p->emu_colblks, p->emu_tblks);
-        for (size_t r = 0; r + 2 < p->s_ranges.size() && e == cudaSuccess; r += 3)
-            e = launch_grouped_products(L, p->d_emu, p->n_emu, p->s_ranges[r + 1],
-                                        p->s_ranges[r + 2], (int)p->s_ranges[r]);
+    for (size_t r = 0; r < p->s_ranges.size() && e == cudaSuccess; ++r) {
+        e = launch_grouped_split(L, p->d_emu, p->n_emu, p->s_ranges[r]);
+        if (e == cudaSuccess)
+            e = launch_grouped_products(L, p->d_emu, p->n_emu, p->s_ranges[r].t_begin,
+                                        p->s_ranges[r].t_end, p->s_ranges[r].s);
     }
     if (e != cudaSuccess) return cuda_fail(e, "grouped launch");
     return GB_OK;
@@ -376,14 +372,7 @@ gb_status gb_grouped_plan_create(gb_queue* q, const gb_gemm_desc* descs, int64_t
     }
     p->d_emu = reinterpret_cast<EmuProb*>(ws + L.off_emu);
     p->n_emu = (int)L.emu.size();
-    if (!L.emu.empty()) {
-        const EmuProb& e = L.emu.back();
-        const int64_t ncb = (e.n + 31) / 32;
-        p->emu_rows = e.first_row + (e.m + kEmuBM - 1) / kEmuBM * kEmuBM;
-        p->emu_colblks = e.first_colblk + ncb;
-        p->emu_tblks = e.first_tblk + ncb * ((e.kp + 63) / 64);
-        p->emu_tiles = e.first_tile + ((e.m + kEmuBM - 1) / kEmuBM) * e.tiles_n;
-    }
+    p->emu_tiles = L.s_ranges.empty() ? 0 : L.s_ranges.back().t_end;
     p->max_s = L.max_s;
     p->s_ranges = L.s_ranges;
     p->flops = L.flops;
@@ -392,7 +381,7 @@ gb_status gb_grouped_plan_create(gb_queue* q, const gb_gemm_desc* descs, int64_t
     if (grid > p->native_tiles) grid = p->native_tiles;
     p->grid_native = (int)(grid > 0 ? grid : 1);
     p->launches = (p->native_tiles > 0 ? 1 : 0) +
-                  (p->n_emu > 0 ? 3 + (int)(L.s_ranges.size() / 3) : 0);
+                  4 * (int)L.s_ranges.size();
 
     cudaError_t e = cudaSuccess;
     if (!L.native.empty())

@@ -18,6 +18,7 @@ struct gb_queue {
     cudaStream_t stream;
     int blocking;
     unsigned* status;  // device status word (kStatus* bits)
+    bool owns_stream;  // created by gb_queue_create_owned: destroyed with the queue
 };
 
 namespace gb {

@@ -107,9 +107,20 @@ struct EmuProb {
     int64_t first_tile;    // 128 x 32 output tiles
 };
 
-// Grouped e1 + e2 over a table of emulated problems (three launches).
+// The emulated problems of one slice count s occupy consecutive table entries;
+// their rows, column blocks, transpose blocks and output tiles are the ranges
+// [*_begin, *_end) of the table's prefixes.
+struct EmuSRange {
+    int s;
+    int64_t row_begin, row_end;
+    int64_t cb_begin, cb_end;
+    int64_t tb_begin, tb_end;
+    int64_t t_begin, t_end;
+};
+
+// Grouped e1 + e2 over the problems of one slice-count range (three launches).
 cudaError_t launch_grouped_split(const Launch& L, const EmuProb* probs, int np,
-                                 int64_t total_rows, int64_t total_colblks, int64_t total_tblks);
+                                 const EmuSRange& r);
 // Grouped e3 + e4: persistent CTAs over the 128 x 32 output tiles
 // [t_begin, t_end) of the table, all of whose problems use s slices.
 cudaError_t launch_grouped_products(const Launch& L, const EmuProb* probs, int np,

@@ -29,17 +29,14 @@ namespace {
 constexpr int kB1 = 4;   // bits of the first digit
 constexpr int kB = 5;    // bits of every further digit
 
-// E4M3 encodings of the integers 0..16 (sign bit 7, exponent bias 7, 3 mantissa bits).
+// E4M3 encoding (sign bit 7, exponent bias 7, 3 mantissa bits) of an integer
+// d with |d| <= 16: magnitudes 0..7 from a byte table (prmt), 8..16 are
+// exponent 10 or 11 with mantissa a - 8 or (a - 16) / 2, i.e. code 0x48 + a.
 __device__ __forceinline__ uint32_t e4m3_of_int(int d) {
     const uint32_t a = (uint32_t)(d < 0 ? -d : d);
-    uint32_t code;
-    if (a == 0) {
-        code = 0;
-    } else {
-        const int E = 31 - __clz(a);                     // 0..4
-        const uint32_t mant = ((a << 3) >> E) & 7u;      // exact for a <= 16
-        code = ((uint32_t)(E + 7) << 3) | mant;
-    }
+    // codes of 0..7: 00 38 40 44 | 48 4A 4C 4E
+    const uint32_t lo = __byte_perm(0x44403800u, 0x4E4C4A48u, a & 7u) & 0xFFu;
+    const uint32_t code = a >= 8 ? 0x48u + a : lo;
     return (d < 0 ? 0x80u : 0u) | code;
 }
 
@@ -54,8 +51,14 @@ __device__ __forceinline__ int frexp_exp_bits(uint64_t absbits) {
 
 // The s digits of one finite double x relative to line exponent e, packed as
 // E4M3 bytes into out[t] (byte lane `lane` of a 64-bit word).
-// S: compile-time maximum of the slice count s (the single-GEMM kernels pass
-// s == S, so the loop bound is a constant).
+// S: compile-time maximum of the slice count s.
+//
+// With x = X 2^E2 (X the signed integer significand) and sh_t = e - 4 - E2 -
+// 5 (t - 1), the recurrence above satisfies  r_t 2^(...) = X - Q_t 2^(sh_t)  with
+// Q_t = RNE(X / 2^(sh_t)) (round to nearest, ties to even): subtracting the
+// integer multiple 32 Q_(t-1) commutes with RNE.  Hence every digit is
+// d_t = Q_t - 32 Q_(t-1), computed independently of the others; |d_t| <= 16,
+// so the low 32 bits of each Q_t suffice (wrapping arithmetic).
 template <int S>
 __device__ __forceinline__ void digits_of(uint64_t bits, int e, int s, int lane,
                                           uint64_t (&out)[S]) {
@@ -68,30 +71,29 @@ __device__ __forceinline__ void digits_of(uint64_t bits, int e, int s, int lane,
         M |= (int64_t)1 << 52;
         E2 = ef - 1075;
     }
-    int64_t R = (bits >> 63) ? -M : M;
-    int sh = e - kB1 - E2;  // y_1 = R / 2^sh
+    const int64_t X = (bits >> 63) ? -M : M;
+    const int sh1 = e - kB1 - E2;
+    uint32_t qprev = 0;
 #pragma unroll
     for (int t = 0; t < S; ++t) {
         if (t >= s) break;
-        int64_t d;
-        if (R == 0 || sh >= 55) {
-            d = 0;                         // |R| < 2^53 <= 2^(sh-2): |y| < 1/2
+        const int sh = sh1 - kB * t;
+        uint32_t q;
+        if (sh >= 55) {
+            q = 0;  // |X| < 2^53 <= 2^(sh-2): |X / 2^sh| < 1/4
         } else if (sh <= 0) {
-            d = R * ((int64_t)1 << (-sh));  // y is an integer
-            R = 0;
+            q = -sh >= 64 ? 0u : (uint32_t)((uint64_t)X << (-sh));
         } else {
-            int64_t q = R >> sh;           // floor
-            const int64_t fr = R - (q << sh);
-            const int64_t half = (int64_t)1 << (sh - 1);
-            if (fr > half || (fr == half && (q & 1))) q += 1;
-            d = q;
-            R -= q << sh;
+            // RNE by add-and-shift: floor((X + 2^(sh-1) - 1 + lsb) / 2^sh),
+            // lsb = floor(X / 2^sh) & 1
+            const int64_t lsb = (X >> sh) & 1;
+            q = (uint32_t)((X + (((int64_t)1 << (sh - 1)) - 1) + lsb) >> sh);
         }
-        out[t] |= (uint64_t)e4m3_of_int((int)d) << (8 * lane);
-        sh -= kB;
+        const int d = (int)(q - (qprev << kB));
+        qprev = q;
+        out[t] |= (uint64_t)e4m3_of_int(d) << (8 * lane);
     }
 }
-
 
 // Byte offset of digit t of line x at K index l0 (l0 % 8 == 0; the 8 bytes
 // l0 .. l0+7 are contiguous) in the tiled layout with R-line tiles.
@@ -124,10 +126,18 @@ __device__ __forceinline__ void split_one_row(int64_t i, int64_t m, int64_t k,
     const uint64_t* row = reinterpret_cast<const uint64_t*>(A + i * lda);
     uint64_t mx = 0;
     int bad = 0;
-    for (int64_t l = tid; l < k; l += blockDim.x) {
-        const uint64_t a = row[l] & 0x7FFFFFFFFFFFFFFFull;
-        if (a >= 0x7FF0000000000000ull) bad = 1;
-        else if (a > mx) mx = a;
+    // the same 8 consecutive elements per thread as the digit pass (L1 reuse),
+    // eight independent loads in flight per thread
+    for (int64_t l0 = (int64_t)tid * 8; l0 < k; l0 += (int64_t)blockDim.x * 8) {
+        uint64_t v[8];
+#pragma unroll
+        for (int u = 0; u < 8; ++u) v[u] = l0 + u < k ? row[l0 + u] : 0ull;
+#pragma unroll
+        for (int u = 0; u < 8; ++u) {
+            const uint64_t a = v[u] & 0x7FFFFFFFFFFFFFFFull;
+            bad |= a >= 0x7FF0000000000000ull;
+            mx = (a < 0x7FF0000000000000ull && a > mx) ? a : mx;
+        }
     }
     for (int o = 16; o > 0; o >>= 1) {
         const uint64_t v = __shfl_xor_sync(0xffffffffu, mx, o);
@@ -297,38 +307,100 @@ __device__ __forceinline__ int find_prob(const EmuProb* __restrict__ P, int np,
     return lo;
 }
 
-__global__ void __launch_bounds__(128) grouped_split_rows_kernel(const EmuProb* __restrict__ P,
-                                                                 int np, int64_t total_rows,
+// Row i of A by one warp (grouped problems have short rows): both passes take
+// 8 consecutive elements per lane and step (the digit pass re-reads them from
+// L1).  No block-wide barrier.
+template <int S>
+__device__ __forceinline__ void split_row_warp(int64_t i, int64_t m, int64_t k,
+                                               const double* __restrict__ A, int64_t lda,
+                                               uint8_t* __restrict__ digits, int64_t kp,
+                                               int32_t* __restrict__ exps, unsigned* status) {
+    const int lane = threadIdx.x & 31;
+    const int64_t nkb = kp >> 5;
+    if (i >= m) {
+        for (int64_t l0 = (int64_t)lane * 8; l0 < kp; l0 += 256)
+#pragma unroll
+            for (int t = 0; t < S; ++t)
+                *reinterpret_cast<uint64_t*>(digits + tiled_offset(i, l0, t, S, nkb, kEmuBM)) = 0;
+        return;
+    }
+    const uint64_t* row = reinterpret_cast<const uint64_t*>(A + i * lda);
+    uint64_t mx = 0;
+    unsigned bad = 0;
+    for (int64_t l0 = (int64_t)lane * 8; l0 < k; l0 += 256) {
+        uint64_t v[8];
+#pragma unroll
+        for (int u = 0; u < 8; ++u) v[u] = l0 + u < k ? row[l0 + u] : 0ull;
+#pragma unroll
+        for (int u = 0; u < 8; ++u) {
+            const uint64_t a = v[u] & 0x7FFFFFFFFFFFFFFFull;
+            bad |= a >= 0x7FF0000000000000ull;
+            mx = (a < 0x7FF0000000000000ull && a > mx) ? a : mx;
+        }
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        const uint64_t v = __shfl_xor_sync(0xffffffffu, mx, o);
+        mx = v > mx ? v : mx;
+    }
+    const bool is_bad = __any_sync(0xffffffffu, bad) != 0;
+    const int e = frexp_exp_bits(mx);
+    if (lane == 0) {
+        exps[i] = is_bad ? GB_BAD_LINE_DEV : e;
+        if (is_bad && status) atomicOr(status, kStatusNonfinite);
+    }
+    for (int64_t l0 = (int64_t)lane * 8; l0 < kp; l0 += 256) {
+        uint64_t w[S];
+#pragma unroll
+        for (int t = 0; t < S; ++t) w[t] = 0;
+        if (!is_bad) {
+#pragma unroll
+            for (int u = 0; u < 8; ++u)
+                if (l0 + u < k) digits_of<S>(row[l0 + u], e, S, u, w);
+        }
+#pragma unroll
+        for (int t = 0; t < S; ++t)
+            *reinterpret_cast<uint64_t*>(digits + tiled_offset(i, l0, t, S, nkb, kEmuBM)) = w[t];
+    }
+}
+
+// Grouped kernels: one launch per step over the problems of one slice count S.
+template <int S>
+__global__ void __launch_bounds__(256) grouped_split_rows_kernel(const EmuProb* __restrict__ P,
+                                                                 int np, int64_t row_begin,
+                                                                 int64_t row_end,
                                                                  unsigned* status) {
-    __shared__ uint64_t red[4];
-    __shared__ int bad_sh;
-    for (int64_t r = blockIdx.x; r < total_rows; r += gridDim.x) {
+    const int64_t warps = (int64_t)gridDim.x * 8;
+    for (int64_t r = row_begin + (int64_t)blockIdx.x * 8 + (threadIdx.x >> 5); r < row_end;
+         r += warps) {
         const EmuProb& q = P[find_prob(P, np, &EmuProb::first_row, r)];
-        split_one_row<16>(r - q.first_row, q.m, q.k, q.A, q.lda, q.s, q.a_digits, q.kp, q.a_exp,
-                          status, red, &bad_sh);
+        split_row_warp<S>(r - q.first_row, q.m, q.k, q.A, q.lda, q.a_digits, q.kp, q.a_exp,
+                          status);
     }
 }
 
 __global__ void __launch_bounds__(256) grouped_colmax_kernel(const EmuProb* __restrict__ P,
-                                                             int np, int64_t total_blocks,
-                                                             unsigned* status) {
+                                                             int np, int64_t cb_begin,
+                                                             int64_t cb_end, unsigned* status) {
     __shared__ uint64_t mx_sh[8][32];
     __shared__ int bad_sh[8][32];
-    for (int64_t b = blockIdx.x; b < total_blocks; b += gridDim.x) {
+    for (int64_t b = cb_begin + blockIdx.x; b < cb_end; b += gridDim.x) {
         const EmuProb& q = P[find_prob(P, np, &EmuProb::first_colblk, b)];
         colmax_block(b - q.first_colblk, q.n, q.k, q.B, q.ldb, q.b_exp, status, mx_sh, bad_sh);
     }
 }
 
+template <int S>
 __global__ void __launch_bounds__(256) grouped_split_cols_kernel(const EmuProb* __restrict__ P,
-                                                                 int np, int64_t total_tiles) {
+                                                                 int np, int64_t tb_begin,
+                                                                 int64_t tb_end) {
     __shared__ uint64_t T[64][33];
-    for (int64_t b = blockIdx.x; b < total_tiles; b += gridDim.x) {
+    for (int64_t b = tb_begin + blockIdx.x; b < tb_end; b += gridDim.x) {
         const EmuProb& q = P[find_prob(P, np, &EmuProb::first_tblk, b)];
         const int64_t local = b - q.first_tblk;
         const int64_t ncb = (q.n + 31) / 32;
-        split_cols_tile<16>(local % ncb, local / ncb, q.n, q.k, q.B, q.ldb, q.s, q.b_digits, q.kp,
-                            q.b_exp, T);
+        split_cols_tile<S>(local % ncb, local / ncb, q.n, q.k, q.B, q.ldb, S, q.b_digits, q.kp,
+                           q.b_exp, T);
     }
 }
 
@@ -349,17 +421,27 @@ cudaError_t launch_split_rows(const Launch& L, int s, int64_t m, int64_t k, cons
 }
 
 cudaError_t launch_grouped_split(const Launch& L, const EmuProb* probs, int np,
-                                 int64_t total_rows, int64_t total_colblks, int64_t total_tblks) {
+                                 const EmuSRange& r) {
     if (np == 0) return cudaSuccess;
     const int64_t cap = (int64_t)L.sm_count * 16;
     auto g = [&](int64_t x) { return (unsigned)(x < cap ? (x > 0 ? x : 1) : cap); };
-    grouped_split_rows_kernel<<<g(total_rows), 128, 0, L.stream>>>(probs, np, total_rows, L.status);
+    const unsigned g_rows = g((r.row_end - r.row_begin + 7) / 8);
+#define GB_LAUNCH_GROWS(SS)                                                                    \
+    grouped_split_rows_kernel<SS><<<g_rows, 256, 0, L.stream>>>(probs, np, r.row_begin,        \
+                                                                r.row_end, L.status)
+    GB_SWITCH_S(r.s, GB_LAUNCH_GROWS)
+#undef GB_LAUNCH_GROWS
     cudaError_t err = cudaGetLastError();
     if (err != cudaSuccess) return err;
-    grouped_colmax_kernel<<<g(total_colblks), 256, 0, L.stream>>>(probs, np, total_colblks, L.status);
+    grouped_colmax_kernel<<<g(r.cb_end - r.cb_begin), 256, 0, L.stream>>>(probs, np, r.cb_begin,
+                                                                           r.cb_end, L.status);
     err = cudaGetLastError();
     if (err != cudaSuccess) return err;
-    grouped_split_cols_kernel<<<g(total_tblks), 256, 0, L.stream>>>(probs, np, total_tblks);
+#define GB_LAUNCH_GCOLS(SS)                                                                    \
+    grouped_split_cols_kernel<SS><<<g(r.tb_end - r.tb_begin), 256, 0, L.stream>>>(             \
+        probs, np, r.tb_begin, r.tb_end)
+    GB_SWITCH_S(r.s, GB_LAUNCH_GCOLS)
+#undef GB_LAUNCH_GCOLS
     return cudaGetLastError();
 }
 

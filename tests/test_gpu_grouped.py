@@ -114,6 +114,34 @@ def test_emulated_and_mixed_group(gb):
     plan.close()
 
 
+def test_emulated_group_with_several_slice_counts(gb):
+    """Problems of different s run in one launch set per slice count (split rows,
+    column maxima, split columns, products); each equals its single launch."""
+    import torch
+    ms, ns, ks = g.grouped_problems(5519, 24)
+    slices = [3, 16, 8, 12]
+    probs, host = [], []
+    for i, (m, n, k) in enumerate(zip(ms, ns, ks)):
+        A = g.matrix("hard", int(m), int(k), 5519 + i, 0)
+        B = g.matrix("hard", int(k), int(n), 5519 + i, 1)
+        C0 = g.matrix("uniform", int(m), int(n), 5519 + i, 2)
+        probs.append(dict(A=to_dev(A), B=to_dev(B), C=to_dev(C0), alpha=-0.75, beta=0.5,
+                          precision="emulated", slices=slices[i % 4]))
+        host.append((A, B, C0))
+    plan = gb.GroupedPlan(probs, use_graph=True)
+    plan.run()
+    torch.cuda.synchronize()
+    info = plan.info()
+    assert info["native_tiles"] == 0 and info["launches"] == 4 * len(set(slices))
+    for p, (A, B, C0) in zip(probs, host):
+        single = to_dev(C0)
+        gb.dgemm(to_dev(A), to_dev(B), single, p["alpha"], p["beta"], precision="emulated",
+                 slices=p["slices"])
+        torch.cuda.synchronize()
+        assert torch.equal(p["C"], single)
+    plan.close()
+
+
 def test_edge_problems_in_a_group(gb):
     import torch
     A, B, C0 = (g.matrix("uniform", 40, 30, 9, 0), g.matrix("uniform", 30, 20, 9, 1),
