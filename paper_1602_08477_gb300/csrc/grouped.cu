@@ -24,6 +24,7 @@ struct gb_grouped_plan {
     unsigned long long* d_counter;
     int grid_native;
     gb::EmuProb* d_emu;
+    gb::EmuKeys d_keys;
     int n_emu;
     int64_t emu_tiles;
     int max_s;
@@ -66,7 +67,9 @@ struct Layout {
     std::vector<EmuLayout> emu_ws;
     std::vector<int64_t> emu_idx;   // descriptor index of each emulated problem
     std::vector<EmuSRange> s_ranges;  // one per distinct slice count
-    size_t off_counter = 0, off_native = 0, off_emu = 0, off_data = 0, total = 0;
+    std::vector<int64_t> keys[4];     // compact prefixes: rows, column blocks, tblks, tiles
+    size_t off_counter = 0, off_native = 0, off_emu = 0, off_keys[4] = {0, 0, 0, 0};
+    size_t off_data = 0, total = 0;
     int max_s = 0;
     double flops = 0;
 };
@@ -141,12 +144,15 @@ gb_status build_layout(const gb_gemm_desc* d, int64_t count, Layout& L) {
         p.first_tile = t;
         t += ((p.m + tile_bm(p.tile) - 1) / tile_bm(p.tile)) * p.tiles_n;
     }
-    // emulated problems of equal slice count together: one persistent launch each
+    // emulated problems of equal slice count together (one launch set each),
+    // long-K problems first within a slice count (their tiles cost the most)
     {
         std::vector<size_t> perm(L.emu.size());
         for (size_t i = 0; i < perm.size(); ++i) perm[i] = i;
-        std::stable_sort(perm.begin(), perm.end(),
-                         [&](size_t a, size_t b) { return L.emu[a].s < L.emu[b].s; });
+        std::stable_sort(perm.begin(), perm.end(), [&](size_t a, size_t b) {
+            if (L.emu[a].s != L.emu[b].s) return L.emu[a].s < L.emu[b].s;
+            return L.emu_ws[a].kp > L.emu_ws[b].kp;
+        });
         std::vector<EmuProb> e2;
         std::vector<EmuLayout> w2;
         std::vector<int64_t> i2;
@@ -162,7 +168,12 @@ gb_status build_layout(const gb_gemm_desc* d, int64_t count, Layout& L) {
     L.off_counter = 0;
     L.off_native = 256;
     L.off_emu = up256(L.off_native + sizeof(GroupProb) * L.native.size());
-    L.off_data = ((L.off_emu + sizeof(EmuProb) * L.emu.size()) + 1023) & ~(size_t)1023;
+    size_t kend = up256(L.off_emu + sizeof(EmuProb) * L.emu.size());
+    for (int a = 0; a < 4; ++a) {
+        L.off_keys[a] = kend;
+        kend = up256(kend + sizeof(int64_t) * L.emu.size());
+    }
+    L.off_data = (kend + 1023) & ~(size_t)1023;
     size_t off = L.off_data;
     int64_t rows = 0, colblks = 0, tblks = 0, tiles = 0;
     for (size_t i = 0; i < L.emu.size(); ++i) {
@@ -174,15 +185,22 @@ gb_status build_layout(const gb_gemm_desc* d, int64_t count, Layout& L) {
         e.first_colblk = colblks;
         e.first_tblk = tblks;
         e.first_tile = tiles;
+        L.keys[0].push_back(rows);
+        L.keys[1].push_back(colblks);
+        L.keys[2].push_back(tblks);
+        L.keys[3].push_back(tiles);
         const int64_t ncb = (e.n + 31) / 32;
         rows += (e.m + kEmuBM - 1) / kEmuBM * kEmuBM;
         colblks += ncb;
         tblks += ncb * ((w.kp + 63) / 64);
-        tiles += ((e.m + kEmuBM - 1) / kEmuBM) * e.tiles_n;
+        const int64_t nt = ((e.m + kEmuBM - 1) / kEmuBM) * e.tiles_n;
+        tiles += nt;
         if (L.s_ranges.empty() || L.s_ranges.back().s != e.s)
-            L.s_ranges.push_back(EmuSRange{e.s, e.first_row, 0, e.first_colblk, 0, e.first_tblk,
-                                           0, e.first_tile, 0});
+            L.s_ranges.push_back(EmuSRange{e.s, (int)i, 0, e.first_row, 0, e.first_colblk, 0,
+                                           e.first_tblk, 0, e.first_tile, 0, 0});
         EmuSRange& r = L.s_ranges.back();
+        r.q_end = (int)i + 1;
+        r.kp_max = std::max(r.kp_max, w.kp);
         r.row_end = rows;
         r.cb_end = colblks;
         r.tb_end = tblks;
@@ -193,10 +211,19 @@ gb_status build_layout(const gb_gemm_desc* d, int64_t count, Layout& L) {
     return GB_OK;
 }
 
+EmuKeys keys_at(uint8_t* base, const Layout& L) {
+    return EmuKeys{reinterpret_cast<const int64_t*>(base + L.off_keys[0]),
+                   reinterpret_cast<const int64_t*>(base + L.off_keys[1]),
+                   reinterpret_cast<const int64_t*>(base + L.off_keys[2]),
+                   reinterpret_cast<const int64_t*>(base + L.off_keys[3])};
+}
+
 }  // namespace
 
 size_t grouped_table_bytes(int64_t count) {
-    return 256 + ((sizeof(GroupProb) * count + 255) & ~(size_t)255) + sizeof(EmuProb) * count + 1024;
+    const size_t c = (size_t)count;
+    return 256 + up256(sizeof(GroupProb) * c) + up256(sizeof(EmuProb) * c) +
+           4 * up256(sizeof(int64_t) * c) + 1024;
 }
 
 gb_status grouped_enqueue_async(const Launch& L, const gb_gemm_desc* descs, int64_t count,
@@ -224,8 +251,11 @@ gb_status grouped_enqueue_async(const Launch& L, const gb_gemm_desc* descs, int6
     std::memset(stg, 0, 256);
     if (!lay.native.empty())
         std::memcpy(stg + lay.off_native, lay.native.data(), sizeof(GroupProb) * lay.native.size());
-    if (!lay.emu.empty())
+    if (!lay.emu.empty()) {
         std::memcpy(stg + lay.off_emu, lay.emu.data(), sizeof(EmuProb) * lay.emu.size());
+        for (int a = 0; a < 4; ++a)
+            std::memcpy(stg + lay.off_keys[a], lay.keys[a].data(), sizeof(int64_t) * lay.emu.size());
+    }
     cudaError_t e = cudaMemcpyAsync(dev, stg, lay.off_data, cudaMemcpyHostToDevice, L.stream);
     int64_t nl = 0;
     if (e == cudaSuccess && !lay.native.empty()) {
@@ -241,11 +271,10 @@ gb_status grouped_enqueue_async(const Launch& L, const gb_gemm_desc* descs, int6
     }
     if (e == cudaSuccess && !lay.emu.empty()) {
         EmuProb* d = reinterpret_cast<EmuProb*>(dev + lay.off_emu);
+        const EmuKeys keys = keys_at(dev, lay);
         for (size_t r = 0; r < lay.s_ranges.size() && e == cudaSuccess; ++r) {
-            e = launch_grouped_split(L, d, (int)lay.emu.size(), lay.s_ranges[r]);
-            if (e == cudaSuccess)
-                e = launch_grouped_products(L, d, (int)lay.emu.size(), lay.s_ranges[r].t_begin,
-                                            lay.s_ranges[r].t_end, lay.s_ranges[r].s);
+            e = launch_grouped_split(L, d, keys, lay.s_ranges[r]);
+            if (e == cudaSuccess) e = launch_grouped_products(L, d, keys, lay.s_ranges[r]);
             nl += 4;
         }
     }
@@ -318,10 +347,8 @@ static gb_status enqueue_plan(gb_grouped_plan* p, cudaStream_t stream) {
                                       p->grid_native);
     }
     for (size_t r = 0; r < p->s_ranges.size() && e == cudaSuccess; ++r) {
-        e = launch_grouped_split(L, p->d_emu, p->n_emu, p->s_ranges[r]);
-        if (e == cudaSuccess)
-            e = launch_grouped_products(L, p->d_emu, p->n_emu, p->s_ranges[r].t_begin,
-                                        p->s_ranges[r].t_end, p->s_ranges[r].s);
+        e = launch_grouped_split(L, p->d_emu, p->d_keys, p->s_ranges[r]);
+        if (e == cudaSuccess) e = launch_grouped_products(L, p->d_emu, p->d_keys, p->s_ranges[r]);
     }
     if (e != cudaSuccess) return cuda_fail(e, "grouped launch");
     return GB_OK;
@@ -371,6 +398,7 @@ gb_status gb_grouped_plan_create(gb_queue* q, const gb_gemm_desc* descs, int64_t
                           ((last.m + tile_bm(last.tile) - 1) / tile_bm(last.tile)) * last.tiles_n;
     }
     p->d_emu = reinterpret_cast<EmuProb*>(ws + L.off_emu);
+    p->d_keys = keys_at(ws, L);
     p->n_emu = (int)L.emu.size();
     p->emu_tiles = L.s_ranges.empty() ? 0 : L.s_ranges.back().t_end;
     p->max_s = L.max_s;
@@ -389,6 +417,9 @@ gb_status gb_grouped_plan_create(gb_queue* q, const gb_gemm_desc* descs, int64_t
                             cudaMemcpyHostToDevice, q->stream);
     if (e == cudaSuccess && !L.emu.empty())
         e = cudaMemcpyAsync(p->d_emu, L.emu.data(), sizeof(EmuProb) * L.emu.size(),
+                            cudaMemcpyHostToDevice, q->stream);
+    for (int a = 0; a < 4 && e == cudaSuccess && !L.emu.empty(); ++a)
+        e = cudaMemcpyAsync(ws + L.off_keys[a], L.keys[a].data(), sizeof(int64_t) * L.emu.size(),
                             cudaMemcpyHostToDevice, q->stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(q->stream);
     if (e != cudaSuccess) {

@@ -107,26 +107,39 @@ struct EmuProb {
     int64_t first_tile;    // 128 x 32 output tiles
 };
 
+// The same four prefixes as compact arrays (one int64 per table entry), the
+// keys of the device-side binary searches: a search touches a few cache lines
+// instead of one EmuProb per probe.
+struct EmuKeys {
+    const int64_t* row;
+    const int64_t* colblk;
+    const int64_t* tblk;
+    const int64_t* tile;
+};
+
 // The emulated problems of one slice count s occupy consecutive table entries;
 // their rows, column blocks, transpose blocks and output tiles are the ranges
 // [*_begin, *_end) of the table's prefixes.
 struct EmuSRange {
     int s;
+    int q_begin, q_end;  // table entries
     int64_t row_begin, row_end;
     int64_t cb_begin, cb_end;
     int64_t tb_begin, tb_end;
     int64_t t_begin, t_end;
+    int64_t kp_max;  // longest padded K of the range's problems
 };
 
 // Grouped e1 + e2 over the problems of one slice-count range (three launches).
-cudaError_t launch_grouped_split(const Launch& L, const EmuProb* probs, int np,
+cudaError_t launch_grouped_split(const Launch& L, const EmuProb* probs, const EmuKeys& keys,
                                  const EmuSRange& r);
-// Grouped e3 + e4: persistent CTAs over the 128 x 32 output tiles
-// [t_begin, t_end) of the table, all of whose problems use s slices.
-cudaError_t launch_grouped_products(const Launch& L, const EmuProb* probs, int np,
-                                    int64_t t_begin, int64_t t_end, int s);
+// Grouped e3 + e4: persistent CTAs over the 128 x 32 output tiles of the
+// problems of one slice-count range.
+cudaError_t launch_grouped_products(const Launch& L, const EmuProb* probs, const EmuKeys& keys,
+                                    const EmuSRange& r);
 constexpr int kEmuBM = 128;      // output tile rows of the products kernel (A digit tile rows)
 constexpr int kEmuGroupBN = 32;  // output tile columns (B digit tile rows)
+
 
 cudaError_t launch_split_rows(const Launch& L, int s, int64_t m, int64_t k, const double* A,
                               int64_t lda, uint8_t* digits, int64_t kp, int32_t* exps);

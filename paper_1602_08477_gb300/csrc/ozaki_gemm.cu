@@ -71,17 +71,6 @@ struct I128 {
     uint64_t lo;
 };
 
-__device__ __forceinline__ void i128_horner(I128& x, int sh, int64_t v) {
-    // x = x * 2^sh + v   (1 <= sh <= 63)
-    x.hi = (int64_t)(((uint64_t)x.hi << sh) | (x.lo >> (64 - sh)));
-    x.lo <<= sh;
-    const uint64_t vlo = (uint64_t)v;
-    const int64_t vhi = v < 0 ? -1 : 0;
-    const uint64_t nlo = x.lo + vlo;
-    x.hi += vhi + (nlo < x.lo ? 1 : 0);
-    x.lo = nlo;
-}
-
 __device__ __forceinline__ double pow2(int e) {  // exact for -1022 <= e <= 1023
     return __longlong_as_double((long long)(e + 1023) << 52);
 }
@@ -151,6 +140,7 @@ struct TileArgs {
     const uint8_t* a_src;  // A digit tiles of this tile row, K block 0 (s * 4 KiB per block)
     const uint8_t* b_src;  // B digit tiles of this tile column, K block 0 (s * 1 KiB per block)
     int s, nkb;
+    bool reverse;  // stream the K blocks last to first
     int64_t m, n, ldc, row0, col0;
     double alpha, beta;
     double* C;
@@ -168,22 +158,33 @@ struct TileArgs {
 // N = 32 (S+1-p) (split at the 256-column limit) covers them all, reading the A
 // tile once.  Fully unrolled: descriptor offsets are immediates, so the single
 // issuing thread spends a few instructions per MMA.
-template <int S>
+// Split accumulators (kSplit): slices p <= G = split_point(S) accumulate into
+// the level columns 0 .. 32 S, slices p > G into a second set of the levels
+// G .. S-1 at columns 32 S + 32 (L - G), so no accumulator collects more than
+// max(G, S - G) pairs per K index.  G is a compile-time constant: the MMA
+// operands stay immediates.
+__host__ __device__ constexpr int split_point(int S) {
+    return (S + 1) / 2 > 2 * S - 16 ? (S + 1) / 2 : 2 * S - 16;
+}
+
+template <int S, bool kSplit>
 __device__ __forceinline__ void issue_kblock(uint64_t adesc, uint64_t bdesc, uint32_t tmem_base,
                                              bool first) {
+    constexpr int G = kSplit ? split_point(S) : S;
 #pragma unroll
     for (int p = 1; p <= S; ++p) {
         const uint64_t ad = adesc + (uint64_t)(((p - 1) * kBM * kBKBytes) >> 4);
-        const uint32_t acc = (first && p == 1) ? 0u : 1u;
-        constexpr int kUnused = 0;
-        (void)kUnused;
+        // the first slice of each accumulator set covers all of its levels
+        const uint32_t acc = (first && (p == 1 || p == G + 1)) ? 0u : 1u;
+        const uint32_t col0 = p > G ? (uint32_t)(kBN * S + (p - 1 - G) * kBN)
+                                    : (uint32_t)((p - 1) * kBN);
         const int rows = kBN * (S + 1 - p);
 #pragma unroll
         for (int r0 = 0; r0 < kBN * S; r0 += 256) {
             if (r0 < rows) {
                 const int nn = rows - r0 < 256 ? rows - r0 : 256;
                 const uint64_t bd = bdesc + (uint64_t)((r0 * kBKBytes) >> 4);
-                ptx::mma_e4m3(tmem_base + (uint32_t)((p - 1) * kBN + r0), ad, bd,
+                ptx::mma_e4m3(tmem_base + col0 + (uint32_t)r0, ad, bd,
                               ptx::idesc_e4m3_f32(kBM, nn), acc);
             }
         }
@@ -201,8 +202,110 @@ __host__ __device__ constexpr int kblocks_per_stage(int S) {
                      : ((kSmemLimit - 2048) / (2 * S * (kBM + kBN) * kBKBytes));
 }
 
-// Persistent CTA over output tiles t = blockIdx.x, blockIdx.x + gridDim.x, ...
-// (tile_of(t) gives a tile's arguments; every role walks the same sequence).
+// Exactness of the FP32 level sums: an accumulator that collects P pair products
+// of digits with |d| <= 16 per K index stays within +-2^24 (every partial sum an
+// exactly representable integer) while K * P * 256 <= 2^24; level g has
+// g - 1 <= S pairs.  For a longer K the pairs are spread over two accumulator sets
+// (issue_kblock<S, true>, for 9 <= S <= 15 where both sets fit in the 512 TMEM
+// columns) or, failing that, K runs in chunks of kchunk_stages(S, KB) pipeline
+// stages: each chunk's level sums are read out and added exactly (128-bit) before
+// the next chunk starts from zero.
+__host__ __device__ constexpr int kchunk_stages(int S, int KB) {
+    return (((1 << 24) / (256 * S)) / kBKBytes) / KB;
+}
+
+// Exact integer of an integer-valued FP32 with |v| < 2^22: adding 1.5 * 2^23
+// lands in [2^23, 2^24), where the unit in the last place is 1.
+__device__ __forceinline__ int32_t f32_small_int_value(uint32_t b) {
+    const float f = __fadd_rn(__uint_as_float(b), 12582912.0f);
+    return (int32_t)(__float_as_uint(f) - 0x4B400000u);
+}
+
+// x += v * 2^sh exactly (0 <= sh <= 127 - 63).
+__device__ __forceinline__ void i128_add_shl(I128& x, int64_t v, int sh) {
+    uint64_t lo, hi;
+    if (sh == 0) {
+        lo = (uint64_t)v;
+        hi = v < 0 ? ~0ull : 0ull;
+    } else if (sh < 64) {
+        lo = (uint64_t)v << sh;
+        hi = (uint64_t)(v >> (64 - sh));
+    } else {
+        lo = 0;
+        hi = (uint64_t)v << (sh - 64);
+    }
+    const uint64_t nlo = x.lo + lo;
+    x.hi += (int64_t)(hi + (nlo < x.lo ? 1 : 0));
+    x.lo = nlo;
+}
+
+// T += sum_g S_g 2^(5 (S+1-g)) over the S levels of one accumulation unit for 8
+// columns (one TMEM lane per thread; level index L = g - 2 at column col_addr +
+// 32 L, plus col_addr + 32 (S + L - G) for L >= G with split accumulators), exactly:
+// Horner in int64 over runs of at most 6 levels (each |S_g| < 2^25 as the sum of
+// two accumulators, so a run stays below 2^55), each run added into the 128-bit
+// T at its own weight, so the chunks of a tile add up in the same T.
+// small: every accumulator below 2^22 (cheaper conversion).
+template <int S, bool kSplit>
+__device__ __forceinline__ void add_levels(uint32_t col_addr, bool small, I128 (&T)[8]) {
+    constexpr int split_g = kSplit ? split_point(S) : S;
+    int64_t G[8];
+#pragma unroll
+    for (int j = 0; j < 8; ++j) G[j] = 0;
+    int in_group = 0;
+#pragma unroll 1
+    for (int L = 0; L < S; ++L) {
+        const bool two = L >= split_g;
+        uint32_t v[8], y[8];
+        ptx::tmem_ld_32x32b_x8(col_addr + (uint32_t)L * kBN, v);
+        if (two) ptx::tmem_ld_32x32b_x8(col_addr + (uint32_t)(S + L - split_g) * kBN, y);
+        ptx::tmem_ld_wait();
+        if (small) {
+#pragma unroll
+            for (int j = 0; j < 8; ++j)
+                G[j] = G[j] * 32 + (int64_t)f32_small_int_value(v[j]) +
+                       (two ? (int64_t)f32_small_int_value(y[j]) : 0);
+        } else {
+#pragma unroll
+            for (int j = 0; j < 8; ++j)
+                G[j] = G[j] * 32 + f32_int_value(v[j]) + (two ? f32_int_value(y[j]) : 0);
+        }
+        ++in_group;
+        if (in_group == 6 || L == S - 1) {
+            const int sh = 5 * (S - 1 - L);  // weight of the run's last level
+#pragma unroll
+            for (int j = 0; j < 8; ++j) {
+                i128_add_shl(T[j], G[j], sh);
+                G[j] = 0;
+            }
+            in_group = 0;
+        }
+    }
+}
+
+// How one launch keeps its level sums exact (see kchunk_stages): split
+// accumulators, or K chunks of chunk_stages pipeline stages (a huge value: none).
+struct AccPlan {
+    bool split;
+    int chunk_stages;
+};
+
+template <int S, int KB>
+AccPlan acc_plan(int64_t kp, bool allow_split) {
+    AccPlan a{false, 1 << 30};
+    const int64_t kmax = (int64_t)1 << 24;  // K * pairs * 256 <= 2^24
+    if (kp * S * 256 <= kmax) return a;
+    constexpr int G = split_point(S);
+    if (allow_split && S >= 9 && S <= 15 && kp * (G > S - G ? G : S - G) * 256 <= kmax) {
+        a.split = true;
+        return a;
+    }
+    a.chunk_stages = kchunk_stages(S, KB);
+    return a;
+}
+
+// Persistent CTA over the output tiles of a Walk (start / valid / next / args;
+// every role walks its own copy of the same sequence).
 // Barriers and the TMEM allocation live for the whole CTA: the producer runs
 // ahead into the next tile's stages, and the epilogue hands TMEM back (tmem_empty)
 // as soon as it has read the level sums, so the next tile's MMAs overlap its
@@ -210,9 +313,9 @@ __host__ __device__ constexpr int kblocks_per_stage(int S) {
 // of `slot_bytes` (>= KB * S * 5 KiB) plus a SmemTail.  A stage holds KB
 // consecutive K blocks: their A tiles (KB * S * 4 KiB, contiguous in the
 // workspace) then their B tiles (KB * S * 1 KiB).
-template <int S, int KB, class TileFn>
-__device__ __forceinline__ void products_persistent(const TileFn& tile_of, int64_t t_begin,
-                                                    int64_t t_end, uint8_t* smem, int stages,
+template <int S, int KB, bool kSplit, class Walk>
+__device__ __forceinline__ void products_persistent(const Walk& walk, int chunk_stages,
+                                                    uint8_t* smem, int stages,
                                                     uint32_t slot_bytes, unsigned* status) {
     constexpr int BN = kBN;
     SmemTail* tail = reinterpret_cast<SmemTail*>(smem + (size_t)stages * slot_bytes);
@@ -223,7 +326,6 @@ __device__ __forceinline__ void products_persistent(const TileFn& tile_of, int64
     uint64_t* drain = tail->bars + 2 * stages + 2;
     volatile int* abort = &tail->abort;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int64_t t0 = t_begin + blockIdx.x, dt = gridDim.x;
 
     if (threadIdx.x == 0) {
         for (int i = 0; i < stages; ++i) {
@@ -250,8 +352,9 @@ __device__ __forceinline__ void products_persistent(const TileFn& tile_of, int64
     if (warp == 0 && lane == 0) {
         // ---- producer: two contiguous bulk copies per stage, across tiles ----
         uint32_t it = 0;
-        for (int64_t t = t0; t < t_end && !*abort; t += dt) {
-            const TileArgs a = tile_of(t);
+        Walk w = walk;
+        for (w.start(); w.valid() && !*abort; w.next()) {
+            const TileArgs a = w.args();
             const int nst = (a.nkb + KB - 1) / KB;
             for (int j = 0; j < nst; ++j, ++it) {
                 const int st = (int)(it % (uint32_t)stages);
@@ -259,7 +362,7 @@ __device__ __forceinline__ void products_persistent(const TileFn& tile_of, int64
                 if (!ptx::mbar_wait_bounded(&empty[st], ph ^ 1u, abort, status, kStatusTimeout,
                                             kWaitTimeoutNs))
                     break;
-                const int kb0 = j * KB;
+                const int kb0 = (a.reverse ? nst - 1 - j : j) * KB;
                 const int kc = a.nkb - kb0 < KB ? a.nkb - kb0 : KB;
                 uint8_t* sa = smem + (size_t)st * slot_bytes;
                 ptx::mbar_arrive_expect_tx(&full[st], (uint32_t)kc * (a_bytes + b_bytes));
@@ -271,83 +374,88 @@ __device__ __forceinline__ void products_persistent(const TileFn& tile_of, int64
         }
     } else if (warp == 1 && lane == 0) {
         // ---- MMA issuer ----
-        uint32_t it = 0, tile_iter = 0;
-        for (int64_t t = t0; t < t_end && !*abort; t += dt, ++tile_iter) {
-            const TileArgs a = tile_of(t);
+        const int kCS = chunk_stages;
+        uint32_t it = 0, chunk_iter = 0;
+        bool stop = false;
+        Walk w = walk;
+        for (w.start(); w.valid() && !*abort && !stop; w.next()) {
+            const TileArgs a = w.args();
             const int nst = (a.nkb + KB - 1) / KB;
-            if (tile_iter > 0) {
-                // the epilogue has read the previous tile's accumulators
-                if (!ptx::mbar_wait_bounded(tmem_empty, (tile_iter - 1) & 1u, abort, status,
-                                            kStatusTimeout, kWaitTimeoutNs))
-                    break;
-                ptx::tc_fence_after();
-            }
+            int in_chunk = 0;  // stages of the current accumulation unit issued so far
             for (int j = 0; j < nst; ++j, ++it) {
+                const bool chunk_start = in_chunk == 0;
+                if (chunk_start) {
+                    if (chunk_iter > 0) {
+                        // the epilogue has read the previous chunk's accumulators
+                        if (!ptx::mbar_wait_bounded(tmem_empty, (chunk_iter - 1) & 1u, abort,
+                                                    status, kStatusTimeout, kWaitTimeoutNs)) {
+                            stop = true;
+                            break;
+                        }
+                        ptx::tc_fence_after();
+                    }
+                    ++chunk_iter;
+                }
                 const int st = (int)(it % (uint32_t)stages);
                 const uint32_t ph = (it / (uint32_t)stages) & 1u;
                 if (!ptx::mbar_wait_bounded(&full[st], ph, abort, status, kStatusTimeout,
-                                            kWaitTimeoutNs))
+                                            kWaitTimeoutNs)) {
+                    stop = true;
                     break;
+                }
                 ptx::tc_fence_after();
                 const uint32_t a0 = ptx::smem_u32(smem + (size_t)st * slot_bytes);
                 const uint64_t adesc = ptx::umma_desc_sw32(a0);
                 const uint64_t bdesc = ptx::umma_desc_sw32(a0 + KB * a_bytes);
-                const int kc = a.nkb - j * KB < KB ? a.nkb - j * KB : KB;
+                const int kb0 = (a.reverse ? nst - 1 - j : j) * KB;
+                const int kc = a.nkb - kb0 < KB ? a.nkb - kb0 : KB;
 #pragma unroll
                 for (int kk = 0; kk < KB; ++kk) {
                     if (kk < kc)
-                        issue_kblock<S>(adesc + (uint64_t)((kk * a_bytes) >> 4),
-                                        bdesc + (uint64_t)((kk * b_bytes) >> 4), tmem_base,
-                                        j == 0 && kk == 0);
+                        issue_kblock<S, kSplit>(adesc + (uint64_t)((kk * a_bytes) >> 4),
+                                                bdesc + (uint64_t)((kk * b_bytes) >> 4),
+                                                tmem_base, chunk_start && kk == 0);
                 }
                 ptx::mma_commit(&empty[st]);
+                if (++in_chunk == kCS || j + 1 == nst) {
+                    ptx::mma_commit(tmem_full);
+                    in_chunk = 0;
+                }
             }
-            ptx::mma_commit(tmem_full);
         }
     } else if (warp >= 2) {
         // ---- epilogue ----
-        // T = sum_g S_g 2^(5 (s+1-g)) exactly: Horner in int64 over groups of at
-        // most 6 levels (each group stays below 2^53 for k * pairs * 256 < 2^28),
-        // folded into a 128-bit integer at group ends; one rounding to FP64.
+        // Every chunk adds its sum_g S_g 2^(5 (s+1-g)) exactly into the tile's
+        // 128-bit T (add_levels); one rounding to FP64 at the end.
+        const int kCS = chunk_stages;
         const int quarter = warp & 3;
         const int cgroup = (warp - 2) >> 2;
         const uint32_t col_addr = tmem_base + ((uint32_t)(quarter * 32) << 16) + cgroup * 8;
-        uint32_t tile_iter = 0;
-        for (int64_t t = t0; t < t_end; t += dt, ++tile_iter) {
-            const TileArgs a = tile_of(t);
-            const bool ok = ptx::mbar_wait_bounded(tmem_full, tile_iter & 1u, abort, status,
-                                                   kStatusTimeout, kWaitTimeoutNs);
-            ptx::tc_fence_after();
-            if (!ok || *abort) break;
+        uint32_t chunk_iter = 0;
+        bool stop = false;
+        Walk w = walk;
+        for (w.start(); w.valid() && !stop; w.next()) {
+            const TileArgs a = w.args();
+            const int nch = ((a.nkb + KB - 1) / KB + kCS - 1) / kCS;
+            const bool small = a.nkb * S < 512;  // every accumulator below 2^22
             I128 T[8];
-            int64_t G[8];
 #pragma unroll
-            for (int j = 0; j < 8; ++j) {
-                T[j] = I128{0, 0};
-                G[j] = 0;
-            }
-            int in_group = 0;
-#pragma unroll 1
-            for (int g = 2; g <= S + 1; ++g) {
-                uint32_t v[8];
-                ptx::tmem_ld_32x32b_x8(col_addr + (uint32_t)(g - 2) * BN, v);
-                ptx::tmem_ld_wait();
-#pragma unroll
-                for (int j = 0; j < 8; ++j) G[j] = G[j] * 32 + f32_int_value(v[j]);
-                ++in_group;
-                if (in_group == 6 || g == S + 1) {
-#pragma unroll
-                    for (int j = 0; j < 8; ++j) {
-                        i128_horner(T[j], 5 * in_group, G[j]);
-                        G[j] = 0;
-                    }
-                    in_group = 0;
+            for (int j = 0; j < 8; ++j) T[j] = I128{0, 0};
+            for (int c = 0; c < nch; ++c, ++chunk_iter) {
+                const bool ok = ptx::mbar_wait_bounded(tmem_full, chunk_iter & 1u, abort, status,
+                                                       kStatusTimeout, kWaitTimeoutNs);
+                ptx::tc_fence_after();
+                if (!ok || *abort) {
+                    stop = true;
+                    break;
                 }
+                add_levels<S, kSplit>(col_addr, small, T);
+                // accumulators read: hand TMEM to the next unit's MMAs
+                ptx::tc_fence_before();
+                __syncwarp();
+                if (lane == 0) ptx::mbar_arrive(tmem_empty);
             }
-            // accumulators read: hand TMEM to the next tile's MMAs
-            ptx::tc_fence_before();
-            __syncwarp();
-            if (lane == 0) ptx::mbar_arrive(tmem_empty);
+            if (stop) break;
             const int64_t row = a.row0 + quarter * 32 + lane;
             if (row < a.m) {
                 const int32_t ei = a.eA[row];
@@ -397,29 +505,39 @@ __device__ __forceinline__ uint8_t* aligned_smem(uint8_t* raw) {
     return reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(raw) + 1023) & ~(uintptr_t)1023);
 }
 
-// One GEMM: persistent CTAs over its tiles in the rasterised order (groups of 8
-// tile rows sweep the tile columns, so concurrent CTAs share A and B strips in L2).
-template <int S>
-__global__ void __launch_bounds__(kThreads, 1)
-    emu_products_kernel(const uint8_t* __restrict__ ad, const uint8_t* __restrict__ bd,
-                        int64_t m, int64_t n, int nkb, double alpha, double beta,
-                        double* __restrict__ C, int64_t ldc, const int32_t* __restrict__ eA,
-                        const int32_t* __restrict__ fB, int tiles_m, int tiles_n, int stages,
-                        uint32_t slot_bytes, unsigned* status) {
-    extern __shared__ uint8_t smem_raw[];
-    uint8_t* smem = aligned_smem(smem_raw);
-    auto tile_of = [&](int64_t t) {
+// One GEMM: persistent CTAs over its tiles t = blockIdx.x, + gridDim.x, ... in the
+// rasterised order (groups of 8 tile rows sweep the tile columns, so concurrent
+// CTAs share A and B strips in L2).  Every other wave of tiles streams K from
+// the end: the next wave keeps the same A strips, and the K blocks the previous
+// wave read last are the ones still in L2.  The order of the K blocks does not
+// change a bit of the result: the level sums are exact integers.
+struct RasterWalk {
+    const uint8_t* ad;
+    const uint8_t* bd;
+    int64_t m, n, ldc;
+    int nkb, tiles_m, tiles_n, s;
+    double alpha, beta;
+    double* C;
+    const int32_t* eA;
+    const int32_t* fB;
+    int64_t t;
+    __device__ void start() { t = blockIdx.x; }
+    __device__ bool valid() const { return t < (int64_t)tiles_m * tiles_n; }
+    __device__ void next() { t += gridDim.x; }
+    __device__ TileArgs args() const {
         const int bid = (int)t;
         const int group_size = 8 * tiles_n;
+        const bool reverse = ((t / gridDim.x) & 1) != 0;
         const int first_m = (bid / group_size) * 8;
         const int gm = min(tiles_m - first_m, 8);
         const int tm = first_m + (bid % group_size) % gm;
         const int tn = (bid % group_size) / gm;
         TileArgs a;
-        a.a_src = ad + (size_t)tm * nkb * S * kBM * kBKBytes;
-        a.b_src = bd + (size_t)tn * nkb * S * kBN * kBKBytes;
-        a.s = S;
+        a.a_src = ad + (size_t)tm * nkb * s * kBM * kBKBytes;
+        a.b_src = bd + (size_t)tn * nkb * s * kBN * kBKBytes;
+        a.s = s;
         a.nkb = nkb;
+        a.reverse = reverse;
         a.m = m;
         a.n = n;
         a.ldc = ldc;
@@ -431,48 +549,77 @@ __global__ void __launch_bounds__(kThreads, 1)
         a.eA = eA;
         a.fB = fB;
         return a;
-    };
-    products_persistent<S, kblocks_per_stage(S)>(tile_of, 0, (int64_t)tiles_m * tiles_n, smem,
-                                                  stages, slot_bytes, status);
-}
+    }
+};
 
-// Grouped: persistent CTAs over the tiles [t_begin, t_end) of the problems of one
-// slice count S (the table keeps problems of equal s together).
-template <int S>
+template <int S, bool kSplit>
 __global__ void __launch_bounds__(kThreads, 1)
-    grouped_products_kernel(const EmuProb* __restrict__ P, int np, int64_t t_begin,
-                            int64_t t_end, int stages, uint32_t slot_bytes, unsigned* status) {
+    emu_products_kernel(const uint8_t* __restrict__ ad, const uint8_t* __restrict__ bd,
+                        int64_t m, int64_t n, int nkb, double alpha, double beta,
+                        double* __restrict__ C, int64_t ldc, const int32_t* __restrict__ eA,
+                        const int32_t* __restrict__ fB, int tiles_m, int tiles_n,
+                        int chunk_stages, int stages, uint32_t slot_bytes, unsigned* status) {
     extern __shared__ uint8_t smem_raw[];
     uint8_t* smem = aligned_smem(smem_raw);
-    auto tile_of = [&](int64_t t) {
-        int lo = 0, hi = np - 1;
+    const RasterWalk w{ad, bd, m, n, ldc, nkb, tiles_m, tiles_n, S, alpha, beta, C, eA, fB, 0};
+    products_persistent<S, kblocks_per_stage(S), kSplit>(w, chunk_stages, smem, stages,
+                                                         slot_bytes, status);
+}
+
+// Grouped: the tiles [t_begin, t_end) of the problems [q_begin, q_end) of the
+// table (all with S slices; the table puts long-K problems first), taken
+// t = t_begin + blockIdx.x, + gridDim.x, ...: concurrent CTAs work on
+// neighbouring tiles, so the digit strips they share stay in L2.  A tile's
+// problem is a binary search over the compact tile-prefix array (L1-resident).
+struct GroupWalk {
+    const EmuProb* P;
+    const int64_t* key;
+    int q_begin, q_end;
+    int64_t t_begin, t_end, t;
+    __device__ void start() { t = t_begin + blockIdx.x; }
+    __device__ bool valid() const { return t < t_end; }
+    __device__ void next() { t += gridDim.x; }
+    __device__ TileArgs args() const {
+        int lo = q_begin, hi = q_end - 1;
         while (lo < hi) {
             const int mid = (lo + hi + 1) >> 1;
-            if (P[mid].first_tile <= t) lo = mid; else hi = mid - 1;
+            if (key[mid] <= t) lo = mid; else hi = mid - 1;
         }
-        const EmuProb& q = P[lo];
-        const int64_t local = t - q.first_tile;
-        const int64_t tm = local / q.tiles_n, tn = local % q.tiles_n;
-        const int nkb = (int)(q.kp / kBKBytes);
+        const EmuProb& e = P[lo];
+        const int64_t local = t - key[lo];
+        const int64_t tm = local / e.tiles_n, tn = local % e.tiles_n;
+        const int nkb = (int)(e.kp / kBKBytes);
         TileArgs a;
-        a.a_src = q.a_digits + (size_t)tm * nkb * S * kBM * kBKBytes;
-        a.b_src = q.b_digits + (size_t)tn * nkb * S * kBN * kBKBytes;
-        a.s = S;
+        a.a_src = e.a_digits + (size_t)tm * nkb * e.s * kBM * kBKBytes;
+        a.b_src = e.b_digits + (size_t)tn * nkb * e.s * kBN * kBKBytes;
+        a.s = e.s;
         a.nkb = nkb;
-        a.m = q.m;
-        a.n = q.n;
-        a.ldc = q.ldc;
+        a.reverse = false;
+        a.m = e.m;
+        a.n = e.n;
+        a.ldc = e.ldc;
         a.row0 = tm * kBM;
         a.col0 = tn * kBN;
-        a.alpha = q.alpha;
-        a.beta = q.beta;
-        a.C = q.C;
-        a.eA = q.a_exp;
-        a.fB = q.b_exp;
+        a.alpha = e.alpha;
+        a.beta = e.beta;
+        a.C = e.C;
+        a.eA = e.a_exp;
+        a.fB = e.b_exp;
         return a;
-    };
-    products_persistent<S, kblocks_per_stage(S)>(tile_of, t_begin, t_end, smem, stages,
-                                                  slot_bytes, status);
+    }
+};
+
+template <int S>
+__global__ void __launch_bounds__(kThreads, 1)
+    grouped_products_kernel(const EmuProb* __restrict__ P, const int64_t* __restrict__ key,
+                            int q_begin, int q_end, int64_t t_begin, int64_t t_end,
+                            int chunk_stages, int stages, uint32_t slot_bytes,
+                            unsigned* status) {
+    extern __shared__ uint8_t smem_raw[];
+    uint8_t* smem = aligned_smem(smem_raw);
+    const GroupWalk w{P, key, q_begin, q_end, t_begin, t_end, 0};
+    products_persistent<S, kblocks_per_stage(S), false>(w, chunk_stages, smem, stages,
+                                                        slot_bytes, status);
 }
 
 struct RingShape {
@@ -502,30 +649,43 @@ cudaError_t launch_products_s(const Launch& L, int64_t m, int64_t n, int64_t kp,
                               const uint8_t* bd, const int32_t* ea, const int32_t* fb) {
     const RingShape r = ring_for(S, kblocks_per_stage(S));
     if (r.stages < 2) return cudaErrorInvalidValue;
-    cudaError_t e = allow_smem(emu_products_kernel<S>);
-    if (e != cudaSuccess) return e;
     const int tiles_m = (int)((m + kBM - 1) / kBM), tiles_n = (int)((n + kBN - 1) / kBN);
     const int nkb = (int)(kp / kBKBytes);
     const int64_t tiles = (int64_t)tiles_m * tiles_n;
     const int grid = (int)(tiles < L.sm_count ? tiles : L.sm_count);
-    emu_products_kernel<S><<<grid, kThreads, r.smem, L.stream>>>(
-        ad, bd, m, n, nkb, alpha, beta, C, ldc, ea, fb, tiles_m, tiles_n, r.stages,
-        r.slot_bytes, L.status);
+    constexpr bool kCanSplit = S >= 9 && S <= 15;
+    const AccPlan plan = acc_plan<S, kblocks_per_stage(S)>(kp, kCanSplit);
+    if constexpr (kCanSplit) {
+        if (plan.split) {
+            cudaError_t e = allow_smem(emu_products_kernel<S, true>);
+            if (e != cudaSuccess) return e;
+            emu_products_kernel<S, true><<<grid, kThreads, r.smem, L.stream>>>(
+                ad, bd, m, n, nkb, alpha, beta, C, ldc, ea, fb, tiles_m, tiles_n,
+                plan.chunk_stages, r.stages, r.slot_bytes, L.status);
+            return cudaGetLastError();
+        }
+    }
+    cudaError_t e = allow_smem(emu_products_kernel<S, false>);
+    if (e != cudaSuccess) return e;
+    emu_products_kernel<S, false><<<grid, kThreads, r.smem, L.stream>>>(
+        ad, bd, m, n, nkb, alpha, beta, C, ldc, ea, fb, tiles_m, tiles_n, plan.chunk_stages,
+        r.stages, r.slot_bytes, L.status);
     return cudaGetLastError();
 }
 
 template <int S>
-cudaError_t launch_grouped_s(const Launch& L, const EmuProb* probs, int np, int64_t t_begin,
-                             int64_t t_end) {
+cudaError_t launch_grouped_s(const Launch& L, const EmuProb* probs, const int64_t* key,
+                             const EmuSRange& g) {
     const RingShape r = ring_for(S, kblocks_per_stage(S));
     if (r.stages < 2) return cudaErrorInvalidValue;
     cudaError_t e = allow_smem(grouped_products_kernel<S>);
     if (e != cudaSuccess) return e;
-    const int64_t tiles = t_end - t_begin;
+    const int64_t tiles = g.t_end - g.t_begin;
     const int grid = (int)(tiles < L.sm_count ? tiles : L.sm_count);
-    grouped_products_kernel<S><<<grid, kThreads, r.smem, L.stream>>>(probs, np, t_begin, t_end,
-                                                                     r.stages, r.slot_bytes,
-                                                                     L.status);
+    const AccPlan plan = acc_plan<S, kblocks_per_stage(S)>(g.kp_max, false);
+    grouped_products_kernel<S><<<grid, kThreads, r.smem, L.stream>>>(
+        probs, key, g.q_begin, g.q_end, g.t_begin, g.t_end, plan.chunk_stages, r.stages,
+        r.slot_bytes, L.status);
     return cudaGetLastError();
 }
 
@@ -552,12 +712,12 @@ cudaError_t launch_emu_products(const Launch& L, int s, int64_t m, int64_t n, in
     }
 }
 
-cudaError_t launch_grouped_products(const Launch& L, const EmuProb* probs, int np,
-                                    int64_t t_begin, int64_t t_end, int s) {
-    if (np == 0 || t_end <= t_begin) return cudaSuccess;
-    switch (s) {
+cudaError_t launch_grouped_products(const Launch& L, const EmuProb* probs, const EmuKeys& keys,
+                                    const EmuSRange& g) {
+    if (g.t_end <= g.t_begin) return cudaSuccess;
+    switch (g.s) {
 #define GB_CASE(SS) \
-    case SS: return launch_grouped_s<SS>(L, probs, np, t_begin, t_end);
+    case SS: return launch_grouped_s<SS>(L, probs, keys.tile, g);
         GB_CASES(GB_CASE)
 #undef GB_CASE
         default: return cudaErrorInvalidValue;

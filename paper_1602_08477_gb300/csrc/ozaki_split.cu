@@ -18,6 +18,7 @@
 //   are all zero and the products mark its outputs NaN).
 #include <cuda_runtime.h>
 #include <cstdint>
+#include <type_traits>
 
 #include "internal.h"
 
@@ -49,19 +50,32 @@ __device__ __forceinline__ int frexp_exp_bits(uint64_t absbits) {
     return p - 1073;
 }
 
-// The s digits of one finite double x relative to line exponent e, packed as
+// Fixed-point image of an element for S digits: int64 holds it for S <= 11,
+// a 128-bit integer above (|F| < 2^(5 S)).
+template <int S>
+struct FixedOf {
+    using type = typename std::conditional<(S <= 11), int64_t, __int128>::type;
+};
+
+// The S digits of one finite double x relative to line exponent e, packed as
 // E4M3 bytes into out[t] (byte lane `lane` of a 64-bit word).
-// S: compile-time maximum of the slice count s.
 //
 // With x = X 2^E2 (X the signed integer significand) and sh_t = e - 4 - E2 -
 // 5 (t - 1), the recurrence above satisfies  r_t 2^(...) = X - Q_t 2^(sh_t)  with
 // Q_t = RNE(X / 2^(sh_t)) (round to nearest, ties to even): subtracting the
 // integer multiple 32 Q_(t-1) commutes with RNE.  Hence every digit is
-// d_t = Q_t - 32 Q_(t-1), computed independently of the others; |d_t| <= 16,
-// so the low 32 bits of each Q_t suffice (wrapping arithmetic).
+// d_t = Q_t - 32 Q_(t-1), computed independently of the others.
+//
+// F = X 2^k (k chosen per element) puts the unit of digit t at the fixed bit
+// 1 + 5 (S - t), so each Q_t comes from a constant shift: W = floor(F / 2^(5(S-t)))
+// = 2 Q0 + h, Q_t = (W + 1 - tie) / 2 with tie = (h == 1, Q0 even, no set bit of
+// F below bit 5 (S - t)), the last read off the trailing-zero count of X.  For
+// k < 0 the shift drops bits, which the trailing-zero count also accounts for.
+// Only Q_t mod 64 is kept; |d_t| <= 16 is recovered by sign extension from 6
+// bits.
 template <int S>
-__device__ __forceinline__ void digits_of(uint64_t bits, int e, int s, int lane,
-                                          uint64_t (&out)[S]) {
+__device__ __forceinline__ void digits_of(uint64_t bits, int e, int lane, uint64_t (&out)[S]) {
+    using Fixed = typename FixedOf<S>::type;
     const int ef = (int)((bits >> 52) & 0x7FF);
     int64_t M = (int64_t)(bits & 0xFFFFFFFFFFFFFull);
     int E2;
@@ -71,27 +85,23 @@ __device__ __forceinline__ void digits_of(uint64_t bits, int e, int s, int lane,
         M |= (int64_t)1 << 52;
         E2 = ef - 1075;
     }
+    if (M == 0) return;  // +-0: every digit 0
     const int64_t X = (bits >> 63) ? -M : M;
-    const int sh1 = e - kB1 - E2;
+    const int k = 1 - (e - kB1 - E2) + kB * (S - 1);
+    const int tzF = (__ffsll((long long)M) - 1) + k;
+    Fixed F;
+    if (k >= 0) F = (Fixed)X << k;  // exact: |F| < 2^(5 S)
+    else F = (Fixed)(X >> (-k < 63 ? -k : 63));
     uint32_t qprev = 0;
 #pragma unroll
-    for (int t = 0; t < S; ++t) {
-        if (t >= s) break;
-        const int sh = sh1 - kB * t;
-        uint32_t q;
-        if (sh >= 55) {
-            q = 0;  // |X| < 2^53 <= 2^(sh-2): |X / 2^sh| < 1/4
-        } else if (sh <= 0) {
-            q = -sh >= 64 ? 0u : (uint32_t)((uint64_t)X << (-sh));
-        } else {
-            // RNE by add-and-shift: floor((X + 2^(sh-1) - 1 + lsb) / 2^sh),
-            // lsb = floor(X / 2^sh) & 1
-            const int64_t lsb = (X >> sh) & 1;
-            q = (uint32_t)((X + (((int64_t)1 << (sh - 1)) - 1) + lsb) >> sh);
-        }
-        const int d = (int)(q - (qprev << kB));
+    for (int t = 1; t <= S; ++t) {
+        const int sh = kB * (S - t);
+        const uint32_t W = (uint32_t)(F >> sh);
+        const uint32_t tie = ((W & 3u) == 1u && tzF >= sh) ? 1u : 0u;
+        const uint32_t q = (W + 1u - tie) >> 1;
+        const int d = ((int)((q - (qprev << kB)) << 26)) >> 26;
         qprev = q;
-        out[t] |= (uint64_t)e4m3_of_int(d) << (8 * lane);
+        out[t - 1] |= (uint64_t)e4m3_of_int(d) << (8 * lane);
     }
 }
 
@@ -168,7 +178,7 @@ __device__ __forceinline__ void split_one_row(int64_t i, int64_t m, int64_t k,
 #pragma unroll
             for (int u = 0; u < 8; ++u) {
                 const int64_t l = l0 + u;
-                if (l < k) digits_of<S>(row[l], e, s, u, w);
+                if (l < k) digits_of<S>(row[l], e, u, w);
             }
         }
 #pragma unroll
@@ -180,7 +190,9 @@ __device__ __forceinline__ void split_one_row(int64_t i, int64_t m, int64_t k,
     __syncthreads();
 }
 
-// Column block jb (32 columns) of B: max |b| over all rows, per column.
+// Column block jb (32 columns) of B: max |b| over all rows, per column, by R
+// warps (R row phases; blockDim.x = 32 R).
+template <int R>
 __device__ __forceinline__ void colmax_block(int64_t jb, int64_t n, int64_t k,
                                              const double* __restrict__ B, int64_t ldb,
                                              int32_t* __restrict__ exps, unsigned* status,
@@ -191,7 +203,8 @@ __device__ __forceinline__ void colmax_block(int64_t jb, int64_t n, int64_t k,
     int bad = 0;
     if (j < n) {
         const uint64_t* col = reinterpret_cast<const uint64_t*>(B) + j;
-        for (int64_t l = ty; l < k; l += 8) {
+#pragma unroll 4
+        for (int64_t l = ty; l < k; l += R) {
             const uint64_t a = col[l * ldb] & 0x7FFFFFFFFFFFFFFFull;
             if (a >= 0x7FF0000000000000ull) bad = 1;
             else if (a > mx) mx = a;
@@ -201,7 +214,7 @@ __device__ __forceinline__ void colmax_block(int64_t jb, int64_t n, int64_t k,
     bad_sh[ty][tx] = bad;
     __syncthreads();
     if (ty == 0 && j < n) {
-        for (int r = 1; r < 8; ++r) {
+        for (int r = 1; r < R; ++r) {
             mx = mx_sh[r][tx] > mx ? mx_sh[r][tx] : mx;
             bad |= bad_sh[r][tx];
         }
@@ -239,7 +252,7 @@ __device__ __forceinline__ void split_cols_tile(int64_t jb, int64_t lb, int64_t 
         if (e != GB_BAD_LINE_DEV) {
 #pragma unroll
             for (int u = 0; u < 8; ++u) {
-                if (lbase + u < k) digits_of<S>(T[lsub + u][jj], e, s, u, w);
+                if (lbase + u < k) digits_of<S>(T[lsub + u][jj], e, u, w);
             }
         }
 #pragma unroll
@@ -266,13 +279,15 @@ __global__ void __launch_bounds__(128) split_rows_kernel(int64_t m, int64_t k,
         split_one_row<S>(i, m, k, A, lda, S, digits, kp, exps, status, red, &bad_sh);
 }
 
-__global__ void __launch_bounds__(256) colmax_kernel(int64_t n, int64_t k,
-                                                     const double* __restrict__ B, int64_t ldb,
-                                                     int32_t* __restrict__ exps,
-                                                     unsigned* status) {
-    __shared__ uint64_t mx_sh[8][32];
-    __shared__ int bad_sh[8][32];
-    colmax_block(blockIdx.x, n, k, B, ldb, exps, status, mx_sh, bad_sh);
+// One GEMM: one CTA of 32 warps per 32 columns (n / 32 CTAs, each reading a long
+// column strip; 32 row phases keep enough loads in flight).
+__global__ void __launch_bounds__(1024) colmax_kernel(int64_t n, int64_t k,
+                                                      const double* __restrict__ B, int64_t ldb,
+                                                      int32_t* __restrict__ exps,
+                                                      unsigned* status) {
+    __shared__ uint64_t mx_sh[32][32];
+    __shared__ int bad_sh[32][32];
+    colmax_block<32>(blockIdx.x, n, k, B, ldb, exps, status, mx_sh, bad_sh);
 }
 
 template <int S>
@@ -297,106 +312,131 @@ __global__ void __launch_bounds__(256) split_cols_kernel(int64_t n, int64_t k,
     }
 
 // ---- grouped: one launch per step over the problems of a table ---------------------
-__device__ __forceinline__ int find_prob(const EmuProb* __restrict__ P, int np,
-                                         int64_t EmuProb::*field, int64_t x) {
-    int lo = 0, hi = np - 1;
+// Last table entry q in [lo, hi] with key[q] <= x (keys ascending).
+__device__ __forceinline__ int find_prob(const int64_t* __restrict__ key, int lo, int hi,
+                                         int64_t x) {
     while (lo < hi) {
         const int mid = (lo + hi + 1) >> 1;
-        if (P[mid].*field <= x) lo = mid; else hi = mid - 1;
+        if (key[mid] <= x) lo = mid; else hi = mid - 1;
     }
     return lo;
 }
 
-// Row i of A by one warp (grouped problems have short rows): both passes take
-// 8 consecutive elements per lane and step (the digit pass re-reads them from
-// L1).  No block-wide barrier.
+// One 128-row tile of A (rows row0 .. row0+127 of a problem, rows >= m are the
+// tile padding) by a CTA of 256 threads.  Pass 1: each warp takes 16 rows, max |a|
+// and finiteness per row with 8 consecutive elements per lane and step.  Pass 2:
+// per K block of 32, thread p of 512 (two per thread) takes row p / 4, elements
+// 8 (p % 4) .. +7, so a warp writes 256 contiguous bytes per digit plane (8 rows x
+// 32 bytes of the tiled layout) and every lane has work even for short rows.
 template <int S>
-__device__ __forceinline__ void split_row_warp(int64_t i, int64_t m, int64_t k,
+__device__ __forceinline__ void split_row_tile(int64_t row0, int64_t m, int64_t k,
                                                const double* __restrict__ A, int64_t lda,
                                                uint8_t* __restrict__ digits, int64_t kp,
-                                               int32_t* __restrict__ exps, unsigned* status) {
-    const int lane = threadIdx.x & 31;
+                                               int32_t* __restrict__ exps, unsigned* status,
+                                               int* e_sh) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    for (int r = warp * 16; r < warp * 16 + 16; ++r) {
+        const int64_t i = row0 + r;
+        if (i >= m) {
+            if (lane == 0) e_sh[r] = GB_BAD_LINE_DEV;  // padding: zero digits
+            continue;
+        }
+        const uint64_t* row = reinterpret_cast<const uint64_t*>(A + i * lda);
+        uint64_t mx = 0;
+        unsigned bad = 0;
+        for (int64_t l0 = (int64_t)lane * 8; l0 < k; l0 += 256) {
+            uint64_t v[8];
+#pragma unroll
+            for (int u = 0; u < 8; ++u) v[u] = l0 + u < k ? row[l0 + u] : 0ull;
+#pragma unroll
+            for (int u = 0; u < 8; ++u) {
+                const uint64_t a = v[u] & 0x7FFFFFFFFFFFFFFFull;
+                bad |= a >= 0x7FF0000000000000ull;
+                mx = (a < 0x7FF0000000000000ull && a > mx) ? a : mx;
+            }
+        }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            const uint64_t w = __shfl_xor_sync(0xffffffffu, mx, o);
+            mx = w > mx ? w : mx;
+        }
+        const bool is_bad = __any_sync(0xffffffffu, bad) != 0;
+        if (lane == 0) {
+            const int e = is_bad ? GB_BAD_LINE_DEV : frexp_exp_bits(mx);
+            exps[i] = e;
+            e_sh[r] = e;
+            if (is_bad && status) atomicOr(status, kStatusNonfinite);
+        }
+    }
+    __syncthreads();
     const int64_t nkb = kp >> 5;
-    if (i >= m) {
-        for (int64_t l0 = (int64_t)lane * 8; l0 < kp; l0 += 256)
+    for (int64_t kb = 0; kb < nkb; ++kb) {
+#pragma unroll
+        for (int half = 0; half < 2; ++half) {
+            const int p = threadIdx.x + 256 * half;
+            const int r = p >> 2;
+            const int64_t i = row0 + r, l0 = kb * 32 + (p & 3) * 8;
+            const int e = e_sh[r];
+            uint64_t w[S];
+#pragma unroll
+            for (int t = 0; t < S; ++t) w[t] = 0;
+            if (e != GB_BAD_LINE_DEV) {
+                const uint64_t* src = reinterpret_cast<const uint64_t*>(A + i * lda) + l0;
+                uint64_t v[8];
+#pragma unroll
+                for (int u = 0; u < 8; ++u) v[u] = l0 + u < k ? src[u] : 0ull;
+#pragma unroll
+                for (int u = 0; u < 8; ++u)
+                    if (l0 + u < k) digits_of<S>(v[u], e, u, w);
+            }
 #pragma unroll
             for (int t = 0; t < S; ++t)
-                *reinterpret_cast<uint64_t*>(digits + tiled_offset(i, l0, t, S, nkb, kEmuBM)) = 0;
-        return;
-    }
-    const uint64_t* row = reinterpret_cast<const uint64_t*>(A + i * lda);
-    uint64_t mx = 0;
-    unsigned bad = 0;
-    for (int64_t l0 = (int64_t)lane * 8; l0 < k; l0 += 256) {
-        uint64_t v[8];
-#pragma unroll
-        for (int u = 0; u < 8; ++u) v[u] = l0 + u < k ? row[l0 + u] : 0ull;
-#pragma unroll
-        for (int u = 0; u < 8; ++u) {
-            const uint64_t a = v[u] & 0x7FFFFFFFFFFFFFFFull;
-            bad |= a >= 0x7FF0000000000000ull;
-            mx = (a < 0x7FF0000000000000ull && a > mx) ? a : mx;
+                *reinterpret_cast<uint64_t*>(digits + tiled_offset(i, l0, t, S, nkb, kEmuBM)) = w[t];
         }
     }
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) {
-        const uint64_t v = __shfl_xor_sync(0xffffffffu, mx, o);
-        mx = v > mx ? v : mx;
-    }
-    const bool is_bad = __any_sync(0xffffffffu, bad) != 0;
-    const int e = frexp_exp_bits(mx);
-    if (lane == 0) {
-        exps[i] = is_bad ? GB_BAD_LINE_DEV : e;
-        if (is_bad && status) atomicOr(status, kStatusNonfinite);
-    }
-    for (int64_t l0 = (int64_t)lane * 8; l0 < kp; l0 += 256) {
-        uint64_t w[S];
-#pragma unroll
-        for (int t = 0; t < S; ++t) w[t] = 0;
-        if (!is_bad) {
-#pragma unroll
-            for (int u = 0; u < 8; ++u)
-                if (l0 + u < k) digits_of<S>(row[l0 + u], e, S, u, w);
-        }
-#pragma unroll
-        for (int t = 0; t < S; ++t)
-            *reinterpret_cast<uint64_t*>(digits + tiled_offset(i, l0, t, S, nkb, kEmuBM)) = w[t];
-    }
+    __syncthreads();
 }
 
 // Grouped kernels: one launch per step over the problems of one slice count S.
 template <int S>
 __global__ void __launch_bounds__(256) grouped_split_rows_kernel(const EmuProb* __restrict__ P,
-                                                                 int np, int64_t row_begin,
+                                                                 const int64_t* __restrict__ key,
+                                                                 int q_begin, int q_end,
+                                                                 int64_t row_begin,
                                                                  int64_t row_end,
                                                                  unsigned* status) {
-    const int64_t warps = (int64_t)gridDim.x * 8;
-    for (int64_t r = row_begin + (int64_t)blockIdx.x * 8 + (threadIdx.x >> 5); r < row_end;
-         r += warps) {
-        const EmuProb& q = P[find_prob(P, np, &EmuProb::first_row, r)];
-        split_row_warp<S>(r - q.first_row, q.m, q.k, q.A, q.lda, q.a_digits, q.kp, q.a_exp,
-                          status);
+    __shared__ int e_sh[kEmuBM];
+    // rows are padded to 128 per problem, so a 128-row block is one problem's tile
+    for (int64_t r0 = row_begin + (int64_t)blockIdx.x * kEmuBM; r0 < row_end;
+         r0 += (int64_t)gridDim.x * kEmuBM) {
+        const EmuProb& q = P[find_prob(key, q_begin, q_end - 1, r0)];
+        split_row_tile<S>(r0 - q.first_row, q.m, q.k, q.A, q.lda, q.a_digits, q.kp, q.a_exp,
+                          status, e_sh);
     }
 }
 
 __global__ void __launch_bounds__(256) grouped_colmax_kernel(const EmuProb* __restrict__ P,
-                                                             int np, int64_t cb_begin,
-                                                             int64_t cb_end, unsigned* status) {
+                                                             const int64_t* __restrict__ key,
+                                                             int q_begin, int q_end,
+                                                             int64_t cb_begin, int64_t cb_end,
+                                                             unsigned* status) {
     __shared__ uint64_t mx_sh[8][32];
     __shared__ int bad_sh[8][32];
     for (int64_t b = cb_begin + blockIdx.x; b < cb_end; b += gridDim.x) {
-        const EmuProb& q = P[find_prob(P, np, &EmuProb::first_colblk, b)];
-        colmax_block(b - q.first_colblk, q.n, q.k, q.B, q.ldb, q.b_exp, status, mx_sh, bad_sh);
+        const EmuProb& q = P[find_prob(key, q_begin, q_end - 1, b)];
+        colmax_block<8>(b - q.first_colblk, q.n, q.k, q.B, q.ldb, q.b_exp, status, mx_sh, bad_sh);
     }
 }
 
 template <int S>
 __global__ void __launch_bounds__(256) grouped_split_cols_kernel(const EmuProb* __restrict__ P,
-                                                                 int np, int64_t tb_begin,
+                                                                 const int64_t* __restrict__ key,
+                                                                 int q_begin, int q_end,
+                                                                 int64_t tb_begin,
                                                                  int64_t tb_end) {
     __shared__ uint64_t T[64][33];
     for (int64_t b = tb_begin + blockIdx.x; b < tb_end; b += gridDim.x) {
-        const EmuProb& q = P[find_prob(P, np, &EmuProb::first_tblk, b)];
+        const EmuProb& q = P[find_prob(key, q_begin, q_end - 1, b)];
         const int64_t local = b - q.first_tblk;
         const int64_t ncb = (q.n + 31) / 32;
         split_cols_tile<S>(local % ncb, local / ncb, q.n, q.k, q.B, q.ldb, S, q.b_digits, q.kp,
@@ -420,26 +460,26 @@ cudaError_t launch_split_rows(const Launch& L, int s, int64_t m, int64_t k, cons
     return cudaGetLastError();
 }
 
-cudaError_t launch_grouped_split(const Launch& L, const EmuProb* probs, int np,
+cudaError_t launch_grouped_split(const Launch& L, const EmuProb* probs, const EmuKeys& keys,
                                  const EmuSRange& r) {
-    if (np == 0) return cudaSuccess;
+    if (r.q_end <= r.q_begin) return cudaSuccess;
     const int64_t cap = (int64_t)L.sm_count * 16;
     auto g = [&](int64_t x) { return (unsigned)(x < cap ? (x > 0 ? x : 1) : cap); };
-    const unsigned g_rows = g((r.row_end - r.row_begin + 7) / 8);
-#define GB_LAUNCH_GROWS(SS)                                                                    \
-    grouped_split_rows_kernel<SS><<<g_rows, 256, 0, L.stream>>>(probs, np, r.row_begin,        \
-                                                                r.row_end, L.status)
+    const unsigned g_rows = g((r.row_end - r.row_begin) / kEmuBM);
+#define GB_LAUNCH_GROWS(SS)                                                                   \
+    grouped_split_rows_kernel<SS><<<g_rows, 256, 0, L.stream>>>(                              \
+        probs, keys.row, r.q_begin, r.q_end, r.row_begin, r.row_end, L.status)
     GB_SWITCH_S(r.s, GB_LAUNCH_GROWS)
 #undef GB_LAUNCH_GROWS
     cudaError_t err = cudaGetLastError();
     if (err != cudaSuccess) return err;
-    grouped_colmax_kernel<<<g(r.cb_end - r.cb_begin), 256, 0, L.stream>>>(probs, np, r.cb_begin,
-                                                                           r.cb_end, L.status);
+    grouped_colmax_kernel<<<g(r.cb_end - r.cb_begin), 256, 0, L.stream>>>(
+        probs, keys.colblk, r.q_begin, r.q_end, r.cb_begin, r.cb_end, L.status);
     err = cudaGetLastError();
     if (err != cudaSuccess) return err;
-#define GB_LAUNCH_GCOLS(SS)                                                                    \
-    grouped_split_cols_kernel<SS><<<g(r.tb_end - r.tb_begin), 256, 0, L.stream>>>(             \
-        probs, np, r.tb_begin, r.tb_end)
+#define GB_LAUNCH_GCOLS(SS)                                                                   \
+    grouped_split_cols_kernel<SS><<<g(r.tb_end - r.tb_begin), 256, 0, L.stream>>>(            \
+        probs, keys.tblk, r.q_begin, r.q_end, r.tb_begin, r.tb_end)
     GB_SWITCH_S(r.s, GB_LAUNCH_GCOLS)
 #undef GB_LAUNCH_GCOLS
     return cudaGetLastError();
@@ -449,7 +489,7 @@ cudaError_t launch_split_cols(const Launch& L, int s, int64_t n, int64_t k, cons
                               int64_t ldb, uint8_t* digits, int64_t kp, int32_t* exps) {
     if (n == 0) return cudaSuccess;
     const unsigned gx = (unsigned)((n + 31) / 32);
-    colmax_kernel<<<gx, 256, 0, L.stream>>>(n, k, B, ldb, exps, L.status);
+    colmax_kernel<<<gx, 1024, 0, L.stream>>>(n, k, B, ldb, exps, L.status);
     cudaError_t err = cudaGetLastError();
     if (err != cudaSuccess) return err;
     const dim3 grid(gx, (unsigned)((kp + 63) / 64));

@@ -117,6 +117,16 @@ def test_integer_variant_bit_exact(gb, s):
     assert np.array_equal(emulate(gb, A, B, C0, 1.5, 0.5, s), want)
 
 
+@pytest.mark.parametrize("s,k", [(16, 4200), (10, 6600), (10, 13100)])
+def test_long_k_accumulates_in_exact_chunks(gb, s, k):
+    # K beyond (2^24 / (256 s)) runs in several tensor-memory chunks whose exact
+    # 128-bit sums are added (one, two and three chunk boundaries); bit-exact
+    # against the model, whose level sums are exact in FP64.
+    A, B, C0 = inputs("hard", 130, 40, k, 34)
+    want = ozaki.emulated_gemm(-0.5, A, B, 2.0, C0, s=s)
+    assert np.array_equal(emulate(gb, A, B, C0, -0.5, 2.0, s), want)
+
+
 def test_largest_level_sums_exact_in_tensor_memory(gb):
     # every digit of A and B is (16, 0, 0, 0, -16): S_2 = 256 k = 2^21 at k = 8192,
     # the largest exact level-2 sum; the result k (1 - 2^-20)^2 is exact (s = 9).
