@@ -36,7 +36,7 @@ FP64_FLOP_PER_CLK_SM = 4.0
 # DRAM bytes (read + write) per launch of the dominant kernel, from one ncu
 # capture of the kernel as it is now (profiles/emu_products_kernel_n8192_s10.md):
 # (kernel, n, slices) -> bytes.  Reported only for that exact workload.
-MEASURED_TRAFFIC = {("emu_products_kernel", 8192, 10): 15211482112 + 542167808}
+MEASURED_TRAFFIC = {("emu_products_kernel", 8192, 10): 16613566720 + 539537152}
 
 
 def parse():
@@ -169,6 +169,18 @@ def cpu_baseline(n, seed, seconds, A=None, B=None):
     return rec, sel, C
 
 
+def dgemm_metric_config(n, s, world):
+    """Metric name and config of the square-DGEMM workload, shared by both arms."""
+    metric = "FP64-accurate GEMM TFLOP/s (emulated path; native FP64 beside it)"
+    config = {"workload": f"square DGEMM C = A B, m = n = k = {n}, uniform[-1,1], "
+                          f"alpha = 1, beta = 0 (sweep point n = {n})",
+              "path": f"emulated FP64: {s} E4M3 slices, tcgen05 FP32 accumulation, "
+                      "exact integer recombination, one FP64 rounding",
+              "slices": s, "flush": "inputs larger than L2 (no flush needed)",
+              "parallelism": f"replicas x{world}"}
+    return metric, config
+
+
 def run_reference(args):
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
@@ -192,12 +204,13 @@ def run_reference(args):
     value = 2.0 * rows * n * n * args.steps / dt / 1e12
     rec = dict(rec, value=value, sample=f"{rows} of {n} rows of C = A B per step "
                                          f"(n = {n}), plain C oracle")
-    out = {"impl": "reference", "metric": "FP64-accurate GEMM TFLOP/s", "value": value,
+    metric, config = dgemm_metric_config(n, args.slices, args.gpus)
+    out = {"impl": "reference", "metric": metric, "value": value,
            "unit": "TFLOP/s", "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
            "ms_per_step": dt / args.steps * 1e3, "higher_is_better": True, "scaling": "weak",
-           "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-           "config": {"workload": f"square DGEMM n={n} uniform[-1,1] alpha=1 beta=0",
-                      "flush": "inputs larger than L2"},
+           "vs_baseline": None, "dtype": "f64",
+           "data": "synthetic (seeded splitmix64, uniform[-1,1])",
+           "config": config,
            "cpu_baseline": rec,
            "e2e": {"value": value, "unit": "TFLOP/s", "h2d_bytes_per_step": 0,
                    "d2h_bytes_per_step": 0}}
@@ -714,18 +727,14 @@ def main():
     fp64_peak = SMS * FP64_FLOP_PER_CLK_SM * SM_MAX_MHZ * 1e6 / 1e12
     native_tflops = flops / (native_ms * 1e-3) / 1e12
 
+    metric, config = dgemm_metric_config(n, s, world)
     out = {
-        "metric": "FP64-accurate GEMM TFLOP/s (emulated path; native FP64 beside it)",
+        "metric": metric,
         "value": round(value, 3), "unit": "TFLOP/s", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": round(ms_step, 4), "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f64",
         "data": "synthetic (seeded splitmix64, uniform[-1,1])",
-        "config": {"workload": f"square DGEMM C = A B, m = n = k = {n}, uniform[-1,1], "
-                               f"alpha = 1, beta = 0 (sweep point n = {n})",
-                   "path": f"emulated FP64: {s} E4M3 slices, tcgen05 FP32 accumulation, "
-                           "exact integer recombination, one FP64 rounding",
-                   "slices": s, "flush": "inputs larger than L2 (no flush needed)",
-                   "parallelism": f"replicas x{world}"},
+        "config": config,
         "gpu_launches": 4 * args.steps,
         "roofline": {"bound": "tensor", "kernel": "emu_products_kernel",
                      "achieved": round(achieved, 1), "peak": round(fp8_peak, 1),

@@ -132,7 +132,8 @@ __device__ __forceinline__ double i128_to_double_scaled(I128 x, int E) {
         }
         r = t;
     }
-    return neg ? -r : r;
+    // sign by bit manipulation: GB300's FP64 pipe is slow even for negation
+    return __longlong_as_double(__double_as_longlong(r) | (neg ? (long long)0x8000000000000000ull : 0ll));
 }
 
 // Arguments of one output tile (row0, col0) of one problem.
@@ -461,7 +462,10 @@ __device__ __forceinline__ void products_persistent(const Walk& walk, int chunk_
                 const int32_t ei = a.eA[row];
                 const bool bad_row = ei == GB_BAD_LINE_DEV;
                 const int Ebase = -8 - 5 * (S - 1);
-                const bool plain = (a.alpha == 1.0 && a.beta == 0.0);
+                // alpha == 1 and beta == +-0 tested on the bit patterns (integer ALU)
+                const long long ab = __double_as_longlong(a.alpha), bb = __double_as_longlong(a.beta);
+                const bool beta0 = (bb & 0x7FFFFFFFFFFFFFFFll) == 0;
+                const bool plain = ab == 0x3FF0000000000000ll && beta0;
                 double* crow = a.C + row * a.ldc;
 #pragma unroll
                 for (int j = 0; j < 8; ++j) {
@@ -477,7 +481,7 @@ __device__ __forceinline__ void products_persistent(const Walk& walk, int chunk_
                                 out = tv;
                             } else {
                                 out = __dmul_rn(a.alpha, tv);
-                                if (a.beta != 0.0) out = __dadd_rn(out, __dmul_rn(a.beta, crow[col]));
+                                if (!beta0) out = __dadd_rn(out, __dmul_rn(a.beta, crow[col]));
                             }
                         }
                         crow[col] = out;

@@ -2,10 +2,12 @@
 the full sizes of the emulated workload (n = 4096, 8192; uniform[-1, 1] and the
 16-decade hard set), on sampled rows against the double-double reference.
 
-Asserts what the slice-count tuning relies on: the error falls with s; the
-default s = 11 meets the bound on uniform inputs and matches native DGEMM's
-error in the sense rho_emu <= max(1, rho_native); the hard set needs s >= 13.
-Writes the table to gpurun_out/accuracy_sweep.json when that folder exists.
+Asserts what the slice-count tuning relies on: the error falls with s; s = 10
+(the emulated benchmark's setting) is at or below native DGEMM's own error
+(rho_emu <= rho_native, rho = max error / FP64 bound) on uniform inputs, s = 11
+on the hard set, and both are within the FP64 bound.
+Writes the table as JSON to the path in the environment variable
+GB_ACCURACY_TABLE when it is set.
 """
 import json
 import os
@@ -18,7 +20,6 @@ from synth import generators as g
 
 pytestmark = pytest.mark.gpu
 
-ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 
 
 def test_error_vs_slices_at_full_size():
@@ -49,9 +50,9 @@ def test_error_vs_slices_at_full_size():
                 table.append(dict(n=n, kind=kind, slices=s, rho=rho, rho_native=rho_native))
             del A, B, C
             torch.cuda.empty_cache()
-    out = os.path.join(ROOT, "gpurun_out")
-    if os.path.isdir(out):
-        with open(os.path.join(out, "accuracy_sweep.json"), "w") as f:
+    out = os.environ.get("GB_ACCURACY_TABLE")
+    if out:
+        with open(out, "w") as f:
             json.dump(table, f, indent=1)
 
     def rho(n, kind, s):
@@ -60,7 +61,7 @@ def test_error_vs_slices_at_full_size():
     for n in (4096, 8192):
         for kind in ("uniform", "hard"):
             assert rho(n, kind, 14) < rho(n, kind, 8)
-        native = next(r["rho_native"] for r in table if r["n"] == n and r["kind"] == "uniform")
-        assert native < 1.0
-        assert rho(n, "uniform", 11) <= max(1.0, native)
-        assert rho(n, "hard", 13) <= 1.0
+        for kind, s in (("uniform", 10), ("hard", 11)):
+            native = next(r["rho_native"] for r in table if r["n"] == n and r["kind"] == kind)
+            assert native < 1.0
+            assert rho(n, kind, s) <= native
