@@ -266,7 +266,7 @@ def run_grouped(args):
     except Exception:
         tuned = "size rule (no tuning table)"
     seed = g.BASE_SEED + 3
-    s = 12
+    s = args.slices  # the slice count tuned on uniform inputs (error at native DGEMM's)
     probs, ms, ns, ks = _grouped_inputs(gb, torch, args.problems, seed, "native", s)
     flops = float(np.sum(2.0 * ms * ns * ks))
     clocks = ClockSampler(0)

@@ -41,6 +41,19 @@ __device__ __forceinline__ uint32_t e4m3_of_int(int d) {
     return (d < 0 ? 0x80u : 0u) | code;
 }
 
+// E4M3 byte of every signed digit d in [-16, 16], indexed by d mod 64.  Each split
+// kernel fills it first (fill_e4m3_table); the lookup runs on the load/store
+// pipe, which these integer-ALU-bound kernels leave idle.
+__shared__ uint8_t s_e4m3[64];
+
+__device__ __forceinline__ void fill_e4m3_table() {
+    if (threadIdx.x < 64) {
+        const int d = threadIdx.x >= 32 ? (int)threadIdx.x - 64 : (int)threadIdx.x;
+        s_e4m3[threadIdx.x] = (uint8_t)(d >= -16 && d <= 16 ? e4m3_of_int(d) : 0u);
+    }
+    __syncthreads();
+}
+
 // frexp exponent of a finite non-negative double given by its bits (0 -> 0).
 __device__ __forceinline__ int frexp_exp_bits(uint64_t absbits) {
     if (absbits == 0) return 0;
@@ -68,11 +81,10 @@ struct FixedOf {
 //
 // F = X 2^k (k chosen per element) puts the unit of digit t at the fixed bit
 // 1 + 5 (S - t), so each Q_t comes from a constant shift: W = floor(F / 2^(5(S-t)))
-// = 2 Q0 + h, Q_t = (W + 1 - tie) / 2 with tie = (h == 1, Q0 even, no set bit of
-// F below bit 5 (S - t)), the last read off the trailing-zero count of X.  For
-// k < 0 the shift drops bits, which the trailing-zero count also accounts for.
-// Only Q_t mod 64 is kept; |d_t| <= 16 is recovered by sign extension from 6
-// bits.
+// = 2 Q0 + h, Q_t = (W + 1 - tie) / 2, where the tie (exactly half, Q0 even) is:
+// the lowest set bit of F is bit 5 (S - t) (read off the trailing-zero count of
+// X, which also covers the bits a right shift drops for k < 0) and bit 1 of W is
+// clear.  Only Q_t mod 64 is kept: d_t mod 64 indexes the E4M3 table.
 template <int S>
 __device__ __forceinline__ void digits_of(uint64_t bits, int e, int lane, uint64_t (&out)[S]) {
     using Fixed = typename FixedOf<S>::type;
@@ -97,11 +109,11 @@ __device__ __forceinline__ void digits_of(uint64_t bits, int e, int lane, uint64
     for (int t = 1; t <= S; ++t) {
         const int sh = kB * (S - t);
         const uint32_t W = (uint32_t)(F >> sh);
-        const uint32_t tie = ((W & 3u) == 1u && tzF >= sh) ? 1u : 0u;
+        const uint32_t tie = (tzF == sh && (W & 2u) == 0u) ? 1u : 0u;
         const uint32_t q = (W + 1u - tie) >> 1;
-        const int d = ((int)((q - (qprev << kB)) << 26)) >> 26;
+        const uint32_t code = s_e4m3[(q - (qprev << kB)) & 63u];
         qprev = q;
-        out[t - 1] |= (uint64_t)e4m3_of_int(d) << (8 * lane);
+        out[t - 1] |= (uint64_t)code << (8 * lane);
     }
 }
 
@@ -272,6 +284,7 @@ __global__ void __launch_bounds__(128) split_rows_kernel(int64_t m, int64_t k,
                                                          uint8_t* __restrict__ digits,
                                                          int64_t kp, int32_t* __restrict__ exps,
                                                          unsigned* status) {
+    fill_e4m3_table();
     __shared__ uint64_t red[4];
     __shared__ int bad_sh;
     const int64_t mp = (m + kEmuBM - 1) / kEmuBM * kEmuBM;
@@ -297,6 +310,7 @@ __global__ void __launch_bounds__(256) split_cols_kernel(int64_t n, int64_t k,
                                                          uint8_t* __restrict__ digits,
                                                          int64_t kp,
                                                          const int32_t* __restrict__ exps) {
+    fill_e4m3_table();
     __shared__ uint64_t T[64][33];
     split_cols_tile<S>(blockIdx.x, blockIdx.y, n, k, B, ldb, S, digits, kp, exps, T);
 }
@@ -405,6 +419,7 @@ __global__ void __launch_bounds__(256) grouped_split_rows_kernel(const EmuProb* 
                                                                  int64_t row_begin,
                                                                  int64_t row_end,
                                                                  unsigned* status) {
+    fill_e4m3_table();
     __shared__ int e_sh[kEmuBM];
     // rows are padded to 128 per problem, so a 128-row block is one problem's tile
     for (int64_t r0 = row_begin + (int64_t)blockIdx.x * kEmuBM; r0 < row_end;
@@ -434,6 +449,7 @@ __global__ void __launch_bounds__(256) grouped_split_cols_kernel(const EmuProb* 
                                                                  int q_begin, int q_end,
                                                                  int64_t tb_begin,
                                                                  int64_t tb_end) {
+    fill_e4m3_table();
     __shared__ uint64_t T[64][33];
     for (int64_t b = tb_begin + blockIdx.x; b < tb_end; b += gridDim.x) {
         const EmuProb& q = P[find_prob(key, q_begin, q_end - 1, b)];

@@ -142,6 +142,26 @@ def test_emulated_group_with_several_slice_counts(gb):
     plan.close()
 
 
+def test_emulated_group_at_the_tuned_slice_count_meets_the_fp64_bound(gb):
+    """The grouped workload's recipe (m, n, k log-uniform in [16, 512], uniform
+    [-1, 1]) at s = 10, the slice count tuned on uniform inputs: every problem
+    within the FP64 bound against the double-double reference."""
+    import torch
+    from gpu_util import within_bound
+    ms, ns, ks = g.grouped_problems(g.BASE_SEED + 3, 40)
+    probs, host = [], []
+    for i, (m, n, k) in enumerate(zip(ms, ns, ks)):
+        A = g.matrix("uniform", int(m), int(k), 7100 + i, 0)
+        B = g.matrix("uniform", int(k), int(n), 7100 + i, 1)
+        probs.append(dict(A=to_dev(A), B=to_dev(B), C=torch.zeros((int(m), int(n)),
+                     dtype=torch.float64, device="cuda"), precision="emulated", slices=10))
+        host.append((A, B))
+    gb.dgemm_grouped(probs)
+    torch.cuda.synchronize()
+    for p, (A, B) in zip(probs, host):
+        assert within_bound(p["C"].cpu().numpy(), 1.0, A, B, 0.0, np.zeros_like(p["C"].cpu().numpy())) <= 1.0
+
+
 def test_edge_problems_in_a_group(gb):
     import torch
     A, B, C0 = (g.matrix("uniform", 40, 30, 9, 0), g.matrix("uniform", 30, 20, 9, 1),
