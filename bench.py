@@ -46,6 +46,7 @@ def parse():
     p.add_argument("--warmup", type=int, default=3)
     p.add_argument("--n", type=int, default=8192)
     p.add_argument("--slices", type=int, default=10)
+    p.add_argument("--group-slices", type=int, default=11)
     p.add_argument("--native-steps", type=int, default=2)
     p.add_argument("--impl", default="ours", choices=["ours", "reference"])
     p.add_argument("--no-cpu-baseline", action="store_true")
@@ -266,7 +267,10 @@ def run_grouped(args):
     except Exception:
         tuned = "size rule (no tuning table)"
     seed = g.BASE_SEED + 3
-    s = args.slices  # the slice count tuned on uniform inputs (error at native DGEMM's)
+    # the smallest slice count at which every problem of this recipe meets the FP64
+    # bound: the bound falls faster with k than the digit-truncation error, and at
+    # s = 10 some problems with k < 32 exceed it
+    s = args.group_slices
     probs, ms, ns, ks = _grouped_inputs(gb, torch, args.problems, seed, "native", s)
     flops = float(np.sum(2.0 * ms * ns * ks))
     clocks = ClockSampler(0)

@@ -144,8 +144,10 @@ def test_emulated_group_with_several_slice_counts(gb):
 
 def test_emulated_group_at_the_tuned_slice_count_meets_the_fp64_bound(gb):
     """The grouped workload's recipe (m, n, k log-uniform in [16, 512], uniform
-    [-1, 1]) at s = 10, the slice count tuned on uniform inputs: every problem
-    within the FP64 bound against the double-double reference."""
+    [-1, 1]) at s = 11, the slice count its benchmark uses: every problem within
+    the FP64 bound against the double-double reference.  (At s = 10 the CPU model
+    of the split-precision steps already exceeds the bound on a k = 19 problem of
+    this set: the bound falls faster with k than the digit-truncation error.)"""
     import torch
     from gpu_util import within_bound
     ms, ns, ks = g.grouped_problems(g.BASE_SEED + 3, 40)
@@ -154,7 +156,7 @@ def test_emulated_group_at_the_tuned_slice_count_meets_the_fp64_bound(gb):
         A = g.matrix("uniform", int(m), int(k), 7100 + i, 0)
         B = g.matrix("uniform", int(k), int(n), 7100 + i, 1)
         probs.append(dict(A=to_dev(A), B=to_dev(B), C=torch.zeros((int(m), int(n)),
-                     dtype=torch.float64, device="cuda"), precision="emulated", slices=10))
+                     dtype=torch.float64, device="cuda"), precision="emulated", slices=11))
         host.append((A, B))
     gb.dgemm_grouped(probs)
     torch.cuda.synchronize()

@@ -140,3 +140,21 @@ def test_bound_met_with_enough_digits_uniform():
         res = exact.residual(out, 1.0, hi, lo)
         bound = exact.error_bound(k, 1.0, cgemm.dgemm(1.0, np.abs(A), np.abs(B)))
         assert np.all(np.abs(res) <= bound)
+
+
+def test_short_k_needs_one_more_digit():
+    # The FP64 bound 2 (k+2) u (|A||B|) grows like k^2 while the error left by the
+    # truncated digits of a random-sign dot product grows only like sqrt(k): short
+    # dot products need more digits.  Problem 36 of the grouped recipe (47 x 38,
+    # k = 19, uniform inputs) exceeds the bound at s = 10 and meets it at s = 11,
+    # the slice count of the grouped benchmark.
+    ms, ns, ks = g.grouped_problems(g.BASE_SEED + 3, 40)
+    m, n, k = int(ms[36]), int(ns[36]), int(ks[36])
+    assert (m, n, k) == (47, 38, 19)
+    A = g.matrix("uniform", m, k, 7100 + 36, 0)
+    B = g.matrix("uniform", k, n, 7100 + 36, 1)
+    hi, lo = cgemm.dgemm_dd_rows(A, B)
+    bound = exact.error_bound(k, 1.0, cgemm.dgemm(1.0, np.abs(A), np.abs(B)))
+    ratio = {s: np.max(np.abs(exact.residual(ozaki.emulated_gemm(1.0, A, B, s=s), 1.0, hi, lo))
+                       / bound) for s in (10, 11)}
+    assert ratio[10] > 1.0 and ratio[11] <= 0.1
