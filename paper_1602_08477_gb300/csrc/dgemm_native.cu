@@ -84,35 +84,111 @@ __global__ void tiled_kernel(int64_t m, int64_t n, int64_t k, double alpha,
     if (i < m && j < n) store_out<kBeta0>(C, i * ldc + j, alpha, s, beta);
 }
 
-// ---- dfma: 16 x 16 threads, VY x VX elements per thread --------------------------------
-// Tile (16 VY) x (16 VX); thread (ty, tx) owns rows ty + 16r and columns tx + 16c
-// (r < VY, c < VX), so shared-memory reads are broadcasts / consecutive and the
-// global stores of a half-warp are 128 contiguous bytes.  K advances in steps of
-// BK through a register-prefetched, double-buffered shared-memory stage.  Every
-// element accumulates fma(A[i,l], B[l,j], acc) for l = 0, 1, ..., k-1 in order, so
-// all tile shapes give bit-identical results.
-template <int VY, int VX>
+// ---- dfma: TY x TX = 256 threads, VY x VX elements per thread -------------------------
+// Tile (TY VY) x (TX VX); thread (ty, tx) = (tid / TX, tid % TX) owns rows ty + TY r
+// and columns tx + TX c (r < VY, c < VX), so shared-memory reads are broadcasts /
+// consecutive and a warp's global stores are runs of TX contiguous doubles.  K
+// advances in steps of BK through a register-prefetched, double-buffered
+// shared-memory stage.  Every element accumulates fma(A[i,l], B[l,j], acc) for
+// l = 0, 1, ..., k-1 in order, so all tile shapes and thread layouts give
+// bit-identical results.
+// FP64 is the bottleneck on GB300: a warp FMA holds the SM's FP64 pipe for 16 clocks
+// whether 1 or 32 of its lanes are active.  So no warp issues an FMA for padding: a
+// warp (rows 32w / TX + [0, 32 / TX)) skips the row parts r that hold no row below m,
+// every warp the column parts c with TX c >= n - col0 (warp-uniform branches into
+// code specialised for the active parts), and the last K step runs only the k % BK
+// remaining indices.  Ragged problems then waste FMAs only at the granularity of a
+// warp's (32 / TX) x TX block, not on whole padded tiles.  TX = 16 serves the
+// single-GEMM kernel, TX = 8 (4 x 8 blocks) the grouped kernel's small problems.
+template <int VY, int VX, int TX = 16>
 struct DfmaShape {
-    static constexpr int BM = 16 * VY, BN = 16 * VX;
+    static_assert(TX == 8 || TX == 16, "8 or 16 threads along the columns");
+    static constexpr int TY = 256 / TX;
+    static constexpr int BM = TY * VY, BN = TX * VX;
     static constexpr int BK = (VY * VX >= 64) ? 8 : 16;   // <= 48 KB static smem
     static constexpr int A_STAGE = BK * (BM + 1), B_STAGE = BK * BN;
     static constexpr int SMEM_DOUBLES = 2 * (A_STAGE + B_STAGE);
 };
 
-template <int VY, int VX>
+// One K index l of the active parts r < RA, c < CA.
+template <int VY, int VX, int TX, int RA, int CA>
+__device__ __forceinline__ void dfma_step(const double* __restrict__ as,
+                                          const double* __restrict__ bs, int l, int ty, int tx,
+                                          double (&acc)[VY][VX]) {
+    using S = DfmaShape<VY, VX, TX>;
+    double av[RA], bv[CA];
+#pragma unroll
+    for (int r = 0; r < RA; ++r) av[r] = as[l * (S::BM + 1) + ty + S::TY * r];
+#pragma unroll
+    for (int c = 0; c < CA; ++c) bv[c] = bs[l * S::BN + tx + TX * c];
+#pragma unroll
+    for (int r = 0; r < RA; ++r)
+#pragma unroll
+        for (int c = 0; c < CA; ++c) acc[r][c] = fma(av[r], bv[c], acc[r][c]);
+}
+
+// The nl (<= BK) K indices of one shared-memory stage for the active parts.
+template <int VY, int VX, int TX, int RA, int CA>
+__device__ __forceinline__ void dfma_stage(const double* __restrict__ as,
+                                           const double* __restrict__ bs, int nl, int ty,
+                                           int tx, double (&acc)[VY][VX]) {
+    constexpr int BK = DfmaShape<VY, VX, TX>::BK;
+    if (nl == BK) {
+#pragma unroll
+        for (int l = 0; l < BK; ++l) dfma_step<VY, VX, TX, RA, CA>(as, bs, l, ty, tx, acc);
+    } else {
+#pragma unroll 1
+        for (int l = 0; l < nl; ++l) dfma_step<VY, VX, TX, RA, CA>(as, bs, l, ty, tx, acc);
+    }
+}
+
+template <int VY, int VX, int TX, int RA, int CA>
+__device__ __forceinline__ void dfma_stage_ca(int ca, const double* __restrict__ as,
+                                              const double* __restrict__ bs, int nl, int ty,
+                                              int tx, double (&acc)[VY][VX]) {
+    if constexpr (CA > 1) {
+        if (ca < CA) return dfma_stage_ca<VY, VX, TX, RA, CA - 1>(ca, as, bs, nl, ty, tx, acc);
+    }
+    dfma_stage<VY, VX, TX, RA, CA>(as, bs, nl, ty, tx, acc);
+}
+
+template <int VY, int VX, int TX, int RA>
+__device__ __forceinline__ void dfma_stage_ra(int ra, int ca, const double* __restrict__ as,
+                                              const double* __restrict__ bs, int nl, int ty,
+                                              int tx, double (&acc)[VY][VX]) {
+    if constexpr (RA > 1) {
+        if (ra < RA) return dfma_stage_ra<VY, VX, TX, RA - 1>(ra, ca, as, bs, nl, ty, tx, acc);
+    }
+    dfma_stage_ca<VY, VX, TX, RA, VX>(ca, as, bs, nl, ty, tx, acc);
+}
+
+// Dispatch on the warp's active row parts ra and the tile's active column parts ca
+// (both >= 1).  Register tiles of more than 16 elements (large square problems,
+// where padding is negligible) keep the full tile and only trim the K tail.
+template <int VY, int VX, int TX>
+__device__ __forceinline__ void dfma_stage_active(int ra, int ca, const double* __restrict__ as,
+                                                  const double* __restrict__ bs, int nl,
+                                                  int ty, int tx, double (&acc)[VY][VX]) {
+    if constexpr (VY * VX <= 16)
+        dfma_stage_ra<VY, VX, TX, VY>(ra, ca, as, bs, nl, ty, tx, acc);
+    else
+        dfma_stage<VY, VX, TX, VY, VX>(as, bs, nl, ty, tx, acc);
+}
+
+template <int VY, int VX, int TX = 16>
 __device__ __forceinline__ void dfma_tile(int64_t m, int64_t n, int64_t k, double alpha,
                                           const double* __restrict__ A, int64_t lda,
                                           const double* __restrict__ B, int64_t ldb,
                                           double beta, double* __restrict__ C, int64_t ldc,
                                           int64_t row0, int64_t col0, double* smem) {
-    using S = DfmaShape<VY, VX>;
-    constexpr int BM = S::BM, BN = S::BN, BK = S::BK;
+    using S = DfmaShape<VY, VX, TX>;
+    constexpr int BM = S::BM, BN = S::BN, BK = S::BK, TY = S::TY;
     constexpr int A_PER_T = BM * BK / 256;  // elements of the A tile each thread loads
     constexpr int B_PER_T = BK * BN / 256;
     double* As = smem;                       // [2][BK][BM + 1]: transposed, As[l][row]
     double* Bs = smem + 2 * S::A_STAGE;      // [2][BK][BN]
     const int tid = threadIdx.x;
-    const int tx = tid & 15, ty = tid >> 4;
+    const int tx = tid % TX, ty = tid / TX;
 
     double acc[VY][VX];
 #pragma unroll
@@ -152,6 +228,12 @@ __device__ __forceinline__ void dfma_tile(int64_t m, int64_t n, int64_t k, doubl
         }
     };
 
+    // active parts: row part r of warp w holds rows 32w / TX + [0, 32 / TX) + TY r
+    const int64_t mr = m - row0, nr = n - col0;
+    const int64_t wrows = mr - (int64_t)((tid >> 5) * (32 / TX));
+    const int act_r = wrows <= 0 ? 0 : (wrows >= (int64_t)TY * VY ? VY
+                                                                   : (int)((wrows + TY - 1) / TY));
+    const int act_c = nr <= 0 ? 0 : (nr >= (int64_t)TX * VX ? VX : (int)((nr + TX - 1) / TX));
     const int64_t nk = (k + BK - 1) / BK;
     if (nk > 0) {
         load_regs(0);
@@ -163,29 +245,22 @@ __device__ __forceinline__ void dfma_tile(int64_t m, int64_t n, int64_t k, doubl
         if (kt + 1 < nk) load_regs((kt + 1) * BK);
         const double* as = As + buf * S::A_STAGE;
         const double* bs = Bs + buf * S::B_STAGE;
-#pragma unroll
-        for (int l = 0; l < BK; ++l) {
-            double av[VY], bv[VX];
-#pragma unroll
-            for (int r = 0; r < VY; ++r) av[r] = as[l * (BM + 1) + ty + 16 * r];
-#pragma unroll
-            for (int c = 0; c < VX; ++c) bv[c] = bs[l * BN + tx + 16 * c];
-#pragma unroll
-            for (int r = 0; r < VY; ++r)
-#pragma unroll
-                for (int c = 0; c < VX; ++c) acc[r][c] = fma(av[r], bv[c], acc[r][c]);
-        }
+        const int nl = kt + 1 < nk ? BK : (int)(k - kt * BK);
+        if (act_r == VY && act_c == VX && nl == BK)
+            dfma_stage<VY, VX, TX, VY, VX>(as, bs, BK, ty, tx, acc);
+        else if (act_r > 0 && act_c > 0)
+            dfma_stage_active<VY, VX, TX>(act_r, act_c, as, bs, nl, ty, tx, acc);
         if (kt + 1 < nk) store_smem(buf ^ 1);
         __syncthreads();
     }
     const bool beta0 = beta == 0.0;
 #pragma unroll
     for (int r = 0; r < VY; ++r) {
-        const int64_t gi = row0 + ty + 16 * r;
+        const int64_t gi = row0 + ty + TY * r;
         if (gi >= m) continue;
 #pragma unroll
         for (int c = 0; c < VX; ++c) {
-            const int64_t gj = col0 + tx + 16 * c;
+            const int64_t gj = col0 + tx + TX * c;
             if (gj < n) {
                 double* cp = &C[gi * ldc + gj];
                 *cp = beta0 ? alpha * acc[r][c] : alpha * acc[r][c] + beta * (*cp);
@@ -365,10 +440,13 @@ __global__ void __launch_bounds__(32 * WARPS_M * WARPS_N)
 // of expensive problems, placed first in the table, start first), finds its
 // problem by binary search over the tile prefix, and runs that problem's tile
 // variant on the FP64 FMA pipe.  One shared buffer serves every variant.
-constexpr int kGroupedSmemDoubles = DfmaShape<4, 4>::SMEM_DOUBLES;
-static_assert(DfmaShape<2, 2>::SMEM_DOUBLES <= kGroupedSmemDoubles, "smem");
-static_assert(DfmaShape<4, 2>::SMEM_DOUBLES <= kGroupedSmemDoubles, "smem");
-static_assert(DfmaShape<2, 4>::SMEM_DOUBLES <= kGroupedSmemDoubles, "smem");
+// Tiles use 32 x 8 threads (TX = 8): a warp covers 4 rows x 8 columns per part, so
+// the ragged edges of small problems cost FMAs only up to that granularity.
+constexpr int kGroupedTX = 8;
+constexpr int kGroupedSmemDoubles = DfmaShape<2, 8, kGroupedTX>::SMEM_DOUBLES;
+static_assert(DfmaShape<1, 4, kGroupedTX>::SMEM_DOUBLES <= kGroupedSmemDoubles, "smem");
+static_assert(DfmaShape<2, 4, kGroupedTX>::SMEM_DOUBLES <= kGroupedSmemDoubles, "smem");
+static_assert(DfmaShape<1, 8, kGroupedTX>::SMEM_DOUBLES <= kGroupedSmemDoubles, "smem");
 
 __global__ void __launch_bounds__(256) grouped_native_kernel(const GroupProb* __restrict__ probs,
                                                              int nprob, int64_t total_tiles,
@@ -391,20 +469,20 @@ __global__ void __launch_bounds__(256) grouped_native_kernel(const GroupProb* __
         const int64_t tm = local / P.tiles_n, tn = local % P.tiles_n;
         switch (P.tile) {
             case kTile64x64:
-                dfma_tile<4, 4>(P.m, P.n, P.k, P.alpha, P.A, P.lda, P.B, P.ldb, P.beta, P.C,
-                                P.ldc, tm * 64, tn * 64, smem);
+                dfma_tile<2, 8, kGroupedTX>(P.m, P.n, P.k, P.alpha, P.A, P.lda, P.B, P.ldb,
+                                            P.beta, P.C, P.ldc, tm * 64, tn * 64, smem);
                 break;
             case kTile32x32:
-                dfma_tile<2, 2>(P.m, P.n, P.k, P.alpha, P.A, P.lda, P.B, P.ldb, P.beta, P.C,
-                                P.ldc, tm * 32, tn * 32, smem);
+                dfma_tile<1, 4, kGroupedTX>(P.m, P.n, P.k, P.alpha, P.A, P.lda, P.B, P.ldb,
+                                            P.beta, P.C, P.ldc, tm * 32, tn * 32, smem);
                 break;
             case kTile64x32:
-                dfma_tile<4, 2>(P.m, P.n, P.k, P.alpha, P.A, P.lda, P.B, P.ldb, P.beta, P.C,
-                                P.ldc, tm * 64, tn * 32, smem);
+                dfma_tile<2, 4, kGroupedTX>(P.m, P.n, P.k, P.alpha, P.A, P.lda, P.B, P.ldb,
+                                            P.beta, P.C, P.ldc, tm * 64, tn * 32, smem);
                 break;
             default:
-                dfma_tile<2, 4>(P.m, P.n, P.k, P.alpha, P.A, P.lda, P.B, P.ldb, P.beta, P.C,
-                                P.ldc, tm * 32, tn * 64, smem);
+                dfma_tile<1, 8, kGroupedTX>(P.m, P.n, P.k, P.alpha, P.A, P.lda, P.B, P.ldb,
+                                            P.beta, P.C, P.ldc, tm * 32, tn * 64, smem);
                 break;
         }
     }
