@@ -174,20 +174,28 @@ gb_status gb_dgemm_workspace_size(gb_precision prec, int slices, int64_t m, int6
 /*
  * Layout of the emulated path's workspace (all offsets in bytes from its
  * start, each 1024-byte aligned), for tests and for callers who run the steps
- * one at a time:
- *   a_digits  s planes of m rows x kp bytes: E4M3 digit t of A[i, l] at
- *             a_digits + (t * m + i) * kp + l, zero for l >= k
- *   b_digits  s planes of n rows x kp bytes: digit t of B[l, j] at
- *             b_digits + (t * n + j) * kp + l (B transposed, K-major)
+ * one at a time.  Digits are E4M3 bytes stored pre-tiled, in the order the
+ * tensor-core products read them: lines (rows of A, columns of B) are grouped in
+ * tiles of R lines (R = a_tile_rows = 128 for A, b_tile_rows for B: 48 when
+ * slices <= 10, else 32), K in blocks of 32 bytes, and per (tile, K block) the
+ * s slices follow one another, each an R x 32-byte K-major block whose 16-byte
+ * halves are swapped on lines with ((line % R) / 4) odd (the 32-byte swizzle):
+ *   digit t of line x at K index l (nkb = kp / 32, c = l % 32, r = x % R):
+ *     base + (((x / R) * nkb + l / 32) * s + t) * R * 32 + r * 32
+ *          + ((c / 16) ^ ((r / 4) & 1)) * 16 + c % 16
+ *   a_digits  base of A's digits (line x = row i of A), rows padded to R
+ *   b_digits  base of B's digits (line x = column j of B), columns padded to R
  *   a_exp     m int32: exponent e_i of max_l |A[i, l]| (frexp convention),
  *             GB_BAD_LINE if row i holds a NaN or Inf
  *   b_exp     n int32: exponent f_j of max_l |B[l, j]|, or GB_BAD_LINE
- * with kp = k rounded up to a multiple of 32.
+ * with kp = k rounded up to a multiple of 32; padding lines and K indices
+ * l >= k hold zero digits.
  */
 #define GB_BAD_LINE 0x40000000
 typedef struct {
     int64_t kp;
     size_t a_digits, b_digits, a_exp, b_exp, total;
+    int32_t a_tile_rows, b_tile_rows;
 } gb_emulated_layout;
 
 gb_status gb_emulated_layout_get(int slices, int64_t m, int64_t n, int64_t k,

@@ -56,7 +56,8 @@ class Workdiv(ctypes.Structure):
 class EmulatedLayout(ctypes.Structure):
     _fields_ = [("kp", ctypes.c_int64), ("a_digits", ctypes.c_size_t),
                 ("b_digits", ctypes.c_size_t), ("a_exp", ctypes.c_size_t),
-                ("b_exp", ctypes.c_size_t), ("total", ctypes.c_size_t)]
+                ("b_exp", ctypes.c_size_t), ("total", ctypes.c_size_t),
+                ("a_tile_rows", ctypes.c_int32), ("b_tile_rows", ctypes.c_int32)]
 
 
 _lock = threading.Lock()

@@ -201,7 +201,8 @@ EmuLayout emu_layout(int s, int64_t m, int64_t n, int64_t k) {
     auto up = [](size_t x) { return (x + 1023) & ~(size_t)1023; };
     size_t off = 0;
     const size_t mp = (size_t)((m + kEmuBM - 1) / kEmuBM) * kEmuBM;
-    const size_t np = (size_t)((n + kEmuGroupBN - 1) / kEmuGroupBN) * kEmuGroupBN;
+    L.bn = emu_bn(s);
+    const size_t np = (size_t)((n + L.bn - 1) / L.bn) * L.bn;
     L.a_digits = off;
     off = up(off + (size_t)s * mp * (size_t)L.kp);
     L.b_digits = off;
@@ -349,6 +350,8 @@ gb_status gb_emulated_layout_get(int slices, int64_t m, int64_t n, int64_t k,
     out->a_exp = L.a_exp;
     out->b_exp = L.b_exp;
     out->total = L.total;
+    out->a_tile_rows = kEmuBM;
+    out->b_tile_rows = L.bn;
     return GB_OK;
 }
 

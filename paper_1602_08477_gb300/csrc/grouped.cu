@@ -126,7 +126,7 @@ gb_status build_layout(const gb_gemm_desc* d, int64_t count, Layout& L) {
             e.alpha = x.alpha;
             e.beta = x.beta;
             e.s = s;
-            e.tiles_n = (int32_t)((x.n + kEmuGroupBN - 1) / kEmuGroupBN);
+            e.tiles_n = (int32_t)((x.n + emu_bn(s) - 1) / emu_bn(s));
             L.emu.push_back(e);
             L.emu_ws.push_back(emu_layout(s, x.m, x.n, x.k));
             L.emu_idx.push_back(i);
@@ -189,10 +189,11 @@ gb_status build_layout(const gb_gemm_desc* d, int64_t count, Layout& L) {
         L.keys[1].push_back(colblks);
         L.keys[2].push_back(tblks);
         L.keys[3].push_back(tiles);
-        const int64_t ncb = (e.n + 31) / 32;
+        const int64_t ncb = (e.n + 31) / 32;                          // real columns
+        const int64_t ncbp = ((int64_t)e.tiles_n * w.bn + 31) / 32;   // padded to tiles
         rows += (e.m + kEmuBM - 1) / kEmuBM * kEmuBM;
         colblks += ncb;
-        tblks += ncb * ((w.kp + 63) / 64);
+        tblks += ncbp * ((w.kp + 63) / 64);
         const int64_t nt = ((e.m + kEmuBM - 1) / kEmuBM) * e.tiles_n;
         tiles += nt;
         if (L.s_ranges.empty() || L.s_ranges.back().s != e.s)

@@ -75,7 +75,7 @@ int grouped_native_occupancy();
 
 // ---- emulated FP64 (ozaki_split.cu, ozaki_gemm.cu) ----
 // Workspace of the emulated path.  Digits are stored pre-tiled: for each tile of
-// R rows (R = 128 for A's rows, 32 for B's columns) and each 32-byte K block,
+// R rows (R = 128 for A's rows, emu_bn(s) for B's columns) and each 32-byte K block,
 // the s slices follow one another, each an R x 32-byte K-major block in the
 // 32-byte swizzle (16-byte chunk c of row r stored at chunk c ^ ((r / 4) & 1)),
 // i.e. exactly the shared-memory image the tensor core reads:
@@ -86,6 +86,7 @@ int grouped_native_occupancy();
 struct EmuLayout {
     int64_t kp;
     size_t a_digits, b_digits, a_exp, b_exp, total;
+    int bn;  // lines of a B digit tile = output tile columns, emu_bn(s)
 };
 EmuLayout emu_layout(int s, int64_t m, int64_t n, int64_t k);
 
@@ -103,8 +104,8 @@ struct EmuProb {
     int32_t s, tiles_n;
     int64_t first_row;     // exclusive prefixes over the table of: rows of A padded to 128,
     int64_t first_colblk;  // 32-column blocks of B,
-    int64_t first_tblk;    // (32-column x 64-row) blocks of B,
-    int64_t first_tile;    // 128 x 32 output tiles
+    int64_t first_tblk;    // (32-column x 64-row) blocks of B's padded columns,
+    int64_t first_tile;    // 128 x emu_bn(s) output tiles
 };
 
 // The same four prefixes as compact arrays (one int64 per table entry), the
@@ -133,12 +134,16 @@ struct EmuSRange {
 // Grouped e1 + e2 over the problems of one slice-count range (three launches).
 cudaError_t launch_grouped_split(const Launch& L, const EmuProb* probs, const EmuKeys& keys,
                                  const EmuSRange& r);
-// Grouped e3 + e4: persistent CTAs over the 128 x 32 output tiles of the
+// Grouped e3 + e4: persistent CTAs over the 128 x emu_bn(s) output tiles of the
 // problems of one slice-count range.
 cudaError_t launch_grouped_products(const Launch& L, const EmuProb* probs, const EmuKeys& keys,
                                     const EmuSRange& r);
-constexpr int kEmuBM = 128;      // output tile rows of the products kernel (A digit tile rows)
-constexpr int kEmuGroupBN = 32;  // output tile columns (B digit tile rows)
+constexpr int kEmuBM = 128;  // output tile rows of the products kernel (A digit tile rows)
+// Output tile columns of the products kernel (= lines of a B digit tile) for s
+// slices: the s level accumulators of a tile take s * BN of the 512 TMEM columns,
+// and a wider tile reuses each staged A slice for more outputs, so BN = 48 while
+// 48 s <= 512 (s <= 10) and 32 above.
+__host__ __device__ constexpr int emu_bn(int s) { return s <= 10 ? 48 : 32; }
 
 
 cudaError_t launch_split_rows(const Launch& L, int s, int64_t m, int64_t k, const double* A,

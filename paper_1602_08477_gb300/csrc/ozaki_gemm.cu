@@ -1,6 +1,7 @@
 // Emulated FP64 GEMM, steps e3 + e4 on the tcgen05 tensor cores.
 //
-// e3: for an output tile of 128 rows x BN columns, the level sums
+// e3: for an output tile of 128 rows x BN columns (BN = emu_bn(s): 48 for
+//     s <= 10, else 32), the level sums
 //       S_g = sum_{p + q = g} DA_p DB_q^T,  g = 2 .. s+1,
 //     of the E4M3 digit planes (|digit| <= 16) are accumulated in tensor memory,
 //     one FP32 accumulator of 128 lanes x BN columns per level (s * BN <= 512
@@ -25,7 +26,7 @@
 //                   sharing an A slice go into one MMA) and commits each stage
 //                   back to the producer.
 //   warps 2 - 17  : epilogue; warp w reads TMEM lanes 32 (w % 4) .. + 31 and
-//                   the 8 columns of group (w - 2) / 4 of every level.
+//                   the BN / 4 columns of group (w - 2) / 4 of every level.
 // Every wait on an mbarrier is bounded (wall-clock); on a timeout the CTA records
 // the timeout bit in the status word, skips its output and still frees TMEM.
 #include <cuda_runtime.h>
@@ -41,7 +42,6 @@ namespace gb {
 namespace {
 
 constexpr int kBM = kEmuBM;
-constexpr int kBN = kEmuGroupBN;
 constexpr int kBKBytes = 32;
 constexpr int kEpiWarps = 16;    // 4 TMEM lane quarters x 4 column groups of 8
 constexpr int kThreads = 32 * (2 + kEpiWarps);
@@ -168,7 +168,7 @@ __host__ __device__ constexpr int split_point(int S) {
     return (S + 1) / 2 > 2 * S - 16 ? (S + 1) / 2 : 2 * S - 16;
 }
 
-template <int S, bool kSplit>
+template <int S, int BN, bool kSplit>
 __device__ __forceinline__ void issue_kblock(uint64_t adesc, uint64_t bdesc, uint32_t tmem_base,
                                              bool first) {
     constexpr int G = kSplit ? split_point(S) : S;
@@ -177,11 +177,11 @@ __device__ __forceinline__ void issue_kblock(uint64_t adesc, uint64_t bdesc, uin
         const uint64_t ad = adesc + (uint64_t)(((p - 1) * kBM * kBKBytes) >> 4);
         // the first slice of each accumulator set covers all of its levels
         const uint32_t acc = (first && (p == 1 || p == G + 1)) ? 0u : 1u;
-        const uint32_t col0 = p > G ? (uint32_t)(kBN * S + (p - 1 - G) * kBN)
-                                    : (uint32_t)((p - 1) * kBN);
-        const int rows = kBN * (S + 1 - p);
+        const uint32_t col0 = p > G ? (uint32_t)(BN * S + (p - 1 - G) * BN)
+                                    : (uint32_t)((p - 1) * BN);
+        const int rows = BN * (S + 1 - p);
 #pragma unroll
-        for (int r0 = 0; r0 < kBN * S; r0 += 256) {
+        for (int r0 = 0; r0 < BN * S; r0 += 256) {
             if (r0 < rows) {
                 const int nn = rows - r0 < 256 ? rows - r0 : 256;
                 const uint64_t bd = bdesc + (uint64_t)((r0 * kBKBytes) >> 4);
@@ -196,11 +196,11 @@ __device__ __forceinline__ void issue_kblock(uint64_t adesc, uint64_t bdesc, uin
 // (at most 4), so the per-stage wait / fence / commit of the issuing thread is
 // shared by KB K blocks.
 __host__ __device__ constexpr int kblocks_per_stage(int S) {
-    return ((kSmemLimit - 2048) / (2 * S * (kBM + kBN) * kBKBytes)) < 1
+    return ((kSmemLimit - 2048) / (2 * S * (kBM + emu_bn(S)) * kBKBytes)) < 1
                ? 1
-               : ((kSmemLimit - 2048) / (2 * S * (kBM + kBN) * kBKBytes)) > 4
+               : ((kSmemLimit - 2048) / (2 * S * (kBM + emu_bn(S)) * kBKBytes)) > 4
                      ? 4
-                     : ((kSmemLimit - 2048) / (2 * S * (kBM + kBN) * kBKBytes));
+                     : ((kSmemLimit - 2048) / (2 * S * (kBM + emu_bn(S)) * kBKBytes));
 }
 
 // Exactness of the FP32 level sums: an accumulator that collects P pair products
@@ -240,42 +240,71 @@ __device__ __forceinline__ void i128_add_shl(I128& x, int64_t v, int sh) {
     x.lo = nlo;
 }
 
-// T += sum_g S_g 2^(5 (S+1-g)) over the S levels of one accumulation unit for 8
-// columns (one TMEM lane per thread; level index L = g - 2 at column col_addr +
-// 32 L, plus col_addr + 32 (S + L - G) for L >= G with split accumulators), exactly:
-// Horner in int64 over runs of at most 6 levels (each |S_g| < 2^25 as the sum of
-// two accumulators, so a run stays below 2^55), each run added into the 128-bit
-// T at its own weight, so the chunks of a tile add up in the same T.
-// small: every accumulator below 2^22 (cheaper conversion).
-template <int S, bool kSplit>
-__device__ __forceinline__ void add_levels(uint32_t col_addr, bool small, I128 (&T)[8]) {
-    constexpr int split_g = kSplit ? split_point(S) : S;
-    int64_t G[8];
+// Columns of an epilogue warp: column group g (0 .. 3) of a BN-column level owns
+// columns 8g .. 8g+7 and, for BN = 48, also 32 + 4g .. 32 + 4g + 3 (so every TMEM
+// load starts on a multiple of its own width).  Column j (< BN / 4) of the group:
+__host__ __device__ constexpr int epi_col(int g, int j) {
+    return j < 8 ? 8 * g + j : 32 + 4 * g + (j - 8);
+}
+
+// The BN / 4 columns of column group g of the level at TMEM address `level`
+// (lane quarter already added) for this warp's 32 lanes.
+template <int BN>
+__device__ __forceinline__ void tmem_ld_cols(uint32_t level, int g, uint32_t (&v)[BN / 4]) {
+    static_assert(BN == 32 || BN == 48, "32 or 48 columns per tile");
+    uint32_t a[8];
+    ptx::tmem_ld_32x32b_x8(level + (uint32_t)(8 * g), a);
 #pragma unroll
-    for (int j = 0; j < 8; ++j) G[j] = 0;
+    for (int j = 0; j < 8; ++j) v[j] = a[j];
+    if constexpr (BN == 48) {
+        uint32_t b[4];
+        ptx::tmem_ld_32x32b_x4(level + (uint32_t)(32 + 4 * g), b);
+#pragma unroll
+        for (int j = 0; j < 4; ++j) v[8 + j] = b[j];
+    }
+}
+
+// T += sum_g S_g 2^(5 (S+1-g)) over the S levels of one accumulation unit for the
+// CW = BN / 4 columns of column group cg of this thread's TMEM lane (level index
+// L = g - 2 at lane_addr + BN L, plus lane_addr + BN (S + L - G) for L >= G with
+// split accumulators), exactly: Horner in int64 over runs of at most 6 levels (each
+// |S_g| < 2^25 as the sum of two accumulators, so a run stays below 2^55), each
+// run added into the 128-bit T at its own weight, so the chunks of a tile add up
+// in the same T.  small: every accumulator below 2^22 (cheaper conversion).
+// With 12 columns per thread the run registers would not fit beside T: each
+// level is added into T directly (runs of one level).
+template <int S, int BN, bool kSplit>
+__device__ __forceinline__ void add_levels(uint32_t lane_addr, int cg, bool small,
+                                           I128 (&T)[BN / 4]) {
+    constexpr int CW = BN / 4;
+    constexpr int kRun = CW <= 8 ? 6 : 1;
+    constexpr int split_g = kSplit ? split_point(S) : S;
+    int64_t G[CW];
+#pragma unroll
+    for (int j = 0; j < CW; ++j) G[j] = 0;
     int in_group = 0;
 #pragma unroll 1
     for (int L = 0; L < S; ++L) {
         const bool two = L >= split_g;
-        uint32_t v[8], y[8];
-        ptx::tmem_ld_32x32b_x8(col_addr + (uint32_t)L * kBN, v);
-        if (two) ptx::tmem_ld_32x32b_x8(col_addr + (uint32_t)(S + L - split_g) * kBN, y);
+        uint32_t v[CW], y[CW];
+        tmem_ld_cols<BN>(lane_addr + (uint32_t)L * BN, cg, v);
+        if (two) tmem_ld_cols<BN>(lane_addr + (uint32_t)(S + L - split_g) * BN, cg, y);
         ptx::tmem_ld_wait();
         if (small) {
 #pragma unroll
-            for (int j = 0; j < 8; ++j)
+            for (int j = 0; j < CW; ++j)
                 G[j] = G[j] * 32 + (int64_t)f32_small_int_value(v[j]) +
                        (two ? (int64_t)f32_small_int_value(y[j]) : 0);
         } else {
 #pragma unroll
-            for (int j = 0; j < 8; ++j)
+            for (int j = 0; j < CW; ++j)
                 G[j] = G[j] * 32 + f32_int_value(v[j]) + (two ? f32_int_value(y[j]) : 0);
         }
         ++in_group;
-        if (in_group == 6 || L == S - 1) {
+        if (in_group == kRun || L == S - 1) {
             const int sh = 5 * (S - 1 - L);  // weight of the run's last level
 #pragma unroll
-            for (int j = 0; j < 8; ++j) {
+            for (int j = 0; j < CW; ++j) {
                 i128_add_shl(T[j], G[j], sh);
                 G[j] = 0;
             }
@@ -311,14 +340,14 @@ AccPlan acc_plan(int64_t kp, bool allow_split) {
 // ahead into the next tile's stages, and the epilogue hands TMEM back (tmem_empty)
 // as soon as it has read the level sums, so the next tile's MMAs overlap its
 // rounding and stores.  `smem` is 1024-byte aligned and holds `stages` ring slots
-// of `slot_bytes` (>= KB * S * 5 KiB) plus a SmemTail.  A stage holds KB
-// consecutive K blocks: their A tiles (KB * S * 4 KiB, contiguous in the
-// workspace) then their B tiles (KB * S * 1 KiB).
-template <int S, int KB, bool kSplit, class Walk>
+// of `slot_bytes` (>= KB * S * (128 + BN) * 32 bytes) plus a SmemTail.  A stage
+// holds KB consecutive K blocks: their A tiles (KB * S * 4 KiB, contiguous in the
+// workspace) then their B tiles (KB * S * BN * 32 bytes).
+template <int S, int BN, int KB, bool kSplit, class Walk>
 __device__ __forceinline__ void products_persistent(const Walk& walk, int chunk_stages,
                                                     uint8_t* smem, int stages,
                                                     uint32_t slot_bytes, unsigned* status) {
-    constexpr int BN = kBN;
+    constexpr int CW = BN / 4;  // columns per epilogue warp
     SmemTail* tail = reinterpret_cast<SmemTail*>(smem + (size_t)stages * slot_bytes);
     uint64_t* full = tail->bars;
     uint64_t* empty = tail->bars + stages;
@@ -413,7 +442,7 @@ __device__ __forceinline__ void products_persistent(const Walk& walk, int chunk_
 #pragma unroll
                 for (int kk = 0; kk < KB; ++kk) {
                     if (kk < kc)
-                        issue_kblock<S, kSplit>(adesc + (uint64_t)((kk * a_bytes) >> 4),
+                        issue_kblock<S, BN, kSplit>(adesc + (uint64_t)((kk * a_bytes) >> 4),
                                                 bdesc + (uint64_t)((kk * b_bytes) >> 4),
                                                 tmem_base, chunk_start && kk == 0);
                 }
@@ -431,7 +460,7 @@ __device__ __forceinline__ void products_persistent(const Walk& walk, int chunk_
         const int kCS = chunk_stages;
         const int quarter = warp & 3;
         const int cgroup = (warp - 2) >> 2;
-        const uint32_t col_addr = tmem_base + ((uint32_t)(quarter * 32) << 16) + cgroup * 8;
+        const uint32_t lane_addr = tmem_base + ((uint32_t)(quarter * 32) << 16);
         uint32_t chunk_iter = 0;
         bool stop = false;
         Walk w = walk;
@@ -439,9 +468,9 @@ __device__ __forceinline__ void products_persistent(const Walk& walk, int chunk_
             const TileArgs a = w.args();
             const int nch = ((a.nkb + KB - 1) / KB + kCS - 1) / kCS;
             const bool small = a.nkb * S < 512;  // every accumulator below 2^22
-            I128 T[8];
+            I128 T[CW];
 #pragma unroll
-            for (int j = 0; j < 8; ++j) T[j] = I128{0, 0};
+            for (int j = 0; j < CW; ++j) T[j] = I128{0, 0};
             for (int c = 0; c < nch; ++c, ++chunk_iter) {
                 const bool ok = ptx::mbar_wait_bounded(tmem_full, chunk_iter & 1u, abort, status,
                                                        kStatusTimeout, kWaitTimeoutNs);
@@ -450,7 +479,7 @@ __device__ __forceinline__ void products_persistent(const Walk& walk, int chunk_
                     stop = true;
                     break;
                 }
-                add_levels<S, kSplit>(col_addr, small, T);
+                add_levels<S, BN, kSplit>(lane_addr, cgroup, small, T);
                 // accumulators read: hand TMEM to the next unit's MMAs
                 ptx::tc_fence_before();
                 __syncwarp();
@@ -468,8 +497,8 @@ __device__ __forceinline__ void products_persistent(const Walk& walk, int chunk_
                 const bool plain = ab == 0x3FF0000000000000ll && beta0;
                 double* crow = a.C + row * a.ldc;
 #pragma unroll
-                for (int j = 0; j < 8; ++j) {
-                    const int64_t col = a.col0 + cgroup * 8 + j;
+                for (int j = 0; j < CW; ++j) {
+                    const int64_t col = a.col0 + epi_col(cgroup, j);
                     if (col < a.n) {
                         const int32_t fj = a.fB[col];
                         double out;
@@ -515,6 +544,7 @@ __device__ __forceinline__ uint8_t* aligned_smem(uint8_t* raw) {
 // the end: the next wave keeps the same A strips, and the K blocks the previous
 // wave read last are the ones still in L2.  The order of the K blocks does not
 // change a bit of the result: the level sums are exact integers.
+template <int BN>
 struct RasterWalk {
     const uint8_t* ad;
     const uint8_t* bd;
@@ -538,7 +568,7 @@ struct RasterWalk {
         const int tn = (bid % group_size) / gm;
         TileArgs a;
         a.a_src = ad + (size_t)tm * nkb * s * kBM * kBKBytes;
-        a.b_src = bd + (size_t)tn * nkb * s * kBN * kBKBytes;
+        a.b_src = bd + (size_t)tn * nkb * s * BN * kBKBytes;
         a.s = s;
         a.nkb = nkb;
         a.reverse = reverse;
@@ -546,7 +576,7 @@ struct RasterWalk {
         a.n = n;
         a.ldc = ldc;
         a.row0 = (int64_t)tm * kBM;
-        a.col0 = (int64_t)tn * kBN;
+        a.col0 = (int64_t)tn * BN;
         a.alpha = alpha;
         a.beta = beta;
         a.C = C;
@@ -565,9 +595,10 @@ __global__ void __launch_bounds__(kThreads, 1)
                         int chunk_stages, int stages, uint32_t slot_bytes, unsigned* status) {
     extern __shared__ uint8_t smem_raw[];
     uint8_t* smem = aligned_smem(smem_raw);
-    const RasterWalk w{ad, bd, m, n, ldc, nkb, tiles_m, tiles_n, S, alpha, beta, C, eA, fB, 0};
-    products_persistent<S, kblocks_per_stage(S), kSplit>(w, chunk_stages, smem, stages,
-                                                         slot_bytes, status);
+    constexpr int BN = emu_bn(S);
+    const RasterWalk<BN> w{ad, bd, m, n, ldc, nkb, tiles_m, tiles_n, S, alpha, beta, C, eA, fB, 0};
+    products_persistent<S, BN, kblocks_per_stage(S), kSplit>(w, chunk_stages, smem, stages,
+                                                             slot_bytes, status);
 }
 
 // Grouped: the tiles [t_begin, t_end) of the problems [q_begin, q_end) of the
@@ -575,6 +606,7 @@ __global__ void __launch_bounds__(kThreads, 1)
 // t = t_begin + blockIdx.x, + gridDim.x, ...: concurrent CTAs work on
 // neighbouring tiles, so the digit strips they share stay in L2.  A tile's
 // problem is a binary search over the compact tile-prefix array (L1-resident).
+template <int BN>
 struct GroupWalk {
     const EmuProb* P;
     const int64_t* key;
@@ -595,7 +627,7 @@ struct GroupWalk {
         const int nkb = (int)(e.kp / kBKBytes);
         TileArgs a;
         a.a_src = e.a_digits + (size_t)tm * nkb * e.s * kBM * kBKBytes;
-        a.b_src = e.b_digits + (size_t)tn * nkb * e.s * kBN * kBKBytes;
+        a.b_src = e.b_digits + (size_t)tn * nkb * e.s * BN * kBKBytes;
         a.s = e.s;
         a.nkb = nkb;
         a.reverse = false;
@@ -603,7 +635,7 @@ struct GroupWalk {
         a.n = e.n;
         a.ldc = e.ldc;
         a.row0 = tm * kBM;
-        a.col0 = tn * kBN;
+        a.col0 = tn * BN;
         a.alpha = e.alpha;
         a.beta = e.beta;
         a.C = e.C;
@@ -621,9 +653,10 @@ __global__ void __launch_bounds__(kThreads, 1)
                             unsigned* status) {
     extern __shared__ uint8_t smem_raw[];
     uint8_t* smem = aligned_smem(smem_raw);
-    const GroupWalk w{P, key, q_begin, q_end, t_begin, t_end, 0};
-    products_persistent<S, kblocks_per_stage(S), false>(w, chunk_stages, smem, stages,
-                                                        slot_bytes, status);
+    constexpr int BN = emu_bn(S);
+    const GroupWalk<BN> w{P, key, q_begin, q_end, t_begin, t_end, 0};
+    products_persistent<S, BN, kblocks_per_stage(S), false>(w, chunk_stages, smem, stages,
+                                                            slot_bytes, status);
 }
 
 struct RingShape {
@@ -634,7 +667,7 @@ struct RingShape {
 
 RingShape ring_for(int max_s, int kb_per_stage) {
     RingShape r{};
-    r.slot_bytes = (uint32_t)kb_per_stage * max_s * (kBM + kBN) * kBKBytes;
+    r.slot_bytes = (uint32_t)kb_per_stage * max_s * (kBM + emu_bn(max_s)) * kBKBytes;
     const int fixed = 1024 + (int)sizeof(SmemTail) + 64;
     r.stages = (kSmemLimit - fixed) / (int)r.slot_bytes;
     if (r.stages > 8) r.stages = 8;
@@ -653,11 +686,13 @@ cudaError_t launch_products_s(const Launch& L, int64_t m, int64_t n, int64_t kp,
                               const uint8_t* bd, const int32_t* ea, const int32_t* fb) {
     const RingShape r = ring_for(S, kblocks_per_stage(S));
     if (r.stages < 2) return cudaErrorInvalidValue;
-    const int tiles_m = (int)((m + kBM - 1) / kBM), tiles_n = (int)((n + kBN - 1) / kBN);
+    constexpr int BN = emu_bn(S);
+    const int tiles_m = (int)((m + kBM - 1) / kBM), tiles_n = (int)((n + BN - 1) / BN);
     const int nkb = (int)(kp / kBKBytes);
     const int64_t tiles = (int64_t)tiles_m * tiles_n;
     const int grid = (int)(tiles < L.sm_count ? tiles : L.sm_count);
-    constexpr bool kCanSplit = S >= 9 && S <= 15;
+    // split accumulators need BN (2S - G) TMEM columns
+    constexpr bool kCanSplit = S >= 9 && S <= 15 && BN * (2 * S - split_point(S)) <= 512;
     const AccPlan plan = acc_plan<S, kblocks_per_stage(S)>(kp, kCanSplit);
     if constexpr (kCanSplit) {
         if (plan.split) {

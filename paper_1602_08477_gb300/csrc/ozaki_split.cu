@@ -237,7 +237,8 @@ __device__ __forceinline__ void colmax_block(int64_t jb, int64_t n, int64_t k,
 }
 
 // Transposing digit pass for B over the tile of 64 rows (l) x 32 columns (j)
-// at (lb, jb).
+// at (lb, jb), into B digit tiles of emu_bn(S) lines; columns n <= j < (n padded
+// to whole tiles) get zero digits, columns beyond are not written.
 template <int S>
 __device__ __forceinline__ void split_cols_tile(int64_t jb, int64_t lb, int64_t n, int64_t k,
                                                 const double* __restrict__ B, int64_t ldb, int s,
@@ -254,9 +255,11 @@ __device__ __forceinline__ void split_cols_tile(int64_t jb, int64_t lb, int64_t 
         T[ty + 8 * r][tx] = (l < k && j < n) ? Bb[l * ldb + j] : 0ull;
     }
     __syncthreads();
+    constexpr int R = emu_bn(S);
     const int jj = tid >> 3, lsub = (tid & 7) * 8;
     const int64_t j = j0 + jj, lbase = l0 + lsub;
-    if (lbase < kp) {  // columns n <= j < (tile padding) get zero digits
+    const int64_t np = (n + R - 1) / R * R;
+    if (lbase < kp && j < np) {
         const int e = j < n ? exps[j] : GB_BAD_LINE_DEV;
         uint64_t w[S];
 #pragma unroll
@@ -270,8 +273,8 @@ __device__ __forceinline__ void split_cols_tile(int64_t jb, int64_t lb, int64_t 
 #pragma unroll
         for (int t = 0; t < S; ++t) {
             if (t >= s) break;
-            *reinterpret_cast<uint64_t*>(digits + tiled_offset(j, lbase, t, s, kp >> 5,
-                                                               kEmuGroupBN)) = w[t];
+            *reinterpret_cast<uint64_t*>(digits + tiled_offset(j, lbase, t, s, kp >> 5, R)) =
+                w[t];
         }
     }
     __syncthreads();
@@ -454,7 +457,8 @@ __global__ void __launch_bounds__(256) grouped_split_cols_kernel(const EmuProb* 
     for (int64_t b = tb_begin + blockIdx.x; b < tb_end; b += gridDim.x) {
         const EmuProb& q = P[find_prob(key, q_begin, q_end - 1, b)];
         const int64_t local = b - q.first_tblk;
-        const int64_t ncb = (q.n + 31) / 32;
+        constexpr int R = emu_bn(S);
+        const int64_t ncb = ((q.n + R - 1) / R * R + 31) / 32;  // padded columns
         split_cols_tile<S>(local % ncb, local / ncb, q.n, q.k, q.B, q.ldb, S, q.b_digits, q.kp,
                            q.b_exp, T);
     }
@@ -508,7 +512,8 @@ cudaError_t launch_split_cols(const Launch& L, int s, int64_t n, int64_t k, cons
     colmax_kernel<<<gx, 1024, 0, L.stream>>>(n, k, B, ldb, exps, L.status);
     cudaError_t err = cudaGetLastError();
     if (err != cudaSuccess) return err;
-    const dim3 grid(gx, (unsigned)((kp + 63) / 64));
+    const int64_t np = (n + emu_bn(s) - 1) / emu_bn(s) * emu_bn(s);  // B digit tile padding
+    const dim3 grid((unsigned)((np + 31) / 32), (unsigned)((kp + 63) / 64));
 #define GB_LAUNCH_COLS(SS) \
     split_cols_kernel<SS><<<grid, 256, 0, L.stream>>>(n, k, B, ldb, digits, kp, exps)
     GB_SWITCH_S(s, GB_LAUNCH_COLS)

@@ -65,8 +65,9 @@ def split_on_gpu(gb, A, B, s):
     torch.cuda.synchronize()
     raw = ws.cpu().numpy()
     kp = lay.kp
-    da = untile(raw, lay.a_digits, s, m, kp, 128)
-    db = untile(raw, lay.b_digits, s, n, kp, 32)
+    assert lay.a_tile_rows == 128 and lay.b_tile_rows == (48 if s <= 10 else 32)
+    da = untile(raw, lay.a_digits, s, m, kp, lay.a_tile_rows)
+    db = untile(raw, lay.b_digits, s, n, kp, lay.b_tile_rows)
     ea = raw[lay.a_exp:lay.a_exp + 4 * m].view(np.int32)
     fb = raw[lay.b_exp:lay.b_exp + 4 * n].view(np.int32)
     return da, db, ea, fb, kp
@@ -74,7 +75,7 @@ def split_on_gpu(gb, A, B, s):
 
 @pytest.mark.parametrize("kind", ["uniform", "hard"])
 @pytest.mark.parametrize("m,n,k,s", [(37, 45, 70, 11), (128, 64, 256, 16), (5, 300, 33, 1),
-                                     (200, 3, 129, 7)])
+                                     (200, 3, 129, 7), (130, 97, 64, 10), (3, 49, 40, 9)])
 def test_split_digits_and_exponents_bit_exact(gb, kind, m, n, k, s):
     A, B, _ = inputs(kind, m, n, k, 31, with_c=False)
     da, db, ea, fb, kp = split_on_gpu(gb, A, B, s)
@@ -117,11 +118,13 @@ def test_integer_variant_bit_exact(gb, s):
     assert np.array_equal(emulate(gb, A, B, C0, 1.5, 0.5, s), want)
 
 
-@pytest.mark.parametrize("s,k", [(16, 4200), (10, 6600), (10, 13100)])
+@pytest.mark.parametrize("s,k", [(16, 4200), (10, 6600), (10, 13100), (12, 6600)])
 def test_long_k_accumulates_in_exact_chunks(gb, s, k):
     # K beyond (2^24 / (256 s)) runs in several tensor-memory chunks whose exact
-    # 128-bit sums are added (one, two and three chunk boundaries); bit-exact
-    # against the model, whose level sums are exact in FP64.
+    # 128-bit sums are added (one and two chunk boundaries at s = 16 and s = 10,
+    # 48-column tiles at s = 10), or, at s = 12 with 32-column tiles, in two sets
+    # of level accumulators; bit-exact against the model, whose level sums are
+    # exact in FP64.
     A, B, C0 = inputs("hard", 130, 40, k, 34)
     want = ozaki.emulated_gemm(-0.5, A, B, 2.0, C0, s=s)
     assert np.array_equal(emulate(gb, A, B, C0, -0.5, 2.0, s), want)

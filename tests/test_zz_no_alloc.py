@@ -28,7 +28,8 @@ def test_noalloc_matches_workspace_entry_point_twice():
     gb.build()
     lib = gb.load()
     stream = torch.cuda.current_stream()
-    cases = [(300, 200, 129, 11, "uniform", 1.5, 0.5), (513, 257, 1000, 13, "hard", 1.0, 0.0)]
+    cases = [(300, 200, 129, 11, "uniform", 1.5, 0.5), (513, 257, 1000, 13, "hard", 1.0, 0.0),
+             (130, 97, 70, 10, "uniform", -0.75, 2.0)]
     for (m, n, k, s, kind, alpha, beta) in cases:
         A = torch.from_numpy(g.matrix(kind, m, k, 91, 0)).cuda()
         B = torch.from_numpy(g.matrix(kind, k, n, 91, 1)).cuda()
