@@ -340,53 +340,59 @@ __device__ __forceinline__ int find_prob(const int64_t* __restrict__ key, int lo
 }
 
 // One 128-row tile of A (rows row0 .. row0+127 of a problem, rows >= m are the
-// tile padding) by a CTA of 256 threads.  Pass 1: each warp takes 16 rows, max |a|
-// and finiteness per row with 8 consecutive elements per lane and step.  Pass 2:
-// per K block of 32, thread p of 512 (two per thread) takes row p / 4, elements
-// 8 (p % 4) .. +7, so a warp writes 256 contiguous bytes per digit plane (8 rows x
-// 32 bytes of the tiled layout) and every lane has work even for short rows.
+// tile padding) by a CTA of 256 threads.  Both passes use the same map: slot p of
+// 512 (two per thread) takes row p / 4 and, in every K block of 32, elements
+// 8 (p % 4) .. +7.  Pass 1: max |a| and finiteness of each slot's elements, then
+// of the row over its 4 neighbouring lanes (all rows' loads in flight at once).
+// Pass 2: the digits, so a warp writes 256 contiguous bytes per digit plane (8
+// rows x 32 bytes of the tiled layout) and every lane has work even for short rows.
 template <int S>
 __device__ __forceinline__ void split_row_tile(int64_t row0, int64_t m, int64_t k,
                                                const double* __restrict__ A, int64_t lda,
                                                uint8_t* __restrict__ digits, int64_t kp,
                                                int32_t* __restrict__ exps, unsigned* status,
                                                int* e_sh) {
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    for (int r = warp * 16; r < warp * 16 + 16; ++r) {
+    const int64_t nkb = kp >> 5;
+#pragma unroll
+    for (int half = 0; half < 2; ++half) {
+        const int p = threadIdx.x + 256 * half;
+        const int r = p >> 2;
         const int64_t i = row0 + r;
-        if (i >= m) {
-            if (lane == 0) e_sh[r] = GB_BAD_LINE_DEV;  // padding: zero digits
-            continue;
-        }
-        const uint64_t* row = reinterpret_cast<const uint64_t*>(A + i * lda);
         uint64_t mx = 0;
         unsigned bad = 0;
-        for (int64_t l0 = (int64_t)lane * 8; l0 < k; l0 += 256) {
-            uint64_t v[8];
+        if (i < m) {
+            const uint64_t* row = reinterpret_cast<const uint64_t*>(A + i * lda);
+            for (int64_t l0 = (p & 3) * 8; l0 < k; l0 += 32) {
+                uint64_t v[8];
 #pragma unroll
-            for (int u = 0; u < 8; ++u) v[u] = l0 + u < k ? row[l0 + u] : 0ull;
+                for (int u = 0; u < 8; ++u) v[u] = l0 + u < k ? row[l0 + u] : 0ull;
 #pragma unroll
-            for (int u = 0; u < 8; ++u) {
-                const uint64_t a = v[u] & 0x7FFFFFFFFFFFFFFFull;
-                bad |= a >= 0x7FF0000000000000ull;
-                mx = (a < 0x7FF0000000000000ull && a > mx) ? a : mx;
+                for (int u = 0; u < 8; ++u) {
+                    const uint64_t a = v[u] & 0x7FFFFFFFFFFFFFFFull;
+                    bad |= a >= 0x7FF0000000000000ull;
+                    mx = (a < 0x7FF0000000000000ull && a > mx) ? a : mx;
+                }
             }
         }
+        // the row's 4 slots are lanes 4q .. 4q+3 of this warp
 #pragma unroll
-        for (int o = 16; o > 0; o >>= 1) {
+        for (int o = 1; o < 4; o <<= 1) {
             const uint64_t w = __shfl_xor_sync(0xffffffffu, mx, o);
             mx = w > mx ? w : mx;
+            bad |= __shfl_xor_sync(0xffffffffu, bad, o);
         }
-        const bool is_bad = __any_sync(0xffffffffu, bad) != 0;
-        if (lane == 0) {
-            const int e = is_bad ? GB_BAD_LINE_DEV : frexp_exp_bits(mx);
-            exps[i] = e;
-            e_sh[r] = e;
-            if (is_bad && status) atomicOr(status, kStatusNonfinite);
+        if ((p & 3) == 0) {
+            if (i >= m) {
+                e_sh[r] = GB_BAD_LINE_DEV;  // padding: zero digits
+            } else {
+                const int e = bad ? GB_BAD_LINE_DEV : frexp_exp_bits(mx);
+                exps[i] = e;
+                e_sh[r] = e;
+                if (bad && status) atomicOr(status, kStatusNonfinite);
+            }
         }
     }
     __syncthreads();
-    const int64_t nkb = kp >> 5;
     for (int64_t kb = 0; kb < nkb; ++kb) {
 #pragma unroll
         for (int half = 0; half < 2; ++half) {
