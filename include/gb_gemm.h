@@ -219,6 +219,38 @@ gb_status gb_emulated_products(gb_queue* q, int slices, int64_t m, int64_t n, in
                                double alpha, double beta, double* C, int64_t ldc,
                                void* workspace, size_t workspace_bytes);
 
+/*
+ * C <- alpha A B + beta C (Section 4.2) with A, B and C in HOST memory, moved by
+ * the explicit host <-> device copies of Section 3.4.4, enqueued by the library
+ * and overlapped with the computation.  A (m x k, lda), B (k x n, ldb), C (m x
+ * n, ldc) are row-major host arrays, 8-byte aligned; they should be page-locked
+ * (cudaHostAlloc / cudaHostRegister, or torch's pin_memory) for the copies to
+ * run asynchronously and overlap.  `workspace` is device memory of at least
+ * gb_dgemm_host_workspace_size() bytes, 256-byte aligned, owned by the caller:
+ * the emulated workspace (emulated precision) followed by dense device copies
+ * of A, B and C.
+ * Emulated precision: B is copied first and split; A (and C when beta != 0) is
+ * copied in bands of whole 128-row tiles (up to 4 bands of >= 1024 rows), each
+ * band split and multiplied as soon as it arrives, and each band of C is copied
+ * back while the next bands compute.  Native precision: A, B (and C) are copied,
+ * multiplied by the default native kernel, C copied back.
+ * The copies run on two streams the queue creates on the first call (one per
+ * direction), ordered after all work already on the queue; the queue's stream
+ * passes the end of this call once C is back in host memory.  The caller must
+ * not touch A, B, C or the workspace before that (gb_queue_wait).  Asynchronous
+ * with respect to the host on a non-blocking queue, synchronous on a blocking one.
+ * Errors: as gb_dgemm; GB_ERR_WORKSPACE for a missing, misaligned or small
+ * workspace.
+ */
+gb_status gb_dgemm_host(gb_queue* q, gb_precision prec, int slices, int64_t m, int64_t n,
+                        int64_t k, double alpha, const double* A, int64_t lda, const double* B,
+                        int64_t ldb, double beta, double* C, int64_t ldc, void* workspace,
+                        size_t workspace_bytes);
+
+/* Device workspace bytes gb_dgemm_host needs for these sizes. */
+gb_status gb_dgemm_host_workspace_size(gb_precision prec, int slices, int64_t m, int64_t n,
+                                       int64_t k, size_t* out);
+
 /* Diagnostic of the failure path (the paper has no failure model; this library
  * bounds every device-side wait): enqueues a kernel that waits on a barrier
  * nothing will ever complete, gives up after timeout_us microseconds (1 .. 2e6),

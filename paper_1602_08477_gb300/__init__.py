@@ -13,7 +13,9 @@ from .gemm import (  # noqa: F401
     alloc_workspace,
     default_queue,
     dgemm,
+    dgemm_host,
     emulated_layout,
+    host_workspace_size,
     emulated_steps,
     workdiv_suggest,
     workspace_size,

@@ -90,6 +90,9 @@ SIGNATURES = {
     "gb_selftest_wait_timeout": (_st, [_vp, ctypes.c_uint32]),
     "gb_dgemm_emulated_noalloc": (_st, [_vp, _int, _i64, _i64, _i64, _dbl, _vp, _i64, _vp, _i64,
                                         _dbl, _vp, _i64]),
+    "gb_dgemm_host": (_st, [_vp, _int, _int, _i64, _i64, _i64, _dbl, _vp, _i64, _vp, _i64, _dbl,
+                            _vp, _i64, _vp, _sz]),
+    "gb_dgemm_host_workspace_size": (_st, [_int, _int, _i64, _i64, _i64, ctypes.POINTER(_sz)]),
 }
 
 

@@ -304,6 +304,7 @@ gb_status gb_queue_destroy(gb_queue* q) {
     if (!q) return GB_OK;
     DeviceScope scope(q->dev->idx);
     cudaStreamSynchronize(q->stream);
+    release_aux(q);
     cudaFree(q->status);
     if (q->owns_stream) cudaStreamDestroy(q->stream);
     delete q;

@@ -13,12 +13,19 @@ struct gb_device {
     int cc_major, cc_minor;
 };
 
+namespace gb {
+constexpr int kAuxEvents = 12;  // events of the host-buffer pipeline (2 + 2 per band, <= 4 bands)
+}
+
 struct gb_queue {
     gb_device* dev;
     cudaStream_t stream;
     int blocking;
     unsigned* status;  // device status word (kStatus* bits)
     bool owns_stream;  // created by gb_queue_create_owned: destroyed with the queue
+    // copy streams and events of gb_dgemm_host, created on its first call
+    cudaStream_t aux_h2d = nullptr, aux_d2h = nullptr;
+    cudaEvent_t aux_ev[gb::kAuxEvents] = {};
 };
 
 namespace gb {
@@ -36,6 +43,9 @@ struct DeviceScope {
         if (prev >= 0 && cudaGetDevice(&cur) == cudaSuccess && cur != prev) cudaSetDevice(prev);
     }
 };
+
+// Destroys the copy streams and events of gb_dgemm_host (if created).
+void release_aux(gb_queue* q);
 
 // Sets the error text for a failed CUDA call and returns GB_ERR_CUDA.
 gb_status cuda_fail(cudaError_t e, const char* what);

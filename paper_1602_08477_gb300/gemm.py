@@ -162,6 +162,51 @@ def dgemm(A, B, C=None, alpha: float = 1.0, beta: float = 0.0, *, kernel: str = 
     return C
 
 
+def host_workspace_size(precision: str, slices: int, m: int, n: int, k: int) -> int:
+    """Device workspace bytes of dgemm_host for these sizes."""
+    out = ctypes.c_size_t()
+    prec = GB_PREC_EMULATED if precision == "emulated" else GB_PREC_NATIVE
+    check(_lib.load().gb_dgemm_host_workspace_size(prec, slices, m, n, k, ctypes.byref(out)),
+          "gb_dgemm_host_workspace_size")
+    return out.value
+
+
+def _host_matrix_args(t, name):
+    import torch
+    if t.dtype != torch.float64 or t.is_cuda or t.dim() != 2:
+        raise ValueError(f"{name} must be a 2-D float64 host (CPU) tensor")
+    if t.stride(1) != 1 and t.shape[1] > 1:
+        raise ValueError(f"{name} must be row-major (unit column stride)")
+    ld = t.stride(0) if t.shape[0] > 1 else max(1, t.shape[1])
+    return ctypes.c_void_p(t.data_ptr()), ld
+
+
+def dgemm_host(A, B, C, alpha: float = 1.0, beta: float = 0.0, *, precision: str = "native",
+               slices: int = 0, queue: Queue | None = None, workspace=None):
+    """C <- alpha * A @ B + beta * C with A, B, C float64 tensors in host memory
+    (pinned for overlapped copies); the library copies them in, computes and
+    copies C back, overlapped on the queue (gb_dgemm_host).  The result is in C
+    once the queue has passed the call (torch.cuda.synchronize or queue.wait)."""
+    m, k = A.shape
+    k2, n = B.shape
+    if k2 != k or tuple(C.shape) != (m, n):
+        raise ValueError(f"shapes differ: {tuple(A.shape)} x {tuple(B.shape)} -> {tuple(C.shape)}")
+    q = queue or default_queue()
+    pa, lda = _host_matrix_args(A, "A")
+    pb, ldb = _host_matrix_args(B, "B")
+    pc, ldc = _host_matrix_args(C, "C")
+    lda, ldb, ldc = max(lda, k, 1), max(ldb, n, 1), max(ldc, n, 1)
+    prec = GB_PREC_EMULATED if precision == "emulated" else GB_PREC_NATIVE
+    need = host_workspace_size(precision, slices, m, n, k)
+    if workspace is None:
+        workspace = alloc_workspace(need)
+    check(_lib.load().gb_dgemm_host(q.handle, prec, slices, m, n, k, alpha, pa, lda, pb, ldb,
+                                    beta, pc, ldc, ctypes.c_void_p(workspace.data_ptr()),
+                                    workspace.numel() * workspace.element_size()),
+          "gb_dgemm_host")
+    return C
+
+
 def emulated_steps(A, B, C, alpha, beta, slices, workspace, queue: Queue | None = None,
                    steps=("split_a", "split_b", "products")):
     """Run the emulated path's steps one by one (e1+e2 for A, for B, e3+e4)."""

@@ -1,0 +1,100 @@
+"""GPU parity of the host-buffer GEMM (gb_dgemm_host): operands and result in
+pinned host memory, copied in bands and overlapped with the computation.
+
+Each result equals, bit for bit, the same GEMM on device copies through gb_dgemm
+(the same kernels on the same data; the band split of the emulated path only
+changes which launch computes a row), for band counts 1, 2 and 4, leading
+dimensions wider than the rows, beta = 0 and beta != 0, two calls in a row on
+one workspace, and the native precision.
+"""
+import numpy as np
+import pytest
+
+from synth import generators as g
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def gb():
+    import torch
+    import paper_1602_08477_gb300 as gb
+    gb.build()
+    assert torch.cuda.is_available()
+    return gb
+
+
+def pinned(a, pad=0):
+    """A pinned host tensor holding `a`, with `pad` extra columns (wider ld)."""
+    import torch
+    rows, cols = a.shape
+    t = torch.empty((rows, cols + pad), dtype=torch.float64, pin_memory=True)
+    t[:, :cols] = torch.from_numpy(a)
+    if pad:
+        t[:, cols:] = float("nan")  # never read
+    return t[:, :cols]
+
+
+def device_reference(gb, A, B, C0, alpha, beta, precision, s):
+    import torch
+    dC = torch.from_numpy(C0.copy()).cuda()
+    gb.dgemm(torch.from_numpy(A).cuda(), torch.from_numpy(B).cuda(), dC, alpha, beta,
+             precision=precision, slices=s)
+    torch.cuda.synchronize()
+    return dC.cpu().numpy()
+
+
+@pytest.mark.parametrize("m,n,k,s,beta,pad", [(900, 130, 70, 10, 0.0, 0),     # one band
+                                              (2100, 300, 257, 10, 0.5, 3),   # two bands
+                                              (4500, 97, 129, 12, -1.0, 1)])  # four bands
+def test_emulated_host_buffers_match_device_gemm(gb, m, n, k, s, beta, pad):
+    import torch
+    seed = 8100 + m
+    A = g.matrix("uniform", m, k, seed, 0)
+    B = g.matrix("uniform", k, n, seed, 1)
+    C0 = g.matrix("uniform", m, n, seed, 2)
+    want = device_reference(gb, A, B, C0, 1.5, beta, "emulated", s)
+    hA, hB, hC = pinned(A, pad), pinned(B, pad), pinned(C0, pad)
+    gb.dgemm_host(hA, hB, hC, 1.5, beta, precision="emulated", slices=s)
+    torch.cuda.synchronize()
+    assert np.array_equal(hC.numpy(), want)
+
+
+def test_two_calls_in_a_row_share_the_workspace(gb):
+    import torch
+    m, n, k, s = 2304, 200, 96, 11
+    ws = gb.alloc_workspace(gb.host_workspace_size("emulated", s, m, n, k))
+    outs, wants = [], []
+    for seed in (8301, 8302):
+        A = g.matrix("uniform", m, k, seed, 0)
+        B = g.matrix("hard", k, n, seed, 1)
+        wants.append(device_reference(gb, A, B, np.zeros((m, n)), 1.0, 0.0, "emulated", s))
+        hC = pinned(np.zeros((m, n)))
+        gb.dgemm_host(pinned(A), pinned(B), hC, precision="emulated", slices=s, workspace=ws)
+        outs.append(hC)
+    torch.cuda.synchronize()
+    for got, want in zip(outs, wants):
+        assert np.array_equal(got.numpy(), want)
+
+
+def test_native_host_buffers_match_device_gemm(gb):
+    import torch
+    m, n, k = 300, 200, 100
+    A = g.matrix("uniform", m, k, 8401, 0)
+    B = g.matrix("uniform", k, n, 8401, 1)
+    C0 = g.matrix("uniform", m, n, 8401, 2)
+    want = device_reference(gb, A, B, C0, -0.5, 2.0, "native", 0)
+    hC = pinned(C0, 2)
+    gb.dgemm_host(pinned(A, 1), pinned(B), hC, -0.5, 2.0, precision="native")
+    torch.cuda.synchronize()
+    assert np.array_equal(hC.numpy(), want)
+
+
+def test_small_workspace_rejected(gb):
+    m, n, k = 64, 64, 64
+    need = gb.host_workspace_size("emulated", 10, m, n, k)
+    ws = gb.alloc_workspace(need - 256)
+    z = np.zeros((m, m))
+    with pytest.raises(gb.GbError, match="WORKSPACE"):
+        gb.dgemm_host(pinned(z), pinned(z), pinned(z), precision="emulated", slices=10,
+                      workspace=ws)
