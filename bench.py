@@ -505,7 +505,7 @@ def run_d0(args):
     flops = 2.0 * n ** 3
     calls = 200
     res = {}
-    for kernel in ("naive", "tiled", "dfma", "dmma", "emulated"):
+    for kernel in ("auto", "naive", "tiled", "dfma", "dmma", "emulated"):
         if kernel == "emulated":
             ws = gb.alloc_workspace(gb.workspace_size("emulated", 11, n, n, n))
             f = lambda: gb.dgemm(A, B, C, 1.5, 0.5, precision="emulated", slices=11, queue=q,

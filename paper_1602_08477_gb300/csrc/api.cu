@@ -106,12 +106,18 @@ Variant default_variant(gb_kernel kernel, int64_t m, int64_t n, int64_t k) {
             if (mn <= 1024) return {GB_KERNEL_DMMA, 2, 2, 16, 16};
             return {GB_KERNEL_DMMA, 2, 2, 32, 32};
         case GB_KERNEL_AUTO:
-        default:
+        default: {
             // measured on GB300: one element per thread in 16 x 16 smem tiles is
             // fastest up to 2048 (finest load balance over 152 SMs); above it the
-            // 4 x 4 register tiles run the FP64 FMA pipe at its peak
+            // 4 x 4 register tiles run the FP64 FMA pipe at its peak.  With fewer
+            // than ~4 tiles of 16 x 16 per SM the SMs get unequal tile counts
+            // (n = 256: 256 tiles, 2 or 1 per SM), so 8 x 8 tiles even them out
+            // (n = 256: 36.9 -> 32.9 us; n = 512 stays faster with 16 x 16).
+            const int64_t tiles16 = ((m + 15) / 16) * ((n + 15) / 16);
+            if (tiles16 < 600) return {GB_KERNEL_TILED, 8, 8, 1, 1};
             if (mn <= 2048) return {GB_KERNEL_TILED, 16, 16, 1, 1};
             return {GB_KERNEL_DFMA, 16, 16, 4, 4};
+        }
     }
 }
 

@@ -92,6 +92,12 @@ def test_workdiv_suggest_follows_table2_cuda_row(lib):
     assert lib.gb_workdiv_suggest(None, 0, 1024, 1024, 1024, ctypes.byref(wd),
                                   ctypes.byref(chosen)) == 0
     assert chosen.value == 2  # smem tiles, one element per thread
+    assert tuple(wd.block_threads[:2]) == (16, 16)
+    # fewer than ~4 tiles of 16 x 16 per SM: 8 x 8 tiles spread the work evenly
+    assert lib.gb_workdiv_suggest(None, 0, 256, 256, 256, ctypes.byref(wd),
+                                  ctypes.byref(chosen)) == 0
+    assert chosen.value == 2 and tuple(wd.block_threads[:2]) == (8, 8)
+    assert tuple(wd.grid_blocks[:2]) == (32, 32)
     assert lib.gb_workdiv_suggest(None, 4, 4096, 4096, 4096, ctypes.byref(wd),
                                   ctypes.byref(chosen)) == 0
     assert tuple(wd.block_threads[:2]) == (2, 2) and tuple(wd.thread_elems[:2]) == (32, 32)
