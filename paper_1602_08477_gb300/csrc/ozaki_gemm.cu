@@ -55,17 +55,6 @@ struct SmemTail {
     int abort;
 };
 
-// exact integer value of an FP32 that holds an integer (|v| < 2^63)
-__device__ __forceinline__ int64_t f32_int_value(uint32_t b) {
-    const uint32_t a = b & 0x7FFFFFFFu;
-    if (a == 0) return 0;
-    const int ex = (int)(a >> 23) - 127;
-    if (ex < 0) return 0;  // not an integer: cannot occur for digit products
-    const int64_t mant = (int64_t)((a & 0x7FFFFFu) | 0x800000u);
-    const int64_t v = ex >= 23 ? (mant << (ex - 23)) : (mant >> (23 - ex));
-    return (b >> 31) ? -v : v;
-}
-
 struct I128 {
     int64_t hi;
     uint64_t lo;
@@ -247,70 +236,74 @@ __host__ __device__ constexpr int epi_col(int g, int j) {
     return j < 8 ? 8 * g + j : 32 + 4 * g + (j - 8);
 }
 
-// The BN / 4 columns of column group g of the level at TMEM address `level`
-// (lane quarter already added) for this warp's 32 lanes.
-template <int BN>
-__device__ __forceinline__ void tmem_ld_cols(uint32_t level, int g, uint32_t (&v)[BN / 4]) {
-    static_assert(BN == 32 || BN == 48, "32 or 48 columns per tile");
-    uint32_t a[8];
-    ptx::tmem_ld_32x32b_x8(level + (uint32_t)(8 * g), a);
-#pragma unroll
-    for (int j = 0; j < 8; ++j) v[j] = a[j];
-    if constexpr (BN == 48) {
-        uint32_t b[4];
-        ptx::tmem_ld_32x32b_x4(level + (uint32_t)(32 + 4 * g), b);
-#pragma unroll
-        for (int j = 0; j < 4; ++j) v[8 + j] = b[j];
+// The W columns of part P of an epilogue warp's column group g of the level at
+// TMEM address `level`: part 0 = columns 8g .. 8g+7 (W = 8), part 1 = columns
+// 32 + 4g .. 32 + 4g + 3 (W = 4, 48-column tiles only).
+template <int P, int W>
+__device__ __forceinline__ void tmem_ld_part(uint32_t level, int g, uint32_t (&v)[W]) {
+    if constexpr (P == 0) {
+        static_assert(W == 8, "part 0 has 8 columns");
+        ptx::tmem_ld_32x32b_x8(level + (uint32_t)(8 * g), v);
+    } else {
+        static_assert(W == 4, "part 1 has 4 columns");
+        ptx::tmem_ld_32x32b_x4(level + (uint32_t)(32 + 4 * g), v);
     }
 }
 
-// T += sum_g S_g 2^(5 (S+1-g)) over the S levels of one accumulation unit for the
-// CW = BN / 4 columns of column group cg of this thread's TMEM lane (level index
-// L = g - 2 at lane_addr + BN L, plus lane_addr + BN (S + L - G) for L >= G with
-// split accumulators), exactly: Horner in int64 over runs of at most 6 levels (each
-// |S_g| < 2^25 as the sum of two accumulators, so a run stays below 2^55), each
-// run added into the 128-bit T at its own weight, so the chunks of a tile add up
-// in the same T.  small: every accumulator below 2^22 (cheaper conversion).
-// With 12 columns per thread the run registers would not fit beside T: each
-// level is added into T directly (runs of one level).
-template <int S, int BN, bool kSplit>
-__device__ __forceinline__ void add_levels(uint32_t lane_addr, int cg, bool small,
-                                           I128 (&T)[BN / 4]) {
-    constexpr int CW = BN / 4;
-    constexpr int kRun = CW <= 8 ? 6 : 1;
+// T[j0 .. j0+W) += sum_g S_g 2^(5 (S+1-g)) over the S levels of one accumulation
+// unit for part P of this thread's columns (level index L = g - 2 at lane_addr +
+// BN L, plus lane_addr + BN (S + L - G) for L >= G with split accumulators),
+// exactly: Horner in int64 over runs of at most 6 levels (each |S_g| < 2^25 as
+// the sum of two accumulators, so a run stays below 2^55), each run added into the
+// 128-bit T at its own weight, so the chunks of a tile add up in the same T.  The
+// next tile's MMAs wait until every level has been read, so this runs unrolled
+// (constant shifts) and converts with one hardware FP32 -> int32 conversion per
+// value (exact: every accumulator is an integer below 2^25); small: every
+// accumulator below 2^22, converted by one FP32 add instead.
+template <int S, int BN, bool kSplit, int P, int W, int J0>
+__device__ __forceinline__ void add_levels_part(uint32_t lane_addr, int cg, bool small,
+                                                I128 (&T)[BN / 4]) {
+    constexpr int kRun = 6;
     constexpr int split_g = kSplit ? split_point(S) : S;
-    int64_t G[CW];
+    int64_t G[W];
 #pragma unroll
-    for (int j = 0; j < CW; ++j) G[j] = 0;
-    int in_group = 0;
-#pragma unroll 1
+    for (int j = 0; j < W; ++j) G[j] = 0;
+#pragma unroll
     for (int L = 0; L < S; ++L) {
         const bool two = L >= split_g;
-        uint32_t v[CW], y[CW];
-        tmem_ld_cols<BN>(lane_addr + (uint32_t)L * BN, cg, v);
-        if (two) tmem_ld_cols<BN>(lane_addr + (uint32_t)(S + L - split_g) * BN, cg, y);
+        uint32_t v[W], y[W];
+        tmem_ld_part<P, W>(lane_addr + (uint32_t)L * BN, cg, v);
+        if (two) tmem_ld_part<P, W>(lane_addr + (uint32_t)(S + L - split_g) * BN, cg, y);
         ptx::tmem_ld_wait();
         if (small) {
 #pragma unroll
-            for (int j = 0; j < CW; ++j)
+            for (int j = 0; j < W; ++j)
                 G[j] = G[j] * 32 + (int64_t)f32_small_int_value(v[j]) +
                        (two ? (int64_t)f32_small_int_value(y[j]) : 0);
         } else {
 #pragma unroll
-            for (int j = 0; j < CW; ++j)
-                G[j] = G[j] * 32 + f32_int_value(v[j]) + (two ? f32_int_value(y[j]) : 0);
+            for (int j = 0; j < W; ++j)
+                G[j] = G[j] * 32 + (int64_t)__float2int_rn(__uint_as_float(v[j])) +
+                       (two ? (int64_t)__float2int_rn(__uint_as_float(y[j])) : 0);
         }
-        ++in_group;
-        if (in_group == kRun || L == S - 1) {
+        if ((L + 1) % kRun == 0 || L == S - 1) {
             const int sh = 5 * (S - 1 - L);  // weight of the run's last level
 #pragma unroll
-            for (int j = 0; j < CW; ++j) {
-                i128_add_shl(T[j], G[j], sh);
+            for (int j = 0; j < W; ++j) {
+                i128_add_shl(T[J0 + j], G[j], sh);
                 G[j] = 0;
             }
-            in_group = 0;
         }
     }
+}
+
+// All BN / 4 columns of this thread (see epi_col): 8 from part 0, and 4 from part 1
+// for 48-column tiles, one part at a time to keep the run registers few.
+template <int S, int BN, bool kSplit>
+__device__ __forceinline__ void add_levels(uint32_t lane_addr, int cg, bool small,
+                                           I128 (&T)[BN / 4]) {
+    add_levels_part<S, BN, kSplit, 0, 8, 0>(lane_addr, cg, small, T);
+    if constexpr (BN == 48) add_levels_part<S, BN, kSplit, 1, 4, 8>(lane_addr, cg, small, T);
 }
 
 // How one launch keeps its level sums exact (see kchunk_stages): split
