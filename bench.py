@@ -36,7 +36,7 @@ FP64_FLOP_PER_CLK_SM = 4.0
 # DRAM bytes (read + write) per launch of the dominant kernel, from one ncu
 # capture of the kernel as it is now (profiles/emu_products_kernel_n8192_s10.md):
 # (kernel, n, slices) -> bytes.  Reported only for that exact workload.
-MEASURED_TRAFFIC = {}
+MEASURED_TRAFFIC = {("emu_products_kernel", 8192, 10): 9924761088 + 538258432}
 
 
 def parse():
@@ -220,20 +220,36 @@ def run_reference(args):
 
 
 def _grouped_inputs(gb, torch, count, seed, precision, slices):
+    """The group's operands: every A, every B and every C packed one after another
+    (16-byte aligned) in three device arenas, so a caller can move all of them
+    with one copy per arena."""
     from synth import generators as g
     ms, ns, ks = g.grouped_problems(seed, count)
+
+    def offsets(sizes):
+        offs, o = [], 0
+        for z in sizes:
+            offs.append(o)
+            o += (int(z) + 1) // 2 * 2
+        return offs, o
+    offA, totA = offsets(ms * ks)
+    offB, totB = offsets(ks * ns)
+    offC, totC = offsets(ms * ns)
+    arenas = {"A": torch.empty(totA, dtype=torch.float64, device="cuda"),
+              "B": torch.empty(totB, dtype=torch.float64, device="cuda"),
+              "C": torch.zeros(totC, dtype=torch.float64, device="cuda")}
     probs = []
     for i, (m, n, k) in enumerate(zip(ms, ns, ks)):
         m, n, k = int(m), int(n), int(k)
-        A = torch.empty((m, k), dtype=torch.float64, device="cuda")
-        B = torch.empty((k, n), dtype=torch.float64, device="cuda")
-        C = torch.zeros((m, n), dtype=torch.float64, device="cuda")
+        A = arenas["A"][offA[i]:offA[i] + m * k].view(m, k)
+        B = arenas["B"][offB[i]:offB[i] + k * n].view(k, n)
+        C = arenas["C"][offC[i]:offC[i] + m * n].view(m, n)
         gb.fill_uniform(A, seed + i, 0)
         gb.fill_uniform(B, seed + i, 1)
         probs.append(dict(A=A, B=B, C=C, alpha=1.0, beta=0.0, precision=precision,
                           slices=slices))
     torch.cuda.synchronize()
-    return probs, ms, ns, ks
+    return probs, ms, ns, ks, arenas
 
 
 def _time_stream(torch, fn, steps, warmup):
@@ -271,7 +287,7 @@ def run_grouped(args):
     # bound: the bound falls faster with k than the digit-truncation error, and at
     # s = 10 some problems with k < 32 exceed it
     s = args.group_slices
-    probs, ms, ns, ks = _grouped_inputs(gb, torch, args.problems, seed, "native", s)
+    probs, ms, ns, ks, arenas = _grouped_inputs(gb, torch, args.problems, seed, "native", s)
     flops = float(np.sum(2.0 * ms * ns * ks))
     clocks = ClockSampler(0)
     clocks.start()
@@ -332,20 +348,19 @@ def run_grouped(args):
         "tiles": {"native": info["native_tiles"], "emulated": einfo["emulated_tiles"]},
         "e2e": None, "clocks": clk,
     }
-    # end to end: operands from pinned host memory, results back
-    hostA = [p["A"].cpu().pin_memory() for p in probs]
-    hostB = [p["B"].cpu().pin_memory() for p in probs]
-    hostC = [torch.empty(p["C"].shape, dtype=torch.float64).pin_memory() for p in probs]
-    h2d = sum(a.numel() + b.numel() for a, b in zip(hostA, hostB)) * 8
-    d2h = sum(c.numel() for c in hostC) * 8
+    # end to end: the packed operands from pinned host memory (one copy per arena),
+    # the graph-captured group, the packed results back
+    hostA = arenas["A"].cpu().pin_memory()
+    hostB = arenas["B"].cpu().pin_memory()
+    hostC = torch.empty(arenas["C"].shape, dtype=torch.float64).pin_memory()
+    h2d = (hostA.numel() + hostB.numel()) * 8
+    d2h = hostC.numel() * 8
 
     def e2e():
-        for p, a, b in zip(probs, hostA, hostB):
-            p["A"].copy_(a, non_blocking=True)
-            p["B"].copy_(b, non_blocking=True)
+        arenas["A"].copy_(hostA, non_blocking=True)
+        arenas["B"].copy_(hostB, non_blocking=True)
         plan.run()
-        for p, c in zip(probs, hostC):
-            c.copy_(p["C"], non_blocking=True)
+        hostC.copy_(arenas["C"], non_blocking=True)
     e2e_ms = _time_stream(torch, e2e, max(1, args.steps // 2), 1)
     out["e2e"] = {"value": round(flops / e2e_ms / 1e9, 4), "unit": "TFLOP/s",
                   "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h)}

@@ -374,14 +374,13 @@ __device__ __forceinline__ void products_persistent(const Walk& walk, int chunk_
 
     if (warp == 0 && lane == 0) {
         // ---- producer: two contiguous bulk copies per stage, across tiles ----
-        uint32_t it = 0;
+        int st = 0;        // ring slot of the next stage
+        uint32_t ph = 0;   // its phase parity (flips at every wrap of the ring)
         Walk w = walk;
         for (w.start(); w.valid() && !*abort; w.next()) {
             const TileArgs a = w.args();
             const int nst = (a.nkb + KB - 1) / KB;
-            for (int j = 0; j < nst; ++j, ++it) {
-                const int st = (int)(it % (uint32_t)stages);
-                const uint32_t ph = (it / (uint32_t)stages) & 1u;
+            for (int j = 0; j < nst; ++j) {
                 if (!ptx::mbar_wait_bounded(&empty[st], ph ^ 1u, abort, status, kStatusTimeout,
                                             kWaitTimeoutNs))
                     break;
@@ -393,19 +392,25 @@ __device__ __forceinline__ void products_persistent(const Walk& walk, int chunk_
                                &full[st]);
                 ptx::bulk_load(sa + KB * a_bytes, a.b_src + (size_t)kb0 * b_bytes,
                                (uint32_t)kc * b_bytes, &full[st]);
+                if (++st == stages) {
+                    st = 0;
+                    ph ^= 1u;
+                }
             }
         }
     } else if (warp == 1 && lane == 0) {
         // ---- MMA issuer ----
         const int kCS = chunk_stages;
-        uint32_t it = 0, chunk_iter = 0;
+        int st = 0;        // ring slot of the next stage
+        uint32_t ph = 0;   // its phase parity
+        uint32_t chunk_iter = 0;
         bool stop = false;
         Walk w = walk;
         for (w.start(); w.valid() && !*abort && !stop; w.next()) {
             const TileArgs a = w.args();
             const int nst = (a.nkb + KB - 1) / KB;
             int in_chunk = 0;  // stages of the current accumulation unit issued so far
-            for (int j = 0; j < nst; ++j, ++it) {
+            for (int j = 0; j < nst; ++j) {
                 const bool chunk_start = in_chunk == 0;
                 if (chunk_start) {
                     if (chunk_iter > 0) {
@@ -419,8 +424,6 @@ __device__ __forceinline__ void products_persistent(const Walk& walk, int chunk_
                     }
                     ++chunk_iter;
                 }
-                const int st = (int)(it % (uint32_t)stages);
-                const uint32_t ph = (it / (uint32_t)stages) & 1u;
                 if (!ptx::mbar_wait_bounded(&full[st], ph, abort, status, kStatusTimeout,
                                             kWaitTimeoutNs)) {
                     stop = true;
@@ -440,6 +443,10 @@ __device__ __forceinline__ void products_persistent(const Walk& walk, int chunk_
                                                 tmem_base, chunk_start && kk == 0);
                 }
                 ptx::mma_commit(&empty[st]);
+                if (++st == stages) {
+                    st = 0;
+                    ph ^= 1u;
+                }
                 if (++in_chunk == kCS || j + 1 == nst) {
                     ptx::mma_commit(tmem_full);
                     in_chunk = 0;
