@@ -119,3 +119,32 @@ def test_missing_library_raises(monkeypatch, tmp_path):
     monkeypatch.setattr(_lib, "LIB_PATH", str(tmp_path / "absent.so"))
     with pytest.raises(RuntimeError, match="not built"):
         _lib.load()
+
+
+def test_host_buffer_workspace_size(lib):
+    # gb_dgemm_host stages dense device copies of A, B, C (256-byte aligned each)
+    # after the emulated workspace; native precision needs only the copies
+    out = ctypes.c_size_t()
+    up = lambda x: (x + 255) // 256 * 256
+    m, n, k = 300, 200, 129
+    assert lib.gb_dgemm_host_workspace_size(0, 0, m, n, k, ctypes.byref(out)) == 0
+    assert out.value == up(8 * m * k) + up(8 * k * n) + up(8 * m * n)
+    emu = ctypes.c_size_t()
+    assert lib.gb_dgemm_workspace_size(1, 10, m, n, k, ctypes.byref(emu)) == 0
+    assert lib.gb_dgemm_host_workspace_size(1, 10, m, n, k, ctypes.byref(out)) == 0
+    assert out.value == up(emu.value) + up(8 * m * k) + up(8 * k * n) + up(8 * m * n)
+    assert lib.gb_dgemm_host_workspace_size(1, 17, m, n, k, ctypes.byref(out)) == 1
+    assert lib.gb_dgemm_host_workspace_size(5, 0, m, n, k, ctypes.byref(out)) == 1
+    assert lib.gb_dgemm_host_workspace_size(0, 0, -1, n, k, ctypes.byref(out)) == 1
+
+
+def test_host_buffer_gemm_rejects_bad_arguments_before_any_device_work(lib):
+    # argument errors come back before the queue or the device is touched
+    P = ctypes.c_void_p
+    buf = (ctypes.c_double * 16)()
+    p = ctypes.cast(buf, P)
+    assert lib.gb_dgemm_host(None, 1, 10, 4, 4, 4, 1.0, p, 4, p, 4, 0.0, p, 4, None, 0) == 1
+    fake_q = P(1)  # never dereferenced: the leading dimension check fails first
+    assert lib.gb_dgemm_host(fake_q, 1, 10, 4, 4, 4, 1.0, p, 3, p, 4, 0.0, p, 4, None, 0) == 1
+    assert lib.gb_dgemm_host(fake_q, 7, 10, 4, 4, 4, 1.0, p, 4, p, 4, 0.0, p, 4, None, 0) == 1
+    assert lib.gb_dgemm_host(fake_q, 1, 99, 4, 4, 4, 1.0, p, 4, p, 4, 0.0, p, 4, None, 0) == 1
