@@ -229,9 +229,11 @@ gb_status gb_emulated_products(gb_queue* q, int slices, int64_t m, int64_t n, in
  * gb_dgemm_host_workspace_size() bytes, 256-byte aligned, owned by the caller:
  * the emulated workspace (emulated precision) followed by dense device copies
  * of A, B and C.
- * Emulated precision: B is copied first and split; A (and C when beta != 0) is
- * copied in bands of whole 128-row tiles (up to 4 bands of >= 1024 rows), each
- * band split and multiplied as soon as it arrives, and each band of C is copied
+ * Emulated precision: A (and C when beta != 0) is copied in bands of whole
+ * 128-row tiles (up to 4, each at least 8 waves of output tiles over the SMs),
+ * each band split and multiplied as soon as it arrives; B is copied first, in
+ * two column blocks when there are several bands, so the first band's products
+ * start on the first block while the second arrives; each block of C is copied
  * back while the next bands compute.  Native precision: A, B (and C) are copied,
  * multiplied by the default native kernel, C copied back.
  * The copies run on two streams the queue creates on the first call (one per

@@ -14,7 +14,7 @@ struct gb_device {
 };
 
 namespace gb {
-constexpr int kAuxEvents = 12;  // events of the host-buffer pipeline (2 + 2 per band, <= 4 bands)
+constexpr int kAuxEvents = 16;  // events of the host-buffer pipeline (see hostpipe.cu)
 }
 
 struct gb_queue {

@@ -7,15 +7,19 @@
 // them with the computation, on the queue's stream plus two streams of its own
 // (one per copy direction), ordered by events:
 //
-//   h2d stream : B, then A and (beta != 0) C in bands of rows
-//   queue      : split of B once B has arrived; per band: split of the band's rows
-//                of A, the band's slice products into its rows of C
-//   d2h stream : each band's rows of C as soon as its products are done
+//   h2d stream : B in one or two blocks of columns and A (and, beta != 0, C) in
+//                bands of rows, in the order the launches below need them
+//   queue      : per row band: split of its rows of A, then its slice products
+//                into its rows of C; the first band in two column blocks, each
+//                block of B split just before its first use
+//   d2h stream : each block of C as soon as its products are done
 //
-// so the copies of A after the first band and of C before the last band run
-// under the tensor-core products.  The native precision copies everything first
-// and C last (its FP64 compute outweighs the transfers by two orders of
-// magnitude).  The device side is a caller workspace: the emulated workspace
+// so the first products start once part of B and the first band of A have
+// arrived, and the other copies run under the tensor-core products.  Band and
+// block sizes are chosen so that each products launch fills whole waves of the
+// SMs where possible.  The native
+// precision copies everything first and C last (its FP64 compute outweighs the
+// transfers by two orders of magnitude).  The device side is a caller workspace: the emulated workspace
 // followed by dense device copies of A, B and C.
 #include <cuda_runtime.h>
 
@@ -51,14 +55,16 @@ HostLayout host_layout(gb_precision prec, int s, int64_t m, int64_t n, int64_t k
     return h;
 }
 
-// Row bands of the emulated pipeline: whole 128-row tiles, at most kMaxBands
-// bands, none smaller than kMinBandRows (each band is one launch of the split and
-// of the products kernel, whose last wave is partly idle).
+// Row bands of the emulated pipeline, on whole 128-row tiles: at most kMaxBands,
+// each with at least kMinWaves waves of output tiles over the SMs (every band is
+// one products launch, whose last wave is partly idle).
 constexpr int kMaxBands = 4;
-constexpr int64_t kMinBandRows = 1024;
+constexpr int kMinWaves = 8;
+static_assert(1 + 2 + kMaxBands + (kMaxBands + 1) <= kAuxEvents, "events of the pipeline");
 
-int band_count(int64_t m) {
-    int64_t nb = m / kMinBandRows;
+int band_count(int64_t tile_rows, int64_t tile_cols, int sms) {
+    int64_t nb = tile_rows * tile_cols / ((int64_t)kMinWaves * sms);
+    if (nb > tile_rows) nb = tile_rows;
     if (nb < 1) nb = 1;
     if (nb > kMaxBands) nb = kMaxBands;
     return (int)nb;
@@ -70,6 +76,27 @@ void band_rows(int64_t m, int nb, int i, int64_t* r0, int64_t* r1) {
     const int64_t t0 = tiles * i / nb, t1 = tiles * (i + 1) / nb;
     *r0 = t0 * kEmuBM;
     *r1 = t1 * kEmuBM < m ? t1 * kEmuBM : m;
+}
+
+// Idle tile slots of a launch of `tiles` tiles in its last wave over `sms` SMs.
+int64_t tail_slots(int64_t tiles, int sms) { return (tiles + sms - 1) / sms * sms - tiles; }
+
+// The first row band (R tile rows) runs as two launches, over tile columns [0, c)
+// and [c, T), so its products start once the first c tile columns of B have
+// arrived.  c lies in [0.4 T, 0.5 T] (the second part of B must arrive while the
+// first block computes) and leaves the fewest idle slots in the two last waves
+// (n = 8192, s = 10: c = 76 of 171, 8 and 10 full waves).  0: no split.
+int64_t first_band_split(int nb, int64_t R, int64_t T, int sms) {
+    if (nb < 2 || T < 16) return 0;
+    int64_t best = 0, best_idle = 0;
+    for (int64_t c = (4 * T + 9) / 10; c <= T / 2; ++c) {
+        const int64_t idle = tail_slots(R * c, sms) + tail_slots(R * (T - c), sms);
+        if (best == 0 || idle < best_idle) {
+            best = c;
+            best_idle = idle;
+        }
+    }
+    return best;
 }
 
 cudaError_t copy_rows(void* dst, size_t dpitch, const void* src, size_t spitch,
@@ -206,44 +233,87 @@ gb_status gb_dgemm_host(gb_queue* q, gb_precision prec, int slices, int64_t m, i
     const EmuLayout lay = emu_layout(s, m, n, k);
     int32_t* ea = reinterpret_cast<int32_t*>(ws + lay.a_exp);
     int32_t* fb = reinterpret_cast<int32_t*>(ws + lay.b_exp);
-    const int nb = band_count(m);
-    // h2d: B first (every band's products need all of B), then the bands of A (and C)
-    if (e == cudaSuccess)
-        e = copy_rows(dB, 8 * (size_t)n, B, 8 * (size_t)ldb, n, k, cudaMemcpyHostToDevice, hs);
-    if (e == cudaSuccess) e = cudaEventRecord(ev[1], hs);
-    for (int i = 0; i < nb && e == cudaSuccess; ++i) {
+    const int bn = lay.bn;
+    const int64_t tile_rows = (m + kEmuBM - 1) / kEmuBM, tile_cols = (n + bn - 1) / bn;
+    const int nb = band_count(tile_rows, tile_cols, q->dev->sm_count);
+    int64_t fr0, fr1;
+    band_rows(m, nb, 0, &fr0, &fr1);
+    const int64_t csplit_tiles =
+        first_band_split(nb, (fr1 - fr0 + kEmuBM - 1) / kEmuBM, tile_cols, q->dev->sm_count);
+    // column blocks of B: [0, csplit) and [csplit, n), or one block
+    const int64_t csplit = csplit_tiles > 0 ? csplit_tiles * bn : n;
+    const int ncb = csplit < n ? 2 : 1;
+    const int64_t cb0[2] = {0, csplit}, cb1[2] = {csplit, n};
+    // events: [1, 3) column blocks of B in, [3, 3 + nb) row bands of A (and C) in,
+    // [3 + nb, ...) one per products launch
+    cudaEvent_t* ev_b = ev + 1;
+    cudaEvent_t* ev_a = ev + 3;
+    cudaEvent_t* ev_p = ev + 3 + nb;
+    auto copy_b = [&](int j) {
+        cudaError_t r = copy_rows(dB + cb0[j], 8 * (size_t)n, B + cb0[j], 8 * (size_t)ldb,
+                                  cb1[j] - cb0[j], k, cudaMemcpyHostToDevice, hs);
+        return r == cudaSuccess ? cudaEventRecord(ev_b[j], hs) : r;
+    };
+    auto copy_a = [&](int i) {
         int64_t r0, r1;
         band_rows(m, nb, i, &r0, &r1);
-        e = copy_rows(dA + r0 * kk, 8 * (size_t)kk, A + r0 * lda, 8 * (size_t)lda, k, r1 - r0,
-                      cudaMemcpyHostToDevice, hs);
-        if (e == cudaSuccess && reads_c)
-            e = copy_rows(dC + r0 * n, 8 * (size_t)n, C + r0 * ldc, 8 * (size_t)ldc, n, r1 - r0,
+        cudaError_t r = copy_rows(dA + r0 * kk, 8 * (size_t)kk, A + r0 * lda, 8 * (size_t)lda, k,
+                                  r1 - r0, cudaMemcpyHostToDevice, hs);
+        if (r == cudaSuccess && reads_c)
+            r = copy_rows(dC + r0 * n, 8 * (size_t)n, C + r0 * ldc, 8 * (size_t)ldc, n, r1 - r0,
                           cudaMemcpyHostToDevice, hs);
-        if (e == cudaSuccess) e = cudaEventRecord(ev[2 + 2 * i], hs);
-    }
-    // queue: split of B, then per band the split of its rows of A and its products
-    if (e == cudaSuccess) e = cudaStreamWaitEvent(qs, ev[1], 0);
-    if (e == cudaSuccess)
-        e = launch_split_cols(L, s, n, k, dB, n, ws + lay.b_digits, lay.kp, fb);
+        return r == cudaSuccess ? cudaEventRecord(ev_a[i], hs) : r;
+    };
+    // h2d in the order the launches need it: B's first column block, A's first row
+    // band, the rest of B, A's other row bands (each with C's rows)
+    if (e == cudaSuccess) e = copy_b(0);
+    if (e == cudaSuccess) e = copy_a(0);
+    if (ncb == 2 && e == cudaSuccess) e = copy_b(1);
+    for (int i = 1; i < nb && e == cudaSuccess; ++i) e = copy_a(i);
+    // queue: per row band the split of its rows of A, then its products (the first
+    // band in two column blocks, each block of B split just before its first use);
+    // d2h: each block of C as soon as it is computed.  Band edges sit on tile
+    // edges (128 rows, bn columns), so a band's digit tiles start r0 * kp * s
+    // (c0 * kp * s) bytes into the planes.
+    int launch = 0;
+    auto products = [&](int64_t r0, int64_t r1, int64_t c0, int64_t c1) {
+        const size_t aoff = (size_t)r0 * (size_t)lay.kp * (size_t)s;
+        const size_t boff = (size_t)c0 * (size_t)lay.kp * (size_t)s;
+        cudaError_t r = launch_emu_products(L, s, r1 - r0, c1 - c0, k, alpha, beta,
+                                            dC + r0 * n + c0, n, ws + lay.a_digits + aoff,
+                                            ws + lay.b_digits + boff, lay.kp, ea + r0, fb + c0);
+        cudaEvent_t done = ev_p[launch++];
+        if (r == cudaSuccess) r = cudaEventRecord(done, qs);
+        if (r == cudaSuccess) r = cudaStreamWaitEvent(ds, done, 0);
+        if (r == cudaSuccess)
+            r = copy_rows(C + r0 * ldc + c0, 8 * (size_t)ldc, dC + r0 * n + c0, 8 * (size_t)n,
+                          c1 - c0, r1 - r0, cudaMemcpyDeviceToHost, ds);
+        return r;
+    };
+    auto split_b = [&](int j) {
+        const size_t boff = (size_t)cb0[j] * (size_t)lay.kp * (size_t)s;
+        cudaError_t r = cudaStreamWaitEvent(qs, ev_b[j], 0);
+        if (r == cudaSuccess)
+            r = launch_split_cols(L, s, cb1[j] - cb0[j], k, dB + cb0[j], n,
+                                  ws + lay.b_digits + boff, lay.kp, fb + cb0[j]);
+        return r;
+    };
     for (int i = 0; i < nb && e == cudaSuccess; ++i) {
         int64_t r0, r1;
         band_rows(m, nb, i, &r0, &r1);
-        // a band starts on a 128-row tile: its digit tiles start r0 * kp * s bytes in
-        const size_t doff = (size_t)r0 * (size_t)lay.kp * (size_t)s;
-        e = cudaStreamWaitEvent(qs, ev[2 + 2 * i], 0);
+        const size_t aoff = (size_t)r0 * (size_t)lay.kp * (size_t)s;
+        e = cudaStreamWaitEvent(qs, ev_a[i], 0);
         if (e == cudaSuccess)
-            e = launch_split_rows(L, s, r1 - r0, k, dA + r0 * kk, kk, ws + lay.a_digits + doff,
+            e = launch_split_rows(L, s, r1 - r0, k, dA + r0 * kk, kk, ws + lay.a_digits + aoff,
                                   lay.kp, ea + r0);
-        if (e == cudaSuccess)
-            e = launch_emu_products(L, s, r1 - r0, n, k, alpha, beta, dC + r0 * n, n,
-                                    ws + lay.a_digits + doff, ws + lay.b_digits, lay.kp, ea + r0,
-                                    fb);
-        if (e == cudaSuccess) e = cudaEventRecord(ev[3 + 2 * i], qs);
-        // d2h: this band's rows of C while the next bands compute
-        if (e == cudaSuccess) e = cudaStreamWaitEvent(ds, ev[3 + 2 * i], 0);
-        if (e == cudaSuccess)
-            e = copy_rows(C + r0 * ldc, 8 * (size_t)ldc, dC + r0 * n, 8 * (size_t)n, n, r1 - r0,
-                          cudaMemcpyDeviceToHost, ds);
+        if (i == 0) {
+            for (int j = 0; j < ncb && e == cudaSuccess; ++j) {
+                e = split_b(j);
+                if (e == cudaSuccess) e = products(r0, r1, cb0[j], cb1[j]);
+            }
+        } else if (e == cudaSuccess) {
+            e = products(r0, r1, 0, n);
+        }
     }
     // the queue completes when C is back in host memory
     if (e == cudaSuccess) e = cudaEventRecord(ev[0], ds);
