@@ -200,6 +200,29 @@ int validate_gemm(int64_t m, int64_t n, int64_t k, double alpha, const double* A
     return (int)check_gemm_args(m, n, k, alpha, A, lda, B, ldb, beta, C, ldc);
 }
 
+bool emu_group_trans(int s, int64_t m, int64_t n) {
+    const int64_t bn = emu_bn(s);
+    auto pad = [](int64_t x, int64_t r) { return (x + r - 1) / r * r; };
+    return pad(n, kEmuBM) * pad(m, bn) < pad(m, kEmuBM) * pad(n, bn);
+}
+
+EmuLayout emu_group_layout(int s, int64_t m, int64_t n, int64_t k) {
+    return emu_group_trans(s, m, n) ? emu_layout(s, n, m, k) : emu_layout(s, m, n, k);
+}
+
+void emu_group_assign(EmuProb& e, uint8_t* base, const EmuLayout& w) {
+    uint8_t* row_side = base + w.a_digits;  // 128-line tiles
+    uint8_t* col_side = base + w.b_digits;  // emu_bn(s)-line tiles
+    int32_t* row_exp = reinterpret_cast<int32_t*>(base + w.a_exp);
+    int32_t* col_exp = reinterpret_cast<int32_t*>(base + w.b_exp);
+    e.a_digits = e.trans ? col_side : row_side;
+    e.b_digits = e.trans ? row_side : col_side;
+    e.a_exp = e.trans ? col_exp : row_exp;
+    e.b_exp = e.trans ? row_exp : col_exp;
+    e.ra = e.trans ? emu_bn(e.s) : kEmuBM;
+    e.rb = e.trans ? kEmuBM : emu_bn(e.s);
+}
+
 EmuLayout emu_layout(int s, int64_t m, int64_t n, int64_t k) {
     EmuLayout L{};
     L.kp = ((k + 31) / 32) * 32;

@@ -126,9 +126,14 @@ gb_status build_layout(const gb_gemm_desc* d, int64_t count, Layout& L) {
             e.alpha = x.alpha;
             e.beta = x.beta;
             e.s = s;
-            e.tiles_n = (int32_t)((x.n + emu_bn(s) - 1) / emu_bn(s));
+            e.trans = emu_group_trans(s, x.m, x.n) ? 1 : 0;
+            e.ra = e.trans ? emu_bn(s) : kEmuBM;
+            e.rb = e.trans ? kEmuBM : emu_bn(s);
+            // output tiles: 128 lines of the row side x emu_bn(s) of the column side
+            const int64_t cols = e.trans ? x.m : x.n;
+            e.tiles_n = (int32_t)((cols + emu_bn(s) - 1) / emu_bn(s));
             L.emu.push_back(e);
-            L.emu_ws.push_back(emu_layout(s, x.m, x.n, x.k));
+            L.emu_ws.push_back(emu_group_layout(s, x.m, x.n, x.k));
             L.emu_idx.push_back(i);
             L.max_s = std::max(L.max_s, s);
         }
@@ -189,12 +194,13 @@ gb_status build_layout(const gb_gemm_desc* d, int64_t count, Layout& L) {
         L.keys[1].push_back(colblks);
         L.keys[2].push_back(tblks);
         L.keys[3].push_back(tiles);
-        const int64_t ncb = (e.n + 31) / 32;                          // real columns
-        const int64_t ncbp = ((int64_t)e.tiles_n * w.bn + 31) / 32;   // padded to tiles
-        rows += (e.m + kEmuBM - 1) / kEmuBM * kEmuBM;
+        const int64_t ncb = (e.n + 31) / 32;                                 // real columns
+        const int64_t ncbp = ((e.n + e.rb - 1) / e.rb * e.rb + 31) / 32;     // padded to tiles
+        rows += (e.m + kEmuBM - 1) / kEmuBM * kEmuBM;  // 128-row blocks of the split of A
         colblks += ncb;
         tblks += ncbp * ((w.kp + 63) / 64);
-        const int64_t nt = ((e.m + kEmuBM - 1) / kEmuBM) * e.tiles_n;
+        const int64_t row_side = e.trans ? e.n : e.m;
+        const int64_t nt = ((row_side + kEmuBM - 1) / kEmuBM) * e.tiles_n;
         tiles += nt;
         if (L.s_ranges.empty() || L.s_ranges.back().s != e.s)
             L.s_ranges.push_back(EmuSRange{e.s, (int)i, 0, e.first_row, 0, e.first_colblk, 0,
@@ -240,12 +246,7 @@ gb_status grouped_enqueue_async(const Launch& L, const gb_gemm_desc* descs, int6
     // each emulated problem uses the workspace of its own descriptor
     for (size_t ei = 0; ei < lay.emu.size(); ++ei) {
         uint8_t* w = static_cast<uint8_t*>(emu_ws[lay.emu_idx[ei]]);
-        EmuProb& e = lay.emu[ei];
-        const EmuLayout& wl = lay.emu_ws[ei];
-        e.a_digits = w + wl.a_digits;
-        e.b_digits = w + wl.b_digits;
-        e.a_exp = reinterpret_cast<int32_t*>(w + wl.a_exp);
-        e.b_exp = reinterpret_cast<int32_t*>(w + wl.b_exp);
+        emu_group_assign(lay.emu[ei], w, lay.emu_ws[ei]);
     }
     uint8_t* stg = static_cast<uint8_t*>(staging);
     uint8_t* dev = static_cast<uint8_t*>(tables);
@@ -374,12 +375,8 @@ gb_status gb_grouped_plan_create(gb_queue* q, const gb_gemm_desc* descs, int64_t
     uint8_t* ws = static_cast<uint8_t*>(workspace);
     size_t off = L.off_data;
     for (size_t i = 0; i < L.emu.size(); ++i) {
-        EmuProb& e = L.emu[i];
         const EmuLayout& w = L.emu_ws[i];
-        e.a_digits = ws + off + w.a_digits;
-        e.b_digits = ws + off + w.b_digits;
-        e.a_exp = reinterpret_cast<int32_t*>(ws + off + w.a_exp);
-        e.b_exp = reinterpret_cast<int32_t*>(ws + off + w.b_exp);
+        emu_group_assign(L.emu[i], ws + off, w);
         off += w.total;
     }
     gb_grouped_plan* p = new (std::nothrow) gb_grouped_plan();

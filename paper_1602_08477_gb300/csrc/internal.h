@@ -90,6 +90,15 @@ struct EmuLayout {
 };
 EmuLayout emu_layout(int s, int64_t m, int64_t n, int64_t k);
 
+// A grouped emulated problem is computed as C^T = B^T A^T (B's columns on the
+// 128-row side of the output tiles, A's rows on the emu_bn(s)-column side) when
+// that pads fewer tile slots: pad(n, 128) pad(m, bn) < pad(m, 128) pad(n, bn).
+bool emu_group_trans(int s, int64_t m, int64_t n);
+// Workspace layout of one grouped emulated problem: emu_layout(s, m, n, k), or for
+// a transposed problem emu_layout(s, n, m, k) with the roles swapped (its a_*
+// regions hold B's column digits and exponents, its b_* regions A's rows').
+EmuLayout emu_group_layout(int s, int64_t m, int64_t n, int64_t k);
+
 // One emulated problem of a grouped launch, as the device reads it.
 struct EmuProb {
     int64_t m, n, k, lda, ldb, ldc, kp;
@@ -97,16 +106,23 @@ struct EmuProb {
     const double* B;
     double* C;
     double alpha, beta;
-    uint8_t* a_digits;
-    uint8_t* b_digits;
+    uint8_t* a_digits;  // digit tiles of A's rows (ra lines per tile)
+    uint8_t* b_digits;  // digit tiles of B's columns (rb lines per tile)
     int32_t* a_exp;
     int32_t* b_exp;
     int32_t s, tiles_n;
+    int32_t trans;   // computed as C^T = B^T A^T: B's columns on the 128-row side
+    int32_t ra, rb;  // tile lines of A's and B's digits: 128 and emu_bn(s), swapped if trans
+    int32_t pad_;
     int64_t first_row;     // exclusive prefixes over the table of: rows of A padded to 128,
     int64_t first_colblk;  // 32-column blocks of B,
     int64_t first_tblk;    // (32-column x 64-row) blocks of B's padded columns,
     int64_t first_tile;    // 128 x emu_bn(s) output tiles
 };
+
+// Points the digit and exponent fields of `e` (m, n, s, trans set) into the
+// problem's workspace at `base`, laid out as emu_group_layout.
+void emu_group_assign(EmuProb& e, uint8_t* base, const EmuLayout& w);
 
 // The same four prefixes as compact arrays (one int64 per table entry), the
 // keys of the device-side binary searches: a search touches a few cache lines

@@ -131,6 +131,7 @@ struct TileArgs {
     const uint8_t* b_src;  // B digit tiles of this tile column, K block 0 (s * 1 KiB per block)
     int s, nkb;
     bool reverse;  // stream the K blocks last to first
+    bool trans;    // the tile's rows are columns of C (C^T = B^T A^T): store transposed
     int64_t m, n, ldc, row0, col0;
     double alpha, beta;
     double* C;
@@ -495,7 +496,10 @@ __device__ __forceinline__ void products_persistent(const Walk& walk, int chunk_
                 const long long ab = __double_as_longlong(a.alpha), bb = __double_as_longlong(a.beta);
                 const bool beta0 = (bb & 0x7FFFFFFFFFFFFFFFll) == 0;
                 const bool plain = ab == 0x3FF0000000000000ll && beta0;
-                double* crow = a.C + row * a.ldc;
+                // C[row][col], or C[col][row] for a transposed problem (a warp's
+                // 32 lanes then store 32 consecutive doubles of one row of C)
+                const int64_t rstride = a.trans ? 1 : a.ldc, cstride = a.trans ? a.ldc : 1;
+                double* crow = a.C + row * rstride;
 #pragma unroll
                 for (int j = 0; j < CW; ++j) {
                     const int64_t col = a.col0 + epi_col(cgroup, j);
@@ -510,10 +514,11 @@ __device__ __forceinline__ void products_persistent(const Walk& walk, int chunk_
                                 out = tv;
                             } else {
                                 out = __dmul_rn(a.alpha, tv);
-                                if (!beta0) out = __dadd_rn(out, __dmul_rn(a.beta, crow[col]));
+                                if (!beta0)
+                                    out = __dadd_rn(out, __dmul_rn(a.beta, crow[col * cstride]));
                             }
                         }
-                        crow[col] = out;
+                        crow[col * cstride] = out;
                     }
                 }
             }
@@ -572,6 +577,7 @@ struct RasterWalk {
         a.s = s;
         a.nkb = nkb;
         a.reverse = reverse;
+        a.trans = false;
         a.m = m;
         a.n = n;
         a.ldc = ldc;
@@ -625,22 +631,26 @@ struct GroupWalk {
         const int64_t local = t - key[lo];
         const int64_t tm = local / e.tiles_n, tn = local % e.tiles_n;
         const int nkb = (int)(e.kp / kBKBytes);
+        // a transposed problem has B's columns on the tile rows and A's rows on the
+        // tile columns
+        const bool tr = e.trans != 0;
         TileArgs a;
-        a.a_src = e.a_digits + (size_t)tm * nkb * e.s * kBM * kBKBytes;
-        a.b_src = e.b_digits + (size_t)tn * nkb * e.s * BN * kBKBytes;
+        a.a_src = (tr ? e.b_digits : e.a_digits) + (size_t)tm * nkb * e.s * kBM * kBKBytes;
+        a.b_src = (tr ? e.a_digits : e.b_digits) + (size_t)tn * nkb * e.s * BN * kBKBytes;
         a.s = e.s;
         a.nkb = nkb;
         a.reverse = false;
-        a.m = e.m;
-        a.n = e.n;
+        a.trans = tr;
+        a.m = tr ? e.n : e.m;
+        a.n = tr ? e.m : e.n;
         a.ldc = e.ldc;
         a.row0 = tm * kBM;
         a.col0 = tn * BN;
         a.alpha = e.alpha;
         a.beta = e.beta;
         a.C = e.C;
-        a.eA = e.a_exp;
-        a.fB = e.b_exp;
+        a.eA = tr ? e.b_exp : e.a_exp;
+        a.fB = tr ? e.a_exp : e.b_exp;
         return a;
     }
 };

@@ -237,14 +237,14 @@ __device__ __forceinline__ void colmax_block(int64_t jb, int64_t n, int64_t k,
 }
 
 // Transposing digit pass for B over the tile of 64 rows (l) x 32 columns (j)
-// at (lb, jb), into B digit tiles of emu_bn(S) lines; columns n <= j < (n padded
-// to whole tiles) get zero digits, columns beyond are not written.
+// at (lb, jb), into B digit tiles of R lines; columns n <= j < (n padded to whole
+// tiles) get zero digits, columns beyond are not written.
 template <int S>
 __device__ __forceinline__ void split_cols_tile(int64_t jb, int64_t lb, int64_t n, int64_t k,
                                                 const double* __restrict__ B, int64_t ldb, int s,
                                                 uint8_t* __restrict__ digits, int64_t kp,
                                                 const int32_t* __restrict__ exps,
-                                                uint64_t (*T)[33]) {
+                                                uint64_t (*T)[33], int R) {
     const int tid = threadIdx.x;
     const int tx = tid & 31, ty = tid >> 5;
     const int64_t j0 = jb * 32, l0 = lb * 64;
@@ -255,7 +255,6 @@ __device__ __forceinline__ void split_cols_tile(int64_t jb, int64_t lb, int64_t 
         T[ty + 8 * r][tx] = (l < k && j < n) ? Bb[l * ldb + j] : 0ull;
     }
     __syncthreads();
-    constexpr int R = emu_bn(S);
     const int jj = tid >> 3, lsub = (tid & 7) * 8;
     const int64_t j = j0 + jj, lbase = l0 + lsub;
     const int64_t np = (n + R - 1) / R * R;
@@ -315,7 +314,7 @@ __global__ void __launch_bounds__(256) split_cols_kernel(int64_t n, int64_t k,
                                                          const int32_t* __restrict__ exps) {
     fill_e4m3_table();
     __shared__ uint64_t T[64][33];
-    split_cols_tile<S>(blockIdx.x, blockIdx.y, n, k, B, ldb, S, digits, kp, exps, T);
+    split_cols_tile<S>(blockIdx.x, blockIdx.y, n, k, B, ldb, S, digits, kp, exps, T, emu_bn(S));
 }
 
 #define GB_SWITCH_S(s, CALL)                                                           \
@@ -351,8 +350,9 @@ __device__ __forceinline__ void split_row_tile(int64_t row0, int64_t m, int64_t 
                                                const double* __restrict__ A, int64_t lda,
                                                uint8_t* __restrict__ digits, int64_t kp,
                                                int32_t* __restrict__ exps, unsigned* status,
-                                               int* e_sh) {
+                                               int* e_sh, int R) {
     const int64_t nkb = kp >> 5;
+    const int64_t mp = (m + R - 1) / R * R;  // rows with digits (R-line tiles)
 #pragma unroll
     for (int half = 0; half < 2; ++half) {
         const int p = threadIdx.x + 256 * half;
@@ -399,6 +399,7 @@ __device__ __forceinline__ void split_row_tile(int64_t row0, int64_t m, int64_t 
             const int p = threadIdx.x + 256 * half;
             const int r = p >> 2;
             const int64_t i = row0 + r, l0 = kb * 32 + (p & 3) * 8;
+            if (i >= mp) continue;  // beyond the last R-line tile of this problem
             const int e = e_sh[r];
             uint64_t w[S];
 #pragma unroll
@@ -414,7 +415,7 @@ __device__ __forceinline__ void split_row_tile(int64_t row0, int64_t m, int64_t 
             }
 #pragma unroll
             for (int t = 0; t < S; ++t)
-                *reinterpret_cast<uint64_t*>(digits + tiled_offset(i, l0, t, S, nkb, kEmuBM)) = w[t];
+                *reinterpret_cast<uint64_t*>(digits + tiled_offset(i, l0, t, S, nkb, R)) = w[t];
         }
     }
     __syncthreads();
@@ -435,7 +436,7 @@ __global__ void __launch_bounds__(256) grouped_split_rows_kernel(const EmuProb* 
          r0 += (int64_t)gridDim.x * kEmuBM) {
         const EmuProb& q = P[find_prob(key, q_begin, q_end - 1, r0)];
         split_row_tile<S>(r0 - q.first_row, q.m, q.k, q.A, q.lda, q.a_digits, q.kp, q.a_exp,
-                          status, e_sh);
+                          status, e_sh, q.ra);
     }
 }
 
@@ -463,10 +464,9 @@ __global__ void __launch_bounds__(256) grouped_split_cols_kernel(const EmuProb* 
     for (int64_t b = tb_begin + blockIdx.x; b < tb_end; b += gridDim.x) {
         const EmuProb& q = P[find_prob(key, q_begin, q_end - 1, b)];
         const int64_t local = b - q.first_tblk;
-        constexpr int R = emu_bn(S);
-        const int64_t ncb = ((q.n + R - 1) / R * R + 31) / 32;  // padded columns
+        const int64_t ncb = ((q.n + q.rb - 1) / q.rb * q.rb + 31) / 32;  // padded columns
         split_cols_tile<S>(local % ncb, local / ncb, q.n, q.k, q.B, q.ldb, S, q.b_digits, q.kp,
-                           q.b_exp, T);
+                           q.b_exp, T, q.rb);
     }
 }
 

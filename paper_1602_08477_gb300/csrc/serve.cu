@@ -126,7 +126,7 @@ struct Slot {
 size_t footprint(const gb_request& r) {
     size_t b = 8 * ((size_t)r.m * r.k + (size_t)r.k * r.n + (size_t)r.m * r.n) + 3 * 1024;
     if (r.precision == GB_PREC_EMULATED)
-        b += emu_layout(r.slices == 0 ? 11 : r.slices, r.m, r.n, r.k).total + 1024;
+        b += emu_group_layout(r.slices == 0 ? 11 : r.slices, r.m, r.n, r.k).total + 1024;
     return b;
 }
 

@@ -226,3 +226,47 @@ def test_native_group_ragged_edges(gb, tile):
                              for row in exact.fraction_gemm(1.5, A, B, 0.5, C0)])
             assert np.array_equal(p["C"].cpu().numpy(), star)
     assert check_bound(probs, host) <= 2.0
+
+
+def test_emulated_group_wide_problems_run_transposed(gb):
+    """Problems with n well above m run as C^T = B^T A^T (B's columns on the
+    128-row side of the tiles): each still equals the single launch bit for bit,
+    with beta != 0, leading dimensions wider than the rows, and NaN / Inf lines
+    (their rows of C, or columns, are NaN)."""
+    import torch
+    sizes = [(16, 500, 40, 10), (20, 300, 129, 11), (33, 2000, 64, 12), (130, 140, 70, 10),
+             (40, 97, 33, 9), (500, 16, 40, 10)]
+    probs, host = [], []
+    for i, (m, n, k, s) in enumerate(sizes):
+        A = g.matrix("uniform", m, k, 9200 + i, 0)
+        B = g.matrix("hard" if i % 2 else "uniform", k, n, 9200 + i, 1)
+        C0 = g.matrix("uniform", m, n, 9200 + i, 2)
+        if i == 0:
+            A[3, 7] = np.nan
+            B[5, 411] = np.inf
+        Aw = np.full((m, k + 3), np.nan)
+        Aw[:, :k] = A
+        dA = to_dev(Aw)[:, :k]
+        probs.append(dict(A=dA, B=to_dev(B), C=to_dev(C0), alpha=1.25, beta=-0.5,
+                          precision="emulated", slices=s))
+        host.append((A, B, C0))
+    gb.dgemm_grouped(probs)
+    torch.cuda.synchronize()
+    for i, (p, (A, B, C0)) in enumerate(zip(probs, host)):
+        single = to_dev(C0)
+        gb.dgemm(to_dev(A), to_dev(B), single, 1.25, -0.5, precision="emulated",
+                 slices=p["slices"])
+        torch.cuda.synchronize()
+        got = p["C"].cpu().numpy()
+        assert np.array_equal(got, single.cpu().numpy(), equal_nan=True)
+        if i == 0:
+            assert np.isnan(got[3]).all() and np.isnan(got[:, 411]).all()
+            mask = np.ones_like(got, dtype=bool)
+            mask[3] = False
+            mask[:, 411] = False
+            assert np.isfinite(got[mask]).all()
+    # the NaN / Inf input left its status on the queue: reported once, then cleared
+    q = gb.default_queue()
+    with pytest.raises(gb.GbError, match="GB_ERR_NONFINITE"):
+        q.wait()
+    q.wait()
