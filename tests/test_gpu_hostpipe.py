@@ -101,3 +101,26 @@ def test_small_workspace_rejected(gb):
     with pytest.raises(gb.GbError, match="WORKSPACE"):
         gb.dgemm_host(pinned(z), pinned(z), pinned(z), precision="emulated", slices=10,
                       workspace=ws)
+
+
+@pytest.mark.parametrize("precision", ["native", "emulated"])
+def test_degenerate_host_buffer_gemms(gb, precision):
+    """alpha = 0 and k = 0 give beta C without reading A or B (the copies of A and
+    B are skipped too); m = 0 is a no-op."""
+    import torch
+    m, n = 70, 90
+    C0 = g.matrix("uniform", m, n, 8501, 2)
+    A = g.matrix("uniform", m, 33, 8501, 0)
+    B = g.matrix("uniform", 33, n, 8501, 1)
+    hC = pinned(C0)
+    gb.dgemm_host(pinned(A), pinned(B), hC, 0.0, 0.25, precision=precision, slices=10)
+    torch.cuda.synchronize()
+    assert np.array_equal(hC.numpy(), 0.25 * C0)
+    hC = pinned(C0)
+    gb.dgemm_host(pinned(np.zeros((m, 0))), pinned(np.zeros((0, n))), hC, 1.0, -2.0,
+                  precision=precision, slices=10)
+    torch.cuda.synchronize()
+    assert np.array_equal(hC.numpy(), -2.0 * C0)
+    empty = pinned(np.zeros((0, n)))
+    gb.dgemm_host(pinned(np.zeros((0, 33))), pinned(B), empty, precision=precision, slices=10)
+    torch.cuda.synchronize()
