@@ -41,15 +41,21 @@ __device__ __forceinline__ uint32_t e4m3_of_int(int d) {
     return (d < 0 ? 0x80u : 0u) | code;
 }
 
-// E4M3 byte of every signed digit d in [-16, 16], indexed by d mod 64.  Each split
-// kernel fills it first (fill_e4m3_table); the lookup runs on the load/store
-// pipe, which these integer-ALU-bound kernels leave idle.
-__shared__ uint8_t s_e4m3[64];
+// E4M3 byte of the digit d_t that a 7-bit window w = bits 5(S-t) .. 5(S-t)+6 of the
+// fixed-point image determines under rounding half up (see digits_of):
+// Q_t mod 64 = bits 1..6 of w + 1, and Q_(t-1) is odd iff bits 5, 6 of w are 01 or
+// 10.  Each split kernel fills the table first (fill_e4m3_table); the lookup runs
+// on the load/store pipe, which these integer-ALU-bound kernels leave idle.
+__shared__ uint8_t s_window[128];
 
 __device__ __forceinline__ void fill_e4m3_table() {
-    if (threadIdx.x < 64) {
-        const int d = threadIdx.x >= 32 ? (int)threadIdx.x - 64 : (int)threadIdx.x;
-        s_e4m3[threadIdx.x] = (uint8_t)(d >= -16 && d <= 16 ? e4m3_of_int(d) : 0u);
+    const int x = threadIdx.x;
+    if (x < 128) {
+        const int qt = ((x + 1) >> 1) & 63;
+        const int qp_odd = (((x >> 5) + 1) >> 1) & 1;
+        const int dm = (qt - 32 * qp_odd) & 63;
+        const int d = dm >= 32 ? dm - 64 : dm;
+        s_window[x] = (uint8_t)(d >= -16 && d <= 16 ? e4m3_of_int(d) : 0u);
     }
     __syncthreads();
 }
@@ -84,7 +90,14 @@ struct FixedOf {
 // = 2 Q0 + h, Q_t = (W + 1 - tie) / 2, where the tie (exactly half, Q0 even) is:
 // the lowest set bit of F is bit 5 (S - t) (read off the trailing-zero count of
 // X, which also covers the bits a right shift drops for k < 0) and bit 1 of W is
-// clear.  Only Q_t mod 64 is kept: d_t mod 64 indexes the E4M3 table.
+// clear.  Only d_t mod 64 is needed (it indexes the E4M3 table), i.e. Q_t mod 64
+// and Q_(t-1) mod 2, and with rounding half up (W + 1) / 2 these depend on the
+// seven bits 5(S-t) .. 5(S-t)+6 of F alone: one window lookup per digit.  A tie
+// can only sit at the one digit t* with 5(S - t*) = tzF, and round-half-up differs
+// from ties-to-even there only when Q0 is even; using F - 1 instead of F then
+// gives the even rounding at t* and changes no other digit (F - 1 stays above
+// every lower rounding point by less than a half unit, and the higher windows
+// see no borrow), so the whole element is one subtraction plus S lookups.
 template <int S>
 __device__ __forceinline__ void digits_of(uint64_t bits, int e, int lane, uint64_t (&out)[S]) {
     using Fixed = typename FixedOf<S>::type;
@@ -104,16 +117,15 @@ __device__ __forceinline__ void digits_of(uint64_t bits, int e, int lane, uint64
     Fixed F;
     if (k >= 0) F = (Fixed)X << k;  // exact: |F| < 2^(5 S)
     else F = (Fixed)(X >> (-k < 63 ? -k : 63));
-    uint32_t qprev = 0;
+    // an exact tie at a digit's rounding point with an even quotient rounds down
+    const bool tie_down = tzF >= 0 && tzF <= kB * (S - 1) && tzF % kB == 0 &&
+                          (((uint32_t)(F >> (tzF + 1))) & 1u) == 0u;
+    F -= tie_down ? 1 : 0;
 #pragma unroll
     for (int t = 1; t <= S; ++t) {
         const int sh = kB * (S - t);
-        const uint32_t W = (uint32_t)(F >> sh);
-        const uint32_t tie = (tzF == sh && (W & 2u) == 0u) ? 1u : 0u;
-        const uint32_t q = (W + 1u - tie) >> 1;
-        const uint32_t code = s_e4m3[(q - (qprev << kB)) & 63u];
-        qprev = q;
-        out[t - 1] |= (uint64_t)code << (8 * lane);
+        const uint32_t w = (uint32_t)(F >> sh) & 127u;
+        out[t - 1] |= (uint64_t)s_window[w] << (8 * lane);
     }
 }
 

@@ -183,3 +183,24 @@ def test_full_size_sampled_rows(gb, n, s):
     want = ozaki.emulated_gemm(1.0, A, B, s=s, rows=rows)
     assert np.array_equal(got[rows], want)
     assert within_bound(got[rows], 1.0, A, B, 0.0, None, rows=rows) <= 1.0
+
+
+@pytest.mark.parametrize("s", [10, 12])
+def test_emulated_writes_only_c(gb, s):
+    """C as a window of a larger canary-filled buffer (ldc > n, rows above and
+    below): the emulated path writes exactly the m x n window."""
+    import torch
+    m, n, k = 200, 97, 150
+    A, B, C0 = inputs("uniform", m, n, k, 35)
+    canary = -12345.678
+    big = np.full((m + 3, n + 7), canary)
+    big[1:1 + m, 2:2 + n] = C0
+    dbig = to_dev(big)
+    dC = dbig[1:1 + m, 2:2 + n]
+    gb.dgemm(to_dev(A), to_dev(B), dC, 1.5, 0.5, precision="emulated", slices=s)
+    torch.cuda.synchronize()
+    out = dbig.cpu().numpy()
+    mask = np.ones_like(out, dtype=bool)
+    mask[1:1 + m, 2:2 + n] = False
+    assert np.all(out[mask] == canary)
+    assert np.array_equal(out[1:1 + m, 2:2 + n], ozaki.emulated_gemm(1.5, A, B, 0.5, C0, s=s))

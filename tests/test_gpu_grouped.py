@@ -270,3 +270,29 @@ def test_emulated_group_wide_problems_run_transposed(gb):
     with pytest.raises(gb.GbError, match="GB_ERR_NONFINITE"):
         q.wait()
     q.wait()
+
+
+def test_emulated_group_writes_only_c(gb):
+    """Every C of a group (wide problems run transposed, tall ones not) is a window
+    of a larger canary-filled buffer: only the m x n windows change."""
+    import torch
+    canary = -777.25
+    sizes = [(16, 500, 40), (300, 20, 64), (50, 51, 33)]
+    probs, bigs, wins = [], [], []
+    for i, (m, n, k) in enumerate(sizes):
+        A = g.matrix("uniform", m, k, 9300 + i, 0)
+        B = g.matrix("uniform", k, n, 9300 + i, 1)
+        big = to_dev(np.full((m + 2, n + 5), canary))
+        C = big[1:1 + m, 3:3 + n]
+        C.zero_()
+        probs.append(dict(A=to_dev(A), B=to_dev(B), C=C, precision="emulated", slices=11))
+        bigs.append(big)
+        wins.append((m, n))
+    gb.dgemm_grouped(probs)
+    torch.cuda.synchronize()
+    for big, (m, n) in zip(bigs, wins):
+        out = big.cpu().numpy()
+        mask = np.ones_like(out, dtype=bool)
+        mask[1:1 + m, 3:3 + n] = False
+        assert np.all(out[mask] == canary)
+        assert np.isfinite(out[1:1 + m, 3:3 + n]).all()
