@@ -232,10 +232,14 @@ gb_status gb_emulated_products(gb_queue* q, int slices, int64_t m, int64_t n, in
  * Emulated precision: A (and C when beta != 0) is copied in bands of whole
  * 128-row tiles (up to 4, each at least 8 waves of output tiles over the SMs),
  * each band split and multiplied as soon as it arrives; B is copied first, in
- * two column blocks when there are several bands, so the first band's products
- * start on the first block while the second arrives; each block of C is copied
- * back while the next bands compute.  Native precision: A, B (and C) are copied,
- * multiplied by the default native kernel, C copied back.
+ * up to 6 column blocks when there are several bands (the first small, each next
+ * as large as the link can deliver while the previous block's products run), so
+ * the first band's products start on the first block while the others arrive;
+ * the last band runs in two launches so that only a small last block of C is
+ * copied back after the products end; each block of C is copied back while the
+ * next launches compute (gb_dgemm_host_schedule lists the launches).  Native
+ * precision: A, B (and C) are copied, multiplied by the default native kernel,
+ * C copied back.
  * The copies run on two streams the queue creates on the first call (one per
  * direction), ordered after all work already on the queue; the queue's stream
  * passes the end of this call once C is back in host memory.  The caller must
@@ -252,6 +256,18 @@ gb_status gb_dgemm_host(gb_queue* q, gb_precision prec, int slices, int64_t m, i
 /* Device workspace bytes gb_dgemm_host needs for these sizes. */
 gb_status gb_dgemm_host_workspace_size(gb_precision prec, int slices, int64_t m, int64_t n,
                                        int64_t k, size_t* out);
+
+/* The products launches gb_dgemm_host makes for an emulated GEMM with these
+ * sizes on a device with sm_count SMs, in enqueue order: launch p computes rows
+ * pieces[4p] .. pieces[4p+1] - 1 and columns pieces[4p+2] .. pieces[4p+3] - 1 of C
+ * (edges on whole 128-row x bn-column output tiles; together the launches cover
+ * C once).  The launches of the first row band use the column blocks of B in the
+ * order they are copied in.  Host-only (no device is touched).  *count receives
+ * the number of launches (at most 10; 0 for an empty product); GB_ERR_INVALID_ARG
+ * when it exceeds max_pieces (nothing written), for negative sizes, sm_count < 1
+ * or slices outside [0, 16]. */
+gb_status gb_dgemm_host_schedule(int slices, int64_t m, int64_t n, int64_t k, double beta,
+                                 int sm_count, int64_t* pieces, int max_pieces, int* count);
 
 /* Diagnostic of the failure path (the paper has no failure model; this library
  * bounds every device-side wait): enqueues a kernel that waits on a barrier

@@ -15,6 +15,7 @@ from .gemm import (  # noqa: F401
     dgemm,
     dgemm_host,
     emulated_layout,
+    host_schedule,
     host_workspace_size,
     emulated_steps,
     workdiv_suggest,

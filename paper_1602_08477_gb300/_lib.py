@@ -93,6 +93,8 @@ SIGNATURES = {
     "gb_dgemm_host": (_st, [_vp, _int, _int, _i64, _i64, _i64, _dbl, _vp, _i64, _vp, _i64, _dbl,
                             _vp, _i64, _vp, _sz]),
     "gb_dgemm_host_workspace_size": (_st, [_int, _int, _i64, _i64, _i64, ctypes.POINTER(_sz)]),
+    "gb_dgemm_host_schedule": (_st, [_int, _i64, _i64, _i64, _dbl, _int, ctypes.POINTER(_i64),
+                                     _int, ctypes.POINTER(_int)]),
 }
 
 

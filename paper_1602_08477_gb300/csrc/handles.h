@@ -14,7 +14,7 @@ struct gb_device {
 };
 
 namespace gb {
-constexpr int kAuxEvents = 16;  // events of the host-buffer pipeline (see hostpipe.cu)
+constexpr int kAuxEvents = 24;  // events of the host-buffer pipeline (see hostpipe.cu)
 }
 
 struct gb_queue {

@@ -7,17 +7,19 @@
 // them with the computation, on the queue's stream plus two streams of its own
 // (one per copy direction), ordered by events:
 //
-//   h2d stream : B in one or two blocks of columns and A (and, beta != 0, C) in
-//                bands of rows, in the order the launches below need them
+//   h2d stream : B in column blocks and A (and, beta != 0, C) in bands of rows,
+//                in the order the launches below need them
 //   queue      : per row band: split of its rows of A, then its slice products
-//                into its rows of C; the first band in two column blocks, each
-//                block of B split just before its first use
+//                into its rows of C; the first band one launch per column block
+//                of B, each block split just before its first use; the last band
+//                in two launches
 //   d2h stream : each block of C as soon as its products are done
 //
-// so the first products start once part of B and the first band of A have
-// arrived, and the other copies run under the tensor-core products.  Band and
-// block sizes are chosen so that each products launch fills whole waves of the
-// SMs where possible.  The native
+// so the first products start once a small first block of B and the first band
+// of A have arrived, the blocks of B grow as fast as the link keeps ahead of the
+// products, the other copies run under the tensor-core products, and only a small
+// last block of C is copied back after the last launch.  Launch sizes are chosen
+// so that each fills whole waves of the SMs where possible.  The native
 // precision copies everything first and C last (its FP64 compute outweighs the
 // transfers by two orders of magnitude).  The device side is a caller workspace: the emulated workspace
 // followed by dense device copies of A, B and C.
@@ -57,10 +59,18 @@ HostLayout host_layout(gb_precision prec, int s, int64_t m, int64_t n, int64_t k
 
 // Row bands of the emulated pipeline, on whole 128-row tiles: at most kMaxBands,
 // each with at least kMinWaves waves of output tiles over the SMs (every band is
-// one products launch, whose last wave is partly idle).
+// one products launch or a few, the last wave of each partly idle).
 constexpr int kMaxBands = 4;
 constexpr int kMinWaves = 8;
-static_assert(1 + 2 + kMaxBands + (kMaxBands + 1) <= kAuxEvents, "events of the pipeline");
+constexpr int kMaxBBlocks = 6;                       // column blocks of B (first band)
+constexpr int kMaxPieces = kMaxBBlocks + kMaxBands;  // products launches
+static_assert(1 + kMaxBBlocks + kMaxBands + kMaxPieces <= kAuxEvents, "events of the pipeline");
+
+// Planning estimates (they order the copies and size the launches; the result does
+// not depend on them): FP8 tensor-core flop of the slice products per SM and
+// second, and bytes per second of the host link in either direction.
+constexpr double kPlanSmFlops = 25e12;
+constexpr double kPlanLinkBytes = 180e9;
 
 int band_count(int64_t tile_rows, int64_t tile_cols, int sms) {
     int64_t nb = tile_rows * tile_cols / ((int64_t)kMinWaves * sms);
@@ -80,23 +90,126 @@ void band_rows(int64_t m, int nb, int i, int64_t* r0, int64_t* r1) {
 
 // Idle tile slots of a launch of `tiles` tiles in its last wave over `sms` SMs.
 int64_t tail_slots(int64_t tiles, int sms) { return (tiles + sms - 1) / sms * sms - tiles; }
+int64_t waves(int64_t tiles, int sms) { return (tiles + sms - 1) / sms; }
+int64_t gcd64(int64_t a, int64_t b) { return b ? gcd64(b, a % b) : a; }
 
-// The first row band (R tile rows) runs as two launches, over tile columns [0, c)
-// and [c, T), so its products start once the first c tile columns of B have
-// arrived.  c lies in [0.4 T, 0.5 T] (the second part of B must arrive while the
-// first block computes) and leaves the fewest idle slots in the two last waves
-// (n = 8192, s = 10: c = 76 of 171, 8 and 10 full waves).  0: no split.
-int64_t first_band_split(int nb, int64_t R, int64_t T, int sms) {
-    if (nb < 2 || T < 16) return 0;
-    int64_t best = 0, best_idle = 0;
-    for (int64_t c = (4 * T + 9) / 10; c <= T / 2; ++c) {
-        const int64_t idle = tail_slots(R * c, sms) + tail_slots(R * (T - c), sms);
-        if (best == 0 || idle < best_idle) {
+// The launches of one host-buffer GEMM, in enqueue order.  Band 0 runs one launch
+// per column block of B (B arrives block by block, the first small); bands
+// 1 .. nb-2 one launch each; the last band two when that hides the copy-back of
+// its first part under the second.
+struct Piece {
+    int64_t r0, r1, c0, c1;  // rows of A / C, columns of B / C
+    int band, bblock;        // row band; column block of B (band 0), else -1
+};
+struct HostSchedule {
+    int nb = 1;     // row bands of A (and C)
+    int nbb = 1;    // column blocks of B, = launches of band 0
+    int64_t bcut[kMaxBBlocks + 1] = {};  // column edges of the blocks of B
+    int np = 0;
+    Piece piece[kMaxPieces] = {};
+};
+
+// Column blocks of B for band 0 (R tile rows, T tile columns; cut[] in tile
+// columns).  Blocks are whole waves of band 0 where the wave quantum allows: the
+// first is one quantum (so the products start after a small part of B), each next
+// the largest number of quanta whose copy ends before the previous block's
+// products do (t_col per tile column of B, t_tile per tile and SM, t_head for the
+// copies that precede the first launch), the last takes the remaining columns.
+// Without a usable quantum: two blocks, [0, c) and [c, T), c in [0.4 T, 0.5 T]
+// leaving the fewest idle slots.
+int b_blocks(int nb, int64_t R, int64_t T, int sms, double t_tile, double t_col,
+             double t_head, int64_t* cut) {
+    cut[0] = 0;
+    if (nb < 2 || T < 16) {
+        cut[1] = T;
+        return 1;
+    }
+    const int64_t q = sms / gcd64(R, (int64_t)sms);  // tile columns per whole wave count
+    if (3 * q > T) {
+        int64_t best = 0, best_idle = 0;
+        for (int64_t c = (4 * T + 9) / 10; c <= T / 2; ++c) {
+            const int64_t idle = tail_slots(R * c, sms) + tail_slots(R * (T - c), sms);
+            if (best == 0 || idle < best_idle) {
+                best = c;
+                best_idle = idle;
+            }
+        }
+        cut[1] = best;
+        cut[2] = T;
+        return 2;
+    }
+    int n = 0;
+    int64_t c = q, used = q;
+    double link = t_head + (double)c * t_col;  // B's block 0 and A's band 0 are in
+    double gpu = link;                          // the first launch starts
+    cut[++n] = used;
+    while (used < T && n < kMaxBBlocks - 1) {
+        const double gpu_end = gpu + (double)waves(R * c, sms) * t_tile;
+        const int64_t cmax = (int64_t)((gpu_end - link) / t_col);
+        c = cmax / q * q;
+        if (c < q) c = q;
+        if (T - used - c < q) c = T - used;  // no room for a further whole block
+        link += (double)c * t_col;
+        gpu = gpu_end > link ? gpu_end : link;
+        used += c;
+        cut[++n] = used;
+    }
+    if (used < T) cut[++n] = T;
+    return n;
+}
+
+// First tile column of the last band's second launch (R tile rows): the split
+// whose first part's copy back runs under the second part's products and saves
+// the most time after the last launch, net of the waves the second launch adds;
+// T (one launch) when no split saves time.
+int64_t last_band_split(int64_t R, int64_t rows, int64_t T, int bn, int sms, double t_tile) {
+    if (T < 16) return T;
+    int64_t best = T;
+    double best_gain = 0.0;
+    for (int64_t c = T - 1; 2 * c >= T; --c) {
+        const double back = 8.0 * (double)rows * (double)(c * bn) / kPlanLinkBytes;
+        if (back > (double)waves(R * (T - c), sms) * t_tile) continue;
+        const int64_t extra = waves(R * c, sms) + waves(R * (T - c), sms) - waves(R * T, sms);
+        const double gain = back - (double)extra * t_tile;
+        if (gain > best_gain) {
             best = c;
-            best_idle = idle;
+            best_gain = gain;
         }
     }
     return best;
+}
+
+HostSchedule host_schedule(int s, int64_t m, int64_t n, int64_t k, bool reads_c, int sms) {
+    HostSchedule h;
+    const EmuLayout lay = emu_layout(s, m, n, k);
+    const int bn = lay.bn;
+    const int64_t tile_rows = (m + kEmuBM - 1) / kEmuBM, tile_cols = (n + bn - 1) / bn;
+    h.nb = band_count(tile_rows, tile_cols, sms);
+    const double t_tile =
+        (double)s * (s + 1) * kEmuBM * bn * (double)lay.kp / kPlanSmFlops;  // s(s+1)/2 pairs
+    const double t_col = 8.0 * (double)k * bn / kPlanLinkBytes;
+    int64_t r0, r1;
+    band_rows(m, h.nb, 0, &r0, &r1);
+    const double t_head = 8.0 * (double)(r1 - r0) * (double)(k + (reads_c ? n : 0)) / kPlanLinkBytes;
+    int64_t cut[kMaxBBlocks + 1];
+    h.nbb = b_blocks(h.nb, (r1 - r0 + kEmuBM - 1) / kEmuBM, tile_cols, sms, t_tile, t_col,
+                     t_head, cut);
+    for (int j = 0; j <= h.nbb; ++j) h.bcut[j] = cut[j] * bn < n ? cut[j] * bn : n;
+    for (int j = 0; j < h.nbb; ++j) h.piece[h.np++] = Piece{r0, r1, h.bcut[j], h.bcut[j + 1], 0, j};
+    for (int i = 1; i < h.nb; ++i) {
+        band_rows(m, h.nb, i, &r0, &r1);
+        const int64_t c = i + 1 == h.nb
+                              ? last_band_split((r1 - r0 + kEmuBM - 1) / kEmuBM, r1 - r0,
+                                                tile_cols, bn, sms, t_tile) * bn
+                              : n;
+        if (c < n) {
+            h.piece[h.np++] = Piece{r0, r1, 0, c, i, -1};
+            h.piece[h.np++] = Piece{r0, r1, c, n, i, -1};
+        } else {
+            h.piece[h.np++] = Piece{r0, r1, 0, n, i, -1};
+        }
+    }
+    return h;
 }
 
 cudaError_t copy_rows(void* dst, size_t dpitch, const void* src, size_t spitch,
@@ -154,6 +267,38 @@ gb_status gb_dgemm_host_workspace_size(gb_precision prec, int slices, int64_t m,
         return GB_ERR_INVALID_ARG;
     }
     *out = host_layout(prec, s, m, n, k).total;
+    return GB_OK;
+}
+
+gb_status gb_dgemm_host_schedule(int slices, int64_t m, int64_t n, int64_t k, double beta,
+                                 int sm_count, int64_t* pieces, int max_pieces, int* count) {
+    if (!count || (max_pieces > 0 && !pieces)) {
+        set_error("count is NULL, or pieces is NULL with max_pieces > 0");
+        return GB_ERR_INVALID_ARG;
+    }
+    *count = 0;
+    if (m < 0 || n < 0 || k < 0 || sm_count < 1) {
+        set_error("m, n, k must be >= 0 and sm_count >= 1");
+        return GB_ERR_INVALID_ARG;
+    }
+    const int s = slices == 0 ? 11 : slices;
+    if (s < 1 || s > 16) {
+        set_error("slices must be in [1, 16] (or 0 for the default), got %d", slices);
+        return GB_ERR_INVALID_ARG;
+    }
+    if (m == 0 || n == 0 || k == 0) return GB_OK;
+    const HostSchedule sch = host_schedule(s, m, n, k, beta != 0.0, sm_count);
+    *count = sch.np;
+    if (max_pieces < sch.np) {
+        set_error("%d launches do not fit max_pieces = %d", sch.np, max_pieces);
+        return GB_ERR_INVALID_ARG;
+    }
+    for (int p = 0; p < sch.np; ++p) {
+        pieces[4 * p + 0] = sch.piece[p].r0;
+        pieces[4 * p + 1] = sch.piece[p].r1;
+        pieces[4 * p + 2] = sch.piece[p].c0;
+        pieces[4 * p + 3] = sch.piece[p].c1;
+    }
     return GB_OK;
 }
 
@@ -233,30 +378,19 @@ gb_status gb_dgemm_host(gb_queue* q, gb_precision prec, int slices, int64_t m, i
     const EmuLayout lay = emu_layout(s, m, n, k);
     int32_t* ea = reinterpret_cast<int32_t*>(ws + lay.a_exp);
     int32_t* fb = reinterpret_cast<int32_t*>(ws + lay.b_exp);
-    const int bn = lay.bn;
-    const int64_t tile_rows = (m + kEmuBM - 1) / kEmuBM, tile_cols = (n + bn - 1) / bn;
-    const int nb = band_count(tile_rows, tile_cols, q->dev->sm_count);
-    int64_t fr0, fr1;
-    band_rows(m, nb, 0, &fr0, &fr1);
-    const int64_t csplit_tiles =
-        first_band_split(nb, (fr1 - fr0 + kEmuBM - 1) / kEmuBM, tile_cols, q->dev->sm_count);
-    // column blocks of B: [0, csplit) and [csplit, n), or one block
-    const int64_t csplit = csplit_tiles > 0 ? csplit_tiles * bn : n;
-    const int ncb = csplit < n ? 2 : 1;
-    const int64_t cb0[2] = {0, csplit}, cb1[2] = {csplit, n};
-    // events: [1, 3) column blocks of B in, [3, 3 + nb) row bands of A (and C) in,
-    // [3 + nb, ...) one per products launch
-    cudaEvent_t* ev_b = ev + 1;
-    cudaEvent_t* ev_a = ev + 3;
-    cudaEvent_t* ev_p = ev + 3 + nb;
+    const HostSchedule sch = host_schedule(s, m, n, k, reads_c, q->dev->sm_count);
+    cudaEvent_t* ev_b = ev + 1;                // column blocks of B in
+    cudaEvent_t* ev_a = ev + 1 + kMaxBBlocks;  // row bands of A (and C) in
+    cudaEvent_t* ev_p = ev_a + kMaxBands;      // products launches done
     auto copy_b = [&](int j) {
-        cudaError_t r = copy_rows(dB + cb0[j], 8 * (size_t)n, B + cb0[j], 8 * (size_t)ldb,
-                                  cb1[j] - cb0[j], k, cudaMemcpyHostToDevice, hs);
+        const int64_t c0 = sch.bcut[j], c1 = sch.bcut[j + 1];
+        cudaError_t r = copy_rows(dB + c0, 8 * (size_t)n, B + c0, 8 * (size_t)ldb, c1 - c0, k,
+                                  cudaMemcpyHostToDevice, hs);
         return r == cudaSuccess ? cudaEventRecord(ev_b[j], hs) : r;
     };
     auto copy_a = [&](int i) {
         int64_t r0, r1;
-        band_rows(m, nb, i, &r0, &r1);
+        band_rows(m, sch.nb, i, &r0, &r1);
         cudaError_t r = copy_rows(dA + r0 * kk, 8 * (size_t)kk, A + r0 * lda, 8 * (size_t)lda, k,
                                   r1 - r0, cudaMemcpyHostToDevice, hs);
         if (r == cudaSuccess && reads_c)
@@ -265,55 +399,54 @@ gb_status gb_dgemm_host(gb_queue* q, gb_precision prec, int slices, int64_t m, i
         return r == cudaSuccess ? cudaEventRecord(ev_a[i], hs) : r;
     };
     // h2d in the order the launches need it: B's first column block, A's first row
-    // band, the rest of B, A's other row bands (each with C's rows)
+    // band, B's other blocks, A's other row bands (each with C's rows)
     if (e == cudaSuccess) e = copy_b(0);
     if (e == cudaSuccess) e = copy_a(0);
-    if (ncb == 2 && e == cudaSuccess) e = copy_b(1);
-    for (int i = 1; i < nb && e == cudaSuccess; ++i) e = copy_a(i);
-    // queue: per row band the split of its rows of A, then its products (the first
-    // band in two column blocks, each block of B split just before its first use);
-    // d2h: each block of C as soon as it is computed.  Band edges sit on tile
-    // edges (128 rows, bn columns), so a band's digit tiles start r0 * kp * s
-    // (c0 * kp * s) bytes into the planes.
-    int launch = 0;
-    auto products = [&](int64_t r0, int64_t r1, int64_t c0, int64_t c1) {
-        const size_t aoff = (size_t)r0 * (size_t)lay.kp * (size_t)s;
-        const size_t boff = (size_t)c0 * (size_t)lay.kp * (size_t)s;
-        cudaError_t r = launch_emu_products(L, s, r1 - r0, c1 - c0, k, alpha, beta,
-                                            dC + r0 * n + c0, n, ws + lay.a_digits + aoff,
-                                            ws + lay.b_digits + boff, lay.kp, ea + r0, fb + c0);
-        cudaEvent_t done = ev_p[launch++];
-        if (r == cudaSuccess) r = cudaEventRecord(done, qs);
-        if (r == cudaSuccess) r = cudaStreamWaitEvent(ds, done, 0);
-        if (r == cudaSuccess)
-            r = copy_rows(C + r0 * ldc + c0, 8 * (size_t)ldc, dC + r0 * n + c0, 8 * (size_t)n,
-                          c1 - c0, r1 - r0, cudaMemcpyDeviceToHost, ds);
-        return r;
-    };
+    for (int j = 1; j < sch.nbb && e == cudaSuccess; ++j) e = copy_b(j);
+    for (int i = 1; i < sch.nb && e == cudaSuccess; ++i) e = copy_a(i);
+    // queue: each block of B split as it arrives, each band of A split before its
+    // first launch, then the launches in schedule order; d2h: each block of C as soon
+    // as it is computed.  Band and block edges sit on tile edges (128 rows, bn
+    // columns), so a piece's digit tiles start r0 * kp * s (c0 * kp * s) bytes into
+    // the planes.
     auto split_b = [&](int j) {
-        const size_t boff = (size_t)cb0[j] * (size_t)lay.kp * (size_t)s;
+        const int64_t c0 = sch.bcut[j], c1 = sch.bcut[j + 1];
+        const size_t boff = (size_t)c0 * (size_t)lay.kp * (size_t)s;
         cudaError_t r = cudaStreamWaitEvent(qs, ev_b[j], 0);
         if (r == cudaSuccess)
-            r = launch_split_cols(L, s, cb1[j] - cb0[j], k, dB + cb0[j], n,
-                                  ws + lay.b_digits + boff, lay.kp, fb + cb0[j]);
+            r = launch_split_cols(L, s, c1 - c0, k, dB + c0, n, ws + lay.b_digits + boff, lay.kp,
+                                  fb + c0);
         return r;
     };
-    for (int i = 0; i < nb && e == cudaSuccess; ++i) {
+    auto split_a = [&](int i) {
         int64_t r0, r1;
-        band_rows(m, nb, i, &r0, &r1);
+        band_rows(m, sch.nb, i, &r0, &r1);
         const size_t aoff = (size_t)r0 * (size_t)lay.kp * (size_t)s;
-        e = cudaStreamWaitEvent(qs, ev_a[i], 0);
-        if (e == cudaSuccess)
-            e = launch_split_rows(L, s, r1 - r0, k, dA + r0 * kk, kk, ws + lay.a_digits + aoff,
+        cudaError_t r = cudaStreamWaitEvent(qs, ev_a[i], 0);
+        if (r == cudaSuccess)
+            r = launch_split_rows(L, s, r1 - r0, k, dA + r0 * kk, kk, ws + lay.a_digits + aoff,
                                   lay.kp, ea + r0);
-        if (i == 0) {
-            for (int j = 0; j < ncb && e == cudaSuccess; ++j) {
-                e = split_b(j);
-                if (e == cudaSuccess) e = products(r0, r1, cb0[j], cb1[j]);
-            }
-        } else if (e == cudaSuccess) {
-            e = products(r0, r1, 0, n);
+        return r;
+    };
+    int band = -1;
+    for (int p = 0; p < sch.np && e == cudaSuccess; ++p) {
+        const Piece& pc = sch.piece[p];
+        if (pc.bblock >= 0) e = split_b(pc.bblock);
+        if (e == cudaSuccess && pc.band != band) {
+            band = pc.band;
+            e = split_a(band);
         }
+        if (e != cudaSuccess) break;
+        const size_t aoff = (size_t)pc.r0 * (size_t)lay.kp * (size_t)s;
+        const size_t boff = (size_t)pc.c0 * (size_t)lay.kp * (size_t)s;
+        e = launch_emu_products(L, s, pc.r1 - pc.r0, pc.c1 - pc.c0, k, alpha, beta,
+                                dC + pc.r0 * n + pc.c0, n, ws + lay.a_digits + aoff,
+                                ws + lay.b_digits + boff, lay.kp, ea + pc.r0, fb + pc.c0);
+        if (e == cudaSuccess) e = cudaEventRecord(ev_p[p], qs);
+        if (e == cudaSuccess) e = cudaStreamWaitEvent(ds, ev_p[p], 0);
+        if (e == cudaSuccess)
+            e = copy_rows(C + pc.r0 * ldc + pc.c0, 8 * (size_t)ldc, dC + pc.r0 * n + pc.c0,
+                          8 * (size_t)n, pc.c1 - pc.c0, pc.r1 - pc.r0, cudaMemcpyDeviceToHost, ds);
     }
     // the queue completes when C is back in host memory
     if (e == cudaSuccess) e = cudaEventRecord(ev[0], ds);

@@ -171,6 +171,17 @@ def host_workspace_size(precision: str, slices: int, m: int, n: int, k: int) -> 
     return out.value
 
 
+def host_schedule(slices: int, m: int, n: int, k: int, beta: float = 0.0, *,
+                  sm_count: int) -> list:
+    """The products launches of dgemm_host (emulated) on a device with `sm_count`
+    SMs, in enqueue order: a list of (row0, row1, col0, col1) blocks of C."""
+    buf = (ctypes.c_int64 * 40)()
+    count = ctypes.c_int()
+    check(_lib.load().gb_dgemm_host_schedule(slices, m, n, k, beta, sm_count, buf, 10,
+                                             ctypes.byref(count)), "gb_dgemm_host_schedule")
+    return [tuple(buf[4 * p:4 * p + 4]) for p in range(count.value)]
+
+
 def _host_matrix_args(t, name):
     import torch
     if t.dtype != torch.float64 or t.is_cuda or t.dim() != 2:

@@ -3,8 +3,8 @@ pinned host memory, copied in bands and overlapped with the computation.
 
 Each result equals, bit for bit, the same GEMM on device copies through gb_dgemm
 (the same kernels on the same data; the band split of the emulated path only
-changes which launch computes an output), for 1, 2 and 4 row bands (the first
-one in two column blocks), leading
+changes which launch computes an output), for 1, 2, 3 and 4 row bands (the first
+one in up to four column blocks of B, the last in one or two launches), leading
 dimensions wider than the rows, beta = 0 and beta != 0, two calls in a row on
 one workspace, and the native precision.
 """
@@ -49,7 +49,9 @@ def device_reference(gb, A, B, C0, alpha, beta, precision, s):
                                               (2100, 300, 257, 10, 0.5, 3),
                                               (4500, 97, 129, 12, -1.0, 1),
                                               (8192, 2048, 32, 10, 0.5, 1),   # 2 bands, split
-                                              (8100, 4090, 24, 11, 0.0, 0)])  # 4 bands, split
+                                              (8100, 4090, 24, 11, 0.0, 0),   # 4 bands, 3 blocks
+                                              (6144, 4096, 96, 10, 0.0, 2),   # 4 blocks of B
+                                              (4096, 4096, 4096, 10, 0.5, 0)])  # last band split
 def test_emulated_host_buffers_match_device_gemm(gb, m, n, k, s, beta, pad):
     import torch
     seed = 8100 + m
