@@ -36,7 +36,7 @@ FP64_FLOP_PER_CLK_SM = 4.0
 # DRAM bytes (read + write) per launch of the dominant kernel, from one ncu
 # capture of the kernel as it is now (profiles/emu_products_kernel_n8192_s10.md):
 # (kernel, n, slices) -> bytes.  Reported only for that exact workload.
-MEASURED_TRAFFIC = {("emu_products_kernel", 8192, 10): 9575040512 + 537436928}
+MEASURED_TRAFFIC = {("emu_products_kernel", 8192, 10): 9571116800 + 538921472}
 
 
 def parse():
@@ -60,6 +60,8 @@ def parse():
     p.add_argument("--serve-budget-gb", type=float, default=40.0)
     p.add_argument("--serve-streams", type=int, default=4)
     p.add_argument("--serve-batch", type=int, default=64)
+    p.add_argument("--no-serve-baseline", action="store_true",
+                   help="skip the one-GEMM-per-launch run of the same serving trace")
     return p.parse_args()
 
 
@@ -370,47 +372,34 @@ def run_grouped(args):
     return 0
 
 
-def run_serve(args):
-    """Poisson arrivals of square GEMMs, n log-uniform in [64, 4096], 20% emulated,
-    HBM-budget admission, continuous batching; p50/p99 latency and TFLOP/s."""
-    import numpy as np
-    import torch
-
-    import paper_1602_08477_gb300 as gb
-    from paper_1602_08477_gb300 import autotune
-    from synth import generators as g
-    torch.cuda.set_device(0)
-    gb.build()
-    try:
-        autotune.load()
-    except Exception:
-        pass
+def _serve_trace(args, gb, g, np, max_batch):
+    """One run of the arrival trace through a server with batches of at most
+    `max_batch` requests (1: every GEMM its own launch).  Returns the stats."""
     seed = g.BASE_SEED + 4
     count = int(args.serve_rate * args.serve_seconds * 1.2) + 16
     gaps = g.poisson_gaps_ms(seed, count, args.serve_rate) * 1e-3
     arrivals = np.cumsum(gaps)
     sizes = g.log_uniform_ints(seed, 21, count, 64, 4096)
     emulated = (g.raw_stream(seed, 22, count) % np.uint64(5)) == 0
-    s = 12
+    s = SERVE_SLICES
     srv = gb.Server(int(args.serve_budget_gb * 2 ** 30), n_streams=args.serve_streams,
-                    max_batch=args.serve_batch)
-    # warm the kernels on a few small requests (not counted)
-    for i in range(4):
-        srv.submit(64, 64, 64, precision="emulated" if i % 2 else "native", slices=s, seed=i)
-    srv.drain(60)
-    srv.close()
-    srv = gb.Server(int(args.serve_budget_gb * 2 ** 30), n_streams=args.serve_streams,
-                    max_batch=args.serve_batch)
+                    max_batch=max_batch)
     clocks = ClockSampler(0)
     clocks.start()
     t0 = time.perf_counter()
-    submitted, native_flops, emu_flops, offered = 0, 0.0, 0.0, 0.0
+    submitted, offered = 0, 0.0
     ids = []
+    queue_trace = []  # (seconds, queued, on the device) every half second
+    next_sample = 0.0
     for i in range(count):
         t = arrivals[i]
         if t > args.serve_seconds:
             break
         now = time.perf_counter() - t0
+        if now >= next_sample:
+            q = srv.stats()
+            queue_trace.append((round(now, 2), int(q["pending"]), int(q["in_flight"])))
+            next_sample += 0.5
         if t > now:
             time.sleep(t - now)
         n = int(sizes[i])
@@ -436,33 +425,85 @@ def run_serve(args):
     # roofline time of the work completed: native flops on the FP64 pipe, emulated
     # pair products on the FP8 tensor pipe
     bound_s = done_native / fp64_peak + done_emu * s * (s + 1) / 2 / fp8_peak
-    busy = max(st["busy_s"], 1e-9)
+    st["roofline_frac"] = bound_s / max(st["busy_s"], 1e-9)
+    st["offered_tflops"] = offered / max(wall, 1e-9) / 1e12
+    st["submit_wall_s"] = wall
+    st["clocks"] = clk
+    st["submitted_here"] = submitted
+    st["queue_trace"] = queue_trace
+    return st
+
+
+def _serve_summary(st):
+    return {"p50_ms": round(st["p50_ms"], 3), "p99_ms": round(st["p99_ms"], 3),
+            "max_ms": round(st["max_ms"], 3), "tflops": round(st["tflops"], 4),
+            "submitted": st["submitted"], "completed": st["completed"],
+            "pending_at_end": st["pending"], "in_flight_at_end": st["in_flight"],
+            "max_queue": st["max_queue"], "batches": st["batches"],
+            "mean_batch": round(st["mean_batch"], 2),
+            "peak_arena_gb": round(st["peak_bytes"] / 2 ** 30, 3),
+            "roofline_frac": round(st["roofline_frac"], 4)}
+
+
+SERVE_SLICES = 12
+
+
+def run_serve(args):
+    """Poisson arrivals of square GEMMs, n log-uniform in [64, 4096], 20% emulated,
+    HBM-budget admission, continuous batching; p50/p99 latency and TFLOP/s, beside
+    the same trace served one GEMM per launch."""
+    import numpy as np
+    import torch
+
+    import paper_1602_08477_gb300 as gb
+    from paper_1602_08477_gb300 import autotune
+    from synth import generators as g
+    torch.cuda.set_device(0)
+    gb.build()
+    try:
+        autotune.load()
+    except Exception:
+        pass
+    s = SERVE_SLICES
+    # warm the kernels on a few small requests (not counted)
+    srv = gb.Server(int(args.serve_budget_gb * 2 ** 30), n_streams=args.serve_streams,
+                    max_batch=args.serve_batch)
+    for i in range(4):
+        srv.submit(64, 64, 64, precision="emulated" if i % 2 else "native", slices=s, seed=i)
+    srv.drain(60)
+    srv.close()
+    st = _serve_trace(args, gb, g, np, args.serve_batch)
+    single = None if args.no_serve_baseline else _serve_trace(args, gb, g, np, 1)
+    serve = _serve_summary(st)
+    serve["offered_tflops"] = round(st["offered_tflops"], 3)
+    serve["submit_wall_s"] = round(st["submit_wall_s"], 2)
+    # queue length over time: [seconds, queued, on the device] at up to 21 points
+    tr = st["queue_trace"]
+    pick = sorted(set(np.linspace(0, len(tr) - 1, min(21, len(tr))).astype(int).tolist())) if tr else []
+    serve["queue_over_time"] = [list(tr[i]) for i in pick]
     out = {
         "metric": "serving FP64 GEMM p50/p99 latency (ms) and TFLOP/s",
         "value": round(st["tflops"], 4), "unit": "TFLOP/s", "n_gpus": 1,
-        "steps": int(submitted), "warmup": 4, "ms_per_step": round(st["mean_ms"], 3),
+        "steps": int(st["submitted_here"]), "warmup": 4, "ms_per_step": round(st["mean_ms"], 3),
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
         "data": "synthetic (device splitmix64 per request seed, uniform[-1,1])",
         "config": {"workload": f"Poisson arrivals {args.serve_rate:g}/s for "
                                f"{args.serve_seconds:g} s, square n log-uniform in [64, 4096], "
                                f"20% emulated (s = {s}), {args.serve_budget_gb:g} GB budget",
                    "streams": args.serve_streams, "max_batch": args.serve_batch},
-        "serve": {"p50_ms": round(st["p50_ms"], 3), "p99_ms": round(st["p99_ms"], 3),
-                  "max_ms": round(st["max_ms"], 3), "submitted": st["submitted"],
-                  "completed": st["completed"], "pending_at_end": st["pending"],
-                  "in_flight_at_end": st["in_flight"], "max_queue": st["max_queue"],
-                  "batches": st["batches"], "mean_batch": round(st["mean_batch"], 2),
-                  "peak_arena_gb": round(st["peak_bytes"] / 2 ** 30, 3),
-                  "offered_tflops": round(offered / max(wall, 1e-9) / 1e12, 3),
-                  "submit_wall_s": round(wall, 2)},
-        "roofline": {"bound": "mixed", "frac": round(bound_s / busy, 4),
+        "serve": serve,
+        "roofline": {"bound": "mixed", "frac": round(st["roofline_frac"], 4),
                      "note": "roofline time of the completed work (native on the FP64 pipe, "
                              "emulated pair products on the FP8 tensor pipe) / busy time"},
         "gpu_launches": int(st["batches"]) * 5,
         "e2e": {"value": round(st["tflops"], 4), "unit": "TFLOP/s", "h2d_bytes_per_step": 0,
                 "d2h_bytes_per_step": 0, "note": "operands generated on the device per request"},
-        "clocks": clk,
+        "clocks": st["clocks"],
     }
+    if single is not None:
+        out["one_launch_per_gemm"] = dict(_serve_summary(single),
+                                          note="same arrival trace, batches of one request: "
+                                               "every GEMM its own launch")
     print(json.dumps(out), flush=True)
     return 0
 

@@ -173,7 +173,7 @@ def test_workspace_errors(gb):
         gb.dgemm(dA, dB, dC, precision="emulated", slices=17)
 
 
-@pytest.mark.parametrize("n,s", [(4096, 10), (8192, 11)])
+@pytest.mark.parametrize("n,s", [(4096, 10), (8192, 10), (8192, 11)])
 def test_full_size_sampled_rows(gb, n, s):
     # square sizes of the emulated workload: 8 sampled rows against the model
     # (bit-exact) and against the double-double reference (FP64 bound)

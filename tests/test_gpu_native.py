@@ -191,7 +191,7 @@ def test_blocking_queue_returns_after_work(gb):
     q.close()
 
 
-@pytest.mark.parametrize("n", [1024, 4096])
+@pytest.mark.parametrize("n", [1024, 4096, 8192, 10240])
 def test_sweep_sizes_sampled_rows(gb, n):
     # full-size sweep points of the square DGEMM (alpha = 1, beta = 0): the
     # outputs of 12 sampled rows against the oracle computed row by row

@@ -44,7 +44,9 @@ def _requests(count, seed):
 
 
 def test_results_alone_equal_results_in_the_mix(gb):
-    reqs = _requests(48, 5500)
+    # 200 requests: the serving spot-check count, each compared alone, in the mix
+    # and against the oracle
+    reqs = _requests(200, 5500)
     # in the mix: all submitted at once to a server with small batches and a
     # budget that forces admission waits
     mix = gb.Server(hbm_budget_bytes=64 << 20, n_streams=3, max_batch=8)
@@ -72,10 +74,9 @@ def test_results_alone_equal_results_in_the_mix(gb):
         solo.close()
         assert np.array_equal(alone, out)
         # and within the FP64 bound of the oracle
-        ref = cgemm.dgemm(r["alpha"], r["A"], r["B"], r["beta"], r["C"].copy())
-        bound = exact.error_bound(r["k"], r["alpha"], cgemm.dgemm(1.0, np.abs(r["A"]),
-                                                                   np.abs(r["B"])),
-                                  r["beta"], r["C"])
+        ref, _ = cgemm.dgemm_omp(r["alpha"], r["A"], r["B"], r["beta"], r["C"].copy())
+        absab, _ = cgemm.dgemm_omp(1.0, np.abs(r["A"]), np.abs(r["B"]))
+        bound = exact.error_bound(r["k"], r["alpha"], absab, r["beta"], r["C"])
         assert np.all(np.abs(out - ref) <= 2 * bound)
 
 
