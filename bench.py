@@ -372,9 +372,10 @@ def run_grouped(args):
     return 0
 
 
-def _serve_trace(args, gb, g, np, max_batch):
+def _serve_trace(args, gb, g, np, max_batch, policy="lanes"):
     """One run of the arrival trace through a server with batches of at most
-    `max_batch` requests (1: every GEMM its own launch).  Returns the stats."""
+    `max_batch` requests under `policy` ("fifo" with max_batch = 1: every GEMM
+    its own launch, in arrival order).  Returns the stats."""
     seed = g.BASE_SEED + 4
     count = int(args.serve_rate * args.serve_seconds * 1.2) + 16
     gaps = g.poisson_gaps_ms(seed, count, args.serve_rate) * 1e-3
@@ -383,7 +384,7 @@ def _serve_trace(args, gb, g, np, max_batch):
     emulated = (g.raw_stream(seed, 22, count) % np.uint64(5)) == 0
     s = SERVE_SLICES
     srv = gb.Server(int(args.serve_budget_gb * 2 ** 30), n_streams=args.serve_streams,
-                    max_batch=max_batch)
+                    max_batch=max_batch, policy=policy)
     clocks = ClockSampler(0)
     clocks.start()
     t0 = time.perf_counter()
@@ -411,9 +412,14 @@ def _serve_trace(args, gb, g, np, max_batch):
     st = srv.stats()
     clk = clocks.stop()
     done_native = done_emu = 0.0
+    lane_lat = {"small": [], "large": []}
+    lane_count = {"small": 0, "large": 0}
     for rid, n, prec in ids:
         done, status, lat = srv.poll(rid)
+        lane = "large" if prec == "native" and 2.0 * n ** 3 >= 2.0 ** 31 else "small"
+        lane_count[lane] += 1
         if done and status == 0:
+            lane_lat[lane].append(lat)
             if prec == "native":
                 done_native += 2.0 * n ** 3
             else:
@@ -431,6 +437,13 @@ def _serve_trace(args, gb, g, np, max_batch):
     st["clocks"] = clk
     st["submitted_here"] = submitted
     st["queue_trace"] = queue_trace
+    # latency per class of request (the lanes' rule: native and 2 n^3 >= 2^31 is
+    # large), completed requests only, with how many of the class were submitted
+    st["by_class"] = {
+        c: {"submitted": lane_count[c], "completed": len(v),
+            "p50_ms": round(float(np.percentile(v, 50)), 3) if v else None,
+            "p99_ms": round(float(np.percentile(v, 99)), 3) if v else None}
+        for c, v in lane_lat.items()}
     return st
 
 
@@ -440,9 +453,9 @@ def _serve_summary(st):
             "submitted": st["submitted"], "completed": st["completed"],
             "pending_at_end": st["pending"], "in_flight_at_end": st["in_flight"],
             "max_queue": st["max_queue"], "batches": st["batches"],
-            "mean_batch": round(st["mean_batch"], 2),
+            "mean_batch": round(st["mean_batch"], 2), "large_launches": st["large_launches"],
             "peak_arena_gb": round(st["peak_bytes"] / 2 ** 30, 3),
-            "roofline_frac": round(st["roofline_frac"], 4)}
+            "roofline_frac": round(st["roofline_frac"], 4), "by_class": st["by_class"]}
 
 
 SERVE_SLICES = 12
@@ -473,7 +486,7 @@ def run_serve(args):
     srv.drain(60)
     srv.close()
     st = _serve_trace(args, gb, g, np, args.serve_batch)
-    single = None if args.no_serve_baseline else _serve_trace(args, gb, g, np, 1)
+    single = None if args.no_serve_baseline else _serve_trace(args, gb, g, np, 1, "fifo")
     serve = _serve_summary(st)
     serve["offered_tflops"] = round(st["offered_tflops"], 3)
     serve["submit_wall_s"] = round(st["submit_wall_s"], 2)
@@ -490,7 +503,9 @@ def run_serve(args):
         "config": {"workload": f"Poisson arrivals {args.serve_rate:g}/s for "
                                f"{args.serve_seconds:g} s, square n log-uniform in [64, 4096], "
                                f"20% emulated (s = {s}), {args.serve_budget_gb:g} GB budget",
-                   "streams": args.serve_streams, "max_batch": args.serve_batch},
+                   "streams": args.serve_streams, "max_batch": args.serve_batch,
+                   "policy": "lanes: native >= 2^31 flops alone on low-priority streams, "
+                             "the rest batched on high-priority streams"},
         "serve": serve,
         "roofline": {"bound": "mixed", "frac": round(st["roofline_frac"], 4),
                      "note": "roofline time of the completed work (native on the FP64 pipe, "
@@ -502,15 +517,16 @@ def run_serve(args):
     }
     if single is not None:
         out["one_launch_per_gemm"] = dict(_serve_summary(single),
-                                          note="same arrival trace, batches of one request: "
-                                               "every GEMM its own launch")
+                                          note="same arrival trace, one queue in arrival "
+                                               "order, every GEMM its own grouped launch")
     print(json.dumps(out), flush=True)
     return 0
 
 
 def run_sweep(args):
     """Native square DGEMM sweep n in {1024, ..., 10240}: naive vs tiled vs DFMA vs
-    DMMA kernels, TFLOP/s and fraction of the FP64 peak."""
+    DMMA kernels, TFLOP/s and fraction of the FP64 peak; the vendor library's FP64
+    GEMM (cuBLAS via torch.matmul) beside them as context."""
     import torch
 
     import paper_1602_08477_gb300 as gb
@@ -524,8 +540,12 @@ def run_sweep(args):
         C = torch.empty((n, n), dtype=torch.float64, device="cuda")
         gb.fill_uniform(A, 1602084771, 0)
         gb.fill_uniform(B, 1602084771, 1)
-        for kernel in ("naive", "tiled", "dfma", "dmma"):
-            f = lambda: gb.dgemm(A, B, C, kernel=kernel)
+        for kernel in ("naive", "tiled", "dfma", "dmma", "cublas"):
+            if kernel == "cublas":
+                # context only: the vendor library's FP64 GEMM through torch.matmul
+                f = lambda: torch.matmul(A, B, out=C)
+            else:
+                f = lambda: gb.dgemm(A, B, C, kernel=kernel)
             ms = _time_stream(torch, f, 1 if n >= 4096 else 3, 1)
             tf = 2.0 * n ** 3 / ms / 1e9
             res.append(dict(n=n, kernel=kernel, ms=round(ms, 3), tflops=round(tf, 4),

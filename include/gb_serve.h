@@ -5,15 +5,29 @@
  * Every request is one DGEMM of Section 4.2, C <- alpha A B + beta C, with the
  * conventions and accuracy contract of gb_gemm.h, in either precision.  The
  * server keeps operands resident in a device arena of a fixed HBM budget: a
- * request is admitted (first in, first out) once its operands (and, for the
- * emulated precision, its workspace) fit in the budget; admitted requests that
- * are ready are batched into one grouped launch (gb_grouped.h kernels) on one
- * of several streams, so batches overlap on the device; a batch's memory
- * returns to the budget when it completes, which admits the next requests.
+ * request is admitted (first in, first out within its lane) once its operands
+ * (and, for the emulated precision, its workspace) fit in the budget; admitted
+ * requests are launched on one of several streams, so their work overlaps on
+ * the device; a batch's memory returns to the budget when it completes, which
+ * admits the next requests.
  *
- * A request's result depends only on its own shape, precision and data (the
- * tile variant comes from its shape, no reduction spans problems), so it is
- * the same, bit for bit, alone and in any mix.
+ * Policies.  GB_SERVE_LANES (the default): a native request of at least 2^31
+ * flops (2 m n k; square n >= 1024) is large and runs alone, as an ordinary
+ * GEMM launch of many short CTAs, on a low-priority stream; every other request
+ * is small and is batched into grouped launches (gb_grouped.h kernels), up to
+ * max_batch requests and 2^33 flops of FP64-pipe work (emulated requests count
+ * 1/16 of theirs), on high-priority streams, so the CTA slots a large GEMM frees
+ * go to waiting small batches first, and no new large request starts while
+ * max_batch or more small requests are queued.  With n_streams >= 2, n_streams / 2 streams
+ * serve the large lane and the rest the small lane; a single stream serves both
+ * lanes, taking whichever head request arrived first.  GB_SERVE_FIFO: one queue,
+ * every batch a grouped launch of up to max_batch requests in arrival order
+ * (with max_batch = 1: one launch per GEMM).
+ *
+ * A request's kernels depend only on its own shape, precision and data and on
+ * the policy (the lane and the tile variant come from its shape, no reduction
+ * spans problems), so its result is the same, bit for bit, alone and in any mix
+ * under the same policy.
  *
  * Threading: submit/poll/stats may be called from any host thread; the server
  * runs one worker thread of its own.
@@ -54,12 +68,21 @@ typedef struct {
     int64_t batches;      /* grouped launches issued */
     double mean_batch;    /* requests per batch */
     size_t peak_bytes;    /* largest arena use */
+    int64_t large_launches;  /* large-lane requests launched (GB_SERVE_LANES) */
 } gb_server_stats;
 
+typedef enum { GB_SERVE_LANES = 0, GB_SERVE_FIFO = 1 } gb_serve_policy;
+
 /* hbm_budget_bytes: device arena (allocated once here);  n_streams: batches
- * in flight at once (1..16);  max_batch: requests per grouped launch (1..4096). */
+ * in flight at once (1..16);  max_batch: requests per grouped launch (1..4096).
+ * The GB_SERVE_LANES policy. */
 gb_status gb_server_create(gb_device* dev, size_t hbm_budget_bytes, int n_streams,
                            int max_batch, gb_server** out);
+
+/* As gb_server_create with an explicit policy (a gb_serve_policy value;
+ * GB_ERR_INVALID_ARG otherwise). */
+gb_status gb_server_create_ex(gb_device* dev, size_t hbm_budget_bytes, int n_streams,
+                              int max_batch, int policy, gb_server** out);
 
 /* Queue a request; returns at once with its id.  GB_ERR_OUT_OF_BUDGET when it
  * can never fit the budget; argument errors as gb_dgemm. */

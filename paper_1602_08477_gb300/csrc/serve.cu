@@ -1,6 +1,16 @@
 // GEMM request server (include/gb_serve.h): HBM-budget admission over a device
-// arena, FIFO queue, continuous batching into grouped launches on several
+// arena, FIFO queues, continuous batching into grouped launches on several
 // streams, and latency accounting.  All host logic runs on one worker thread.
+//
+// Lanes (the default policy): a native request of at least kLargeFlops is
+// "large" and runs alone as an ordinary GEMM launch (many short CTAs, no
+// persistent grid) on a low-priority stream; every other request is "small" and
+// is batched, up to a cost cap, into grouped launches on high-priority streams.
+// A persistent grouped kernel holds its SMs until its last tile, so a small
+// request batched with (or queued behind) a 100 ms GEMM waited for all of it;
+// with lanes the block scheduler hands each CTA slot that a large GEMM frees to
+// the pending small batch first.  The lane depends only on the request itself,
+// so its kernels, and its result, do not depend on the mix.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -102,8 +112,17 @@ class Arena {
     size_t total_ = 0, used_ = 0, peak_ = 0;
 };
 
+// Native requests of at least 2^31 flops (square n >= 1024, >= 1.7 ms on the whole
+// FP64 pipe) take the large lane; a small-lane batch stops growing at 2^33 flops
+// of FP64-pipe work (an emulated request counts 1/16 of its flops: its pair
+// products run on the tensor pipe).
+constexpr double kLargeFlops = 2147483648.0;
+constexpr double kBatchCost = 8589934592.0;
+
 struct Request {
     uint64_t id;
+    int lane = 0;     // 0 small (grouped batches), 1 large (alone, plain GEMM launch)
+    double cost = 0;  // FP64-pipe-equivalent flops
     gb_request r;
     size_t bytes;     // arena footprint
     size_t off = 0;   // arena offset
@@ -114,6 +133,7 @@ struct Request {
 };
 
 struct Slot {
+    int lane = -1;    // lane served; -1: either (a server with one stream)
     cudaStream_t stream = nullptr;
     cudaEvent_t done = nullptr;
     void* staging = nullptr;   // pinned host tables
@@ -141,13 +161,15 @@ struct gb_server {
     std::vector<gb::Slot> slots;
     std::mutex mu;
     std::condition_variable cv;
-    std::deque<gb::Request*> fifo;
+    int policy = GB_SERVE_LANES;
+    std::deque<gb::Request*> fifo[2];  // per lane (FIFO policy: lane 0 only)
     std::unordered_map<uint64_t, gb::Request*> all;
     std::atomic<bool> stop{false};
     std::thread worker;
     uint64_t next_id = 1;
     int64_t submitted = 0, completed = 0, rejected = 0, in_flight = 0, batches = 0, batched_reqs = 0;
     int64_t max_queue = 0;
+    int64_t large_launches = 0;
     double done_flops = 0;
     bool have_first = false;
     gb::Clock::time_point t_first, t_last;
@@ -183,20 +205,89 @@ void complete_batch(gb_server* S, Slot& sl) {
     S->cv.notify_all();
 }
 
-// Forms one batch from the FIFO head (first in, first out; stops at the first
-// request that does not fit the budget) and enqueues it on the slot's stream.
+// Lane a slot takes its next batch from: its own, or for a slot that serves
+// either lane, the lane whose head request arrived first.  -1: nothing queued.
+int pick_lane(gb_server* S, const Slot& sl) {
+    // a large-lane slot starts nothing new while a full small batch waits: the
+    // FP64 pipe goes to the short requests first (the GEMMs already running
+    // finish, their pending CTAs behind the small batches' in priority)
+    if (sl.lane == 1 && (int64_t)S->fifo[0].size() >= S->max_batch) return -1;
+    if (sl.lane >= 0) return S->fifo[sl.lane].empty() ? -1 : sl.lane;
+    if (S->fifo[0].empty()) return S->fifo[1].empty() ? -1 : 1;
+    if (S->fifo[1].empty()) return 0;
+    return S->fifo[1].front()->t_submit < S->fifo[0].front()->t_submit ? 1 : 0;
+}
+
+// Operands of a request in its arena block: copied from the host or generated.
+cudaError_t stage_operands(gb_server* S, const Request* rq, cudaStream_t st, double** pA,
+                           double** pB, double** pC, void** emu_ws) {
+    const gb_request& q = rq->r;
+    const int sms = S->dev->sm_count;
+    uint8_t* base = S->arena_base + rq->off;
+    double* A = reinterpret_cast<double*>(base);
+    double* B = A + q.m * q.k;
+    double* C = B + q.k * q.n;
+    size_t used = 8 * ((size_t)q.m * q.k + (size_t)q.k * q.n + (size_t)q.m * q.n);
+    *emu_ws = base + ((used + 1023) & ~(size_t)1023);
+    *pA = A;
+    *pB = B;
+    *pC = C;
+    cudaError_t e;
+    if (q.A_host) {
+        e = cudaMemcpyAsync(A, q.A_host, 8 * q.m * q.k, cudaMemcpyHostToDevice, st);
+        if (e == cudaSuccess)
+            e = cudaMemcpyAsync(B, q.B_host, 8 * q.k * q.n, cudaMemcpyHostToDevice, st);
+    } else {
+        e = fill_uniform(st, A, q.m, q.k, q.k, q.seed, 0, sms);
+        if (e == cudaSuccess) e = fill_uniform(st, B, q.k, q.n, q.n, q.seed, 1, sms);
+    }
+    if (e == cudaSuccess && q.beta != 0.0) {
+        if (q.C_host)
+            e = cudaMemcpyAsync(C, q.C_host, 8 * q.m * q.n, cudaMemcpyHostToDevice, st);
+        else if (!q.A_host)
+            e = fill_uniform(st, C, q.m, q.n, q.n, q.seed, 2, sms);
+        else
+            e = cudaMemsetAsync(C, 0, 8 * q.m * q.n, st);
+    }
+    return e;
+}
+
+// A large native request: one ordinary GEMM launch with the library's default
+// kernel for its size (16 x 16 shared-memory tiles up to 2048, 4 x 4 register
+// tiles above), whose many short CTAs leave their slots to higher-priority work.
+cudaError_t launch_large_native(const Launch& L, const gb_request& q, const double* A,
+                                const double* B, double* C) {
+    const Gemm g{q.m, q.n, q.k, q.alpha, q.beta, A, q.k > 0 ? q.k : 1, B, q.n > 0 ? q.n : 1,
+                 C, q.n > 0 ? q.n : 1};
+    if (q.m == 0 || q.n == 0) return cudaSuccess;
+    if (q.alpha == 0.0 || q.k == 0) return launch_scale(L, g);
+    const int64_t mn = q.m < q.n ? q.m : q.n;
+    return mn <= 2048 ? launch_tiled(L, g, 16) : launch_dfma(L, g, 4);
+}
+
+// Forms one batch from the head of the slot's lane (first in, first out; stops at
+// the first request that does not fit the budget) and enqueues it on the slot's
+// stream: a large request alone, small ones up to max_batch and the cost cap.
 bool launch_batch(gb_server* S, Slot& sl) {
     std::vector<Request*> batch;
+    int lane = -1;
     {
         std::lock_guard<std::mutex> lock(S->mu);
-        while (!S->fifo.empty() && (int)batch.size() < S->max_batch) {
-            Request* r = S->fifo.front();
+        lane = pick_lane(S, sl);
+        if (lane < 0) return false;
+        std::deque<Request*>& fifo = S->fifo[lane];
+        const int cap = lane == 1 ? 1 : S->max_batch;
+        double cost = 0;
+        while (!fifo.empty() && (int)batch.size() < cap) {
+            Request* r = fifo.front();
+            if (S->policy == GB_SERVE_LANES && !batch.empty() && cost + r->cost > kBatchCost) break;
             size_t off = 0;
             if (!S->arena.alloc(r->bytes, &off)) break;
             r->off = off;
             r->state = 1;
-            S->fifo.pop_front();
+            fifo.pop_front();
             batch.push_back(r);
+            cost += r->cost;
             ++S->in_flight;
         }
     }
@@ -204,30 +295,18 @@ bool launch_batch(gb_server* S, Slot& sl) {
     const int sms = S->dev->sm_count;
     std::vector<gb_gemm_desc> descs(batch.size());
     std::vector<void*> emu_ws(batch.size(), nullptr);
+    std::vector<double*> outC(batch.size(), nullptr);
     cudaError_t e = cudaSuccess;
+    gb_status st = GB_OK;
+    const Launch L{sl.stream, sl.status, sms};
     for (size_t i = 0; i < batch.size() && e == cudaSuccess; ++i) {
         const gb_request& q = batch[i]->r;
-        uint8_t* base = S->arena_base + batch[i]->off;
-        double* A = reinterpret_cast<double*>(base);
-        double* B = A + q.m * q.k;
-        double* C = B + q.k * q.n;
-        size_t used = 8 * ((size_t)q.m * q.k + (size_t)q.k * q.n + (size_t)q.m * q.n);
-        emu_ws[i] = base + ((used + 1023) & ~(size_t)1023);
-        if (q.A_host) {
-            e = cudaMemcpyAsync(A, q.A_host, 8 * q.m * q.k, cudaMemcpyHostToDevice, sl.stream);
-            if (e == cudaSuccess)
-                e = cudaMemcpyAsync(B, q.B_host, 8 * q.k * q.n, cudaMemcpyHostToDevice, sl.stream);
-        } else {
-            e = fill_uniform(sl.stream, A, q.m, q.k, q.k, q.seed, 0, sms);
-            if (e == cudaSuccess) e = fill_uniform(sl.stream, B, q.k, q.n, q.n, q.seed, 1, sms);
-        }
-        if (e == cudaSuccess && q.beta != 0.0) {
-            if (q.C_host)
-                e = cudaMemcpyAsync(C, q.C_host, 8 * q.m * q.n, cudaMemcpyHostToDevice, sl.stream);
-            else if (!q.A_host)
-                e = fill_uniform(sl.stream, C, q.m, q.n, q.n, q.seed, 2, sms);
-            else
-                e = cudaMemsetAsync(C, 0, 8 * q.m * q.n, sl.stream);
+        double *A, *B, *C;
+        e = stage_operands(S, batch[i], sl.stream, &A, &B, &C, &emu_ws[i]);
+        outC[i] = C;
+        if (lane == 1) {
+            if (e == cudaSuccess) e = launch_large_native(L, q, A, B, C);
+            continue;
         }
         gb_gemm_desc& d = descs[i];
         std::memset(&d, 0, sizeof(d));
@@ -246,9 +325,7 @@ bool launch_batch(gb_server* S, Slot& sl) {
         d.slices = q.slices;
         d.tile = GB_TILE_AUTO;
     }
-    gb_status st = GB_OK;
-    if (e == cudaSuccess) {
-        const Launch L{sl.stream, sl.status, sms};
+    if (e == cudaSuccess && lane == 0) {
         int64_t nl = 0;
         st = grouped_enqueue_async(L, descs.data(), (int64_t)descs.size(), sl.tables,
                                    S->table_bytes, sl.staging, emu_ws.data(), &nl);
@@ -256,7 +333,7 @@ bool launch_batch(gb_server* S, Slot& sl) {
     for (size_t i = 0; i < batch.size() && e == cudaSuccess && st == GB_OK; ++i) {
         const gb_request& q = batch[i]->r;
         if (q.C_out)
-            e = cudaMemcpyAsync(q.C_out, descs[i].C, 8 * q.m * q.n, cudaMemcpyDeviceToHost,
+            e = cudaMemcpyAsync(q.C_out, outC[i], 8 * q.m * q.n, cudaMemcpyDeviceToHost,
                                 sl.stream);
     }
     if (e == cudaSuccess) e = cudaEventRecord(sl.done, sl.stream);
@@ -281,6 +358,7 @@ bool launch_batch(gb_server* S, Slot& sl) {
         std::lock_guard<std::mutex> lock(S->mu);
         ++S->batches;
         S->batched_reqs += (int64_t)sl.batch.size();
+        if (lane == 1) ++S->large_launches;
     }
     return true;
 }
@@ -332,9 +410,15 @@ gb_status gb_fill_uniform(void* cuda_stream, double* dst, int64_t rows, int64_t 
 
 gb_status gb_server_create(gb_device* dev, size_t hbm_budget_bytes, int n_streams, int max_batch,
                            gb_server** out) {
+    return gb_server_create_ex(dev, hbm_budget_bytes, n_streams, max_batch, GB_SERVE_LANES, out);
+}
+
+gb_status gb_server_create_ex(gb_device* dev, size_t hbm_budget_bytes, int n_streams,
+                              int max_batch, int policy, gb_server** out) {
     if (!dev || !out || n_streams < 1 || n_streams > 16 || max_batch < 1 || max_batch > 4096 ||
-        hbm_budget_bytes < (1u << 20)) {
-        set_error("gb_server_create: bad device, budget (>= 1 MiB), streams (1..16) or batch (1..4096)");
+        hbm_budget_bytes < (1u << 20) || (policy != GB_SERVE_LANES && policy != GB_SERVE_FIFO)) {
+        set_error("gb_server_create: bad device, budget (>= 1 MiB), streams (1..16), batch "
+                  "(1..4096) or policy");
         return GB_ERR_INVALID_ARG;
     }
     *out = nullptr;
@@ -346,6 +430,7 @@ gb_status gb_server_create(gb_device* dev, size_t hbm_budget_bytes, int n_stream
     }
     S->dev = dev;
     S->max_batch = max_batch;
+    S->policy = policy;
     S->table_bytes = grouped_table_bytes(max_batch);
     cudaError_t e = cudaMalloc(&S->arena_base, hbm_budget_bytes);
     if (e != cudaSuccess) {
@@ -354,8 +439,25 @@ gb_status gb_server_create(gb_device* dev, size_t hbm_budget_bytes, int n_stream
     }
     S->arena.init(hbm_budget_bytes);
     S->slots.resize(n_streams);
-    for (Slot& sl : S->slots) {
-        if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&sl.stream, cudaStreamNonBlocking);
+    // lanes: half the streams (rounded down) for large requests at the lowest
+    // stream priority, the rest for small batches at the highest; one stream
+    // serves both lanes at the default priority
+    int prio_low = 0, prio_high = 0;
+    if (e == cudaSuccess) e = cudaDeviceGetStreamPriorityRange(&prio_low, &prio_high);
+    const int n_large = (policy == GB_SERVE_LANES && n_streams > 1) ? n_streams / 2 : 0;
+    for (int i = 0; i < n_streams; ++i) {
+        Slot& sl = S->slots[i];
+        int prio = 0;
+        if (policy == GB_SERVE_FIFO) {
+            sl.lane = 0;
+        } else if (n_streams == 1) {
+            sl.lane = -1;
+        } else {
+            sl.lane = i < n_large ? 1 : 0;
+            prio = sl.lane == 1 ? prio_low : prio_high;
+        }
+        if (e == cudaSuccess)
+            e = cudaStreamCreateWithPriority(&sl.stream, cudaStreamNonBlocking, prio);
         if (e == cudaSuccess) e = cudaEventCreateWithFlags(&sl.done, cudaEventDisableTiming);
         if (e == cudaSuccess) e = cudaHostAlloc(&sl.staging, S->table_bytes, cudaHostAllocDefault);
         if (e == cudaSuccess) e = cudaMalloc(&sl.tables, S->table_bytes);
@@ -400,6 +502,9 @@ gb_status gb_server_submit(gb_server* S, const gb_request* req, uint64_t* reques
     r->r = q;
     r->bytes = footprint(q);
     r->flops = 2.0 * (double)q.m * (double)q.n * (double)q.k;
+    r->cost = q.precision == GB_PREC_EMULATED ? r->flops / 16.0 : r->flops;
+    r->lane = (S->policy == GB_SERVE_LANES && q.precision == GB_PREC_NATIVE &&
+               r->flops >= kLargeFlops) ? 1 : 0;
     r->t_submit = Clock::now();
     std::lock_guard<std::mutex> lock(S->mu);
     if (r->bytes > S->arena.total()) {
@@ -411,9 +516,10 @@ gb_status gb_server_submit(gb_server* S, const gb_request* req, uint64_t* reques
     }
     r->id = S->next_id++;
     S->all[r->id] = r;
-    S->fifo.push_back(r);
+    S->fifo[r->lane].push_back(r);
     ++S->submitted;
-    S->max_queue = std::max<int64_t>(S->max_queue, (int64_t)S->fifo.size());
+    S->max_queue =
+        std::max<int64_t>(S->max_queue, (int64_t)(S->fifo[0].size() + S->fifo[1].size()));
     if (!S->have_first) {
         S->have_first = true;
         S->t_first = r->t_submit;
@@ -452,11 +558,11 @@ gb_status gb_server_drain(gb_server* S, double timeout_s) {
     }
     const auto deadline = Clock::now() + std::chrono::duration<double>(timeout_s);
     std::unique_lock<std::mutex> lock(S->mu);
-    while (!(S->fifo.empty() && S->in_flight == 0)) {
-        if (S->cv.wait_until(lock, deadline) == std::cv_status::timeout &&
-            !(S->fifo.empty() && S->in_flight == 0)) {
-            set_error("drain timed out with %zu queued and %lld in flight", S->fifo.size(),
-                      (long long)S->in_flight);
+    auto idle = [&] { return S->fifo[0].empty() && S->fifo[1].empty() && S->in_flight == 0; };
+    while (!idle()) {
+        if (S->cv.wait_until(lock, deadline) == std::cv_status::timeout && !idle()) {
+            set_error("drain timed out with %zu queued and %lld in flight",
+                      S->fifo[0].size() + S->fifo[1].size(), (long long)S->in_flight);
             return GB_ERR_TIMEOUT;
         }
     }
@@ -473,7 +579,8 @@ gb_status gb_server_stats_get(gb_server* S, gb_server_stats* out) {
     out->submitted = S->submitted;
     out->completed = S->completed;
     out->rejected = S->rejected;
-    out->pending = (int64_t)S->fifo.size();
+    out->pending = (int64_t)(S->fifo[0].size() + S->fifo[1].size());
+    out->large_launches = S->large_launches;
     out->in_flight = S->in_flight;
     out->max_queue = S->max_queue;
     out->batches = S->batches;
@@ -504,11 +611,13 @@ gb_status gb_server_destroy(gb_server* S) {
     if (!S) return GB_OK;
     {
         std::lock_guard<std::mutex> lock(S->mu);
-        for (Request* r : S->fifo) {
-            r->status = GB_ERR_BUSY;
-            r->state = 2;
+        for (auto& fifo : S->fifo) {
+            for (Request* r : fifo) {
+                r->status = GB_ERR_BUSY;
+                r->state = 2;
+            }
+            fifo.clear();
         }
-        S->fifo.clear();
     }
     S->stop.store(true);
     S->cv.notify_all();

@@ -24,7 +24,7 @@ class ServerStats(ctypes.Structure):
                 ("max_ms", ctypes.c_double), ("tflops", ctypes.c_double),
                 ("busy_s", ctypes.c_double), ("max_queue", ctypes.c_int64),
                 ("batches", ctypes.c_int64), ("mean_batch", ctypes.c_double),
-                ("peak_bytes", ctypes.c_size_t)]
+                ("peak_bytes", ctypes.c_size_t), ("large_launches", ctypes.c_int64)]
 
     def as_dict(self):
         return {f: getattr(self, f) for f, _ in self._fields_}
@@ -33,6 +33,7 @@ class ServerStats(ctypes.Structure):
 _i64, _int, _vp, _sz, _st = ctypes.c_int64, ctypes.c_int, ctypes.c_void_p, ctypes.c_size_t, ctypes.c_int
 _lib.extra_signatures({
     "gb_server_create": (_st, [_vp, _sz, _int, _int, ctypes.POINTER(_vp)]),
+    "gb_server_create_ex": (_st, [_vp, _sz, _int, _int, _int, ctypes.POINTER(_vp)]),
     "gb_server_submit": (_st, [_vp, ctypes.POINTER(Request), ctypes.POINTER(ctypes.c_uint64)]),
     "gb_server_poll": (_st, [_vp, ctypes.c_uint64, ctypes.POINTER(_int), ctypes.POINTER(_int),
                              ctypes.POINTER(ctypes.c_double)]),
@@ -52,13 +53,21 @@ def _ptr(a):
 class Server:
     """Requests in, results out; budget-admitted and batched on the device."""
 
+    POLICIES = {"lanes": 0, "fifo": 1}
+
     def __init__(self, hbm_budget_bytes: int, n_streams: int = 4, max_batch: int = 64,
-                 device=None):
+                 device=None, policy: str = "lanes"):
+        """policy "lanes": large native requests alone on low-priority streams,
+        small ones batched on high-priority streams; "fifo": one queue, every
+        batch a grouped launch (max_batch = 1: one launch per GEMM)."""
         from .gemm import Device
+        if policy not in self.POLICIES:
+            raise ValueError(f"policy must be one of {sorted(self.POLICIES)}")
         self.device = device or Device(0)
         h = ctypes.c_void_p()
-        check(_lib.load().gb_server_create(self.device.handle, hbm_budget_bytes, n_streams,
-                                           max_batch, ctypes.byref(h)), "gb_server_create")
+        check(_lib.load().gb_server_create_ex(self.device.handle, hbm_budget_bytes, n_streams,
+                                              max_batch, self.POLICIES[policy],
+                                              ctypes.byref(h)), "gb_server_create_ex")
         self.handle = h
         self._keep = {}
 

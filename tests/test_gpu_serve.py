@@ -80,6 +80,57 @@ def test_results_alone_equal_results_in_the_mix(gb):
         assert np.all(np.abs(out - ref) <= 2 * bound)
 
 
+def test_lanes_run_large_requests_alone(gb):
+    # native requests of >= 2^31 flops take the large lane (one plain GEMM launch
+    # each); the rest are batched.  Each result equals the same request served
+    # alone (single-stream server, same policy) and meets the FP64 bound; the FIFO
+    # policy serves the same requests through grouped launches only.
+    reqs = _requests(24, 7100)
+    for i, (m, n, k) in enumerate([(1100, 1100, 1100), (700, 1500, 2100), (2050, 1030, 1040)]):
+        seed = 7200 + i
+        reqs.insert(5 * i + 2, dict(m=m, n=n, k=k, A=g.matrix("uniform", m, k, seed, 0),
+                                    B=g.matrix("uniform", k, n, seed, 1),
+                                    C=g.matrix("uniform", m, n, seed, 2), alpha=-0.75, beta=0.5,
+                                    precision="native", slices=0))
+    large = sum(1 for r in reqs if r["precision"] == "native"
+                and 2.0 * r["m"] * r["n"] * r["k"] >= 2.0 ** 31)
+    assert large == 3
+    results = {}
+    for policy, streams in (("lanes", 4), ("fifo", 2)):
+        srv = gb.Server(hbm_budget_bytes=256 << 20, n_streams=streams, max_batch=16,
+                        policy=policy)
+        outs = []
+        for r in reqs:
+            out = np.empty((r["m"], r["n"]))
+            outs.append(out)
+            srv.submit(r["m"], r["n"], r["k"], r["alpha"], r["beta"], r["precision"],
+                       r["slices"], A=r["A"], B=r["B"], C=r["C"], out=out)
+        srv.drain(600)
+        st = srv.stats()
+        srv.close()
+        assert st["completed"] == len(reqs)
+        assert st["large_launches"] == (large if policy == "lanes" else 0)
+        results[policy] = outs
+    for i, r in enumerate(reqs):
+        solo = gb.Server(hbm_budget_bytes=256 << 20, n_streams=1, max_batch=16)
+        alone = np.empty((r["m"], r["n"]))
+        solo.submit(r["m"], r["n"], r["k"], r["alpha"], r["beta"], r["precision"], r["slices"],
+                    A=r["A"], B=r["B"], C=r["C"], out=alone)
+        solo.drain(600)
+        solo.close()
+        assert np.array_equal(alone, results["lanes"][i])
+        ref, _ = cgemm.dgemm_omp(r["alpha"], r["A"], r["B"], r["beta"], r["C"].copy())
+        absab, _ = cgemm.dgemm_omp(1.0, np.abs(r["A"]), np.abs(r["B"]))
+        bound = exact.error_bound(r["k"], r["alpha"], absab, r["beta"], r["C"])
+        for policy in ("lanes", "fifo"):
+            assert np.all(np.abs(results[policy][i] - ref) <= 2 * bound)
+
+
+def test_server_rejects_an_unknown_policy(gb):
+    with pytest.raises(ValueError):
+        gb.Server(hbm_budget_bytes=8 << 20, policy="lifo")
+
+
 def test_device_generated_operands(gb):
     import torch
     srv = gb.Server(hbm_budget_bytes=256 << 20, n_streams=2, max_batch=16)
