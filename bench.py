@@ -526,7 +526,8 @@ def run_serve(args):
 def run_sweep(args):
     """Native square DGEMM sweep n in {1024, ..., 10240}: naive vs tiled vs DFMA vs
     DMMA kernels, TFLOP/s and fraction of the FP64 peak; the vendor library's FP64
-    GEMM (cuBLAS via torch.matmul) beside them as context."""
+    GEMM (cuBLAS via torch.matmul) beside them as context, and the emulated path
+    (FP64-accurate, --slices digit slices) at the same sizes."""
     import torch
 
     import paper_1602_08477_gb300 as gb
@@ -540,17 +541,23 @@ def run_sweep(args):
         C = torch.empty((n, n), dtype=torch.float64, device="cuda")
         gb.fill_uniform(A, 1602084771, 0)
         gb.fill_uniform(B, 1602084771, 1)
-        for kernel in ("naive", "tiled", "dfma", "dmma", "cublas"):
+        ws = gb.alloc_workspace(gb.workspace_size("emulated", args.slices, n, n, n))
+        for kernel in ("naive", "tiled", "dfma", "dmma", "cublas", "emulated"):
             if kernel == "cublas":
                 # context only: the vendor library's FP64 GEMM through torch.matmul
                 f = lambda: torch.matmul(A, B, out=C)
+            elif kernel == "emulated":
+                # the FP64-accurate split-precision path at the bench's slice count
+                f = lambda: gb.dgemm(A, B, C, precision="emulated", slices=args.slices,
+                                     workspace=ws)
             else:
                 f = lambda: gb.dgemm(A, B, C, kernel=kernel)
-            ms = _time_stream(torch, f, 1 if n >= 4096 else 3, 1)
+            steps = 10 if kernel == "emulated" else (1 if n >= 4096 else 3)
+            ms = _time_stream(torch, f, steps, 1)
             tf = 2.0 * n ** 3 / ms / 1e9
             res.append(dict(n=n, kernel=kernel, ms=round(ms, 3), tflops=round(tf, 4),
                             frac_fp64_peak=round(tf / fp64_peak, 4)))
-        del A, B, C
+        del A, B, C, ws
         torch.cuda.empty_cache()
     print(json.dumps({"metric": "native FP64 DGEMM TFLOP/s per kernel", "unit": "TFLOP/s",
                       "peak": round(fp64_peak, 4), "sweep": res}), flush=True)

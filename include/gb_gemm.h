@@ -189,7 +189,8 @@ gb_status gb_dgemm_workspace_size(gb_precision prec, int slices, int64_t m, int6
  *             GB_BAD_LINE if row i holds a NaN or Inf
  *   b_exp     n int32: exponent f_j of max_l |B[l, j]|, or GB_BAD_LINE
  * with kp = k rounded up to a multiple of 32; padding lines and K indices
- * l >= k hold zero digits.
+ * l >= k hold zero digits.  After b_exp, `total` also covers 128 n bytes of
+ * scratch for the partial column maxima of B (up to 16 K ranges per column).
  */
 #define GB_BAD_LINE 0x40000000
 typedef struct {

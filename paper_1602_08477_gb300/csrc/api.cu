@@ -207,7 +207,7 @@ bool emu_group_trans(int s, int64_t m, int64_t n) {
 }
 
 EmuLayout emu_group_layout(int s, int64_t m, int64_t n, int64_t k) {
-    return emu_group_trans(s, m, n) ? emu_layout(s, n, m, k) : emu_layout(s, m, n, k);
+    return emu_group_trans(s, m, n) ? emu_layout(s, n, m, k, false) : emu_layout(s, m, n, k, false);
 }
 
 void emu_group_assign(EmuProb& e, uint8_t* base, const EmuLayout& w) {
@@ -223,7 +223,7 @@ void emu_group_assign(EmuProb& e, uint8_t* base, const EmuLayout& w) {
     e.rb = e.trans ? kEmuBM : emu_bn(e.s);
 }
 
-EmuLayout emu_layout(int s, int64_t m, int64_t n, int64_t k) {
+EmuLayout emu_layout(int s, int64_t m, int64_t n, int64_t k, bool colmax_scratch) {
     EmuLayout L{};
     L.kp = ((k + 31) / 32) * 32;
     if (L.kp == 0) L.kp = 32;
@@ -240,6 +240,8 @@ EmuLayout emu_layout(int s, int64_t m, int64_t n, int64_t k) {
     off = up(off + sizeof(int32_t) * (size_t)m);
     L.b_exp = off;
     off = up(off + sizeof(int32_t) * (size_t)n);
+    L.b_part = off;
+    if (colmax_scratch) off = up(off + sizeof(uint64_t) * (size_t)kColmaxParts * (size_t)n);
     L.total = off;
     return L;
 }
@@ -436,7 +438,8 @@ gb_status gb_emulated_split_b(gb_queue* q, int slices, int64_t m, int64_t n, int
     const EmuLayout L = emu_layout(s, m, n, k);
     uint8_t* ws = static_cast<uint8_t*>(workspace);
     cudaError_t e = launch_split_cols(launch_of(q), s, n, k, B, ldb, ws + L.b_digits, L.kp,
-                                      reinterpret_cast<int32_t*>(ws + L.b_exp));
+                                      reinterpret_cast<int32_t*>(ws + L.b_exp),
+                                      reinterpret_cast<uint64_t*>(ws + L.b_part));
     return finish_call(q, e, "split of B");
 }
 
@@ -511,7 +514,9 @@ gb_status gb_dgemm(gb_queue* q, const gb_workdiv* wd, gb_kernel kernel, gb_preci
         int32_t* ea = reinterpret_cast<int32_t*>(ws + lay.a_exp);
         int32_t* fb = reinterpret_cast<int32_t*>(ws + lay.b_exp);
         cudaError_t e = launch_split_rows(L, s, m, k, A, lda, ws + lay.a_digits, lay.kp, ea);
-        if (e == cudaSuccess) e = launch_split_cols(L, s, n, k, B, ldb, ws + lay.b_digits, lay.kp, fb);
+        if (e == cudaSuccess)
+            e = launch_split_cols(L, s, n, k, B, ldb, ws + lay.b_digits, lay.kp, fb,
+                                  reinterpret_cast<uint64_t*>(ws + lay.b_part));
         if (e == cudaSuccess)
             e = launch_emu_products(L, s, m, n, k, alpha, beta, C, ldc, ws + lay.a_digits,
                                     ws + lay.b_digits, lay.kp, ea, fb);

@@ -415,7 +415,7 @@ gb_status gb_dgemm_host(gb_queue* q, gb_precision prec, int slices, int64_t m, i
         cudaError_t r = cudaStreamWaitEvent(qs, ev_b[j], 0);
         if (r == cudaSuccess)
             r = launch_split_cols(L, s, c1 - c0, k, dB + c0, n, ws + lay.b_digits + boff, lay.kp,
-                                  fb + c0);
+                                  fb + c0, reinterpret_cast<uint64_t*>(ws + lay.b_part));
         return r;
     };
     auto split_a = [&](int i) {

@@ -83,12 +83,15 @@ int grouped_native_occupancy();
 //     ((x / R) * nkb + l / 32) * s + t) * (R * 32) + (x % R) * 32
 //     + (((l % 32) / 16) ^ (((x % R) / 4) & 1)) * 16 + l % 16,   nkb = kp / 32.
 // Lines are padded to multiples of R (zero digits); columns to kp (zero digits).
+// After the exponents: b_part, scratch for the partial column maxima of B
+// (kColmaxParts x n uint64, see launch_split_cols).
 struct EmuLayout {
     int64_t kp;
-    size_t a_digits, b_digits, a_exp, b_exp, total;
+    size_t a_digits, b_digits, a_exp, b_exp, b_part, total;
     int bn;  // lines of a B digit tile = output tile columns, emu_bn(s)
 };
-EmuLayout emu_layout(int s, int64_t m, int64_t n, int64_t k);
+constexpr int kColmaxParts = 16;  // K ranges of the column maxima of one launch, at most
+EmuLayout emu_layout(int s, int64_t m, int64_t n, int64_t k, bool colmax_scratch = true);
 
 // A grouped emulated problem is computed as C^T = B^T A^T (B's columns on the
 // 128-row side of the output tiles, A's rows on the emu_bn(s)-column side) when
@@ -96,7 +99,8 @@ EmuLayout emu_layout(int s, int64_t m, int64_t n, int64_t k);
 bool emu_group_trans(int s, int64_t m, int64_t n);
 // Workspace layout of one grouped emulated problem: emu_layout(s, m, n, k), or for
 // a transposed problem emu_layout(s, n, m, k) with the roles swapped (its a_*
-// regions hold B's column digits and exponents, its b_* regions A's rows').
+// regions hold B's column digits and exponents, its b_* regions A's rows'); no
+// b_part scratch (the grouped column maxima need none).
 EmuLayout emu_group_layout(int s, int64_t m, int64_t n, int64_t k);
 
 // One emulated problem of a grouped launch, as the device reads it.
@@ -164,8 +168,11 @@ __host__ __device__ constexpr int emu_bn(int s) { return s <= 10 ? 48 : 32; }
 
 cudaError_t launch_split_rows(const Launch& L, int s, int64_t m, int64_t k, const double* A,
                               int64_t lda, uint8_t* digits, int64_t kp, int32_t* exps);
+// e1 + e2 for the columns of B: partial column maxima over up to kColmaxParts K
+// ranges into `part` (kColmaxParts x n uint64 of scratch), then exponents and digits.
 cudaError_t launch_split_cols(const Launch& L, int s, int64_t n, int64_t k, const double* B,
-                              int64_t ldb, uint8_t* digits, int64_t kp, int32_t* exps);
+                              int64_t ldb, uint8_t* digits, int64_t kp, int32_t* exps,
+                              uint64_t* part);
 cudaError_t launch_emu_products(const Launch& L, int s, int64_t m, int64_t n, int64_t k,
                                 double alpha, double beta, double* C, int64_t ldc,
                                 const uint8_t* a_digits, const uint8_t* b_digits, int64_t kp,

@@ -108,7 +108,9 @@ extern "C" gb_status gb_dgemm_emulated_noalloc(void* cuda_stream, int slices, in
     // The split kernels write every byte of the layout (digit padding included),
     // so nothing left by an earlier call needs clearing.
     e = launch_split_rows(L, s, m, k, A, lda, ws + lay.a_digits, lay.kp, ea);
-    if (e == cudaSuccess) e = launch_split_cols(L, s, n, k, B, ldb, ws + lay.b_digits, lay.kp, fb);
+    if (e == cudaSuccess)
+        e = launch_split_cols(L, s, n, k, B, ldb, ws + lay.b_digits, lay.kp, fb,
+                              reinterpret_cast<uint64_t*>(ws + lay.b_part));
     if (e == cudaSuccess)
         e = launch_emu_products(L, s, m, n, k, alpha, beta, C, ldc, ws + lay.a_digits,
                                 ws + lay.b_digits, lay.kp, ea, fb);

@@ -250,28 +250,33 @@ __device__ __forceinline__ void colmax_block(int64_t jb, int64_t n, int64_t k,
 
 // Transposing digit pass for B over the tile of 64 rows (l) x 32 columns (j)
 // at (lb, jb), into B digit tiles of R lines; columns n <= j < (n padded to whole
-// tiles) get zero digits, columns beyond are not written.
-template <int S>
+// tiles) get zero digits, columns beyond are not written.  `pre()` runs between
+// the tile's loads and the barrier after them (its own loads overlap theirs);
+// `ecol(jj, j)` gives the exponent of column j = 32 jb + jj after the barrier.
+template <int S, class Pre, class ECol>
 __device__ __forceinline__ void split_cols_tile(int64_t jb, int64_t lb, int64_t n, int64_t k,
                                                 const double* __restrict__ B, int64_t ldb, int s,
                                                 uint8_t* __restrict__ digits, int64_t kp,
-                                                const int32_t* __restrict__ exps,
-                                                uint64_t (*T)[33], int R) {
+                                                uint64_t (*T)[33], int R, Pre pre, ECol ecol) {
     const int tid = threadIdx.x;
     const int tx = tid & 31, ty = tid >> 5;
     const int64_t j0 = jb * 32, l0 = lb * 64;
     const uint64_t* Bb = reinterpret_cast<const uint64_t*>(B);
+    uint64_t v[8];
 #pragma unroll
     for (int r = 0; r < 8; ++r) {
         const int64_t l = l0 + ty + 8 * r, j = j0 + tx;
-        T[ty + 8 * r][tx] = (l < k && j < n) ? Bb[l * ldb + j] : 0ull;
+        v[r] = (l < k && j < n) ? Bb[l * ldb + j] : 0ull;
     }
+    pre();
+#pragma unroll
+    for (int r = 0; r < 8; ++r) T[ty + 8 * r][tx] = v[r];
     __syncthreads();
     const int jj = tid >> 3, lsub = (tid & 7) * 8;
     const int64_t j = j0 + jj, lbase = l0 + lsub;
     const int64_t np = (n + R - 1) / R * R;
     if (lbase < kp && j < np) {
-        const int e = j < n ? exps[j] : GB_BAD_LINE_DEV;
+        const int e = ecol(jj, j);
         uint64_t w[S];
 #pragma unroll
         for (int t = 0; t < S; ++t) w[t] = 0;
@@ -306,27 +311,85 @@ __global__ void __launch_bounds__(128) split_rows_kernel(int64_t m, int64_t k,
         split_one_row<S>(i, m, k, A, lda, S, digits, kp, exps, status, red, &bad_sh);
 }
 
-// One GEMM: one CTA of 32 warps per 32 columns (n / 32 CTAs, each reading a long
-// column strip; 32 row phases keep enough loads in flight).
-__global__ void __launch_bounds__(1024) colmax_kernel(int64_t n, int64_t k,
-                                                      const double* __restrict__ B, int64_t ldb,
-                                                      int32_t* __restrict__ exps,
-                                                      unsigned* status) {
-    __shared__ uint64_t mx_sh[32][32];
-    __shared__ int bad_sh[32][32];
-    colmax_block<32>(blockIdx.x, n, k, B, ldb, exps, status, mx_sh, bad_sh);
+// One GEMM, first half of e1 for B: the column maxima over a K range.  CTA (x, y)
+// takes columns 32 x .. 32 x + 31 and rows y rows_per .. (y + 1) rows_per - 1 by 8
+// row phases; part[y n + j] = the largest absolute bit pattern in the range, or
+// bit 63 alone when it holds a NaN or Inf (larger than every finite pattern, so the
+// maximum over the ranges keeps it).  Many short strips keep every SM loading: one
+// CTA per column strip left a narrow B bound by the latency of a strip of all rows.
+__global__ void __launch_bounds__(256) colmax_part_kernel(int64_t n, int64_t k,
+                                                          const double* __restrict__ B,
+                                                          int64_t ldb, int64_t rows_per,
+                                                          uint64_t* __restrict__ part) {
+    __shared__ uint64_t mx_sh[8][32];
+    const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
+    const int64_t j = (int64_t)blockIdx.x * 32 + tx;
+    const int64_t l0 = (int64_t)blockIdx.y * rows_per;
+    const int64_t l1 = l0 + rows_per < k ? l0 + rows_per : k;
+    uint64_t mx = 0;
+    if (j < n) {
+        const uint64_t* col = reinterpret_cast<const uint64_t*>(B) + j;
+#pragma unroll 8
+        for (int64_t l = l0 + ty; l < l1; l += 8) {
+            const uint64_t a = col[l * ldb] & 0x7FFFFFFFFFFFFFFFull;
+            const uint64_t t = a >= 0x7FF0000000000000ull ? (1ull << 63) : a;
+            mx = t > mx ? t : mx;
+        }
+    }
+    mx_sh[ty][tx] = mx;
+    __syncthreads();
+    if (ty == 0 && j < n) {
+#pragma unroll
+        for (int r = 1; r < 8; ++r) mx = mx_sh[r][tx] > mx ? mx_sh[r][tx] : mx;
+        part[(int64_t)blockIdx.y * n + j] = mx;
+    }
 }
 
+// One GEMM, second half of e1 and e2 for B: each CTA reduces the `ks` partial
+// maxima of its 32 columns to their exponents (the CTAs of the first K tile also
+// store them in exps and flag non-finite columns), then writes the digit tiles of
+// its 64 rows x 32 columns.
 template <int S>
 __global__ void __launch_bounds__(256) split_cols_kernel(int64_t n, int64_t k,
                                                          const double* __restrict__ B,
                                                          int64_t ldb,
                                                          uint8_t* __restrict__ digits,
-                                                         int64_t kp,
-                                                         const int32_t* __restrict__ exps) {
+                                                         int64_t kp, int32_t* __restrict__ exps,
+                                                         const uint64_t* __restrict__ part, int ks,
+                                                         unsigned* status) {
     fill_e4m3_table();
     __shared__ uint64_t T[64][33];
-    split_cols_tile<S>(blockIdx.x, blockIdx.y, n, k, B, ldb, S, digits, kp, exps, T, emu_bn(S));
+    __shared__ uint64_t red[8][32];
+    const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
+    static_assert(kColmaxParts <= 16, "two partial maxima per thread of 8 row phases");
+    // every thread loads two of the (up to 16) partial maxima of column tx while
+    // the tile loads fly; the barrier after the tile's loads publishes red
+    auto partial_maxima = [&]() {
+        const int64_t j = (int64_t)blockIdx.x * 32 + tx;
+        uint64_t mx = 0;
+        if (j < n) {
+            const uint64_t a = ty < ks ? part[(int64_t)ty * n + j] : 0ull;
+            const uint64_t b = ty + 8 < ks ? part[(int64_t)(ty + 8) * n + j] : 0ull;
+            mx = a > b ? a : b;
+        }
+        red[ty][tx] = mx;
+    };
+    // column exponent from the 8 row-phase maxima; the first K tile's CTAs store it
+    auto column_exponent = [&](int jj, int64_t j) {
+        if (j >= n) return (int)GB_BAD_LINE_DEV;
+        uint64_t mx = 0;
+#pragma unroll
+        for (int r = 0; r < 8; ++r) mx = red[r][jj] > mx ? red[r][jj] : mx;
+        const bool bad = (mx >> 63) != 0;
+        const int e = bad ? GB_BAD_LINE_DEV : frexp_exp_bits(mx);
+        if (blockIdx.y == 0 && (threadIdx.x & 7) == 0) {
+            exps[j] = e;
+            if (bad && status) atomicOr(status, kStatusNonfinite);
+        }
+        return e;
+    };
+    split_cols_tile<S>(blockIdx.x, blockIdx.y, n, k, B, ldb, S, digits, kp, T, emu_bn(S),
+                       partial_maxima, column_exponent);
 }
 
 #define GB_SWITCH_S(s, CALL)                                                           \
@@ -477,8 +540,12 @@ __global__ void __launch_bounds__(256) grouped_split_cols_kernel(const EmuProb* 
         const EmuProb& q = P[find_prob(key, q_begin, q_end - 1, b)];
         const int64_t local = b - q.first_tblk;
         const int64_t ncb = ((q.n + q.rb - 1) / q.rb * q.rb + 31) / 32;  // padded columns
+        const int32_t* b_exp = q.b_exp;
+        const int64_t qn = q.n;
         split_cols_tile<S>(local % ncb, local / ncb, q.n, q.k, q.B, q.ldb, S, q.b_digits, q.kp,
-                           q.b_exp, T, q.rb);
+                           T, q.rb, [] {}, [=](int, int64_t j) {
+                               return j < qn ? (int)b_exp[j] : (int)GB_BAD_LINE_DEV;
+                           });
     }
 }
 
@@ -524,16 +591,28 @@ cudaError_t launch_grouped_split(const Launch& L, const EmuProb* probs, const Em
 }
 
 cudaError_t launch_split_cols(const Launch& L, int s, int64_t n, int64_t k, const double* B,
-                              int64_t ldb, uint8_t* digits, int64_t kp, int32_t* exps) {
+                              int64_t ldb, uint8_t* digits, int64_t kp, int32_t* exps,
+                              uint64_t* part) {
     if (n == 0) return cudaSuccess;
-    const unsigned gx = (unsigned)((n + 31) / 32);
-    colmax_kernel<<<gx, 1024, 0, L.stream>>>(n, k, B, ldb, exps, L.status);
+    // K ranges of the column maxima: about sixteen CTAs per SM over the column
+    // strips (enough loads in flight to stream B), at least 64 rows each, at most
+    // kColmaxParts
+    const int64_t ncb = (n + 31) / 32;
+    int64_t ks = (16 * (int64_t)L.sm_count + ncb - 1) / ncb;
+    const int64_t kcap = (k + 63) / 64;
+    if (ks > kcap) ks = kcap;
+    if (ks > kColmaxParts) ks = kColmaxParts;
+    if (ks < 1) ks = 1;
+    const int64_t rows_per = (k + ks - 1) / ks;
+    colmax_part_kernel<<<dim3((unsigned)ncb, (unsigned)ks), 256, 0, L.stream>>>(n, k, B, ldb,
+                                                                              rows_per, part);
     cudaError_t err = cudaGetLastError();
     if (err != cudaSuccess) return err;
     const int64_t np = (n + emu_bn(s) - 1) / emu_bn(s) * emu_bn(s);  // B digit tile padding
     const dim3 grid((unsigned)((np + 31) / 32), (unsigned)((kp + 63) / 64));
-#define GB_LAUNCH_COLS(SS) \
-    split_cols_kernel<SS><<<grid, 256, 0, L.stream>>>(n, k, B, ldb, digits, kp, exps)
+#define GB_LAUNCH_COLS(SS)                                                                   \
+    split_cols_kernel<SS><<<grid, 256, 0, L.stream>>>(n, k, B, ldb, digits, kp, exps, part, \
+                                                      (int)ks, L.status)
     GB_SWITCH_S(s, GB_LAUNCH_COLS)
 #undef GB_LAUNCH_COLS
     return cudaGetLastError();
