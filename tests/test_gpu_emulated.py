@@ -143,11 +143,18 @@ def test_largest_level_sums_exact_in_tensor_memory(gb):
     assert np.all(got5 == k * (1.0 - 2.0 ** -19))
 
 
-def test_nonfinite_rows_and_columns(gb):
+@pytest.mark.parametrize("k", [40, 3000])
+def test_nonfinite_rows_and_columns(gb, k):
+    # k = 3000: the column maxima of B run over 16 K ranges; the non-finite values
+    # of B sit in the first and the last range, and a column's largest magnitude
+    # in a middle one
     import torch
-    A, B, _ = inputs("uniform", 70, 50, 40, 33, with_c=False)
+    A, B, _ = inputs("uniform", 70, 50, k, 33, with_c=False)
     A[4, 7] = np.inf
     B[9, 13] = np.nan
+    if k > 40:
+        B[k - 3, 40] = -np.inf
+        B[k // 2, 20] = 1.0e6
     q = gb.Queue(gb.Device(0), torch.cuda.current_stream())
     dA, dB = to_dev(A), to_dev(B)
     dC = torch.zeros((70, 50), dtype=torch.float64, device="cuda")
@@ -157,6 +164,9 @@ def test_nonfinite_rows_and_columns(gb):
     q.wait()  # the status was cleared by the first wait
     got = dC.cpu().numpy()
     want = ozaki.emulated_gemm(1.0, A, B, s=8)
+    assert np.all(np.isnan(got[4, :])) and np.all(np.isnan(got[:, 13]))
+    if k > 40:
+        assert np.all(np.isnan(got[:, 40])) and not np.any(np.isnan(got[:3, 20]))
     assert np.array_equal(np.isnan(got), np.isnan(want))
     fin = ~np.isnan(want)
     assert np.array_equal(got[fin], want[fin])
