@@ -95,9 +95,14 @@ def save(entries, path: str = DEFAULT_TABLE, report=None, meta=None):
                    "meta": meta or {}, "report": report or []}, f, indent=1)
 
 
-def load(path: str = DEFAULT_TABLE, apply: bool = True):
-    """Read a table and (by default) install it in the library."""
-    with open(path) as f:
+def table_path(path: str | None = None) -> str:
+    """The table to read: `path`, else $GB_TUNE_TABLE, else the shipped table."""
+    return path or os.environ.get("GB_TUNE_TABLE") or DEFAULT_TABLE
+
+
+def load(path: str | None = None, apply: bool = True):
+    """Read a table (see table_path) and (by default) install it in the library."""
+    with open(table_path(path)) as f:
         d = json.load(f)
     entries = [tuple(e) for e in d["entries"]]
     if apply:

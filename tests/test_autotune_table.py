@@ -24,3 +24,14 @@ def test_shipped_table_covers_every_cell(tmp_path):
     autotune.save(entries, str(p))
     assert autotune.load(str(p), apply=False) == entries
     assert json.load(open(p))["thresholds"] == list(T)
+
+
+def test_table_path_prefers_argument_then_environment(tmp_path, monkeypatch):
+    monkeypatch.delenv("GB_TUNE_TABLE", raising=False)
+    assert autotune.table_path() == autotune.DEFAULT_TABLE
+    own = tmp_path / "own.json"
+    autotune.save([(32, 32, 32, "32x32")], str(own))
+    monkeypatch.setenv("GB_TUNE_TABLE", str(own))
+    assert autotune.table_path() == str(own)
+    assert autotune.load(apply=False) == [(32, 32, 32, "32x32")]
+    assert autotune.table_path("x.json") == "x.json"
