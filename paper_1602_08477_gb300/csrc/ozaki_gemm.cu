@@ -472,6 +472,10 @@ __device__ __forceinline__ void products_persistent(const Walk& walk, int chunk_
             const TileArgs a = w.args();
             const int nch = ((a.nkb + KB - 1) / KB + kCS - 1) / kCS;
             const bool small = a.nkb * S < 512;  // every accumulator below 2^22
+            // a warp whose 32 rows, or whose columns (8 cgroup .. on), all lie in the
+            // tile's padding has no output: it skips the level reads, the
+            // recombination and the stores, and only hands TMEM back (warp-uniform)
+            const bool live = a.row0 + quarter * 32 < a.m && a.col0 + 8 * cgroup < a.n;
             I128 T[CW];
 #pragma unroll
             for (int j = 0; j < CW; ++j) T[j] = I128{0, 0};
@@ -483,7 +487,7 @@ __device__ __forceinline__ void products_persistent(const Walk& walk, int chunk_
                     stop = true;
                     break;
                 }
-                add_levels<S, BN, kSplit>(lane_addr, cgroup, small, T);
+                if (live) add_levels<S, BN, kSplit>(lane_addr, cgroup, small, T);
                 // accumulators read: hand TMEM to the next unit's MMAs
                 ptx::tc_fence_before();
                 __syncwarp();
@@ -491,7 +495,7 @@ __device__ __forceinline__ void products_persistent(const Walk& walk, int chunk_
             }
             if (stop) break;
             const int64_t row = a.row0 + quarter * 32 + lane;
-            if (row < a.m) {
+            if (live && row < a.m) {
                 const int32_t ei = a.eA[row];
                 const bool bad_row = ei == GB_BAD_LINE_DEV;
                 const int Ebase = -8 - 5 * (S - 1);
@@ -680,7 +684,10 @@ struct RingShape {
 
 RingShape ring_for(int max_s, int kb_per_stage) {
     RingShape r{};
-    r.slot_bytes = (uint32_t)kb_per_stage * max_s * (kBM + emu_bn(max_s)) * kBKBytes;
+    // slots start on 1024-byte boundaries (the operand tiles inside are 256-byte
+    // aligned, as the 32-byte swizzle's 8-row pattern needs)
+    r.slot_bytes = ((uint32_t)kb_per_stage * max_s * (kBM + emu_bn(max_s)) * kBKBytes + 1023u) &
+                   ~1023u;
     const int fixed = 1024 + (int)sizeof(SmemTail) + 64;
     r.stages = (kSmemLimit - fixed) / (int)r.slot_bytes;
     if (r.stages > 8) r.stages = 8;

@@ -97,8 +97,10 @@ def test_gpu_reproduces_the_integer_fixture_bit_for_bit(precision, kernel):
 
 
 @pytest.mark.gpu
-@pytest.mark.parametrize("precision,kernel", KERNELS)
+@pytest.mark.parametrize("precision,kernel", [pk for pk in KERNELS if pk != ("emulated", 2)])
 def test_gpu_within_the_bound_of_the_exact_dyadic_fixture(precision, kernel):
+    # (two slices carry 9 bits: FP64 accuracy needs the tuned count, here 11; the
+    # integer fixture above fits in the first slice, so there s = 2 is exact)
     import paper_1602_08477_gb300 as gb
     gb.build()
     Cs = dyadic_fixture()
