@@ -21,18 +21,21 @@ kernels can be compared with it step by step:
   e3  level sums: S_g = sum_{p+q=g} DA_p DB_q over 2 <= g <= s+1 (pairs with
       p + q > s + 1 are dropped), exact integers.
   e4  recombination: the levels are summed exactly as one integer in units of
-      the smallest level, T = sum_{g=2..s+1} S_g 2^(b (s+1-g)), then rounded once
-      to FP64 (round to nearest, ties to even) and scaled by the exact power of
-      two 2^(e_i + f_j - 2 b1 - b (s-1)):  t = RN(T) * 2^E  (a scaling outside
-      the double range is applied as two multiplications by in-range powers of
-      two).  Then C = alpha * t + beta * C0 with each product and the sum one
-      IEEE rounding (beta = 0: C0 not read; alpha = 1 and beta = 0: C = t).
-      Rows of A or columns of B flagged in e1 give NaN outputs.
+      the smallest level, T = sum_{g=2..s+1} S_g 2^(b (s+1-g)); the exact value
+      T * 2^E, E = e_i + f_j - 2 b1 - b (s-1), is rounded once to FP64:
+      t = RN(T * 2^E), round to nearest with ties to even, gradual underflow
+      (subnormal results) and overflow to +-inf, as one IEEE operation on the
+      exact value would round it.  Then C = alpha * t + beta * C0 with each
+      product and the sum one IEEE rounding (beta = 0: C0 not read; alpha = 1
+      and beta = 0: C = t).  Rows of A or columns of B flagged in e1 give NaN
+      outputs.
 
 BLAS conventions as for the FP64 oracle: alpha == 0 or k == 0 gives beta*C0
 (0 when beta == 0); m == 0 or n == 0 is empty.
 """
 from __future__ import annotations
+
+import math
 
 import numpy as np
 
@@ -98,29 +101,34 @@ def level_sums(DA: np.ndarray, DBt: np.ndarray, s: int) -> np.ndarray:
     return S
 
 
-def pow2_scale(x: np.ndarray, E: np.ndarray) -> np.ndarray:
-    """x * 2^E as IEEE multiplications by powers of two that are normal doubles:
-    one multiplication when -1022 <= E <= 1023, else two with E split in halves."""
-    E = np.asarray(E, dtype=np.int64)
-    one = (E >= -1022) & (E <= 1023)
-    E1 = np.where(one, E, E // 2)
-    E2 = np.where(one, 0, E - E // 2)
-    return (x * np.ldexp(1.0, E1)) * np.ldexp(1.0, E2)
+def round_scaled(T: int, E: int) -> float:
+    """RN(T * 2^E) for a Python integer T and any integer E: the double nearest to
+    the exact value (ties to even), subnormal when it lies below 2^-1022, +-inf
+    when it rounds beyond the largest double.  Python's int -> float conversion
+    and int / int true division are both correctly rounded, so the exact value
+    is handed to one of them whole."""
+    T, E = int(T), int(E)
+    if T == 0:
+        return 0.0
+    try:
+        return float(T << E) if E >= 0 else T / (1 << -E)
+    except OverflowError:
+        return math.copysign(math.inf, T)
 
 
 def recombine(S: np.ndarray, e: np.ndarray, f: np.ndarray, alpha: float, beta: float = 0.0,
               C0: np.ndarray | None = None, fmt: str = "e4m3",
               bad_rows=None, bad_cols=None) -> np.ndarray:
-    """e4: exact integer sum of the levels, one rounding to FP64, exact scaling,
-    then alpha/beta."""
+    """e4: exact integer sum of the levels, T * 2^E rounded once to FP64, then
+    alpha/beta."""
     b1, b, _ = FORMATS[fmt]
     s = S.shape[0]
     T = np.zeros(S.shape[1:], dtype=object)
     for g in range(2, s + 2):                   # Horner form of sum S_g 2^(b(s+1-g))
         T = T * (2 ** b) + S[g - 2].astype(object)
-    rT = np.vectorize(float, otypes=[np.float64])(T) if T.size else np.zeros(T.shape)
     E = e[:, None] + f[None, :] - (2 * b1 + b * (s - 1))
-    t = pow2_scale(rT, E)
+    t = (np.vectorize(round_scaled, otypes=[np.float64])(T, E) if T.size
+         else np.zeros(T.shape))
     if alpha == 1.0 and beta == 0.0:
         out = t.copy()
     else:

@@ -9,9 +9,9 @@
 //     an exact integer in FP32 while it stays below 2^24 (k * pairs * 256).
 // e4: the epilogue reads the levels back, forms the exact integer
 //       T = sum_g S_g 2^(5 (s+1-g))
-//     in 128-bit integer arithmetic, rounds it once to FP64 (nearest, ties to
-//     even), scales by the power of two 2^(e_i + f_j - 8 - 5 (s-1)) and writes
-//     C = alpha t + beta C.  GB300 runs FP64 at a small fraction of its integer
+//     in 128-bit integer arithmetic, rounds T 2^(e_i + f_j - 8 - 5 (s-1)) once
+//     to FP64 (nearest, ties to even, gradual underflow, overflow to +-Inf) and
+//     writes C = alpha t + beta C.  GB300 runs FP64 at a small fraction of its integer
 //     rate, so only the alpha / beta step uses the FP64 pipe.
 //
 // Pipeline per CTA (one output tile, 192 threads):
@@ -60,13 +60,13 @@ struct I128 {
     uint64_t lo;
 };
 
-__device__ __forceinline__ double pow2(int e) {  // exact for -1022 <= e <= 1023
-    return __longlong_as_double((long long)(e + 1023) << 52);
-}
-
-// RN(T) * 2^E as an FP64 (T a signed 128-bit integer).  The scaling is exact
-// when the result is a normal double; otherwise RN(T) is multiplied by powers
-// of two in the normal range (one multiplication, or two when E is out of it).
+// RN(T * 2^E) as an FP64 (T a signed 128-bit integer, E any int): the double
+// nearest to the exact value, ties to even, with gradual underflow (subnormal
+// results carry the unit 2^-1074) and overflow to +-Inf.  One rounding, done on
+// the integer: the result's last place sits at bit q of |T|, q = p - 52 for a
+// normal result (p = index of the leading one) or q = -1074 - E for a subnormal
+// one; |T| is rounded at bit q and the bit pattern is assembled directly, so no
+// FP64 multiplication (and no power of two outside the double range) is used.
 __device__ __forceinline__ double i128_to_double_scaled(I128 x, int E) {
     const bool neg = x.hi < 0;
     uint64_t hi = (uint64_t)x.hi, lo = x.lo;
@@ -76,14 +76,24 @@ __device__ __forceinline__ double i128_to_double_scaled(I128 x, int E) {
     }
     if (hi == 0 && lo == 0) return 0.0;
     int p = hi ? 64 + 63 - __clzll((long long)hi) : 63 - __clzll((long long)lo);
-    uint64_t M;
-    if (p <= 52) {
-        M = lo << (52 - p);
+    const bool sub = -1074 - E > p - 52;  // the result lies below 2^-1022
+    const int q = sub ? -1074 - E : p - 52;
+    uint64_t M;  // |T| / 2^q rounded: the significand (normal) or the bit pattern (subnormal)
+    if (q <= 0) {
+        M = lo << (-q);  // exact: q <= 0 means p <= 52 and |T| < 2^53
+    } else if (q > p + 1) {
+        M = 0;           // below half of the last place
+    } else if (q == p + 1) {
+        // |T| in [2^p, 2^(p+1)): at least half of the last place; exactly half
+        // (|T| = 2^p) ties to the even 0
+        const bool is_pow2 = p >= 64 ? (lo == 0 && hi == (1ull << (p - 64)))
+                                     : (hi == 0 && lo == (1ull << p));
+        M = is_pow2 ? 0 : 1;
     } else {
-        const int sh = p - 52;  // 1 .. 74
+        const int sh = q;  // 1 .. p <= 127
         uint64_t rem_hi, rem_lo, half_hi, half_lo;
         if (sh < 64) {
-            M = (lo >> sh) | (sh ? (hi << (64 - sh)) : 0);
+            M = (lo >> sh) | (hi << (64 - sh));
             rem_hi = 0;
             rem_lo = lo & ((1ull << sh) - 1);
             half_hi = 0;
@@ -98,31 +108,23 @@ __device__ __forceinline__ double i128_to_double_scaled(I128 x, int E) {
         }
         const bool gt = rem_hi > half_hi || (rem_hi == half_hi && rem_lo > half_lo);
         const bool eq = rem_hi == half_hi && rem_lo == half_lo;
-        if (gt || (eq && (M & 1))) {
-            M += 1;
-            if (M == (1ull << 53)) {
-                M >>= 1;
-                p += 1;
-            }
-        }
+        if (gt || (eq && (M & 1))) M += 1;
     }
-    const int biased = p + E + 1023;
-    double r;
-    if (biased >= 1 && biased <= 2046) {
-        r = __longlong_as_double((long long)(((uint64_t)biased << 52) | (M & 0xFFFFFFFFFFFFFull)));
+    uint64_t bits;
+    if (sub) {
+        // M <= 2^52: the subnormal's bit pattern (2^52 is the smallest normal's)
+        bits = M;
     } else {
-        double t = __longlong_as_double(
-            (long long)(((uint64_t)(p + 1023) << 52) | (M & 0xFFFFFFFFFFFFFull)));
-        if (E >= -1022 && E <= 1023) {
-            t = __dmul_rn(t, pow2(E));
-        } else {
-            const int E1 = (E >= 0) ? E / 2 : -((-E + 1) / 2);  // floor(E / 2)
-            t = __dmul_rn(__dmul_rn(t, pow2(E1)), pow2(E - E1));
+        if (M == (1ull << 53)) {  // rounding carried into a new binade
+            M >>= 1;
+            p += 1;
         }
-        r = t;
+        const int biased = p + E + 1023;  // >= 1: not subnormal
+        bits = biased >= 2047 ? 0x7FF0000000000000ull
+                              : (((uint64_t)biased << 52) | (M & 0xFFFFFFFFFFFFFull));
     }
     // sign by bit manipulation: GB300's FP64 pipe is slow even for negation
-    return __longlong_as_double(__double_as_longlong(r) | (neg ? (long long)0x8000000000000000ull : 0ll));
+    return __longlong_as_double((long long)(bits | (neg ? 0x8000000000000000ull : 0ull)));
 }
 
 // Arguments of one output tile (row0, col0) of one problem.
