@@ -280,23 +280,32 @@ gb_status gb_selftest_wait_timeout(gb_queue* q, uint32_t timeout_us);
 /*
  * The emulated GEMM without any allocation or workspace argument.  The paper
  * has no counterpart: this entry point exists for callers that cannot allocate
- * device memory when they need the product -- code inside a CUDA stream
- * capture that forbids allocation, programs whose memory pool owns the whole
- * device, or plug-ins handed only their input and output buffers.
+ * device memory when they need the product -- programs whose memory pool owns
+ * the whole device (a cudaMalloc would fail), plug-ins that are handed only
+ * their input and output buffers, and latency-bound loops that must not pay
+ * for cudaMalloc / cudaFree, which may synchronize the whole device.
  *
  * Same operation, arguments and result as gb_dgemm(prec = GB_PREC_EMULATED,
  * slices) with C <- alpha A B + beta C, enqueued on `cuda_stream` (a
- * cudaStream_t of the current device, or NULL).  Its scratch (digit planes and
- * exponents) is a 64 MiB array in the library's device memory, reserved on every
- * GPU that loads the library until the process exits; a GEMM whose
- * gb_dgemm_workspace_size() exceeds 64 MiB is rejected with
- * GB_ERR_UNSUPPORTED.  No cudaMalloc, cudaFree or other allocating call is made.
- * The first call on a device looks up the scratch's device address (make that
- * first call before any stream capture).  Every call uses the same scratch: two
- * calls that can run at the same time on the GPU (different streams, no
- * ordering between them) race and corrupt each other's result.  Device-side
- * status (NaN/Inf input, a timed-out wait) is not reported: rows of A and
- * columns of B with NaN/Inf give NaN outputs as in gb_dgemm.
+ * cudaStream_t of the current device, or NULL); slices = 0 takes 11.  Its
+ * scratch (digit planes and exponents) is one 64 MiB array in the library's
+ * device memory; a GEMM whose gb_dgemm_workspace_size() exceeds 64 MiB is
+ * rejected with GB_ERR_UNSUPPORTED.  No cudaMalloc, cudaFree or other
+ * allocating call is made by this function.
+ * Set-up: the first call on a device, with that device current, looks up the
+ * array's device address (cudaGetSymbolAddress).  With CUDA's lazy module
+ * loading (the default) that first call is also when the 64 MiB are reserved
+ * on the device, held from then until the process exits; so make the first
+ * call on each device early -- before any stream capture, and before a memory
+ * pool takes the rest of the device.
+ * Every call uses the same scratch and leaves its contents behind (nothing in
+ * it needs clearing: each call rewrites every byte it reads).  Two calls that
+ * can run at the same time on the GPU (different streams, no ordering between
+ * them) race on the scratch and corrupt each other's result.
+ * Device-side status is not reported: rows of A and columns of B with NaN/Inf
+ * give NaN outputs as in gb_dgemm, and if a device-side wait of the products
+ * kernel gives up (after 4 s, which only a stalled GPU reaches) the output tiles
+ * of that CTA are not written, so C is then undefined and no error says so.
  * Errors: those of gb_dgemm's argument checks, GB_ERR_UNSUPPORTED,
  * GB_ERR_NO_DEVICE, GB_ERR_CUDA.
  */

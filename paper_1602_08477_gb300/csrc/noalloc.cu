@@ -1,18 +1,19 @@
 // Emulated FP64 GEMM for callers that cannot allocate device memory.
 //
-// Some callers cannot call cudaMalloc at the point where they need a GEMM: code
-// running while a CUDA graph is being captured on a stream that forbids
-// allocation, custom allocators or memory pools that own every byte of the
-// device, or plug-ins that are handed only the buffers of their inputs and
-// outputs.  The emulated path needs scratch memory for its digit planes and
-// exponents, so this entry point takes that scratch from one file-scope
-// __device__ array of fixed size instead of a caller workspace.
+// Some callers cannot call cudaMalloc at the point where they need a GEMM:
+// programs whose custom allocator or memory pool owns every byte of the
+// device, plug-ins that are handed only the buffers of their inputs and
+// outputs, and latency-bound loops that cannot afford cudaMalloc / cudaFree,
+// which may synchronize the device.  The emulated path needs scratch memory for
+// its digit planes and exponents, so this entry point takes that scratch from
+// one file-scope __device__ array of fixed size instead of a caller workspace.
 //
-// The array is kNoAllocScratchBytes (64 MiB) on every GPU that loads this
-// library, held until the process exits.  Host code cannot pass the array's
-// name to a kernel (on the host it names a stand-in, not device memory), so
-// the first call on each device, with that device current, looks up its
-// device address once with cudaGetSymbolAddress and keeps it.
+// The array is kNoAllocScratchBytes (64 MiB) per GPU, held until the process
+// exits; with lazy module loading it is reserved when the first call on a
+// device loads this file's module.  Host code cannot pass the array's name to
+// a kernel (on the host it names a stand-in, not device memory), so the first
+// call on each device, with that device current, looks up its device address
+// once with cudaGetSymbolAddress and keeps it.
 #include <cuda_runtime.h>
 
 #include <atomic>

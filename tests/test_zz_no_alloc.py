@@ -1,12 +1,14 @@
 """The emulated GEMM entry point that allocates nothing (static device scratch).
 
-Callers that cannot allocate device memory (inside an allocation-free stream
-capture, under a memory pool that owns the device, or as a plug-in handed only
-its buffers) use gb_dgemm_emulated_noalloc.  This test calls it through the C
-ABI twice in a row and checks each result against gb_dgemm with a caller
-workspace, with the same tolerance as the other parity tests (bit-exact: the
-two run the same kernels on the same digits).  It lives in a file collected
-last so that a failure here leaves every other test already run.
+Callers that cannot allocate device memory (a memory pool that owns the device,
+a plug-in handed only its buffers, a loop that cannot pay for cudaMalloc's
+device synchronization) use gb_dgemm_emulated_noalloc.  This test calls it
+through the C ABI twice in a row and checks each result against gb_dgemm with a
+caller workspace, bit for bit (the two run the same kernels on the same
+digits), and against the CPU model of the split-precision steps, also bit for
+bit; the cases include the default slice count (slices = 0) and operands that
+are views with leading dimensions wider than the matrix.  It lives in a file
+collected last so that a failure here leaves every other test already run.
 """
 import ctypes
 
@@ -25,24 +27,40 @@ def _ptr(t):
 def test_noalloc_matches_workspace_entry_point_twice():
     import torch
     import paper_1602_08477_gb300 as gb
+    from oracle import ozaki
     gb.build()
     lib = gb.load()
     stream = torch.cuda.current_stream()
-    cases = [(300, 200, 129, 11, "uniform", 1.5, 0.5), (513, 257, 1000, 13, "hard", 1.0, 0.0),
-             (130, 97, 70, 10, "uniform", -0.75, 2.0)]
-    for (m, n, k, s, kind, alpha, beta) in cases:
-        A = torch.from_numpy(g.matrix(kind, m, k, 91, 0)).cuda()
-        B = torch.from_numpy(g.matrix(kind, k, n, 91, 1)).cuda()
-        C0 = torch.from_numpy(g.matrix(kind, m, n, 91, 2)).cuda()
+    # (m, n, k, slices, kind, alpha, beta, pad): pad > 0 makes A, B and C views
+    # into wider buffers (lda = k + pad, ldb = ldc = n + pad)
+    cases = [(300, 200, 129, 11, "uniform", 1.5, 0.5, 0), (513, 257, 1000, 13, "hard", 1.0, 0.0, 0),
+             (130, 97, 70, 10, "uniform", -0.75, 2.0, 0), (200, 75, 90, 0, "uniform", 1.0, 0.5, 0),
+             (150, 61, 77, 9, "hard", 2.0, -1.0, 5)]
+    for (m, n, k, s, kind, alpha, beta, pad) in cases:
+        A_h = g.matrix(kind, m, k, 91, 0)
+        B_h = g.matrix(kind, k, n, 91, 1)
+        C_h = g.matrix(kind, m, n, 91, 2)
+        Abuf = torch.full((m, k + pad), float("nan"), dtype=torch.float64, device="cuda")
+        Bbuf = torch.full((k, n + pad), float("nan"), dtype=torch.float64, device="cuda")
+        A, B = Abuf[:, :k], Bbuf[:, :n]
+        A.copy_(torch.from_numpy(A_h))
+        B.copy_(torch.from_numpy(B_h))
+        C0 = torch.from_numpy(C_h).cuda()
         want = C0.clone()
-        gb.dgemm(A, B, want, alpha, beta, precision="emulated", slices=s)
+        gb.dgemm(A, B, want, alpha, beta, precision="emulated", slices=s or 11)
+        model = ozaki.emulated_gemm(alpha, A_h, B_h, beta, C_h, s=s or 11)
+        assert np.array_equal(want.cpu().numpy(), model)
         for _ in range(2):                 # two calls in a row share the scratch
-            got = C0.clone()
+            Cbuf = torch.full((m, n + pad), -7.0, dtype=torch.float64, device="cuda")
+            got = Cbuf[:, :n]
+            got.copy_(C0)
             st = lib.gb_dgemm_emulated_noalloc(ctypes.c_void_p(stream.cuda_stream), s, m, n, k,
-                                               alpha, _ptr(A), k, _ptr(B), n, beta, _ptr(got), n)
+                                               alpha, _ptr(A), k + pad, _ptr(B), n + pad, beta,
+                                               _ptr(got), n + pad)
             assert st == 0, gb._lib.last_error()
             torch.cuda.synchronize()
             assert torch.equal(got, want)
+            assert bool(torch.all(Cbuf[:, n:] == -7.0))   # nothing beyond the n columns
 
 
 def test_noalloc_rejects_sizes_beyond_the_static_scratch():
