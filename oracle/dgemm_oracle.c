@@ -113,21 +113,34 @@ static inline void two_sum(double a, double b, double* s, double* e) {
 void oracle_dgemm_dd_rows(int64_t nrows, const int64_t* rows, int64_t n, int64_t k,
                           const double* A, int64_t lda, const double* B, int64_t ldb,
                           double* hi, double* lo, int64_t ldo) {
+    /* Loop order r, l, j with the running (hi, lo) pair of every output kept in
+     * the output rows: each entry still takes l = 0, 1, ..., k-1 in order through
+     * the same steps as an i, j, l loop, so the bits do not depend on the order;
+     * rows and blocks of 256 columns go to OpenMP threads. */
+    const int64_t JB = 256;
+    const int64_t nb = (n + JB - 1) / JB;
+#ifdef _OPENMP
+#pragma omp parallel for collapse(2) schedule(dynamic)
+#endif
     for (int64_t r = 0; r < nrows; ++r) {
-        const int64_t i = rows ? rows[r] : r;
-        for (int64_t j = 0; j < n; ++j) {
-            double sh = 0.0, sl = 0.0;
+        for (int64_t b = 0; b < nb; ++b) {
+            const int64_t i = rows ? rows[r] : r;
+            const int64_t j0 = b * JB, j1 = (j0 + JB < n) ? j0 + JB : n;
+            double* h = &hi[r * ldo];
+            double* o = &lo[r * ldo];
+            for (int64_t j = j0; j < j1; ++j) h[j] = o[j] = 0.0;
             for (int64_t l = 0; l < k; ++l) {
-                const double a = A[i * lda + l], b = B[l * ldb + j];
-                const double p = a * b;
-                const double pe = fma(a, b, -p);
-                double t, te;
-                two_sum(sh, p, &t, &te);
-                te += pe + sl;
-                two_sum(t, te, &sh, &sl);
+                const double a = A[i * lda + l];
+                const double* bl = &B[l * ldb];
+                for (int64_t j = j0; j < j1; ++j) {
+                    const double p = a * bl[j];
+                    const double pe = fma(a, bl[j], -p);
+                    double t, te;
+                    two_sum(h[j], p, &t, &te);
+                    te += pe + o[j];
+                    two_sum(t, te, &h[j], &o[j]);
+                }
             }
-            hi[r * ldo + j] = sh;
-            lo[r * ldo + j] = sl;
         }
     }
 }

@@ -194,12 +194,17 @@ def test_blocking_queue_returns_after_work(gb):
 @pytest.mark.parametrize("n", [1024, 4096, 8192, 10240])
 def test_sweep_sizes_sampled_rows(gb, n):
     # full-size sweep points of the square DGEMM (alpha = 1, beta = 0): the
-    # outputs of 12 sampled rows against the oracle computed row by row
+    # outputs of 12 sampled rows of every kernel the sweep reports (naive, tiled,
+    # DFMA, DMMA, and the AUTO choice) against the double-double reference and
+    # the oracle computed row by row
     A, B, _ = inputs("uniform", n, n, n, g.BASE_SEED + 1, with_c=False)
-    got = run(gb, "auto", A, B, None, 1.0, 0.0)
     rows = np.random.default_rng(n).choice(n, 12, replace=False)
-    assert within_bound(got[rows], 1.0, A, B, 0.0, None, rows=rows) <= 1.0
-    # and the oracle itself on those rows is within the same bound
     ref = cgemm.dgemm_rows(rows, 1.0, A, B)
-    assert np.max(np.abs(got[rows] - ref)) <= np.max(
-        exact.error_bound(n, 1.0, cgemm.dgemm_rows(rows, 1.0, np.abs(A), np.abs(B)))) * 2
+    hi, lo = cgemm.dgemm_dd_rows(A, B, rows)
+    bound = exact.error_bound(n, 1.0, cgemm.dgemm_rows(rows, 1.0, np.abs(A), np.abs(B)))
+    kernels = ["auto"] if n in (1024, 8192) else ["auto", "naive", "tiled", "dfma", "dmma"]
+    for kernel in kernels:
+        got = run(gb, kernel, A, B, None, 1.0, 0.0)
+        assert np.all(np.abs(exact.residual(got[rows], 1.0, hi, lo)) <= bound), kernel
+        # and the oracle itself on those rows is within the same bound
+        assert np.all(np.abs(got[rows] - ref) <= 2 * bound), kernel
