@@ -3,10 +3,16 @@
 One step = one FP64-accurate GEMM at the configured n through the emulated path
 (split of A, split of B, tensor-core slice products + FP64 recombination), the
 path whose result is checked against the FP64 error bound; the native FP64 path
-(DMMA kernel) is timed beside it on the same inputs.  Inputs (8 n^2 bytes each)
-are larger than the 129 MB L2 at the default n, so no flush is needed.
+(the library's default kernel at that size) is timed beside it on the same
+inputs.  Inputs (8 n^2 bytes each) are larger than the 129 MB L2 at the default
+n, so no flush is needed.  At one GPU the same JSON line also carries, as
+sub-records: the accuracy of both paths against a double-double reference on
+sampled rows (`parity`), the 16-decade hard set at its slice count (`hard`),
+the 2048-problem grouped workload against one launch per GEMM (`grouped`) and
+two short serving runs, at the specified and at a sustainable arrival rate
+(`serve`).  Other workloads print their own line (--workload).
 
-  python bench.py [--gpus N] [--steps K] [--warmup W] [--n 8192] [--slices 11]
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--n 8192] [--slices 10]
   python bench.py --impl reference ...   # the CPU oracle on a bounded sample
 
 Multi-GPU: independent replicas (no collective on the data path); value is the
@@ -62,6 +68,10 @@ def parse():
     p.add_argument("--serve-batch", type=int, default=64)
     p.add_argument("--no-serve-baseline", action="store_true",
                    help="skip the one-GEMM-per-launch run of the same serving trace")
+    p.add_argument("--hard-slices", type=int, default=11)
+    p.add_argument("--sub-serve-seconds", type=float, default=10.0)
+    p.add_argument("--no-sub-records", action="store_true",
+                   help="default workload only: skip the hard, grouped and serving sub-records")
     return p.parse_args()
 
 
@@ -177,11 +187,47 @@ def dgemm_metric_config(n, s, world):
     metric = "FP64-accurate GEMM TFLOP/s (emulated path; native FP64 beside it)"
     config = {"workload": f"square DGEMM C = A B, m = n = k = {n}, uniform[-1,1], "
                           f"alpha = 1, beta = 0 (sweep point n = {n})",
-              "path": f"emulated FP64: {s} E4M3 slices, tcgen05 FP32 accumulation, "
-                      "exact integer recombination, one FP64 rounding",
               "slices": s, "flush": "inputs larger than L2 (no flush needed)",
               "parallelism": f"replicas x{world}"}
     return metric, config
+
+
+def gpu_path(s):
+    return (f"GPU: emulated FP64, {s} E4M3 slices, tcgen05 FP32 accumulation, exact integer "
+            "recombination, one FP64 rounding")
+
+
+CPU_PATH = ("CPU oracle: plain C definition loops (-O2, no FMA contraction), OpenMP over "
+            "rows, on a sample of rows of C")
+
+
+def matrix_threads(kind, rows, cols, seed, sid, workers=None):
+    """synth.generators.matrix built from row blocks on several threads (the
+    values are a pure function of the element index, so blocks are independent)."""
+    import numpy as np
+    from concurrent.futures import ThreadPoolExecutor
+    from synth import generators as g
+    workers = workers or min(16, os.cpu_count() or 1)
+    out = np.empty((rows, cols), dtype=np.float64)
+    step = -(-rows // (4 * workers))
+
+    def block(r0):
+        r1 = min(rows, r0 + step)
+        out[r0:r1] = g.matrix(kind, rows, cols, seed, sid, row_indices=np.arange(r0, r1))
+    with ThreadPoolExecutor(workers) as ex:
+        list(ex.map(block, range(0, rows, step)))
+    return out
+
+
+def rho_rows(got_rows, A, B, rows, hilo=None):
+    """max |C - C*| / bound over the given rows, C* the double-double value of A B
+    (alpha = 1, beta = 0)."""
+    import numpy as np
+    from oracle import cgemm, exact
+    hi, lo = hilo if hilo is not None else cgemm.dgemm_dd_rows(A, B, rows)
+    bound = exact.error_bound(A.shape[1], 1.0, cgemm.dgemm_rows(rows, 1.0, np.abs(A), np.abs(B)))
+    res = exact.residual(got_rows, 1.0, hi, lo)
+    return float(np.max(np.abs(res) / bound))
 
 
 def run_reference(args):
@@ -208,7 +254,7 @@ def run_reference(args):
     rec = dict(rec, value=value, sample=f"{rows} of {n} rows of C = A B per step "
                                          f"(n = {n}), plain C oracle")
     metric, config = dgemm_metric_config(n, args.slices, args.gpus)
-    out = {"impl": "reference", "metric": metric, "value": value,
+    out = {"impl": "reference", "path": CPU_PATH, "metric": metric, "value": value,
            "unit": "TFLOP/s", "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
            "ms_per_step": dt / args.steps * 1e3, "higher_is_better": True, "scaling": "weak",
            "vs_baseline": None, "dtype": "f64",
@@ -268,17 +314,16 @@ def _time_stream(torch, fn, steps, warmup):
     return e0.elapsed_time(e1) / steps
 
 
-def run_grouped(args):
+def grouped_measure(args, steps, warmup, baselines=True, e2e=True):
     """2048 independent GEMMs, m, n, k log-uniform in [16, 512]: one persistent
-    launch in a CUDA graph, native and emulated, against one launch per GEMM."""
+    launch in a CUDA graph, native and emulated, against one launch per GEMM.
+    Returns the record (without printing)."""
     import numpy as np
     import torch
 
     import paper_1602_08477_gb300 as gb
     from paper_1602_08477_gb300 import autotune
     from synth import generators as g
-    torch.cuda.set_device(0)
-    gb.build()
     try:
         autotune.load()
         tuned = "shipped tuning table"
@@ -295,28 +340,30 @@ def run_grouped(args):
     clocks.start()
     time.sleep(0.3)
     plan = gb.GroupedPlan(probs, use_graph=True)
-    native_ms = _time_stream(torch, plan.run, args.steps, args.warmup)
+    native_ms = _time_stream(torch, plan.run, steps, warmup)
     info = plan.info()
-    # one launch per GEMM, same kernels' default variants, uncaptured
-    q = gb.default_queue()
+    per_ms = per_graph_ms = None
+    if baselines:
+        # one launch per GEMM, same kernels' default variants, uncaptured
+        q = gb.default_queue()
 
-    def per_gemm():
-        for p in probs:
-            gb.dgemm(p["A"], p["B"], p["C"], 1.0, 0.0, kernel="auto", queue=q)
-    per_ms = _time_stream(torch, per_gemm, max(1, args.steps // 2), 1)
-    # one launch per GEMM, captured in a CUDA graph
-    cap_stream = torch.cuda.Stream()
-    cap_q = gb.Queue(gb.Device(0), cap_stream)
-    graph = torch.cuda.CUDAGraph()
-    torch.cuda.synchronize()
-    with torch.cuda.graph(graph, stream=cap_stream):
-        for p in probs:
-            gb.dgemm(p["A"], p["B"], p["C"], 1.0, 0.0, kernel="auto", queue=cap_q)
-    per_graph_ms = _time_stream(torch, graph.replay, args.steps, 1)
+        def per_gemm():
+            for p in probs:
+                gb.dgemm(p["A"], p["B"], p["C"], 1.0, 0.0, kernel="auto", queue=q)
+        per_ms = _time_stream(torch, per_gemm, max(1, steps // 2), 1)
+        # one launch per GEMM, captured in a CUDA graph
+        cap_stream = torch.cuda.Stream()
+        cap_q = gb.Queue(gb.Device(0), cap_stream)
+        graph = torch.cuda.CUDAGraph()
+        torch.cuda.synchronize()
+        with torch.cuda.graph(graph, stream=cap_stream):
+            for p in probs:
+                gb.dgemm(p["A"], p["B"], p["C"], 1.0, 0.0, kernel="auto", queue=cap_q)
+        per_graph_ms = _time_stream(torch, graph.replay, steps, 1)
     # emulated group (same problems)
     eprobs = [dict(p, precision="emulated", C=torch.zeros_like(p["C"])) for p in probs]
     eplan = gb.GroupedPlan(eprobs, use_graph=True)
-    emu_ms = _time_stream(torch, eplan.run, args.steps, args.warmup)
+    emu_ms = _time_stream(torch, eplan.run, steps, warmup)
     einfo = eplan.info()
     clk = clocks.stop()
     pk, pk_kind = peaks()
@@ -326,23 +373,19 @@ def run_grouped(args):
     pair_flops = s * (s + 1) / 2 * flops
     out = {
         "metric": "grouped FP64 GEMM TFLOP/s (one persistent launch in a CUDA graph)",
-        "value": round(value, 4), "unit": "TFLOP/s", "n_gpus": 1, "steps": args.steps,
-        "warmup": args.warmup, "ms_per_step": round(native_ms, 4), "higher_is_better": True,
+        "value": round(value, 4), "unit": "TFLOP/s", "n_gpus": 1, "steps": steps,
+        "warmup": warmup, "ms_per_step": round(native_ms, 4), "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f64",
         "data": "synthetic (device splitmix64, uniform[-1,1])",
         "config": {"workload": f"{args.problems} independent GEMMs, m, n, k log-uniform in "
                                "[16, 512], alpha = 1, beta = 0", "tiles": tuned,
                    "flush": "none: operands (~1 GB) larger than L2"},
-        "gpu_launches": info["launches"] * args.steps,
+        "gpu_launches": info["launches"] * steps,
         "roofline": {"bound": "alu", "kernel": "grouped_native_kernel",
                      "achieved": round(value, 4), "peak": round(fp64_peak, 4),
                      "unit": "TFLOP/s", "frac": round(value / fp64_peak, 4),
                      "peak_kind": "derived: 152 SM x 4 flop/clk x 2070 MHz",
                      "algorithmic": f"sum 2mnk = {flops:.4g} flop per launch"},
-        "one_launch_per_gemm": {"ms": round(per_ms, 3), "tflops": round(flops / per_ms / 1e9, 4),
-                                "graph_ms": round(per_graph_ms, 3),
-                                "graph_tflops": round(flops / per_graph_ms / 1e9, 4),
-                                "launches": args.problems},
         "emulated": {"slices": s, "ms": round(emu_ms, 3), "tflops_fp64_equiv": round(emu_tf, 3),
                      "tensor_frac": round(pair_flops / (emu_ms * 1e-3) / 1e12 /
                                           (2.0 * pk["bf16_tflops"]), 4),
@@ -350,25 +393,44 @@ def run_grouped(args):
         "tiles": {"native": info["native_tiles"], "emulated": einfo["emulated_tiles"]},
         "e2e": None, "clocks": clk,
     }
-    # end to end: the packed operands from pinned host memory (one copy per arena),
-    # the graph-captured group, the packed results back
-    hostA = arenas["A"].cpu().pin_memory()
-    hostB = arenas["B"].cpu().pin_memory()
-    hostC = torch.empty(arenas["C"].shape, dtype=torch.float64).pin_memory()
-    h2d = (hostA.numel() + hostB.numel()) * 8
-    d2h = hostC.numel() * 8
+    if baselines:
+        out["one_launch_per_gemm"] = {
+            "ms": round(per_ms, 3), "tflops": round(flops / per_ms / 1e9, 4),
+            "graph_ms": round(per_graph_ms, 3),
+            "graph_tflops": round(flops / per_graph_ms / 1e9, 4), "launches": args.problems}
+    if e2e:
+        # end to end: the packed operands from pinned host memory (one copy per
+        # arena), the graph-captured group, the packed results back
+        hostA = arenas["A"].cpu().pin_memory()
+        hostB = arenas["B"].cpu().pin_memory()
+        hostC = torch.empty(arenas["C"].shape, dtype=torch.float64).pin_memory()
+        h2d = (hostA.numel() + hostB.numel()) * 8
+        d2h = hostC.numel() * 8
 
-    def e2e():
-        arenas["A"].copy_(hostA, non_blocking=True)
-        arenas["B"].copy_(hostB, non_blocking=True)
-        plan.run()
-        hostC.copy_(arenas["C"], non_blocking=True)
-    e2e_ms = _time_stream(torch, e2e, max(1, args.steps // 2), 1)
-    out["e2e"] = {"value": round(flops / e2e_ms / 1e9, 4), "unit": "TFLOP/s",
-                  "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h)}
+        def e2e_step():
+            arenas["A"].copy_(hostA, non_blocking=True)
+            arenas["B"].copy_(hostB, non_blocking=True)
+            plan.run()
+            hostC.copy_(arenas["C"], non_blocking=True)
+        e2e_ms = _time_stream(torch, e2e_step, max(1, steps // 2), 1)
+        out["e2e"] = {"value": round(flops / e2e_ms / 1e9, 4), "unit": "TFLOP/s",
+                      "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h)}
     plan.close()
     eplan.close()
-    print(json.dumps(out), flush=True)
+    del probs, eprobs, arenas
+    torch.cuda.synchronize()
+    torch.cuda.empty_cache()
+    return out
+
+
+def run_grouped(args):
+    """The grouped workload alone (its own JSON line)."""
+    import torch
+
+    import paper_1602_08477_gb300 as gb
+    torch.cuda.set_device(0)
+    gb.build()
+    print(json.dumps(grouped_measure(args, args.steps, args.warmup)), flush=True)
     return 0
 
 
@@ -461,6 +523,29 @@ def _serve_summary(st):
 SERVE_SLICES = 12
 
 
+def serve_warm(args, gb, s):
+    """Warm the serving kernels on a few small requests (not counted)."""
+    srv = gb.Server(int(args.serve_budget_gb * 2 ** 30), n_streams=args.serve_streams,
+                    max_batch=args.serve_batch)
+    for i in range(4):
+        srv.submit(64, 64, 64, precision="emulated" if i % 2 else "native", slices=s, seed=i)
+    srv.drain(60)
+    srv.close()
+
+
+def serve_record(args, gb, g, np, rate, seconds):
+    """A short run of the serving trace at `rate` requests/s: the summary."""
+    a = argparse.Namespace(**vars(args))
+    a.serve_rate, a.serve_seconds = rate, seconds
+    st = _serve_trace(a, gb, g, np, args.serve_batch)
+    out = _serve_summary(st)
+    out["rate_per_s"] = rate
+    out["seconds"] = seconds
+    out["offered_tflops"] = round(st["offered_tflops"], 3)
+    out["clocks"] = st["clocks"]
+    return out
+
+
 def run_serve(args):
     """Poisson arrivals of square GEMMs, n log-uniform in [64, 4096], 20% emulated,
     HBM-budget admission, continuous batching; p50/p99 latency and TFLOP/s, beside
@@ -478,13 +563,7 @@ def run_serve(args):
     except Exception:
         pass
     s = SERVE_SLICES
-    # warm the kernels on a few small requests (not counted)
-    srv = gb.Server(int(args.serve_budget_gb * 2 ** 30), n_streams=args.serve_streams,
-                    max_batch=args.serve_batch)
-    for i in range(4):
-        srv.submit(64, 64, 64, precision="emulated" if i % 2 else "native", slices=s, seed=i)
-    srv.drain(60)
-    srv.close()
+    serve_warm(args, gb, s)
     st = _serve_trace(args, gb, g, np, args.serve_batch)
     single = None if args.no_serve_baseline else _serve_trace(args, gb, g, np, 1, "fifo")
     serve = _serve_summary(st)
@@ -684,6 +763,67 @@ def run_daxpy(args):
     return 0
 
 
+def hard_record(args, gb, g, np, torch, A, B, C, q):
+    """The 16-decade hard set at n, emulated with the slice count it needs
+    (--hard-slices), the whole path (split + products) per step; rho of both
+    paths against the double-double reference on sampled rows."""
+    n, s = args.n, args.hard_slices
+    seed = g.BASE_SEED + 3
+    A_h = matrix_threads("hard", n, n, seed, g.STREAM_A)
+    B_h = matrix_threads("hard", n, n, seed, g.STREAM_B)
+    A.copy_(torch.from_numpy(A_h))
+    B.copy_(torch.from_numpy(B_h))
+    ws = gb.alloc_workspace(gb.workspace_size("emulated", s, n, n, n))
+    clocks = ClockSampler(0)
+    clocks.start()
+    step = lambda: gb.dgemm(A, B, C, precision="emulated", slices=s, queue=q, workspace=ws)
+    ms = _time_stream(torch, step, 5, 2)
+    clk = clocks.stop()
+    q.wait()
+    rows = np.random.default_rng(n + s).choice(n, 4, replace=False)
+    got_e = C[torch.from_numpy(rows).cuda()].cpu().numpy()
+    Cn = torch.zeros_like(C)
+    gb.dgemm(A, B, Cn, 1.0, 0.0, kernel="auto", queue=q)
+    got_n = Cn[torch.from_numpy(rows).cuda()].cpu().numpy()
+    from oracle import cgemm
+    hilo = cgemm.dgemm_dd_rows(A_h, B_h, rows)
+    del ws, Cn
+    torch.cuda.empty_cache()
+    return {"workload": f"square DGEMM C = A B, n = {n}, entries +-(1+f) 2^E with E uniform in "
+                        "[-27, 26] (16 decades), random signs",
+            "slices": s, "ms_per_step": round(ms, 3),
+            "tflops": round(2.0 * n ** 3 / (ms * 1e-3) / 1e12, 3),
+            "rho_emulated": rho_rows(got_e, A_h, B_h, rows, hilo),
+            "rho_native": rho_rows(got_n, A_h, B_h, rows, hilo),
+            "rows_checked": len(rows), "steps": 5, "warmup": 2, "clocks": clk}
+
+
+def grouped_sub_record(args):
+    """The grouped workload, summarised for the default line."""
+    r = grouped_measure(args, 5, 2, baselines=True, e2e=False)
+    return {"workload": r["config"]["workload"], "tiles": r["config"]["tiles"],
+            "native_tflops": r["value"], "native_ms": r["ms_per_step"],
+            "native_frac_fp64_peak": r["roofline"]["frac"],
+            "emulated": r["emulated"], "one_launch_per_gemm": r["one_launch_per_gemm"],
+            "launches_per_step": r["gpu_launches"] // 5, "clocks": r["clocks"]}
+
+
+SUSTAINABLE_RATE = 100.0
+
+
+def serve_sub_record(args, gb, g, np):
+    """Two short serving runs: the specified 2000 requests/s (overloaded: large
+    native requests queue without bound) and a rate the GPU sustains."""
+    serve_warm(args, gb, SERVE_SLICES)
+    out = {"workload": "Poisson arrivals, square n log-uniform in [64, 4096], 20% emulated "
+                       f"(s = {SERVE_SLICES}), {args.serve_budget_gb:g} GB budget, "
+                       f"{args.serve_streams} streams, batches of <= {args.serve_batch}"}
+    out["specified_rate"] = serve_record(args, gb, g, np, args.serve_rate, args.sub_serve_seconds)
+    out["sustainable_rate"] = serve_record(args, gb, g, np, SUSTAINABLE_RATE,
+                                           args.sub_serve_seconds)
+    return out
+
+
 def main():
     args = parse()
     if args.impl == "reference":
@@ -726,8 +866,8 @@ def main():
 
     n, s = args.n, args.slices
     seed = g.BASE_SEED + 1
-    A_h = g.matrix("uniform", n, n, seed, g.STREAM_A)
-    B_h = g.matrix("uniform", n, n, seed, g.STREAM_B)
+    A_h = matrix_threads("uniform", n, n, seed, g.STREAM_A)
+    B_h = matrix_threads("uniform", n, n, seed, g.STREAM_B)
     A = torch.from_numpy(A_h).cuda()
     B = torch.from_numpy(B_h).cuda()
     C = torch.zeros((n, n), dtype=torch.float64, device="cuda")
@@ -817,6 +957,7 @@ def main():
 
     metric, config = dgemm_metric_config(n, s, world)
     out = {
+        "path": gpu_path(s),
         "metric": metric,
         "value": round(value, 3), "unit": "TFLOP/s", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": round(ms_step, 4), "higher_is_better": True,
@@ -852,10 +993,22 @@ def main():
         bound = exact.error_bound(n, 1.0, absab)
         got_e = emu_C[torch.from_numpy(sel).cuda()].cpu().numpy()
         got_n = Cn[torch.from_numpy(sel).cuda()].cpu().numpy()
-        out["parity"] = {"rows_checked": int(len(sel)),
-                         "emulated_max_err_over_bound": float(np.max(np.abs(got_e - Crows) / bound)),
-                         "native_max_err_over_bound": float(np.max(np.abs(got_n - Crows) / bound)),
-                         "note": "vs the FP64 oracle's rows (itself within the bound)"}
+        hilo = cgemm.dgemm_dd_rows(A_h, B_h, sel)
+        out["parity"] = {
+            "rows_checked": int(len(sel)),
+            "rho_emulated": rho_rows(got_e, A_h, B_h, sel, hilo),
+            "rho_native": rho_rows(got_n, A_h, B_h, sel, hilo),
+            "emulated_vs_oracle_over_bound": float(np.max(np.abs(got_e - Crows) / bound)),
+            "native_vs_oracle_over_bound": float(np.max(np.abs(got_n - Crows) / bound)),
+            "note": "rho = max |C - C*| / (2 (k+2) u |A||B|), C* the double-double value of A B "
+                    "on the sampled rows; the *_vs_oracle figures compare with the FP64 oracle's "
+                    "own rows, which carry their own rounding error"}
+    if rank == 0 and world == 1 and not args.no_sub_records:
+        del A_p, B_p, C_p, hws
+        torch.cuda.empty_cache()
+        out["hard"] = hard_record(args, gb, g, np, torch, A, B, C, q)
+        out["grouped"] = grouped_sub_record(args)
+        out["serve"] = serve_sub_record(args, gb, g, np)
     if rank == 0:
         print(json.dumps(out), flush=True)
     if world > 1:
