@@ -23,7 +23,10 @@ extern "C" {
  * process: a CUDA runtime kernel pointer, or one returned by gb_kernel_handle)
  * on q with the work division wd and the argument array `args` (one pointer per
  * kernel parameter, as cudaLaunchKernel takes them) and `shared_bytes` of
- * dynamic shared memory.  Dimension d of a D-dimensional work division runs on
+ * dynamic shared memory.  The library uses the shared CUDA runtime
+ * (libcudart.so.13): a kernel compiled into the caller's own module is found
+ * when that module links the same shared runtime (nvcc --cudart shared), so
+ * that its kernels register where the library launches them.  Dimension d of a D-dimensional work division runs on
  * the CUDA axis x for d = D-1, y for d = D-2, z for d = D-3
  * (include/gb_workdiv_device.cuh gives the matching device-side index
  * functions); the element level is the kernel's own loop.

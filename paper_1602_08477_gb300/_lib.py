@@ -121,6 +121,14 @@ def load():
                 raise RuntimeError(
                     f"the CUDA library is not built ({LIB_PATH} missing); run "
                     "`python -c 'import __graft_entry__ as g; g.build()'` first")
+            # PyTorch loads its CUDA runtime (libcudart.so.13) by path; loading it
+            # first lets the library bind to that same copy, so one runtime holds
+            # every module's kernels (the library's, PyTorch's, and a caller's own
+            # kernels launched through gb_enqueue)
+            try:
+                import torch  # noqa: F401
+            except ImportError:
+                pass
             lib = ctypes.CDLL(LIB_PATH)
             _apply(lib, SIGNATURES)
             _lib = lib

@@ -3,6 +3,11 @@
 Every translation unit is compiled by nvcc for sm_103a only
 (-gencode arch=compute_103a,code=sm_103a), in parallel, then linked into one
 shared library with the C ABI of include/gb_gemm.h.  Rebuilds only what changed.
+
+The library links the CUDA runtime as a shared library (libcudart.so, the one
+PyTorch also loads), not nvcc's default static copy: kernels that a caller
+compiles into its own module register with that same runtime, so the runtime
+kernel handles they pass to gb_enqueue resolve inside the library.
 """
 from __future__ import annotations
 
@@ -29,6 +34,15 @@ def _nvcc() -> str:
         if cand and os.path.exists(cand):
             return cand
     raise RuntimeError("nvcc not found: the CUDA toolkit is required to build the library")
+
+
+def cuda_libdir(nvcc: str) -> str:
+    """The toolkit's library directory (holds libcudart.so) next to nvcc."""
+    root = os.path.dirname(os.path.dirname(os.path.realpath(nvcc)))
+    for sub in ("lib64", "lib"):
+        if os.path.isdir(os.path.join(root, sub)):
+            return os.path.join(root, sub)
+    return os.path.join(root, "lib64")
 
 
 def _sources():
@@ -73,14 +87,16 @@ def build(verbose: bool = False, ptxas_info: bool = False) -> str:
                     sys.stderr.write(r.stdout + r.stderr)
                 if r.returncode != 0:
                     raise RuntimeError(f"nvcc failed: {' '.join(cmd)}")
-    if jobs or _stale(LIB, objs):
+    if jobs or _stale(LIB, objs) or _stale(LIB, [os.path.abspath(__file__)]):
         tmp = LIB + f".tmp{os.getpid()}"
-        cmd = [nvcc, *ARCH, "-shared", "-o", tmp, *objs, "-lcuda"]
+        link = [nvcc, *ARCH, "-shared", "--cudart", "shared", "-Xlinker", "-rpath",
+                "-Xlinker", cuda_libdir(nvcc), "-o", tmp, *objs]
+        cmd = link + ["-lcuda"]
         r = subprocess.run(cmd, capture_output=True, text=True)
         if r.returncode != 0:
             # libcuda is resolved at run time through the runtime's entry-point query;
             # link without it where no driver library is present at build time.
-            cmd = [nvcc, *ARCH, "-shared", "-o", tmp, *objs]
+            cmd = link
             r = subprocess.run(cmd, capture_output=True, text=True)
         if r.returncode != 0:
             sys.stderr.write(r.stdout + r.stderr)

@@ -148,3 +148,16 @@ def test_host_buffer_gemm_rejects_bad_arguments_before_any_device_work(lib):
     assert lib.gb_dgemm_host(fake_q, 1, 10, 4, 4, 4, 1.0, p, 3, p, 4, 0.0, p, 4, None, 0) == 1
     assert lib.gb_dgemm_host(fake_q, 7, 10, 4, 4, 4, 1.0, p, 4, p, 4, 0.0, p, 4, None, 0) == 1
     assert lib.gb_dgemm_host(fake_q, 1, 99, 4, 4, 4, 1.0, p, 4, p, 4, 0.0, p, 4, None, 0) == 1
+
+
+def test_library_binds_the_shared_cuda_runtime(lib):
+    # the library links libcudart.so (not a private static runtime), so a caller's
+    # own kernels, compiled against the same shared runtime, launch through
+    # gb_enqueue; loaded alone (no PyTorch) it brings that runtime in itself
+    import subprocess
+    import sys
+    code = ("import ctypes, sys; ctypes.CDLL(sys.argv[1]); "
+            "print(any('libcudart.so' in l for l in open('/proc/self/maps')))")
+    r = subprocess.run([sys.executable, "-c", code, _lib.LIB_PATH], capture_output=True,
+                       text=True, check=True)
+    assert r.stdout.strip() == "True"
