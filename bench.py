@@ -58,7 +58,9 @@ def parse():
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--cpu-seconds", type=float, default=12.0)
     p.add_argument("--workload", default="dgemm",
-                   choices=["dgemm", "grouped", "serve", "sweep", "d0", "daxpy"])
+                   choices=["dgemm", "grouped", "serve", "serve-sweep", "sweep", "d0", "daxpy"])
+    p.add_argument("--rates", default="50,75,100,125,150,200",
+                   help="arrival rates (requests/s) of --workload serve-sweep")
     p.add_argument("--sizes", default="1024,2048,4096,8192,10240")
     p.add_argument("--problems", type=int, default=2048)
     p.add_argument("--serve-seconds", type=float, default=60.0)
@@ -476,8 +478,10 @@ def _serve_trace(args, gb, g, np, max_batch, policy="lanes"):
     done_native = done_emu = 0.0
     lane_lat = {"small": [], "large": []}
     lane_count = {"small": 0, "large": 0}
-    for rid, n, prec in ids:
+    arrival_lat = []  # (arrival second, latency ms or None when not completed)
+    for idx, (rid, n, prec) in enumerate(ids):
         done, status, lat = srv.poll(rid)
+        arrival_lat.append((float(arrivals[idx]), lat if done and status == 0 else None))
         lane = "large" if prec == "native" and 2.0 * n ** 3 >= 2.0 ** 31 else "small"
         lane_count[lane] += 1
         if done and status == 0:
@@ -499,6 +503,7 @@ def _serve_trace(args, gb, g, np, max_batch, policy="lanes"):
     st["clocks"] = clk
     st["submitted_here"] = submitted
     st["queue_trace"] = queue_trace
+    st["arrival_lat"] = arrival_lat
     # latency per class of request (the lanes' rule: native and 2 n^3 >= 2^31 is
     # large), completed requests only, with how many of the class were submitted
     st["by_class"] = {
@@ -543,6 +548,7 @@ def serve_record(args, gb, g, np, rate, seconds):
     out["seconds"] = seconds
     out["offered_tflops"] = round(st["offered_tflops"], 3)
     out["clocks"] = st["clocks"]
+    out.update(stability(st, seconds))
     return out
 
 
@@ -599,6 +605,64 @@ def run_serve(args):
                                           note="same arrival trace, one queue in arrival "
                                                "order, every GEMM its own grouped launch")
     print(json.dumps(out), flush=True)
+    return 0
+
+
+def stability(st, seconds):
+    """p99 latency of the requests that arrived in the first and in the second
+    half of the run (a request still unfinished at the end counts as waiting
+    until the end), and whether the run was sustainable: every request finished
+    and p99 did not grow from the first half to the second by more than half."""
+    import numpy as np
+    halves = ([], [])
+    unfinished = 0
+    for t, lat in st["arrival_lat"]:
+        if lat is None:
+            unfinished += 1
+            lat = (seconds - t) * 1e3
+        halves[0 if t < seconds / 2 else 1].append(lat)
+    p99 = [float(np.percentile(h, 99)) if h else None for h in halves]
+    ok = unfinished == 0 and p99[0] is not None and p99[1] is not None and p99[1] <= 1.5 * p99[0]
+    return {"p99_first_half_ms": round(p99[0], 2) if p99[0] is not None else None,
+            "p99_second_half_ms": round(p99[1], 2) if p99[1] is not None else None,
+            "unfinished": unfinished, "sustainable": bool(ok)}
+
+
+def run_serve_sweep(args):
+    """Serving at increasing Poisson arrival rates (--rates, --serve-seconds each,
+    the specified size and precision mix): p50/p99, TFLOP/s and whether p99 stays
+    flat over the run; the highest rate that does is the sustainable rate."""
+    import numpy as np
+    import torch
+
+    import paper_1602_08477_gb300 as gb
+    from paper_1602_08477_gb300 import autotune
+    from synth import generators as g
+    torch.cuda.set_device(0)
+    gb.build()
+    try:
+        autotune.load()
+    except Exception:
+        pass
+    serve_warm(args, gb, SERVE_SLICES)
+    res = []
+    for rate in (float(x) for x in args.rates.split(",")):
+        a = argparse.Namespace(**vars(args))
+        a.serve_rate = rate
+        st = _serve_trace(a, gb, g, np, args.serve_batch)
+        rec = dict(_serve_summary(st), rate_per_s=rate, offered_tflops=round(st["offered_tflops"], 3),
+                   clocks=st["clocks"])
+        rec.update(stability(st, args.serve_seconds))
+        res.append(rec)
+    ok = [r["rate_per_s"] for r in res if r["sustainable"]]
+    print(json.dumps({"metric": "serving p50/p99 latency (ms) and TFLOP/s per arrival rate",
+                      "unit": "ms", "seconds_per_rate": args.serve_seconds,
+                      "config": {"workload": "Poisson arrivals, square n log-uniform in [64, 4096], "
+                                             f"20% emulated (s = {SERVE_SLICES}), "
+                                             f"{args.serve_budget_gb:g} GB budget",
+                                 "streams": args.serve_streams, "max_batch": args.serve_batch},
+                      "highest_sustainable_rate_per_s": max(ok) if ok else None,
+                      "rates": res}), flush=True)
     return 0
 
 
@@ -832,6 +896,8 @@ def main():
         return run_grouped(args)
     if args.workload == "serve":
         return run_serve(args)
+    if args.workload == "serve-sweep":
+        return run_serve_sweep(args)
     if args.workload == "sweep":
         return run_sweep(args)
     if args.workload == "d0":

@@ -158,3 +158,57 @@ def test_request_that_never_fits_is_rejected_on_the_host(gb):
     assert srv.poll(ok)[0]
     assert srv.stats()["rejected"] == 1
     srv.close()
+
+
+def test_requests_admitted_while_a_large_gemm_runs(gb):
+    # continuous batching: a large native GEMM (n = 6144, ~0.37 s on the FP64
+    # pipe) is on the device when 24 small requests arrive; they are admitted,
+    # batched and finished while it still runs, and every result (the large one
+    # too) equals the same request served alone, bit for bit
+    import time
+    import torch
+    big = 6144
+    srv = gb.Server(hbm_budget_bytes=2 << 30, n_streams=4, max_batch=8)
+    big_out = np.empty((big, big))
+    big_id = srv.submit(big, big, big, 1.0, 0.0, "native", 0, out=big_out, seed=9100)
+    t0 = time.perf_counter()
+    while srv.stats()["in_flight"] == 0 and time.perf_counter() - t0 < 10:
+        time.sleep(0.001)
+    assert srv.stats()["in_flight"] >= 1
+    reqs = _requests(24, 9200)
+    outs, ids = [], []
+    for r in reqs:
+        out = np.empty((r["m"], r["n"]))
+        outs.append(out)
+        ids.append(srv.submit(r["m"], r["n"], r["k"], r["alpha"], r["beta"], r["precision"],
+                              r["slices"], A=r["A"], B=r["B"], C=r["C"], out=out))
+    while not all(srv.poll(i)[0] for i in ids) and time.perf_counter() - t0 < 60:
+        time.sleep(0.001)
+    assert all(srv.poll(i)[0] for i in ids)
+    # the small requests finished while the large GEMM was still on the device
+    assert not srv.poll(big_id)[0]
+    srv.drain(120)
+    assert srv.poll(big_id)[0] and srv.poll(big_id)[1] == 0
+    srv.close()
+    for r, out in zip(reqs, outs):
+        solo = gb.Server(hbm_budget_bytes=64 << 20, n_streams=1, max_batch=1)
+        alone = np.empty((r["m"], r["n"]))
+        solo.submit(r["m"], r["n"], r["k"], r["alpha"], r["beta"], r["precision"], r["slices"],
+                    A=r["A"], B=r["B"], C=r["C"], out=alone)
+        solo.drain(600)
+        solo.close()
+        assert np.array_equal(alone, out)
+    solo = gb.Server(hbm_budget_bytes=2 << 30, n_streams=1, max_batch=1)
+    alone = np.empty((big, big))
+    solo.submit(big, big, big, 1.0, 0.0, "native", 0, out=alone, seed=9100)
+    solo.drain(120)
+    solo.close()
+    assert np.array_equal(alone, big_out)
+    # and the large result against the oracle on sampled rows
+    rows = np.array([0, 1777, big - 1])
+    A = g.matrix("uniform", big, big, 9100, 0, row_indices=rows)
+    B = g.matrix("uniform", big, big, 9100, 1)
+    ref = cgemm.dgemm(1.0, A, B)
+    bound = exact.error_bound(big, 1.0, cgemm.dgemm(1.0, np.abs(A), np.abs(B)))
+    assert np.all(np.abs(big_out[rows] - ref) <= 2 * bound)
+    torch.cuda.synchronize()
