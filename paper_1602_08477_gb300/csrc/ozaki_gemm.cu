@@ -148,9 +148,10 @@ struct TileArgs {
 // count S: for a fixed A slice p the pairs (p, q), q = 1 .. S+1-p, land in the
 // consecutive levels p-1 .. S-1, whose accumulators are consecutive TMEM column
 // blocks, and the B slices q are consecutive in shared memory.  So one MMA with
-// N = 32 (S+1-p) (split at the 256-column limit) covers them all, reading the A
-// tile once.  Fully unrolled: descriptor offsets are immediates, so the single
-// issuing thread spends a few instructions per MMA.
+// N = BN (S+1-p) covers them all, reading the A tile once (above the 256-column
+// limit, two MMAs that share the A tile through the collector buffer).  Fully
+// unrolled: descriptor offsets are immediates, so the single issuing thread
+// spends a few instructions per MMA.
 // Split accumulators (kSplit): slices p <= G = split_point(S) accumulate into
 // the level columns 0 .. 32 S, slices p > G into a second set of the levels
 // G .. S-1 at columns 32 S + 32 (L - G), so no accumulator collects more than
@@ -172,14 +173,18 @@ __device__ __forceinline__ void issue_kblock(uint64_t adesc, uint64_t bdesc, uin
         const uint32_t col0 = p > G ? (uint32_t)(BN * S + (p - 1 - G) * BN)
                                     : (uint32_t)((p - 1) * BN);
         const int rows = BN * (S + 1 - p);
-#pragma unroll
-        for (int r0 = 0; r0 < BN * S; r0 += 256) {
-            if (r0 < rows) {
-                const int nn = rows - r0 < 256 ? rows - r0 : 256;
-                const uint64_t bd = bdesc + (uint64_t)((r0 * kBKBytes) >> 4);
-                ptx::mma_e4m3(tmem_base + col0 + (uint32_t)r0, ad, bd,
-                              ptx::idesc_e4m3_f32(kBM, nn), acc);
-            }
+        if (rows <= 256) {
+            ptx::mma_e4m3(tmem_base + col0, ad, bdesc, ptx::idesc_e4m3_f32(kBM, rows), acc);
+        } else {
+            // N above the 256-column limit: two MMAs on the same A tile, which the
+            // second takes from the collector buffer instead of shared memory
+            // (shared-memory bandwidth bounds this kernel)
+            static_assert(BN * S <= 512, "at most two MMAs per A slice");
+            ptx::mma_e4m3_collect<ptx::ACollector::kFill>(tmem_base + col0, ad, bdesc,
+                                                          ptx::idesc_e4m3_f32(kBM, 256), acc);
+            ptx::mma_e4m3_collect<ptx::ACollector::kLastUse>(
+                tmem_base + col0 + 256u, ad, bdesc + (uint64_t)((256 * kBKBytes) >> 4),
+                ptx::idesc_e4m3_f32(kBM, rows - 256), acc);
         }
     }
 }

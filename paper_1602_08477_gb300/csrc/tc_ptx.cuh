@@ -141,6 +141,36 @@ __device__ __forceinline__ void mma_e4m3(uint32_t tmem_d, uint64_t adesc, uint64
         : "memory");
 }
 
+// The same MMA with the A operand kept in the tensor core's collector buffer:
+// A_FILL reads A from shared memory and keeps it, A_LASTUSE takes A from the
+// collector (the descriptor must name the same A as the filling MMA) and then
+// releases it, so two MMAs of one A tile read it from shared memory once.
+enum class ACollector { kFill, kLastUse };
+
+template <ACollector U>
+__device__ __forceinline__ void mma_e4m3_collect(uint32_t tmem_d, uint64_t adesc, uint64_t bdesc,
+                                                 uint32_t idesc, uint32_t accumulate) {
+    if constexpr (U == ACollector::kFill) {
+        asm volatile(
+            "{\n"
+            ".reg .pred p;\n"
+            "setp.ne.b32 p, %4, 0;\n"
+            "tcgen05.mma.cta_group::1.kind::f8f6f4.collector::a::fill [%0], %1, %2, %3, p;\n"
+            "}\n" ::"r"(tmem_d),
+            "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate)
+            : "memory");
+    } else {
+        asm volatile(
+            "{\n"
+            ".reg .pred p;\n"
+            "setp.ne.b32 p, %4, 0;\n"
+            "tcgen05.mma.cta_group::1.kind::f8f6f4.collector::a::lastuse [%0], %1, %2, %3, p;\n"
+            "}\n" ::"r"(tmem_d),
+            "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate)
+            : "memory");
+    }
+}
+
 // Arrive on `bar` once all tcgen05 operations issued so far by this thread completed.
 __device__ __forceinline__ void mma_commit(uint64_t* bar) {
     asm volatile(
