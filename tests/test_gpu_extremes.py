@@ -157,14 +157,14 @@ def test_native_overflow_to_signed_infinity(gb, kernel):
 
 @pytest.mark.parametrize("kernel", ["auto", "naive", "tiled", "dfma", "dmma"])
 def test_native_rounded_subnormal_products_within_widened_bound(gb, kernel):
-    # uniform rows at 2^-540 against columns at 2^-536: products near 2^-1076 are
+    # uniform rows at 2^-530 against columns at 2^-532: products near 2^-1064 are
     # rounded to the subnormal grid (absolute error up to 2^-1075 each), so the
     # relative FP64 bound is widened by (k + 2) 2^-1074 for the kernel and the
     # oracle alike
     import torch
     m, n, k = 80, 60, 128
-    A = np.ldexp(g.matrix("uniform", m, k, 95, 0), -540)
-    B = np.ldexp(g.matrix("uniform", k, n, 95, 1), -536)
+    A = np.ldexp(g.matrix("uniform", m, k, 95, 0), -530)
+    B = np.ldexp(g.matrix("uniform", k, n, 95, 1), -532)
     dC = torch.zeros((m, n), dtype=torch.float64, device="cuda")
     gb.dgemm(to_dev(A), to_dev(B), dC, 1.0, 0.0, kernel=kernel)
     torch.cuda.synchronize()
