@@ -49,12 +49,6 @@ constexpr uint32_t kTmemCols = 512;
 constexpr uint64_t kWaitTimeoutNs = 4000000000ull;  // 4 s
 constexpr int kSmemLimit = 227 * 1024;
 
-struct SmemTail {
-    uint64_t bars[2 * 8 + 3];
-    uint32_t tmem_holder;
-    int abort;
-};
-
 struct I128 {
     int64_t hi;
     uint64_t lo;
@@ -63,24 +57,17 @@ struct I128 {
 // RN(T * 2^E) as an FP64 (T a signed 128-bit integer, E any int): the double
 // nearest to the exact value, ties to even, with gradual underflow (subnormal
 // results carry the unit 2^-1074) and overflow to +-Inf.  One rounding, done on
-// the integer: the result's last place sits at bit q of |T|, q = p - 52 for a
-// normal result (p = index of the leading one) or q = -1074 - E for a subnormal
-// one; |T| is rounded at bit q and the bit pattern is assembled directly, so no
-// FP64 multiplication (and no power of two outside the double range) is used.
-__device__ __forceinline__ double i128_to_double_scaled(I128 x, int E) {
-    const bool neg = x.hi < 0;
-    uint64_t hi = (uint64_t)x.hi, lo = x.lo;
-    if (neg) {
-        lo = ~lo + 1;
-        hi = ~hi + (lo == 0 ? 1 : 0);
-    }
-    if (hi == 0 && lo == 0) return 0.0;
-    int p = hi ? 64 + 63 - __clzll((long long)hi) : 63 - __clzll((long long)lo);
-    const bool sub = -1074 - E > p - 52;  // the result lies below 2^-1022
-    const int q = sub ? -1074 - E : p - 52;
-    uint64_t M;  // |T| / 2^q rounded: the significand (normal) or the bit pattern (subnormal)
+// the integer, so no FP64 multiplication (and no power of two outside the double
+// range) is used.  Normal results (the usual case) take a branch-free path: |T|
+// is shifted so that its leading one sits at bit 127, the significand is then
+// bits 75..127, the round bit bit 74 and the sticky bits 0..73.  Subnormal
+// results round |T| at bit q = -1074 - E instead (the general path).
+__device__ __forceinline__ double i128_to_double_subnormal(uint64_t hi, uint64_t lo, int p, int E,
+                                                        bool neg) {
+    const int q = -1074 - E;  // > p - 52: the last place of the subnormal grid
+    uint64_t M;               // |T| / 2^q rounded: the subnormal's bit pattern
     if (q <= 0) {
-        M = lo << (-q);  // exact: q <= 0 means p <= 52 and |T| < 2^53
+        M = lo << (-q);  // exact: q <= 0 here means p <= 52 and |T| < 2^53
     } else if (q > p + 1) {
         M = 0;           // below half of the last place
     } else if (q == p + 1) {
@@ -110,19 +97,36 @@ __device__ __forceinline__ double i128_to_double_scaled(I128 x, int E) {
         const bool eq = rem_hi == half_hi && rem_lo == half_lo;
         if (gt || (eq && (M & 1))) M += 1;
     }
-    uint64_t bits;
-    if (sub) {
-        // M <= 2^52: the subnormal's bit pattern (2^52 is the smallest normal's)
-        bits = M;
-    } else {
-        if (M == (1ull << 53)) {  // rounding carried into a new binade
-            M >>= 1;
-            p += 1;
-        }
-        const int biased = p + E + 1023;  // >= 1: not subnormal
-        bits = biased >= 2047 ? 0x7FF0000000000000ull
-                              : (((uint64_t)biased << 52) | (M & 0xFFFFFFFFFFFFFull));
-    }
+    // M <= 2^52: the subnormal's bit pattern (2^52 is the smallest normal's)
+    return __longlong_as_double((long long)(M | (neg ? 0x8000000000000000ull : 0ull)));
+}
+
+__device__ __forceinline__ double i128_to_double_scaled(I128 x, int E) {
+    const bool neg = x.hi < 0;
+    uint64_t hi = (uint64_t)x.hi, lo = x.lo;
+    // |T| (two's complement negation of the 128-bit value when negative)
+    lo = neg ? ~lo + 1 : lo;
+    hi = neg ? ~hi + (lo == 0 ? 1 : 0) : hi;
+    if ((hi | lo) == 0) return 0.0;
+    const int p = hi ? 127 - __clzll((long long)hi) : 63 - __clzll((long long)lo);
+    const int eb = p + E + 1023;  // biased exponent before a rounding carry
+    if (eb < 1) return i128_to_double_subnormal(hi, lo, p, E, neg);
+    // leading one to bit 127: by 64 first when the high word is empty
+    const int c = 127 - p;                    // 0 .. 127
+    const uint64_t h1 = c >= 64 ? lo : hi;
+    const uint64_t l1 = c >= 64 ? 0 : lo;
+    const int c1 = c & 63;
+    const uint64_t nh = c1 ? (h1 << c1) | (l1 >> (64 - c1)) : h1;
+    const uint64_t nl = l1 << c1;
+    uint64_t M = nh >> 11;                                  // 53 bits, leading one at 52
+    const bool rb = (nh >> 10) & 1;                         // half of the last place
+    const bool sticky = ((nh & 0x3FFull) | nl) != 0;        // anything below it
+    M += (rb && (sticky || (M & 1))) ? 1 : 0;               // nearest, ties to even
+    const bool carry = (M >> 53) != 0;                      // rounded up to 2^53
+    M = carry ? M >> 1 : M;
+    const int e = eb + (carry ? 1 : 0);
+    const uint64_t bits = e >= 2047 ? 0x7FF0000000000000ull
+                                    : (((uint64_t)e << 52) | (M & 0xFFFFFFFFFFFFFull));
     // sign by bit manipulation: GB300's FP64 pipe is slow even for negation
     return __longlong_as_double((long long)(bits | (neg ? 0x8000000000000000ull : 0ull)));
 }
@@ -139,6 +143,21 @@ struct TileArgs {
     double* C;
     const int32_t* eA;  // row exponents (indexed by row)
     const int32_t* fB;  // column exponents (indexed by column)
+};
+
+// Tile arguments travel from the producer, which resolves each tile once (for a
+// group: a binary search of the tile prefix and the problem record, thousands of
+// cycles of dependent loads), to the MMA issuer and the epilogue warps through a
+// ring of kArgSlots records in shared memory.
+constexpr int kArgSlots = 4;
+
+struct SmemTail {
+    uint64_t bars[2 * 8 + 3];
+    uint64_t args_full[kArgSlots];   // the producer wrote the record
+    uint64_t args_empty[kArgSlots];  // the MMA issuer and every epilogue warp copied it
+    TileArgs args[kArgSlots];
+    uint32_t tmem_holder;
+    int abort;
 };
 
 // One 128 x BN output tile: level sums on the tensor cores, recombination into
@@ -273,33 +292,51 @@ __device__ __forceinline__ void add_levels_part(uint32_t lane_addr, int cg, bool
                                                 I128 (&T)[BN / 4]) {
     constexpr int kRun = 6;
     constexpr int split_g = kSplit ? split_point(S) : S;
+    // levels read NB at a time, one wait per batch: the reads of a tile end hold
+    // up the next tile's MMAs, and each wait costs a TMEM load round trip
+    // (16 loaded values per batch with the 48-column tiles' 12 128-bit sums, 24
+    // with 32-column tiles, 16 when split accumulators double the loads)
+    constexpr int NB = (BN == 48 || kSplit ? 16 : 24) / W;
     int64_t G[W];
 #pragma unroll
     for (int j = 0; j < W; ++j) G[j] = 0;
 #pragma unroll
-    for (int L = 0; L < S; ++L) {
-        const bool two = L >= split_g;
-        uint32_t v[W], y[W];
-        tmem_ld_part<P, W>(lane_addr + (uint32_t)L * BN, cg, v);
-        if (two) tmem_ld_part<P, W>(lane_addr + (uint32_t)(S + L - split_g) * BN, cg, y);
-        ptx::tmem_ld_wait();
-        if (small) {
+    for (int L0 = 0; L0 < S; L0 += NB) {
+        uint32_t v[NB][W], y[NB][W];
 #pragma unroll
-            for (int j = 0; j < W; ++j)
-                G[j] = G[j] * 32 + (int64_t)f32_small_int_value(v[j]) +
-                       (two ? (int64_t)f32_small_int_value(y[j]) : 0);
-        } else {
-#pragma unroll
-            for (int j = 0; j < W; ++j)
-                G[j] = G[j] * 32 + (int64_t)__float2int_rn(__uint_as_float(v[j])) +
-                       (two ? (int64_t)__float2int_rn(__uint_as_float(y[j])) : 0);
+        for (int b = 0; b < NB; ++b) {
+            const int L = L0 + b;
+            if (L < S) {
+                tmem_ld_part<P, W>(lane_addr + (uint32_t)L * BN, cg, v[b]);
+                if (L >= split_g)
+                    tmem_ld_part<P, W>(lane_addr + (uint32_t)(S + L - split_g) * BN, cg, y[b]);
+            }
         }
-        if ((L + 1) % kRun == 0 || L == S - 1) {
-            const int sh = 5 * (S - 1 - L);  // weight of the run's last level
+        ptx::tmem_ld_wait();
 #pragma unroll
-            for (int j = 0; j < W; ++j) {
-                i128_add_shl(T[J0 + j], G[j], sh);
-                G[j] = 0;
+        for (int b = 0; b < NB; ++b) {
+            const int L = L0 + b;
+            if (L < S) {
+                const bool two = L >= split_g;
+                if (small) {
+#pragma unroll
+                    for (int j = 0; j < W; ++j)
+                        G[j] = G[j] * 32 + (int64_t)f32_small_int_value(v[b][j]) +
+                               (two ? (int64_t)f32_small_int_value(y[b][j]) : 0);
+                } else {
+#pragma unroll
+                    for (int j = 0; j < W; ++j)
+                        G[j] = G[j] * 32 + (int64_t)__float2int_rn(__uint_as_float(v[b][j])) +
+                               (two ? (int64_t)__float2int_rn(__uint_as_float(y[b][j])) : 0);
+                }
+                if ((L + 1) % kRun == 0 || L == S - 1) {
+                    const int sh = 5 * (S - 1 - L);  // weight of the run's last level
+#pragma unroll
+                    for (int j = 0; j < W; ++j) {
+                        i128_add_shl(T[J0 + j], G[j], sh);
+                        G[j] = 0;
+                    }
+                }
             }
         }
     }
@@ -312,6 +349,43 @@ __device__ __forceinline__ void add_levels(uint32_t lane_addr, int cg, bool smal
                                            I128 (&T)[BN / 4]) {
     add_levels_part<S, BN, kSplit, 0, 8, 0>(lane_addr, cg, small, T);
     if constexpr (BN == 48) add_levels_part<S, BN, kSplit, 1, 4, 8>(lane_addr, cg, small, T);
+}
+
+// Columns J0 .. J0+W-1 of this thread (see epi_col) of one output row: all column
+// exponents loaded first (L1 hits), all outputs RN(T 2^E) formed, alpha / beta
+// applied, then the stores; `crow` is the row (stride `cstride` between columns).
+template <int S, int J0, int W, int N>
+__device__ __forceinline__ void store_part(const I128 (&T)[N], int32_t ei, int Ebase,
+                                           const int32_t* fB, int64_t col0, int64_t n, int cg,
+                                           bool plain, bool beta0, double alpha, double beta,
+                                           double* crow, int64_t cstride) {
+    const bool bad_row = ei == GB_BAD_LINE_DEV;
+    int32_t fj[W];
+#pragma unroll
+    for (int j = 0; j < W; ++j) {
+        const int64_t col = col0 + epi_col(cg, J0 + j);
+        fj[j] = col < n ? fB[col] : 0;
+    }
+    double out[W];
+#pragma unroll
+    for (int j = 0; j < W; ++j) {
+        const bool bad = bad_row || fj[j] == GB_BAD_LINE_DEV;
+        out[j] = bad ? __longlong_as_double(0x7FF8000000000000ll)
+                     : i128_to_double_scaled(T[J0 + j], ei + fj[j] + Ebase);
+        if (!plain && !bad) {
+            const int64_t col = col0 + epi_col(cg, J0 + j);
+            if (col < n) {
+                double o = __dmul_rn(alpha, out[j]);
+                if (!beta0) o = __dadd_rn(o, __dmul_rn(beta, crow[col * cstride]));
+                out[j] = o;
+            }
+        }
+    }
+#pragma unroll
+    for (int j = 0; j < W; ++j) {
+        const int64_t col = col0 + epi_col(cg, J0 + j);
+        if (col < n) crow[col * cstride] = out[j];
+    }
 }
 
 // How one launch keeps its level sums exact (see kchunk_stages): split
@@ -366,6 +440,10 @@ __device__ __forceinline__ void products_persistent(const Walk& walk, int chunk_
         ptx::mbar_init(tmem_full, 1);
         ptx::mbar_init(tmem_empty, kEpiWarps);
         ptx::mbar_init(drain, 1);
+        for (int i = 0; i < kArgSlots; ++i) {
+            ptx::mbar_init(&tail->args_full[i], 1);
+            ptx::mbar_init(&tail->args_empty[i], 1 + kEpiWarps);
+        }
         tail->abort = 0;
         ptx::mbar_init_fence();
     }
@@ -385,8 +463,15 @@ __device__ __forceinline__ void products_persistent(const Walk& walk, int chunk_
         int st = 0;        // ring slot of the next stage
         uint32_t ph = 0;   // its phase parity (flips at every wrap of the ring)
         Walk w = walk;
-        for (w.start(); w.valid() && !*abort; w.next()) {
+        int ti = 0;  // tiles walked so far: the record's slot and phase
+        for (w.start(); w.valid() && !*abort; w.next(), ++ti) {
             const TileArgs a = w.args();
+            const int as = ti % kArgSlots;
+            if (!ptx::mbar_wait_bounded(&tail->args_empty[as], ((ti / kArgSlots) & 1u) ^ 1u, abort,
+                                        status, kStatusTimeout, kWaitTimeoutNs))
+                break;
+            tail->args[as] = a;
+            ptx::mbar_arrive(&tail->args_full[as]);  // release: the record is visible
             const int nst = (a.nkb + KB - 1) / KB;
             for (int j = 0; j < nst; ++j) {
                 if (!ptx::mbar_wait_bounded(&empty[st], ph ^ 1u, abort, status, kStatusTimeout,
@@ -414,8 +499,14 @@ __device__ __forceinline__ void products_persistent(const Walk& walk, int chunk_
         uint32_t chunk_iter = 0;
         bool stop = false;
         Walk w = walk;
-        for (w.start(); w.valid() && !*abort && !stop; w.next()) {
-            const TileArgs a = w.args();
+        int ti = 0;
+        for (w.start(); w.valid() && !*abort && !stop; w.next(), ++ti) {
+            const int as = ti % kArgSlots;
+            if (!ptx::mbar_wait_bounded(&tail->args_full[as], (ti / kArgSlots) & 1u, abort, status,
+                                        kStatusTimeout, kWaitTimeoutNs))
+                break;
+            const TileArgs a = tail->args[as];
+            ptx::mbar_arrive(&tail->args_empty[as]);
             const int nst = (a.nkb + KB - 1) / KB;
             int in_chunk = 0;  // stages of the current accumulation unit issued so far
             // two stages per loop pass: the issuing thread's per-pass bookkeeping
@@ -475,14 +566,35 @@ __device__ __forceinline__ void products_persistent(const Walk& walk, int chunk_
         uint32_t chunk_iter = 0;
         bool stop = false;
         Walk w = walk;
-        for (w.start(); w.valid() && !stop; w.next()) {
-            const TileArgs a = w.args();
+        int ti = 0;
+        for (w.start(); w.valid() && !stop; w.next(), ++ti) {
+            const int as = ti % kArgSlots;
+            if (!ptx::mbar_wait_bounded(&tail->args_full[as], (ti / kArgSlots) & 1u, abort, status,
+                                        kStatusTimeout, kWaitTimeoutNs))
+                break;
+            // the record stays in shared memory (read where needed, not held in
+            // registers across the level reads) until this warp's stores are done
+            const TileArgs& a = tail->args[as];
             const int nch = ((a.nkb + KB - 1) / KB + kCS - 1) / kCS;
             const bool small = a.nkb * S < 512;  // every accumulator below 2^22
             // a warp whose 32 rows, or whose columns (8 cgroup .. on), all lie in the
             // tile's padding has no output: it skips the level reads, the
             // recombination and the stores, and only hands TMEM back (warp-uniform)
             const bool live = a.row0 + quarter * 32 < a.m && a.col0 + 8 * cgroup < a.n;
+            // the row and column exponents are brought into L1 now, so that their
+            // latency passes while the tile's MMAs run (read from L2 one by one after
+            // the level sums, behind the stores to C, they were most of the
+            // epilogue's time on short tiles); held in registers across the level
+            // reads they would spill
+            const int64_t row = a.row0 + quarter * 32 + lane;
+            const bool row_ok = live && row < a.m;
+            if (row_ok) {
+                ptx::prefetch_l1(a.eA + row);
+                if (lane == 0) {
+                    ptx::prefetch_l1(a.fB + a.col0 + 8 * cgroup);
+                    if (CW > 8) ptx::prefetch_l1(a.fB + a.col0 + 32 + 4 * cgroup);
+                }
+            }
             I128 T[CW];
 #pragma unroll
             for (int j = 0; j < CW; ++j) T[j] = I128{0, 0};
@@ -501,41 +613,34 @@ __device__ __forceinline__ void products_persistent(const Walk& walk, int chunk_
                 if (lane == 0) ptx::mbar_arrive(tmem_empty);
             }
             if (stop) break;
-            const int64_t row = a.row0 + quarter * 32 + lane;
-            if (live && row < a.m) {
+            if (row_ok) {
+                // the fields of the store phase in registers, all exponents loaded
+                // (L1 hits, prefetched) and all outputs formed before the first store:
+                // read through the shared record between stores, every field and
+                // exponent was a dependent reload per column
+                const int64_t n = a.n, col0 = a.col0;
+                const int32_t* fB = a.fB;
+                const double alpha = a.alpha, beta = a.beta;
+                const int64_t rstride = a.trans ? 1 : a.ldc, cstride = a.trans ? a.ldc : 1;
+                double* crow = a.C + row * rstride;
                 const int32_t ei = a.eA[row];
-                const bool bad_row = ei == GB_BAD_LINE_DEV;
                 const int Ebase = -8 - 5 * (S - 1);
                 // alpha == 1 and beta == +-0 tested on the bit patterns (integer ALU)
-                const long long ab = __double_as_longlong(a.alpha), bb = __double_as_longlong(a.beta);
+                const long long ab = __double_as_longlong(alpha), bb = __double_as_longlong(beta);
                 const bool beta0 = (bb & 0x7FFFFFFFFFFFFFFFll) == 0;
                 const bool plain = ab == 0x3FF0000000000000ll && beta0;
                 // C[row][col], or C[col][row] for a transposed problem (a warp's
-                // 32 lanes then store 32 consecutive doubles of one row of C)
-                const int64_t rstride = a.trans ? 1 : a.ldc, cstride = a.trans ? a.ldc : 1;
-                double* crow = a.C + row * rstride;
-#pragma unroll
-                for (int j = 0; j < CW; ++j) {
-                    const int64_t col = a.col0 + epi_col(cgroup, j);
-                    if (col < a.n) {
-                        const int32_t fj = a.fB[col];
-                        double out;
-                        if (bad_row || fj == GB_BAD_LINE_DEV) {
-                            out = __longlong_as_double(0x7FF8000000000000ll);
-                        } else {
-                            const double tv = i128_to_double_scaled(T[j], ei + fj + Ebase);
-                            if (plain) {
-                                out = tv;
-                            } else {
-                                out = __dmul_rn(a.alpha, tv);
-                                if (!beta0)
-                                    out = __dadd_rn(out, __dmul_rn(a.beta, crow[col * cstride]));
-                            }
-                        }
-                        crow[col * cstride] = out;
-                    }
-                }
+                // 32 lanes then store 32 consecutive doubles of one row of C); the
+                // thread's columns in the parts of add_levels (8, then 4 for
+                // 48-column tiles) to stay within the registers
+                store_part<S, 0, 8>(T, ei, Ebase, fB, col0, n, cgroup, plain, beta0, alpha, beta,
+                                    crow, cstride);
+                if constexpr (CW > 8)
+                    store_part<S, 8, 4>(T, ei, Ebase, fB, col0, n, cgroup, plain, beta0, alpha,
+                                        beta, crow, cstride);
             }
+            __syncwarp();
+            if (lane == 0) ptx::mbar_arrive(&tail->args_empty[as]);
         }
     }
     ptx::tc_fence_before();

@@ -67,6 +67,11 @@ __device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t parity
     }
 }
 
+// Bring the line holding `p` into this SM's L1 (no register is written).
+__device__ __forceinline__ void prefetch_l1(const void* p) {
+    asm volatile("prefetch.global.L1 [%0];" ::"l"(p));
+}
+
 // ---- TMA ---------------------------------------------------------------------------
 // Contiguous global -> shared copy of `bytes` (multiple of 16, both addresses
 // 16-byte aligned) that signals complete_tx on `bar`.
