@@ -367,6 +367,27 @@ def grouped_measure(args, steps, warmup, baselines=True, e2e=True):
     eplan = gb.GroupedPlan(eprobs, use_graph=True)
     emu_ms = _time_stream(torch, eplan.run, steps, warmup)
     einfo = eplan.info()
+    rules = None
+    if baselines and tuned == "shipped tuning table":
+        # the same groups with the tuning table emptied: the native size rule and
+        # the emulated padding rule choose every tile
+        gb.tune_set([])
+        try:
+            rplan = gb.GroupedPlan(probs, use_graph=True)
+            rn_ms = _time_stream(torch, rplan.run, steps, warmup)
+            rplan.close()
+            reprobs = [dict(p, C=torch.zeros_like(p["C"])) for p in eprobs]
+            replan = gb.GroupedPlan(reprobs, use_graph=True)
+            re_ms = _time_stream(torch, replan.run, steps, warmup)
+            re_tiles = replan.info()["emulated_tiles"]
+            replan.close()
+        finally:
+            autotune.load()
+        rules = {"native_ms": round(rn_ms, 3), "native_tflops": round(flops / rn_ms / 1e9, 4),
+                 "emulated_ms": round(re_ms, 3),
+                 "emulated_tflops_fp64_equiv": round(flops / re_ms / 1e9, 3),
+                 "emulated_tiles": re_tiles,
+                 "note": "tuning table emptied: native size rule, emulated padding rule"}
     clk = clocks.stop()
     pk, pk_kind = peaks()
     fp64_peak = SMS * FP64_FLOP_PER_CLK_SM * SM_MAX_MHZ * 1e6 / 1e12
@@ -395,6 +416,8 @@ def grouped_measure(args, steps, warmup, baselines=True, e2e=True):
         "tiles": {"native": info["native_tiles"], "emulated": einfo["emulated_tiles"]},
         "e2e": None, "clocks": clk,
     }
+    if rules is not None:
+        out["untuned_rules"] = rules
     if baselines:
         out["one_launch_per_gemm"] = {
             "ms": round(per_ms, 3), "tflops": round(flops / per_ms / 1e9, 4),
@@ -869,6 +892,7 @@ def grouped_sub_record(args):
             "native_tflops": r["value"], "native_ms": r["ms_per_step"],
             "native_frac_fp64_peak": r["roofline"]["frac"],
             "emulated": r["emulated"], "one_launch_per_gemm": r["one_launch_per_gemm"],
+            "untuned_rules": r.get("untuned_rules"),
             "launches_per_step": r["gpu_launches"] // 5, "clocks": r["clocks"]}
 
 

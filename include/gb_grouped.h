@@ -22,15 +22,20 @@
 extern "C" {
 #endif
 
-/* Tile variants of the native grouped kernel (rows x columns of C per CTA,
- * 256 threads with 4 x 4, 2 x 2, 4 x 2 or 2 x 4 elements each on the FP64
- * FMA pipe). */
+/* Tile variants.  Native problems: the grouped kernel's tiles (rows x columns
+ * of C per CTA, 256 threads with 4 x 4, 2 x 2, 4 x 2 or 2 x 4 elements each on
+ * the FP64 FMA pipe).  Emulated problems: the orientation of the 128 x
+ * emu_bn(s) product tiles -- A's rows on the 128-line side, or B's columns
+ * there (the problem runs as C^T = B^T A^T); the result is the same bit for
+ * bit, only the padding and the tile count differ. */
 typedef enum {
     GB_TILE_AUTO = 0,   /* from the tuning table (gb_tune_set), else a size rule */
     GB_TILE_64x64 = 1,
     GB_TILE_32x32 = 2,
     GB_TILE_64x32 = 3,
-    GB_TILE_32x64 = 4
+    GB_TILE_32x64 = 4,
+    GB_TILE_EMU_ROWS = 5, /* emulated: A's rows on the 128-line side */
+    GB_TILE_EMU_COLS = 6  /* emulated: B's columns on the 128-line side */
 } gb_tile;
 
 /* One GEMM of a group: layout and conventions of gb_dgemm. */
@@ -45,7 +50,8 @@ typedef struct {
     int64_t ldc;
     int32_t precision; /* gb_precision */
     int32_t slices;    /* emulated: 1..16, 0 = default (11) */
-    int32_t tile;      /* native: gb_tile */
+    int32_t tile;      /* native: GB_TILE_AUTO .. GB_TILE_32x64; emulated: GB_TILE_AUTO,
+                          GB_TILE_EMU_ROWS or GB_TILE_EMU_COLS */
     int32_t reserved;  /* must be 0 */
 } gb_gemm_desc;
 
@@ -77,9 +83,12 @@ gb_status gb_grouped_plan_destroy(gb_grouped_plan* plan);
 gb_status gb_dgemm_grouped(gb_queue* q, const gb_gemm_desc* descs, int64_t count,
                            void* workspace, size_t workspace_bytes);
 
-/* Tuning table of the native grouped kernel: for a problem with
- * tile == GB_TILE_AUTO the first entry with m <= m_max, n <= n_max and
- * k <= k_max gives its tile.  Written by the autotuner; empty = size rule. */
+/* Tuning table of the grouped kernels: for a problem with tile == GB_TILE_AUTO
+ * the first entry of its own kind (tile 1..4 for native problems, 5..6 for
+ * emulated ones) with m <= m_max, n <= n_max and k <= k_max gives its tile or
+ * orientation.  Written by the autotuner; no matching entry = the size rule
+ * (native) or the padding rule (emulated: the orientation with fewer padded
+ * output slots).  GB_ERR_INVALID_ARG for a tile outside 1..6. */
 typedef struct {
     int32_t m_max, n_max, k_max;
     int32_t tile;
@@ -88,8 +97,13 @@ typedef struct {
 gb_status gb_tune_set(const gb_tune_entry* entries, int64_t count);
 gb_status gb_tune_get(gb_tune_entry* entries, int64_t capacity, int64_t* count);
 
-/* The tile a problem of this shape would get (GB_TILE_AUTO resolved). */
+/* The tile a native problem of this shape would get (GB_TILE_AUTO resolved). */
 gb_status gb_tune_lookup(int64_t m, int64_t n, int64_t k, int32_t* tile);
+
+/* The orientation (GB_TILE_EMU_ROWS or GB_TILE_EMU_COLS) an emulated problem of
+ * this shape and slice count (1..16, 0 = 11) would get with GB_TILE_AUTO.
+ * Host only. */
+gb_status gb_tune_lookup_emulated(int slices, int64_t m, int64_t n, int64_t k, int32_t* tile);
 
 #ifdef __cplusplus
 }

@@ -55,7 +55,10 @@ typedef struct {
     const double* A_host;
     const double* B_host;
     const double* C_host;   /* initial C when beta != 0 (NULL: from the seed / zeros) */
-    double* C_out;          /* host array receiving C when done (NULL: not copied back) */
+    double* C_out;          /* host array receiving C when done (NULL: not copied back);
+                               page-locked memory is filled by a copy on the batch's
+                               stream, pageable memory by the server's worker thread
+                               once the batch has completed */
     uint64_t seed;
 } gb_request;
 

@@ -33,6 +33,7 @@ from .grouped import (  # noqa: E402,F401
     dgemm_grouped,
     tune_get,
     tune_lookup,
+    tune_lookup_emulated,
     tune_set,
 )
 from .serve import Server, fill_uniform  # noqa: E402,F401

@@ -1,15 +1,21 @@
-"""Autotuner of the grouped native kernel's tile shape per problem-size cell.
+"""Autotuner of the grouped kernels per problem-size cell.
 
 The problem space (m, n, k) is cut into cells by the thresholds THRESHOLDS
 (a cell is (m_max, n_max, k_max), the smallest thresholds >= the sizes).  For
 every cell the tuner builds a batch of problems of that cell's sizes, runs the
-grouped kernel once per candidate tile variant with that variant forced
-(CUDA-event timing, median of several graph replays) and keeps the fastest.
-The result is a first-match table (cells in lexicographic order, so the first
-entry a problem matches is its own cell), saved as JSON and loaded into the
-library with gb_tune_set.
+grouped plan once per candidate with that candidate forced (CUDA-event timing,
+median of several graph replays) and keeps the fastest:
 
-    python -m paper_1602_08477_gb300.autotune [--out tune_table.json]
+  * native problems: the DFMA tile variant (64x64, 32x32, 64x32, 32x64);
+  * emulated problems: the orientation of the 128 x bn product tiles (A's rows
+    or B's columns on the 128-line side), which sets the padding, the tile count
+    and whether the epilogue's stores to C are coalesced.
+
+The result is one first-match table (cells in lexicographic order, so the first
+entry of a problem's kind that it matches is its own cell), saved as JSON and
+loaded into the library with gb_tune_set.
+
+    python -m paper_1602_08477_gb300.autotune [--out tune_table.json] [--kinds native,emulated]
 """
 from __future__ import annotations
 
@@ -20,6 +26,8 @@ import statistics
 
 THRESHOLDS = (32, 64, 128, 256, 512)
 CANDIDATES = ("64x64", "32x32", "64x32", "32x64")
+EMU_CANDIDATES = ("emu_rows", "emu_cols")
+EMU_SLICES = 11
 DEFAULT_TABLE = os.path.join(os.path.dirname(os.path.abspath(__file__)), "tune_table.json")
 
 
@@ -62,11 +70,13 @@ def time_variant(problems, tile: str, reps: int = 5) -> float:
     return statistics.median(times)
 
 
-def tune(batch: int = 96, seed: int = 20240, reps: int = 5, log=print):
-    """Measure every cell; returns the entry list [(m_max, n_max, k_max, tile)]."""
+def tune(batch: int = 96, seed: int = 20240, reps: int = 5, log=print, kind: str = "native"):
+    """Measure every cell for problems of `kind` ("native" or "emulated");
+    returns the entry list [(m_max, n_max, k_max, tile)] and a report."""
     import numpy as np
     import torch
-    rng = np.random.default_rng(seed)
+    rng = np.random.default_rng(seed + (0 if kind == "native" else 1))
+    cands = CANDIDATES if kind == "native" else EMU_CANDIDATES
     entries, report = [], []
     for mm in THRESHOLDS:
         for nn in THRESHOLDS:
@@ -79,12 +89,15 @@ def tune(batch: int = 96, seed: int = 20240, reps: int = 5, log=print):
                     A = torch.rand((m, k), dtype=torch.float64, device="cuda")
                     B = torch.rand((k, n), dtype=torch.float64, device="cuda")
                     C = torch.empty((m, n), dtype=torch.float64, device="cuda")
-                    probs.append(dict(A=A, B=B, C=C, alpha=1.0, beta=0.0))
-                ms = {t: time_variant(probs, t, reps) for t in CANDIDATES}
+                    p = dict(A=A, B=B, C=C, alpha=1.0, beta=0.0)
+                    if kind == "emulated":
+                        p.update(precision="emulated", slices=EMU_SLICES)
+                    probs.append(p)
+                ms = {t: time_variant(probs, t, reps) for t in cands}
                 best = min(ms, key=ms.get)
                 entries.append((mm, nn, kk, best))
-                report.append(dict(cell=[mm, nn, kk], ms=ms, best=best))
-                log(f"cell m<={mm} n<={nn} k<={kk}: " +
+                report.append(dict(kind=kind, cell=[mm, nn, kk], ms=ms, best=best))
+                log(f"{kind} cell m<={mm} n<={nn} k<={kk}: " +
                     " ".join(f"{t}={v:.3f}ms" for t, v in ms.items()) + f" -> {best}")
     return entries, report
 
@@ -116,15 +129,37 @@ def main():
     ap.add_argument("--out", default=DEFAULT_TABLE)
     ap.add_argument("--batch", type=int, default=96)
     ap.add_argument("--reps", type=int, default=5)
+    ap.add_argument("--kinds", default="native,emulated",
+                    help="problem kinds to tune; the other kind's entries are kept from "
+                         "the current table")
     a = ap.parse_args()
     import torch
 
     from .compile_lib import build
+    from .grouped import TILES
     build()
-    entries, report = tune(batch=a.batch, reps=a.reps)
-    save(entries, a.out, report, meta={"device": torch.cuda.get_device_name(0),
-                                       "batch": a.batch, "reps": a.reps})
-    print(f"wrote {a.out} ({len(entries)} cells)")
+    kinds = [k for k in a.kinds.split(",") if k]
+    try:
+        with open(table_path()) as f:
+            old = json.load(f)
+    except Exception:
+        old = {"entries": [], "report": [], "meta": {}}
+    emu_ids = (TILES["emu_rows"], TILES["emu_cols"])
+
+    def kind_of(tile):
+        return "emulated" if (TILES[tile] if isinstance(tile, str) else tile) in emu_ids \
+            else "native"
+    entries = [tuple(e) for e in old["entries"] if kind_of(e[3]) not in kinds]
+    report = [r for r in old.get("report", []) if r.get("kind", "native") not in kinds]
+    for kind in kinds:
+        e, r = tune(batch=a.batch, reps=a.reps, kind=kind)
+        entries += e
+        report += r
+    meta = dict(old.get("meta", {}))
+    meta.update({"device": torch.cuda.get_device_name(0), "batch": a.batch, "reps": a.reps,
+                 "emulated_slices": EMU_SLICES})
+    save(entries, a.out, report, meta=meta)
+    print(f"wrote {a.out} ({len(entries)} entries)")
 
 
 if __name__ == "__main__":

@@ -206,8 +206,8 @@ bool emu_group_trans(int s, int64_t m, int64_t n) {
     return pad(n, kEmuBM) * pad(m, bn) < pad(m, kEmuBM) * pad(n, bn);
 }
 
-EmuLayout emu_group_layout(int s, int64_t m, int64_t n, int64_t k) {
-    return emu_group_trans(s, m, n) ? emu_layout(s, n, m, k, false) : emu_layout(s, m, n, k, false);
+EmuLayout emu_group_layout(int s, int64_t m, int64_t n, int64_t k, bool trans) {
+    return trans ? emu_layout(s, n, m, k, false) : emu_layout(s, m, n, k, false);
 }
 
 void emu_group_assign(EmuProb& e, uint8_t* base, const EmuLayout& w) {

@@ -46,11 +46,27 @@ int default_tile(int64_t m, int64_t n) {
     return kTile32x32;
 }
 
+bool native_tile(int t) { return t >= GB_TILE_64x64 && t <= GB_TILE_32x64; }
+bool emu_orientation(int t) { return t == GB_TILE_EMU_ROWS || t == GB_TILE_EMU_COLS; }
+
+// First matching entry of the native kind, else the size rule.
 int lookup_tile(int64_t m, int64_t n, int64_t k) {
     std::lock_guard<std::mutex> lock(g_tune_mu);
     for (const auto& e : g_tune)
-        if (m <= e.m_max && n <= e.n_max && k <= e.k_max) return e.tile;
+        if (native_tile(e.tile) && m <= e.m_max && n <= e.n_max && k <= e.k_max) return e.tile;
     return default_tile(m, n);
+}
+
+// Orientation of an emulated problem: first matching entry of the emulated
+// kind, else the padding rule (emu_group_trans).
+int lookup_emu(int s, int64_t m, int64_t n, int64_t k) {
+    {
+        std::lock_guard<std::mutex> lock(g_tune_mu);
+        for (const auto& e : g_tune)
+            if (emu_orientation(e.tile) && m <= e.m_max && n <= e.n_max && k <= e.k_max)
+                return e.tile;
+    }
+    return emu_group_trans(s, m, n) ? GB_TILE_EMU_COLS : GB_TILE_EMU_ROWS;
 }
 
 size_t up256(size_t x) { return (x + 255) & ~(size_t)255; }
@@ -88,8 +104,11 @@ gb_status build_layout(const gb_gemm_desc* d, int64_t count, Layout& L) {
         if (x.precision != GB_PREC_NATIVE && x.precision != GB_PREC_EMULATED)
             return bad("problem %lld: unknown precision", (long long)i);
         if (x.reserved != 0) return bad("problem %lld: reserved field must be 0", (long long)i);
-        if (x.tile < GB_TILE_AUTO || x.tile > GB_TILE_32x64)
-            return bad("problem %lld: unknown tile variant", (long long)i);
+        if (x.precision == GB_PREC_NATIVE && x.tile != GB_TILE_AUTO && !native_tile(x.tile))
+            return bad("problem %lld: unknown native tile variant", (long long)i);
+        if (x.precision == GB_PREC_EMULATED && x.tile != GB_TILE_AUTO && !emu_orientation(x.tile))
+            return bad("problem %lld: an emulated problem's tile is AUTO, EMU_ROWS or EMU_COLS",
+                       (long long)i);
         const int s = x.slices == 0 ? 11 : x.slices;
         if (x.precision == GB_PREC_EMULATED && (s < 1 || s > 16))
             return bad("problem %lld: slices must be in [1, 16] (or 0)", (long long)i);
@@ -109,7 +128,7 @@ gb_status build_layout(const gb_gemm_desc* d, int64_t count, Layout& L) {
             p.C = x.C;
             p.alpha = x.alpha;
             p.beta = x.beta;
-            p.tile = x.tile != GB_TILE_AUTO ? x.tile : lookup_tile(x.m, x.n, x.k);
+            p.tile = native_tile(x.tile) ? x.tile : lookup_tile(x.m, x.n, x.k);
             p.tiles_n = (int32_t)((x.n + tile_bn(p.tile) - 1) / tile_bn(p.tile));
             L.native.push_back(p);
         } else {
@@ -126,14 +145,15 @@ gb_status build_layout(const gb_gemm_desc* d, int64_t count, Layout& L) {
             e.alpha = x.alpha;
             e.beta = x.beta;
             e.s = s;
-            e.trans = emu_group_trans(s, x.m, x.n) ? 1 : 0;
+            const int orient = x.tile != GB_TILE_AUTO ? x.tile : lookup_emu(s, x.m, x.n, x.k);
+            e.trans = orient == GB_TILE_EMU_COLS ? 1 : 0;
             e.ra = e.trans ? emu_bn(s) : kEmuBM;
             e.rb = e.trans ? kEmuBM : emu_bn(s);
             // output tiles: 128 lines of the row side x emu_bn(s) of the column side
             const int64_t cols = e.trans ? x.m : x.n;
             e.tiles_n = (int32_t)((cols + emu_bn(s) - 1) / emu_bn(s));
             L.emu.push_back(e);
-            L.emu_ws.push_back(emu_group_layout(s, x.m, x.n, x.k));
+            L.emu_ws.push_back(emu_group_layout(s, x.m, x.n, x.k, e.trans != 0));
             L.emu_idx.push_back(i);
             L.max_s = std::max(L.max_s, s);
         }
@@ -297,8 +317,8 @@ gb_status gb_tune_set(const gb_tune_entry* entries, int64_t count) {
         return GB_ERR_INVALID_ARG;
     }
     for (int64_t i = 0; i < count; ++i) {
-        if (entries[i].tile < GB_TILE_64x64 || entries[i].tile > GB_TILE_32x64) {
-            set_error("tuning entry %lld: tile must be a concrete variant (1..4)", (long long)i);
+        if (!native_tile(entries[i].tile) && !emu_orientation(entries[i].tile)) {
+            set_error("tuning entry %lld: tile must be a concrete variant (1..6)", (long long)i);
             return GB_ERR_INVALID_ARG;
         }
     }
@@ -324,6 +344,16 @@ gb_status gb_tune_lookup(int64_t m, int64_t n, int64_t k, int32_t* tile) {
         return GB_ERR_INVALID_ARG;
     }
     *tile = lookup_tile(m, n, k);
+    return GB_OK;
+}
+
+gb_status gb_tune_lookup_emulated(int slices, int64_t m, int64_t n, int64_t k, int32_t* tile) {
+    const int s = slices == 0 ? 11 : slices;
+    if (!tile || m < 0 || n < 0 || k < 0 || s < 1 || s > 16) {
+        set_error("tile is NULL, a size is negative or slices is outside [0, 16]");
+        return GB_ERR_INVALID_ARG;
+    }
+    *tile = lookup_emu(s, m, n, k);
     return GB_OK;
 }
 

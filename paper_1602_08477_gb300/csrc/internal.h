@@ -98,10 +98,10 @@ EmuLayout emu_layout(int s, int64_t m, int64_t n, int64_t k, bool colmax_scratch
 // that pads fewer tile slots: pad(n, 128) pad(m, bn) < pad(m, 128) pad(n, bn).
 bool emu_group_trans(int s, int64_t m, int64_t n);
 // Workspace layout of one grouped emulated problem: emu_layout(s, m, n, k), or for
-// a transposed problem emu_layout(s, n, m, k) with the roles swapped (its a_*
+// a transposed problem (trans) emu_layout(s, n, m, k) with the roles swapped (its a_*
 // regions hold B's column digits and exponents, its b_* regions A's rows'); no
 // b_part scratch (the grouped column maxima need none).
-EmuLayout emu_group_layout(int s, int64_t m, int64_t n, int64_t k);
+EmuLayout emu_group_layout(int s, int64_t m, int64_t n, int64_t k, bool trans);
 
 // One emulated problem of a grouped launch, as the device reads it.
 struct EmuProb {

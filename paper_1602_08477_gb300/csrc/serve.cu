@@ -130,6 +130,10 @@ struct Request {
     gb_status status = GB_OK;
     int state = 0;    // 0 queued, 1 batched, 2 done
     double flops;
+    // C in the arena, copied to a pageable C_out when the batch is done (a copy
+    // into pageable memory enqueued on the stream would hold the worker thread
+    // until the GEMM and the copy finished, and no other batch could start)
+    double* late_copy = nullptr;
 };
 
 struct Slot {
@@ -145,8 +149,14 @@ struct Slot {
 
 size_t footprint(const gb_request& r) {
     size_t b = 8 * ((size_t)r.m * r.k + (size_t)r.k * r.n + (size_t)r.m * r.n) + 3 * 1024;
-    if (r.precision == GB_PREC_EMULATED)
-        b += emu_group_layout(r.slices == 0 ? 11 : r.slices, r.m, r.n, r.k).total + 1024;
+    if (r.precision == GB_PREC_EMULATED) {
+        // either orientation (the tuning table may pick the one the padding rule
+        // does not): the larger workspace
+        const int s = r.slices == 0 ? 11 : r.slices;
+        b += std::max(emu_group_layout(s, r.m, r.n, r.k, false).total,
+                      emu_group_layout(s, r.m, r.n, r.k, true).total) +
+             1024;
+    }
     return b;
 }
 
@@ -184,9 +194,18 @@ void complete_batch(gb_server* S, Slot& sl) {
     unsigned h = 0;
     cudaMemcpy(&h, sl.status, sizeof(h), cudaMemcpyDeviceToHost);
     if (h) cudaMemset(sl.status, 0, sizeof(h));
-    const gb_status st = (h & kStatusTimeout) ? GB_ERR_TIMEOUT
-                         : (h & kStatusNonfinite) ? GB_ERR_NONFINITE
-                                                  : GB_OK;
+    gb_status st = (h & kStatusTimeout) ? GB_ERR_TIMEOUT
+                   : (h & kStatusNonfinite) ? GB_ERR_NONFINITE
+                                            : GB_OK;
+    // results bound for pageable host memory: the batch is done, copy them now
+    for (Request* r : sl.batch) {
+        if (r->late_copy &&
+            cudaMemcpy(r->r.C_out, r->late_copy, 8 * r->r.m * r->r.n, cudaMemcpyDeviceToHost) !=
+                cudaSuccess &&
+            st == GB_OK)
+            st = GB_ERR_CUDA;
+        r->late_copy = nullptr;
+    }
     const auto now = Clock::now();
     std::lock_guard<std::mutex> lock(S->mu);
     for (Request* r : sl.batch) {
@@ -332,9 +351,17 @@ bool launch_batch(gb_server* S, Slot& sl) {
     }
     for (size_t i = 0; i < batch.size() && e == cudaSuccess && st == GB_OK; ++i) {
         const gb_request& q = batch[i]->r;
-        if (q.C_out)
+        if (!q.C_out) continue;
+        // page-locked destinations are copied on the stream; pageable ones when
+        // the batch is done (complete_batch)
+        cudaPointerAttributes pa{};
+        const bool pinned = cudaPointerGetAttributes(&pa, q.C_out) == cudaSuccess &&
+                            pa.type == cudaMemoryTypeHost;
+        if (pinned)
             e = cudaMemcpyAsync(q.C_out, outC[i], 8 * q.m * q.n, cudaMemcpyDeviceToHost,
                                 sl.stream);
+        else
+            batch[i]->late_copy = outC[i];
     }
     if (e == cudaSuccess) e = cudaEventRecord(sl.done, sl.stream);
     if (e != cudaSuccess || st != GB_OK) {

@@ -10,7 +10,8 @@ import ctypes
 from . import _lib
 from ._lib import check
 
-TILES = {"auto": 0, "64x64": 1, "32x32": 2, "64x32": 3, "32x64": 4}
+TILES = {"auto": 0, "64x64": 1, "32x32": 2, "64x32": 3, "32x64": 4,
+         "emu_rows": 5, "emu_cols": 6}
 TILE_NAMES = {v: k for k, v in TILES.items()}
 
 
@@ -42,6 +43,7 @@ _lib.extra_signatures({
     "gb_tune_set": (_st, [ctypes.POINTER(TuneEntry), _i64]),
     "gb_tune_get": (_st, [ctypes.POINTER(TuneEntry), _i64, ctypes.POINTER(_i64)]),
     "gb_tune_lookup": (_st, [_i64, _i64, _i64, ctypes.POINTER(ctypes.c_int32)]),
+    "gb_tune_lookup_emulated": (_st, [_int, _i64, _i64, _i64, ctypes.POINTER(ctypes.c_int32)]),
 })
 
 
@@ -151,6 +153,15 @@ def tune_get():
 
 
 def tune_lookup(m, n, k) -> str:
+    """Tile of a native problem of this shape under the installed table."""
     t = ctypes.c_int32()
     check(_lib.load().gb_tune_lookup(m, n, k, ctypes.byref(t)), "gb_tune_lookup")
+    return TILE_NAMES[t.value]
+
+
+def tune_lookup_emulated(m, n, k, slices=11) -> str:
+    """Orientation ("emu_rows" or "emu_cols") of an emulated problem of this shape."""
+    t = ctypes.c_int32()
+    check(_lib.load().gb_tune_lookup_emulated(slices, m, n, k, ctypes.byref(t)),
+          "gb_tune_lookup_emulated")
     return TILE_NAMES[t.value]

@@ -296,3 +296,43 @@ def test_emulated_group_writes_only_c(gb):
         mask[1:1 + m, 3:3 + n] = False
         assert np.all(out[mask] == canary)
         assert np.isfinite(out[1:1 + m, 3:3 + n]).all()
+
+
+def test_emulated_orientations_give_the_same_bits(gb):
+    # the two orientations of the emulated product tiles (A's rows or B's columns
+    # on the 128-line side, as the tuning table may choose per size cell) compute
+    # the same exact level sums and round them once: bit-identical results, equal
+    # to single launches, and different tile counts
+    import torch
+    results, tiles = {}, {}
+    for orient in ("emu_rows", "emu_cols", "auto"):
+        probs, host = make_group(40, 4409)
+        for p in probs:
+            p["precision"] = "emulated"
+            p["slices"] = 11
+            p["tile"] = orient
+        plan = gb.GroupedPlan(probs, use_graph=True)
+        plan.run()
+        torch.cuda.synchronize()
+        tiles[orient] = plan.info()["emulated_tiles"]
+        results[orient] = [p["C"].clone() for p in probs]
+        plan.close()
+    for a, b, c in zip(results["emu_rows"], results["emu_cols"], results["auto"]):
+        assert torch.equal(a, b) and torch.equal(a, c)
+    assert tiles["emu_rows"] != tiles["emu_cols"]
+    for (A, B, C0), got in zip(host, results["auto"]):
+        single = to_dev(C0)
+        gb.dgemm(to_dev(A), to_dev(B), single, 1.0, 0.5, precision="emulated", slices=11)
+        torch.cuda.synchronize()
+        assert torch.equal(got, single)
+
+
+def test_unknown_orientations_rejected(gb):
+    probs, _ = make_group(2, 4410)
+    probs[0]["tile"] = "emu_rows"          # native problem with an emulated orientation
+    with pytest.raises(gb.GbError, match="INVALID_ARG"):
+        gb.GroupedPlan(probs, use_graph=False)
+    probs[0]["tile"] = "64x64"
+    probs[1].update(precision="emulated", tile="32x32")   # emulated problem, native tile
+    with pytest.raises(gb.GbError, match="INVALID_ARG"):
+        gb.GroupedPlan(probs, use_graph=False)

@@ -168,6 +168,7 @@ def test_requests_admitted_while_a_large_gemm_runs(gb):
     import time
     import torch
     big = 6144
+    reqs = _requests(24, 9200)  # host operands made first: generating them takes ~1 s
     srv = gb.Server(hbm_budget_bytes=2 << 30, n_streams=4, max_batch=8)
     big_out = np.empty((big, big))
     big_id = srv.submit(big, big, big, 1.0, 0.0, "native", 0, out=big_out, seed=9100)
@@ -175,7 +176,6 @@ def test_requests_admitted_while_a_large_gemm_runs(gb):
     while srv.stats()["in_flight"] == 0 and time.perf_counter() - t0 < 10:
         time.sleep(0.001)
     assert srv.stats()["in_flight"] >= 1
-    reqs = _requests(24, 9200)
     outs, ids = [], []
     for r in reqs:
         out = np.empty((r["m"], r["n"]))

@@ -36,3 +36,28 @@ def test_invalid_entries_rejected(gb):
         gb.tune_set([(1, 1, 1, 0)])
     with pytest.raises(gb.GbError, match="INVALID_ARG"):
         gb.tune_set([(1, 1, 1, 7)])
+
+
+def test_emulated_orientation_padding_rule(gb):
+    # no emulated entry: the orientation with fewer padded output slots (128 x bn
+    # tiles, bn = 32 at s = 11): wide problems put B's columns on the 128-line side
+    gb.tune_set([])
+    assert gb.tune_lookup_emulated(500, 20, 64) == "emu_rows"
+    assert gb.tune_lookup_emulated(20, 500, 64) == "emu_cols"
+    assert gb.tune_lookup_emulated(128, 128, 64) == "emu_rows"   # equal padding: rows
+    with pytest.raises(gb.GbError, match="INVALID_ARG"):
+        gb.tune_lookup_emulated(10, 10, 10, slices=17)
+
+
+def test_entries_of_each_kind_apply_to_their_own_problems(gb):
+    # an emulated entry does not change native lookups and a native entry does not
+    # change emulated ones; first match per kind
+    gb.tune_set([(64, 64, 1 << 30, "emu_cols"), (64, 64, 1 << 30, "32x64"),
+                 (1 << 30, 1 << 30, 1 << 30, "emu_rows")])
+    try:
+        assert gb.tune_lookup(60, 60, 100) == "32x64"
+        assert gb.tune_lookup(300, 300, 100) == "64x64"          # size rule
+        assert gb.tune_lookup_emulated(60, 60, 100) == "emu_cols"
+        assert gb.tune_lookup_emulated(20, 500, 100) == "emu_rows"  # second emulated entry
+    finally:
+        gb.tune_set([])
