@@ -287,16 +287,34 @@ __device__ __forceinline__ void tmem_ld_part(uint32_t level, int g, uint32_t (&v
 // (constant shifts) and converts with one hardware FP32 -> int32 conversion per
 // value (exact: every accumulator is an integer below 2^25); small: every
 // accumulator below 2^22, converted by one FP32 add instead.
+// Exact integer value of level L's sum for the W columns, from its FP32
+// accumulator v (and the second set's y for split accumulators): below 2^25.
+template <int W>
+__device__ __forceinline__ void level_values(const uint32_t (&v)[W], const uint32_t (&y)[W],
+                                             bool two, bool small, int32_t (&x)[W]) {
+#pragma unroll
+    for (int j = 0; j < W; ++j) {
+        if (small)
+            x[j] = f32_small_int_value(v[j]) + (two ? f32_small_int_value(y[j]) : 0);
+        else
+            x[j] = __float2int_rn(__uint_as_float(v[j])) +
+                   (two ? __float2int_rn(__uint_as_float(y[j])) : 0);
+    }
+}
+
 template <int S, int BN, bool kSplit, int P, int W, int J0>
 __device__ __forceinline__ void add_levels_part(uint32_t lane_addr, int cg, bool small,
                                                 I128 (&T)[BN / 4]) {
     constexpr int kRun = 6;
     constexpr int split_g = kSplit ? split_point(S) : S;
     // levels read NB at a time, one wait per batch: the reads of a tile end hold
-    // up the next tile's MMAs, and each wait costs a TMEM load round trip
-    // (16 loaded values per batch with the 48-column tiles' 12 128-bit sums, 24
-    // with 32-column tiles, 16 when split accumulators double the loads)
-    constexpr int NB = (BN == 48 || kSplit ? 16 : 24) / W;
+    // up the next tile's MMAs, and each wait costs a TMEM load round trip.  NB is
+    // even, so that consecutive levels L, L+1 (L even: runs start at multiples of
+    // 6) are in one batch and enter the Horner sum as one 32-bit pair
+    // x_L 32 + x_(L+1) (|x| < 2^25, so the pair is below 2^31): one 64-bit step
+    // per two levels in this integer-ALU-bound epilogue
+    constexpr int NB = 16 / W;
+    static_assert(NB % 2 == 0, "level pairs within a batch");
     int64_t G[W];
 #pragma unroll
     for (int j = 0; j < W; ++j) G[j] = 0;
@@ -314,23 +332,25 @@ __device__ __forceinline__ void add_levels_part(uint32_t lane_addr, int cg, bool
         }
         ptx::tmem_ld_wait();
 #pragma unroll
-        for (int b = 0; b < NB; ++b) {
+        for (int b = 0; b < NB; b += 2) {
             const int L = L0 + b;
             if (L < S) {
-                const bool two = L >= split_g;
-                if (small) {
+                int32_t x0[W];
+                level_values<W>(v[b], y[b], L >= split_g, small, x0);
+                int last = L;  // last level folded into G by this step
+                if (L + 1 < S) {
+                    int32_t x1[W];
+                    level_values<W>(v[b + 1], y[b + 1], L + 1 >= split_g, small, x1);
 #pragma unroll
                     for (int j = 0; j < W; ++j)
-                        G[j] = G[j] * 32 + (int64_t)f32_small_int_value(v[b][j]) +
-                               (two ? (int64_t)f32_small_int_value(y[b][j]) : 0);
+                        G[j] = G[j] * 1024 + (int64_t)(x0[j] * 32 + x1[j]);
+                    last = L + 1;
                 } else {
 #pragma unroll
-                    for (int j = 0; j < W; ++j)
-                        G[j] = G[j] * 32 + (int64_t)__float2int_rn(__uint_as_float(v[b][j])) +
-                               (two ? (int64_t)__float2int_rn(__uint_as_float(y[b][j])) : 0);
+                    for (int j = 0; j < W; ++j) G[j] = G[j] * 32 + (int64_t)x0[j];
                 }
-                if ((L + 1) % kRun == 0 || L == S - 1) {
-                    const int sh = 5 * (S - 1 - L);  // weight of the run's last level
+                if ((last + 1) % kRun == 0 || last == S - 1) {
+                    const int sh = 5 * (S - 1 - last);  // weight of the run's last level
 #pragma unroll
                     for (int j = 0; j < W; ++j) {
                         i128_add_shl(T[J0 + j], G[j], sh);
