@@ -42,7 +42,7 @@ FP64_FLOP_PER_CLK_SM = 4.0
 # DRAM bytes (read + write) per launch of the dominant kernel, from one ncu
 # capture of the kernel as it is now (profiles/emu_products_kernel_n8192_s10.md):
 # (kernel, n, slices) -> bytes.  Reported only for that exact workload.
-MEASURED_TRAFFIC = {("emu_products_kernel", 8192, 10): 9660124416 + 538920192}
+MEASURED_TRAFFIC = {("emu_products_kernel", 8192, 10): int(9.79e9 + 624.83e6)}
 
 
 def parse():

@@ -183,11 +183,13 @@ def test_workspace_errors(gb):
         gb.dgemm(dA, dB, dC, precision="emulated", slices=17)
 
 
-@pytest.mark.parametrize("n,s", [(4096, 10), (8192, 10), (8192, 11)])
-def test_full_size_sampled_rows(gb, n, s):
-    # square sizes of the emulated workload: 8 sampled rows against the model
-    # (bit-exact) and against the double-double reference (FP64 bound)
-    A, B, _ = inputs("uniform", n, n, n, g.BASE_SEED + 2, with_c=False)
+@pytest.mark.parametrize("n,s,kind", [(4096, 10, "uniform"), (8192, 10, "uniform"),
+                                      (8192, 11, "uniform"), (8192, 11, "hard")])
+def test_full_size_sampled_rows(gb, n, s, kind):
+    # square sizes of the emulated workload (uniform, and the 16-decade hard set
+    # at the slice count it needs): 8 sampled rows against the model (bit-exact)
+    # and against the double-double reference (FP64 bound)
+    A, B, _ = inputs(kind, n, n, n, g.BASE_SEED + (2 if kind == "uniform" else 3), with_c=False)
     got = emulate(gb, A, B, None, 1.0, 0.0, s)
     rows = np.random.default_rng(n + s).choice(n, 8, replace=False)
     want = ozaki.emulated_gemm(1.0, A, B, s=s, rows=rows)
