@@ -39,8 +39,8 @@ SM_MAX_MHZ = 2070.0
 # chip's unit counts and clocks; the DFMA kernels reach 99% of it.
 FP64_FLOP_PER_CLK_SM = 4.0
 
-# DRAM bytes (read + write) per launch of the dominant kernel, from one ncu
-# capture of the kernel as it is now (profiles/emu_products_kernel_n8192_s10.md):
+# DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) of one launch of the
+# dominant kernel, from one ncu capture of the kernel as it is now:
 # (kernel, n, slices) -> bytes.  Reported only for that exact workload.
 MEASURED_TRAFFIC = {("emu_products_kernel", 8192, 10): int(9.79e9 + 624.83e6)}
 
