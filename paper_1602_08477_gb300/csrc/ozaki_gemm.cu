@@ -14,13 +14,14 @@
 //     writes C = alpha t + beta C.  GB300 runs FP64 at a small fraction of its integer
 //     rate, so only the alpha / beta step uses the FP64 pipe.
 //
-// Pipeline per CTA (one output tile, 192 threads):
-//   warp 0 lane 0 : producer.  Stage = one 32-byte K block of all s digit planes
-//                   of A (128 x 32 B each) and B (BN x 32 B each).  The split
-//                   kernels store each such block pre-tiled and pre-swizzled
-//                   (the 32-byte-swizzled K-major image the tensor core reads),
-//                   so a stage is two contiguous 1-D bulk copies (s * 4 KiB and
-//                   s * 1 KiB) instead of thousands of 32-byte row requests.
+// Persistent CTAs, one per SM, 576 threads, over the output tiles:
+//   warp 0 lane 0 : producer.  Resolves each tile's arguments once and shares
+//                   them through a ring in shared memory.  Stage = KB 32-byte K
+//                   blocks of all s digit planes of A (128 x 32 B each) and B
+//                   (BN x 32 B each).  The split kernels store each such block
+//                   pre-tiled and pre-swizzled (the 32-byte-swizzled K-major image
+//                   the tensor core reads), so a stage is two contiguous 1-D bulk
+//                   copies instead of thousands of 32-byte row requests.
 //   warp 1        : allocates 512 TMEM columns; lane 0 issues the pair
 //                   products of a stage (M = 128, K = 32, N up to 256; all pairs
 //                   sharing an A slice go into one MMA) and commits each stage
