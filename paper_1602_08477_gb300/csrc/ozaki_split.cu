@@ -77,7 +77,8 @@ struct FixedOf {
 };
 
 // The S digits of one finite double x relative to line exponent e, packed as
-// E4M3 bytes into out[t] (byte lane `lane` of a 64-bit word).
+// E4M3 bytes into out[t] (byte `lane` of the 8-byte word of digit plane t, as
+// its two 32-bit halves out[t][0] (bytes 0-3) and out[t][1] (bytes 4-7)).
 //
 // With x = X 2^E2 (X the signed integer significand) and sh_t = e - 4 - E2 -
 // 5 (t - 1), the recurrence above satisfies  r_t 2^(...) = X - Q_t 2^(sh_t)  with
@@ -98,8 +99,13 @@ struct FixedOf {
 // gives the even rounding at t* and changes no other digit (F - 1 stays above
 // every lower rounding point by less than a half unit, and the higher windows
 // see no borrow), so the whole element is one subtraction plus S lookups.
+// Byte `pos` (0..3) of x replaced by the low byte of y (one byte permute).
+__device__ __forceinline__ uint32_t insert_byte(uint32_t x, uint32_t y, int pos) {
+    return __byte_perm(x, y, pos == 0 ? 0x3214u : pos == 1 ? 0x3240u : pos == 2 ? 0x3410u : 0x4210u);
+}
+
 template <int S>
-__device__ __forceinline__ void digits_of(uint64_t bits, int e, int lane, uint64_t (&out)[S]) {
+__device__ __forceinline__ void digits_of(uint64_t bits, int e, int lane, uint32_t (&out)[S][2]) {
     using Fixed = typename FixedOf<S>::type;
     const int ef = (int)((bits >> 52) & 0x7FF);
     int64_t M = (int64_t)(bits & 0xFFFFFFFFFFFFFull);
@@ -125,7 +131,9 @@ __device__ __forceinline__ void digits_of(uint64_t bits, int e, int lane, uint64
     for (int t = 1; t <= S; ++t) {
         const int sh = kB * (S - t);
         const uint32_t w = (uint32_t)(F >> sh) & 127u;
-        out[t - 1] |= (uint64_t)s_window[w] << (8 * lane);
+        // lane is a compile-time constant in the unrolled callers: one byte
+        // permute into the right half of the digit plane's 8-byte word
+        out[t - 1][lane >> 2] = insert_byte(out[t - 1][lane >> 2], s_window[w], lane & 3);
     }
 }
 
@@ -195,9 +203,9 @@ __device__ __forceinline__ void split_one_row(int64_t i, int64_t m, int64_t k,
     }
     // pass 2: 8 consecutive elements per thread -> one 8-byte word per plane
     for (int64_t l0 = (int64_t)tid * 8; l0 < kp; l0 += (int64_t)blockDim.x * 8) {
-        uint64_t w[S];
+        uint32_t w[S][2];
 #pragma unroll
-        for (int t = 0; t < S; ++t) w[t] = 0;
+        for (int t = 0; t < S; ++t) w[t][0] = w[t][1] = 0;
         if (!is_bad) {
 #pragma unroll
             for (int u = 0; u < 8; ++u) {
@@ -208,7 +216,8 @@ __device__ __forceinline__ void split_one_row(int64_t i, int64_t m, int64_t k,
 #pragma unroll
         for (int t = 0; t < S; ++t) {
             if (t >= s) break;
-            *reinterpret_cast<uint64_t*>(digits + tiled_offset(i, l0, t, s, nkb, kEmuBM)) = w[t];
+            *reinterpret_cast<uint2*>(digits + tiled_offset(i, l0, t, s, nkb, kEmuBM)) =
+                make_uint2(w[t][0], w[t][1]);
         }
     }
     __syncthreads();
@@ -277,9 +286,9 @@ __device__ __forceinline__ void split_cols_tile(int64_t jb, int64_t lb, int64_t 
     const int64_t np = (n + R - 1) / R * R;
     if (lbase < kp && j < np) {
         const int e = ecol(jj, j);
-        uint64_t w[S];
+        uint32_t w[S][2];
 #pragma unroll
-        for (int t = 0; t < S; ++t) w[t] = 0;
+        for (int t = 0; t < S; ++t) w[t][0] = w[t][1] = 0;
         if (e != GB_BAD_LINE_DEV) {
 #pragma unroll
             for (int u = 0; u < 8; ++u) {
@@ -289,8 +298,8 @@ __device__ __forceinline__ void split_cols_tile(int64_t jb, int64_t lb, int64_t 
 #pragma unroll
         for (int t = 0; t < S; ++t) {
             if (t >= s) break;
-            *reinterpret_cast<uint64_t*>(digits + tiled_offset(j, lbase, t, s, kp >> 5, R)) =
-                w[t];
+            *reinterpret_cast<uint2*>(digits + tiled_offset(j, lbase, t, s, kp >> 5, R)) =
+                make_uint2(w[t][0], w[t][1]);
         }
     }
     __syncthreads();
@@ -476,9 +485,9 @@ __device__ __forceinline__ void split_row_tile(int64_t row0, int64_t m, int64_t 
             const int64_t i = row0 + r, l0 = kb * 32 + (p & 3) * 8;
             if (i >= mp) continue;  // beyond the last R-line tile of this problem
             const int e = e_sh[r];
-            uint64_t w[S];
+            uint32_t w[S][2];
 #pragma unroll
-            for (int t = 0; t < S; ++t) w[t] = 0;
+            for (int t = 0; t < S; ++t) w[t][0] = w[t][1] = 0;
             if (e != GB_BAD_LINE_DEV) {
                 const uint64_t* src = reinterpret_cast<const uint64_t*>(A + i * lda) + l0;
                 uint64_t v[8];
@@ -490,7 +499,8 @@ __device__ __forceinline__ void split_row_tile(int64_t row0, int64_t m, int64_t 
             }
 #pragma unroll
             for (int t = 0; t < S; ++t)
-                *reinterpret_cast<uint64_t*>(digits + tiled_offset(i, l0, t, S, nkb, R)) = w[t];
+                *reinterpret_cast<uint2*>(digits + tiled_offset(i, l0, t, S, nkb, R)) =
+                    make_uint2(w[t][0], w[t][1]);
         }
     }
     __syncthreads();
