@@ -175,7 +175,9 @@ __device__ __forceinline__ void dfma_stage_active(int ra, int ca, const double* 
         dfma_stage<VY, VX, TX, VY, VX>(as, bs, nl, ty, tx, acc);
 }
 
-template <int VY, int VX, int TX = 16>
+// kMayBeEmpty: the tile may belong to a problem with k == 0 (grouped problems with
+// alpha == 0 or k == 0 run here as C <- beta C); single launches never do.
+template <int VY, int VX, int TX = 16, bool kMayBeEmpty = false>
 __device__ __forceinline__ void dfma_tile(int64_t m, int64_t n, int64_t k, double alpha,
                                           const double* __restrict__ A, int64_t lda,
                                           const double* __restrict__ B, int64_t ldb,
@@ -254,6 +256,10 @@ __device__ __forceinline__ void dfma_tile(int64_t m, int64_t n, int64_t k, doubl
         __syncthreads();
     }
     const bool beta0 = beta == 0.0;
+    // k == 0 (a grouped problem with alpha == 0 or k == 0): C <- beta C exactly as
+    // the scaling kernel writes it (beta C, or 0 when beta == 0), not alpha 0 + beta C,
+    // whose zeros would differ in sign
+    const bool scale_only = kMayBeEmpty && k == 0;
 #pragma unroll
     for (int r = 0; r < VY; ++r) {
         const int64_t gi = row0 + ty + TY * r;
@@ -263,7 +269,10 @@ __device__ __forceinline__ void dfma_tile(int64_t m, int64_t n, int64_t k, doubl
             const int64_t gj = col0 + tx + TX * c;
             if (gj < n) {
                 double* cp = &C[gi * ldc + gj];
-                *cp = beta0 ? alpha * acc[r][c] : alpha * acc[r][c] + beta * (*cp);
+                if (scale_only)
+                    *cp = beta0 ? 0.0 : beta * (*cp);
+                else
+                    *cp = beta0 ? alpha * acc[r][c] : alpha * acc[r][c] + beta * (*cp);
             }
         }
     }
@@ -469,19 +478,19 @@ __global__ void __launch_bounds__(256) grouped_native_kernel(const GroupProb* __
         const int64_t tm = local / P.tiles_n, tn = local % P.tiles_n;
         switch (P.tile) {
             case kTile64x64:
-                dfma_tile<2, 8, kGroupedTX>(P.m, P.n, P.k, P.alpha, P.A, P.lda, P.B, P.ldb,
+                dfma_tile<2, 8, kGroupedTX, true>(P.m, P.n, P.k, P.alpha, P.A, P.lda, P.B, P.ldb,
                                             P.beta, P.C, P.ldc, tm * 64, tn * 64, smem);
                 break;
             case kTile32x32:
-                dfma_tile<1, 4, kGroupedTX>(P.m, P.n, P.k, P.alpha, P.A, P.lda, P.B, P.ldb,
+                dfma_tile<1, 4, kGroupedTX, true>(P.m, P.n, P.k, P.alpha, P.A, P.lda, P.B, P.ldb,
                                             P.beta, P.C, P.ldc, tm * 32, tn * 32, smem);
                 break;
             case kTile64x32:
-                dfma_tile<2, 4, kGroupedTX>(P.m, P.n, P.k, P.alpha, P.A, P.lda, P.B, P.ldb,
+                dfma_tile<2, 4, kGroupedTX, true>(P.m, P.n, P.k, P.alpha, P.A, P.lda, P.B, P.ldb,
                                             P.beta, P.C, P.ldc, tm * 64, tn * 32, smem);
                 break;
             default:
-                dfma_tile<1, 8, kGroupedTX>(P.m, P.n, P.k, P.alpha, P.A, P.lda, P.B, P.ldb,
+                dfma_tile<1, 8, kGroupedTX, true>(P.m, P.n, P.k, P.alpha, P.A, P.lda, P.B, P.ldb,
                                             P.beta, P.C, P.ldc, tm * 32, tn * 64, smem);
                 break;
         }

@@ -336,3 +336,32 @@ def test_unknown_orientations_rejected(gb):
     probs[1].update(precision="emulated", tile="32x32")   # emulated problem, native tile
     with pytest.raises(gb.GbError, match="INVALID_ARG"):
         gb.GroupedPlan(probs, use_graph=False)
+
+
+def test_trivial_problems_write_beta_c_bit_exactly(gb):
+    # alpha == 0 or k == 0 in a group: C <- beta C with the bits of a single
+    # launch (and of the oracle): a zero of C times a negative beta stays -0.0,
+    # and beta == 0 writes +0.0 whatever alpha is
+    import torch
+    C0 = np.zeros((9, 7))
+    C0[::2] = g.matrix("int8", 5, 7, 4420, 2)
+    A = g.matrix("uniform", 9, 6, 4420, 0)
+    B = g.matrix("uniform", 6, 7, 4420, 1)
+    cases = [(0.0, -2.0, 6), (1.5, -2.0, 0), (-1.5, 0.0, 0), (0.0, 0.0, 6), (2.0, 0.5, 0)]
+    probs = []
+    for alpha, beta, k in cases:
+        Ak = np.ascontiguousarray(A[:, :max(k, 1)])
+        Bk = np.ascontiguousarray(B[:max(k, 1)])
+        dA = to_dev(Ak)[:, :k] if k else torch.empty((9, 0), dtype=torch.float64, device="cuda")
+        dB = to_dev(Bk)[:k] if k else torch.empty((0, 7), dtype=torch.float64, device="cuda")
+        probs.append(dict(A=dA, B=dB, C=to_dev(C0), alpha=alpha, beta=beta))
+    gb.dgemm_grouped(probs)
+    torch.cuda.synchronize()
+    for p, (alpha, beta, k) in zip(probs, cases):
+        want = cgemm.dgemm(alpha, np.zeros((9, 1)), np.zeros((1, 7)), beta, C0.copy(), k=0)
+        got = p["C"].cpu().numpy()
+        assert np.array_equal(got.view(np.int64), want.view(np.int64)), (alpha, beta, k)
+        single = to_dev(C0)
+        gb.dgemm(p["A"], p["B"], single, alpha, beta)
+        torch.cuda.synchronize()
+        assert torch.equal(single.view(torch.int64), p["C"].view(torch.int64)), (alpha, beta, k)

@@ -84,3 +84,53 @@ def test_random_shapes_both_paths(gb, case):
             # integers with exact partial sums: every kernel gives the exact result
             assert np.array_equal(got, cgemm.dgemm(alpha, A, B, beta, C0.copy())), kernel
         assert bool(torch.isnan(cbuf[:, n:]).all())
+
+
+@pytest.mark.parametrize("group", range(3))
+def test_random_groups(gb, group):
+    # 40 problems of random shapes, precisions, slice counts, alpha / beta and
+    # padded leading dimensions in one graph-captured plan: each result equals the
+    # same GEMM as a single launch (native: the DFMA kernel the grouped tiles
+    # accumulate like; emulated: bit for bit, and the step model)
+    import torch
+    rng = np.random.default_rng(99100 + group)
+    probs, host, bufs = [], [], []
+    for i in range(40):
+        m, n = (int(x) for x in rng.integers(1, 260, 2))
+        k = int(rng.integers(1, 600))
+        emulated = bool(rng.random() < 0.5)
+        s = int(rng.integers(1, 17))
+        alpha = ALPHAS[int(rng.integers(len(ALPHAS)))]
+        beta = BETAS[int(rng.integers(len(BETAS)))]
+        kind = KINDS[int(rng.integers(len(KINDS)))]
+        pads = [int(x) for x in rng.integers(0, 6, 3)]
+        seed = 8800 + 100 * group + i
+        A = g.matrix(kind, m, k, seed, g.STREAM_A)
+        B = g.matrix(kind, k, n, seed, g.STREAM_B)
+        C0 = g.matrix(kind, m, n, seed, g.STREAM_C)
+        ba, dA = padded(torch, A, pads[0])
+        bb, dB = padded(torch, B, pads[1])
+        bc, dC = padded(torch, C0, pads[2])
+        bufs += [ba, bb, bc]
+        probs.append(dict(A=dA, B=dB, C=dC, alpha=alpha, beta=beta,
+                          precision="emulated" if emulated else "native", slices=s))
+        host.append((A, B, C0, pads))
+    plan = gb.GroupedPlan(probs, use_graph=True)
+    plan.run()
+    torch.cuda.synchronize()
+    for p, (A, B, C0, pads) in zip(probs, host):
+        _, dA = padded(torch, A, pads[0])
+        _, dB = padded(torch, B, pads[1])
+        _, single = padded(torch, C0, pads[2])
+        if p["precision"] == "emulated":
+            gb.dgemm(dA, dB, single, p["alpha"], p["beta"], precision="emulated",
+                     slices=p["slices"])
+        else:
+            gb.dgemm(dA, dB, single, p["alpha"], p["beta"], kernel="dfma")
+        torch.cuda.synchronize()
+        got = p["C"].cpu().numpy()
+        assert np.array_equal(got.view(np.int64), single.cpu().numpy().view(np.int64))
+        if p["precision"] == "emulated":
+            want = ozaki.emulated_gemm(p["alpha"], A, B, p["beta"], C0, s=p["slices"])
+            assert np.array_equal(got.view(np.int64), np.ascontiguousarray(want).view(np.int64))
+    plan.close()
