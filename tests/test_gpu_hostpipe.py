@@ -126,3 +126,28 @@ def test_degenerate_host_buffer_gemms(gb, precision):
     empty = pinned(np.zeros((0, n)))
     gb.dgemm_host(pinned(np.zeros((0, 33))), pinned(B), empty, precision=precision, slices=10)
     torch.cuda.synchronize()
+
+
+@pytest.mark.parametrize("case", range(12))
+def test_random_host_buffer_gemms(gb, case):
+    # seeded random shapes across the band / column-block schedule (m up to 8192
+    # rows, n up to 3000 columns), slice counts, alpha, beta and padded host rows:
+    # every result equals the device GEMM bit for bit
+    import torch
+    rng = np.random.default_rng(8300 + case)
+    m = int(rng.integers(1, 8193))
+    n = int(rng.integers(1, 3001))
+    k = int(rng.integers(1, 301))
+    s = int(rng.integers(1, 17))
+    alpha = float(rng.choice([1.0, -0.75, 2.0, 0.5]))
+    beta = float(rng.choice([0.0, 0.5, -1.0]))
+    pad = int(rng.integers(0, 4))
+    seed = 8400 + case
+    A = g.matrix("uniform", m, k, seed, 0)
+    B = g.matrix("uniform", k, n, seed, 1)
+    C0 = g.matrix("uniform", m, n, seed, 2)
+    want = device_reference(gb, A, B, C0, alpha, beta, "emulated", s)
+    hA, hB, hC = pinned(A, pad), pinned(B, pad), pinned(C0, pad)
+    gb.dgemm_host(hA, hB, hC, alpha, beta, precision="emulated", slices=s)
+    torch.cuda.synchronize()
+    assert np.array_equal(hC.numpy().view(np.int64), want.view(np.int64)), (m, n, k, s)
