@@ -63,7 +63,9 @@ def slice_digits(X: np.ndarray, e: np.ndarray, s: int, fmt: str = "e4m3", axis: 
     """e2: signed digits of X scaled by 2^-e along ``axis`` (e per row: axis=1).
 
     Lines flagged ``bad`` (non-finite, from e1) get all-zero digits.
-    Returns (digits int8 of shape (s,) + X.shape, final remainders r_s)."""
+    Returns (digits of shape (s,) + X.shape, final remainders r_s); the digits
+    are int8 for E4M3 (|d| <= 16) and int16 for BF16 (|d| <= 128 does not fit
+    int8)."""
     b1, b, dmax = FORMATS[fmt]
     X = np.asarray(X, dtype=np.float64)
     eb = e[:, None] if axis == 1 else e[None, :]
@@ -71,7 +73,8 @@ def slice_digits(X: np.ndarray, e: np.ndarray, s: int, fmt: str = "e4m3", axis: 
     if bad is not None:
         Xf = np.where(bad[:, None] if axis == 1 else bad[None, :], 0.0, Xf)
     x = np.ldexp(Xf, -eb)
-    D = np.zeros((s,) + X.shape, dtype=np.int8)
+    dtype = np.int8 if dmax <= 127 else np.int16
+    D = np.zeros((s,) + X.shape, dtype=dtype)
     y = x * float(2 ** b1)
     for t in range(s):
         if t > 0:
@@ -79,7 +82,7 @@ def slice_digits(X: np.ndarray, e: np.ndarray, s: int, fmt: str = "e4m3", axis: 
         d = np.rint(y)
         r = y - d
         assert np.abs(d).max(initial=0) <= dmax
-        D[t] = d.astype(np.int8)
+        D[t] = d.astype(dtype)
     return D, r
 
 
@@ -88,11 +91,13 @@ def level_sums(DA: np.ndarray, DBt: np.ndarray, s: int) -> np.ndarray:
 
     DA: (s, m, k) digits of A's rows; DBt: (s, n, k) digits of B's columns.
     The products are formed by a float64 matrix multiply: every digit product
-    is an integer <= 256 and every partial sum an integer far below 2^53, so the
-    library matmul is exact whatever its summation order."""
+    is an integer of magnitude <= dmax^2 (256 for E4M3 digits, 2^14 for BF16
+    digits) and every partial sum an integer far below 2^53, so the library
+    matmul is exact whatever its summation order."""
     m, n = DA.shape[1], DBt.shape[1]
     S = np.zeros((s, m, n), dtype=np.int64)
-    assert DA.shape[2] * s * 256 < 2 ** 53
+    dmax = max(int(np.abs(DA).max(initial=0)), int(np.abs(DBt).max(initial=0)), 1)
+    assert DA.shape[2] * s * dmax * dmax < 2 ** 53
     fa = [DA[p].astype(np.float64) for p in range(s)]
     for q in range(1, s + 1):
         fbq = DBt[q - 1].astype(np.float64).T      # one plane at a time (memory)
