@@ -86,8 +86,9 @@ typedef struct {
 } gb_workdiv;
 
 typedef enum {
-    GB_PREC_NATIVE = 0,    /* FP64 arithmetic on the FP64 pipes */
-    GB_PREC_EMULATED = 1   /* FP64 result from E4M3 slices on the tcgen05 tensor cores */
+    GB_PREC_NATIVE = 0,        /* FP64 arithmetic on the FP64 pipes */
+    GB_PREC_EMULATED = 1,      /* FP64 result from E4M3 slices on the tcgen05 tensor cores */
+    GB_PREC_EMULATED_BF16 = 2  /* the same from BF16 slices (8-bit digits, kind::f16 MMAs) */
 } gb_precision;
 
 typedef enum {
@@ -152,10 +153,26 @@ gb_status gb_workdiv_suggest(const gb_device* dev, gb_kernel kernel, int64_t m, 
  *   wd        work division, or NULL for the library's choice.  Native only;
  *             the emulated precision takes NULL.
  *   kernel    native variant (GB_KERNEL_AUTO for the library's choice).
- *   prec      GB_PREC_NATIVE or GB_PREC_EMULATED.
- *   slices    emulated only: number s of E4M3 digit slices per operand,
- *             1 <= s <= 16 (each slice carries 5 bits; 0 selects the default
- *             of 11); ignored for native.
+ *   prec      GB_PREC_NATIVE, GB_PREC_EMULATED or GB_PREC_EMULATED_BF16.
+ *   slices    emulated only: number s of digit slices per operand; E4M3:
+ *             1 <= s <= 16 (the first slice carries 4 bits, each further one
+ *             5; 0 selects the default of 11); BF16: 1 <= s <= 8 (7 bits, then
+ *             8 each; 0 selects 7, which covers 55 bits of each row's and
+ *             column's scale like 11 E4M3 slices; 8 covers 63, like 13 E4M3
+ *             slices); ignored for native.
+ *             BF16 digits: the same steps and rounding as E4M3 digits with
+ *             digits |d| <= 128 (b1 = 7, b = 8), the level sums read out of the
+ *             FP32 accumulators every 1024 / s K indices (each exact there) and
+ *             summed exactly in integers; k <= 2^22 (larger k:
+ *             GB_ERR_UNSUPPORTED).  gb_dgemm is its only entry point (the
+ *             step-by-step, host-buffer, grouped, serving and no-allocation
+ *             calls take E4M3 digits).  Its workspace holds, each part
+ *             1024-byte aligned and in this order: A's digits (2 s mp kp bytes,
+ *             mp = m rounded up to 128, kp = k rounded up to 16), B's digits
+ *             (2 s np kp, np = n rounded up to 32), A's row exponents (m int32),
+ *             B's column exponents (n int32), scratch; the digits are BF16 codes
+ *             tiled as in the E4M3 layout below, with R = 128 (A) and 32 (B)
+ *             lines per tile and 16 digits per 32-byte K block.
  *   workspace device buffer of at least gb_dgemm_workspace_size() bytes,
  *             256-byte aligned (emulated only; native takes NULL, 0).
  * Errors: GB_ERR_INVALID_ARG (sizes, pointers, leading dimensions, slices),
@@ -167,7 +184,7 @@ gb_status gb_dgemm(gb_queue* q, const gb_workdiv* wd, gb_kernel kernel, gb_preci
                    const double* A, int64_t lda, const double* B, int64_t ldb, double beta,
                    double* C, int64_t ldc, void* workspace, size_t workspace_bytes);
 
-/* Workspace bytes gb_dgemm needs (0 for native). */
+/* Workspace bytes gb_dgemm needs (0 for native; per emulated precision). */
 gb_status gb_dgemm_workspace_size(gb_precision prec, int slices, int64_t m, int64_t n,
                                   int64_t k, size_t* out);
 

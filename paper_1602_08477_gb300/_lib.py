@@ -19,7 +19,18 @@ STATUS_NAMES = {
     8: "GB_ERR_NONFINITE", 9: "GB_ERR_BUSY", 10: "GB_ERR_WORKSPACE",
 }
 
-GB_PREC_NATIVE, GB_PREC_EMULATED = 0, 1
+GB_PREC_NATIVE, GB_PREC_EMULATED, GB_PREC_EMULATED_BF16 = 0, 1, 2
+#: precision names of the Python API -> gb_precision
+PRECISIONS = {"native": GB_PREC_NATIVE, "emulated": GB_PREC_EMULATED,
+              "emulated_bf16": GB_PREC_EMULATED_BF16}
+
+
+def precision_code(name: str) -> int:
+    """gb_precision value of a precision name ("native", "emulated", "emulated_bf16")."""
+    try:
+        return PRECISIONS[name]
+    except KeyError:
+        raise ValueError(f"unknown precision {name!r}; one of {sorted(PRECISIONS)}") from None
 KERNELS = {"auto": 0, "naive": 1, "tiled": 2, "dfma": 3, "dmma": 4}
 GB_BAD_LINE = 0x40000000
 

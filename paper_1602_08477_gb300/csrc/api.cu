@@ -246,9 +246,36 @@ EmuLayout emu_layout(int s, int64_t m, int64_t n, int64_t k, bool colmax_scratch
     return L;
 }
 
+
+EmuLayout emu_layout_bf16(int s, int64_t m, int64_t n, int64_t k) {
+    EmuLayout L{};
+    L.kp = ((k + 15) / 16) * 16;
+    if (L.kp == 0) L.kp = 16;
+    auto up = [](size_t x) { return (x + 1023) & ~(size_t)1023; };
+    size_t off = 0;
+    const size_t mp = (size_t)((m + kEmuBM - 1) / kEmuBM) * kEmuBM;
+    L.bn = kBf16BN;
+    const size_t np = (size_t)((n + L.bn - 1) / L.bn) * L.bn;
+    L.a_digits = off;
+    off = up(off + 2 * (size_t)s * mp * (size_t)L.kp);
+    L.b_digits = off;
+    off = up(off + 2 * (size_t)s * np * (size_t)L.kp);
+    L.a_exp = off;
+    off = up(off + sizeof(int32_t) * (size_t)m);
+    L.b_exp = off;
+    off = up(off + sizeof(int32_t) * (size_t)n);
+    L.b_part = off;
+    off = up(off + sizeof(uint64_t) * (size_t)kColmaxParts * (size_t)n);
+    L.total = off;
+    return L;
+}
+
 }  // namespace gb
 
 using namespace gb;
+
+// Slice count of the BF16-digit precision: 0 selects 7 (55 bits of each line).
+static int resolve_bf16_slices(int slices) { return slices == 0 ? 7 : slices; }
 
 extern "C" {
 
@@ -362,6 +389,14 @@ gb_status gb_dgemm_workspace_size(gb_precision prec, int slices, int64_t m, int6
         *out = 0;
         return GB_OK;
     }
+    if (prec == GB_PREC_EMULATED_BF16) {
+        const int s = resolve_bf16_slices(slices);
+        if (s < 1 || s > kBf16MaxSlices)
+            return invalid("BF16-digit slices must be in [1, %d] (or 0 for the default), got %d",
+                           kBf16MaxSlices, slices);
+        *out = emu_layout_bf16(s, m, n, k).total;
+        return GB_OK;
+    }
     if (prec != GB_PREC_EMULATED) return invalid("unknown precision %d", (int)prec);
     const int s = resolve_slices(slices);
     if (s < 1 || s > 16) return invalid("slices must be in [1, 16] (or 0 for the default), got %d", slices);
@@ -387,8 +422,7 @@ gb_status gb_emulated_layout_get(int slices, int64_t m, int64_t n, int64_t k,
     return GB_OK;
 }
 
-static gb_status check_workspace(int s, int64_t m, int64_t n, int64_t k, void* ws, size_t bytes) {
-    const EmuLayout L = emu_layout(s, m, n, k);
+static gb_status check_workspace_layout(const EmuLayout& L, void* ws, size_t bytes) {
     if (!ws) {
         set_error("the emulated path needs a workspace of %zu bytes", L.total);
         return GB_ERR_WORKSPACE;
@@ -402,6 +436,10 @@ static gb_status check_workspace(int s, int64_t m, int64_t n, int64_t k, void* w
         return GB_ERR_WORKSPACE;
     }
     return GB_OK;
+}
+
+static gb_status check_workspace(int s, int64_t m, int64_t n, int64_t k, void* ws, size_t bytes) {
+    return check_workspace_layout(emu_layout(s, m, n, k), ws, bytes);
 }
 
 gb_status gb_emulated_split_a(gb_queue* q, int slices, int64_t m, int64_t n, int64_t k,
@@ -471,16 +509,27 @@ gb_status gb_dgemm(gb_queue* q, const gb_workdiv* wd, gb_kernel kernel, gb_preci
     if (!q) return invalid("q is NULL");
     gb_status st = check_gemm_args(m, n, k, alpha, A, lda, B, ldb, beta, C, ldc);
     if (st != GB_OK) return st;
-    if (prec != GB_PREC_NATIVE && prec != GB_PREC_EMULATED) return invalid("unknown precision %d", (int)prec);
+    if (prec != GB_PREC_NATIVE && prec != GB_PREC_EMULATED && prec != GB_PREC_EMULATED_BF16)
+        return invalid("unknown precision %d", (int)prec);
     if (kernel < GB_KERNEL_AUTO || kernel > GB_KERNEL_DMMA) return invalid("unknown kernel %d", (int)kernel);
     int s = 0;
     if (prec == GB_PREC_EMULATED) {
         s = resolve_slices(slices);
         if (s < 1 || s > 16) return invalid("slices must be in [1, 16] (or 0), got %d", slices);
-        if (wd) {
-            set_error("the emulated precision takes no work division (pass NULL)");
-            return GB_ERR_INVALID_WORKDIV;
+    } else if (prec == GB_PREC_EMULATED_BF16) {
+        s = resolve_bf16_slices(slices);
+        if (s < 1 || s > kBf16MaxSlices)
+            return invalid("BF16-digit slices must be in [1, %d] (or 0), got %d", kBf16MaxSlices,
+                           slices);
+        if (k > kBf16MaxK) {
+            set_error("the BF16-digit precision supports k <= %lld, got %lld",
+                      (long long)kBf16MaxK, (long long)k);
+            return GB_ERR_UNSUPPORTED;
         }
+    }
+    if (prec != GB_PREC_NATIVE && wd) {
+        set_error("the emulated precisions take no work division (pass NULL)");
+        return GB_ERR_INVALID_WORKDIV;
     }
     Variant v{};
     gb_workdiv resolved;
@@ -521,6 +570,22 @@ gb_status gb_dgemm(gb_queue* q, const gb_workdiv* wd, gb_kernel kernel, gb_preci
             e = launch_emu_products(L, s, m, n, k, alpha, beta, C, ldc, ws + lay.a_digits,
                                     ws + lay.b_digits, lay.kp, ea, fb);
         return finish_call(q, e, "emulated dgemm");
+    }
+    if (prec == GB_PREC_EMULATED_BF16) {
+        const EmuLayout lay = emu_layout_bf16(s, m, n, k);
+        st = check_workspace_layout(lay, workspace, workspace_bytes);
+        if (st != GB_OK) return st;
+        uint8_t* ws = static_cast<uint8_t*>(workspace);
+        int32_t* ea = reinterpret_cast<int32_t*>(ws + lay.a_exp);
+        int32_t* fb = reinterpret_cast<int32_t*>(ws + lay.b_exp);
+        cudaError_t e = launch_bf16_split_rows(L, s, m, k, A, lda, ws + lay.a_digits, lay.kp, ea);
+        if (e == cudaSuccess)
+            e = launch_bf16_split_cols(L, s, n, k, B, ldb, ws + lay.b_digits, lay.kp, fb,
+                                       reinterpret_cast<uint64_t*>(ws + lay.b_part));
+        if (e == cudaSuccess)
+            e = launch_bf16_products(L, s, m, n, alpha, beta, C, ldc, ws + lay.a_digits,
+                                     ws + lay.b_digits, lay.kp, ea, fb);
+        return finish_call(q, e, "emulated (BF16 digits) dgemm");
     }
 
     cudaError_t e = cudaSuccess;

@@ -101,6 +101,10 @@ gb_status build_layout(const gb_gemm_desc* d, int64_t count, Layout& L) {
             set_error("%s", msg);
             return (gb_status)v;
         }
+        if (x.precision == GB_PREC_EMULATED_BF16) {
+            set_error("problem %lld: a group takes native or E4M3-digit precision", (long long)i);
+            return GB_ERR_UNSUPPORTED;
+        }
         if (x.precision != GB_PREC_NATIVE && x.precision != GB_PREC_EMULATED)
             return bad("problem %lld: unknown precision", (long long)i);
         if (x.reserved != 0) return bad("problem %lld: reserved field must be 0", (long long)i);

@@ -257,6 +257,10 @@ gb_status gb_dgemm_host_workspace_size(gb_precision prec, int slices, int64_t m,
         set_error("m, n, k must be >= 0");
         return GB_ERR_INVALID_ARG;
     }
+    if (prec == GB_PREC_EMULATED_BF16) {
+        set_error("the host-buffer GEMM takes native or E4M3-digit precision");
+        return GB_ERR_UNSUPPORTED;
+    }
     if (prec != GB_PREC_NATIVE && prec != GB_PREC_EMULATED) {
         set_error("unknown precision %d", (int)prec);
         return GB_ERR_INVALID_ARG;
@@ -312,6 +316,10 @@ gb_status gb_dgemm_host(gb_queue* q, gb_precision prec, int slices, int64_t m, i
     }
     const int v = validate_gemm(m, n, k, alpha, A, lda, B, ldb, beta, C, ldc);
     if (v != GB_OK) return (gb_status)v;
+    if (prec == GB_PREC_EMULATED_BF16) {
+        set_error("the host-buffer GEMM takes native or E4M3-digit precision");
+        return GB_ERR_UNSUPPORTED;
+    }
     if (prec != GB_PREC_NATIVE && prec != GB_PREC_EMULATED) {
         set_error("unknown precision %d", (int)prec);
         return GB_ERR_INVALID_ARG;

@@ -165,6 +165,33 @@ constexpr int kEmuBM = 128;  // output tile rows of the products kernel (A digit
 // 48 s <= 512 (s <= 10) and 32 above.
 __host__ __device__ constexpr int emu_bn(int s) { return s <= 10 ? 48 : 32; }
 
+// ---- emulated FP64 with BF16 digits (ozaki_bf16.cu) ----
+// 8-bit signed digits (|d| <= 128) in BF16, kind::f16 MMAs.  Output tiles of
+// 128 x kBf16BN; digits stored pre-tiled as for E4M3 with 16 digits (32 bytes)
+// per K block, so K is padded to a multiple of 16:
+//   byte of digit t of line x at K index l (nks = kp / 16, c = 2 (l % 16)):
+//     ((x / R) * nks + l / 16) * s + t) * (R * 32) + (x % R) * 32
+//     + ((c / 16) ^ (((x % R) / 4) & 1)) * 16 + c % 16,   R = 128 (A) or 32 (B).
+constexpr int kBf16BN = 32;
+constexpr int kBf16MaxSlices = 8;          // two sets of 8 levels x 32 columns fill TMEM
+constexpr int64_t kBf16MaxK = (int64_t)1 << 22;  // the epilogue's int64 sums stay exact
+EmuLayout emu_layout_bf16(int s, int64_t m, int64_t n, int64_t k);
+cudaError_t launch_bf16_split_rows(const Launch& L, int s, int64_t m, int64_t k, const double* A,
+                                   int64_t lda, uint8_t* digits, int64_t kp, int32_t* exps);
+cudaError_t launch_bf16_split_cols(const Launch& L, int s, int64_t n, int64_t k, const double* B,
+                                   int64_t ldb, uint8_t* digits, int64_t kp, int32_t* exps,
+                                   uint64_t* part);
+cudaError_t launch_bf16_products(const Launch& L, int s, int64_t m, int64_t n, double alpha,
+                                 double beta, double* C, int64_t ldc, const uint8_t* a_digits,
+                                 const uint8_t* b_digits, int64_t kp, const int32_t* a_exp,
+                                 const int32_t* b_exp);
+
+
+// First half of e1 for the columns of B: partial column maxima over *ks_out (at
+// most kColmaxParts) K ranges into `part` (ks_out x n uint64): the largest
+// absolute bit pattern of each range, bit 63 alone for a range with NaN or Inf.
+cudaError_t launch_colmax_part(const Launch& L, int64_t n, int64_t k, const double* B,
+                               int64_t ldb, uint64_t* part, int* ks_out);
 
 cudaError_t launch_split_rows(const Launch& L, int s, int64_t m, int64_t k, const double* A,
                               int64_t lda, uint8_t* digits, int64_t kp, int32_t* exps);

@@ -20,9 +20,8 @@
 #include <cstdint>
 #include <type_traits>
 
+#include "emu_common.cuh"
 #include "internal.h"
-
-#define GB_BAD_LINE_DEV 0x40000000
 
 namespace gb {
 namespace {
@@ -58,15 +57,6 @@ __device__ __forceinline__ void fill_e4m3_table() {
         s_window[x] = (uint8_t)(d >= -16 && d <= 16 ? e4m3_of_int(d) : 0u);
     }
     __syncthreads();
-}
-
-// frexp exponent of a finite non-negative double given by its bits (0 -> 0).
-__device__ __forceinline__ int frexp_exp_bits(uint64_t absbits) {
-    if (absbits == 0) return 0;
-    const int ef = (int)(absbits >> 52);
-    if (ef != 0) return ef - 1022;
-    const int p = 63 - __clzll((long long)absbits);  // subnormal: value = mant * 2^-1074
-    return p - 1073;
 }
 
 // Fixed-point image of an element for S digits: int64 holds it for S <= 11,
@@ -600,10 +590,8 @@ cudaError_t launch_grouped_split(const Launch& L, const EmuProb* probs, const Em
     return cudaGetLastError();
 }
 
-cudaError_t launch_split_cols(const Launch& L, int s, int64_t n, int64_t k, const double* B,
-                              int64_t ldb, uint8_t* digits, int64_t kp, int32_t* exps,
-                              uint64_t* part) {
-    if (n == 0) return cudaSuccess;
+cudaError_t launch_colmax_part(const Launch& L, int64_t n, int64_t k, const double* B,
+                               int64_t ldb, uint64_t* part, int* ks_out) {
     // K ranges of the column maxima: about sixteen CTAs per SM over the column
     // strips (enough loads in flight to stream B), at least 64 rows each, at most
     // kColmaxParts
@@ -613,16 +601,25 @@ cudaError_t launch_split_cols(const Launch& L, int s, int64_t n, int64_t k, cons
     if (ks > kcap) ks = kcap;
     if (ks > kColmaxParts) ks = kColmaxParts;
     if (ks < 1) ks = 1;
+    *ks_out = (int)ks;
     const int64_t rows_per = (k + ks - 1) / ks;
     colmax_part_kernel<<<dim3((unsigned)ncb, (unsigned)ks), 256, 0, L.stream>>>(n, k, B, ldb,
                                                                               rows_per, part);
-    cudaError_t err = cudaGetLastError();
+    return cudaGetLastError();
+}
+
+cudaError_t launch_split_cols(const Launch& L, int s, int64_t n, int64_t k, const double* B,
+                              int64_t ldb, uint8_t* digits, int64_t kp, int32_t* exps,
+                              uint64_t* part) {
+    if (n == 0) return cudaSuccess;
+    int ks = 1;
+    cudaError_t err = launch_colmax_part(L, n, k, B, ldb, part, &ks);
     if (err != cudaSuccess) return err;
     const int64_t np = (n + emu_bn(s) - 1) / emu_bn(s) * emu_bn(s);  // B digit tile padding
     const dim3 grid((unsigned)((np + 31) / 32), (unsigned)((kp + 63) / 64));
 #define GB_LAUNCH_COLS(SS)                                                                   \
     split_cols_kernel<SS><<<grid, 256, 0, L.stream>>>(n, k, B, ldb, digits, kp, exps, part, \
-                                                      (int)ks, L.status)
+                                                      ks, L.status)
     GB_SWITCH_S(s, GB_LAUNCH_COLS)
 #undef GB_LAUNCH_COLS
     return cudaGetLastError();

@@ -515,6 +515,10 @@ gb_status gb_server_submit(gb_server* S, const gb_request* req, uint64_t* reques
         return GB_ERR_INVALID_ARG;
     }
     const gb_request& q = *req;
+    if (q.precision == GB_PREC_EMULATED_BF16) {
+        set_error("gb_server_submit: requests take native or E4M3-digit precision");
+        return GB_ERR_UNSUPPORTED;
+    }
     if (q.m < 0 || q.n < 0 || q.k < 0 || (q.precision != GB_PREC_NATIVE && q.precision != GB_PREC_EMULATED) ||
         q.slices < 0 || q.slices > 16 || (q.A_host && !q.B_host) || !(q.alpha == q.alpha) ||
         !(q.beta == q.beta)) {

@@ -146,6 +146,30 @@ __device__ __forceinline__ void mma_e4m3(uint32_t tmem_d, uint64_t adesc, uint64
         : "memory");
 }
 
+// Instruction descriptor of kind::f16 with BF16 A and B (both operands of one
+// MMA of this kind have the same type), F32 accumulator, both K-major, M x N.
+__host__ __device__ constexpr uint32_t idesc_bf16_f32(int M, int N) {
+    return (1u << 4)                        // D format: F32
+           | (1u << 7) | (1u << 10)         // A, B format: BF16
+           | (0u << 15) | (0u << 16)        // A, B K-major
+           | ((uint32_t)(N >> 3) << 17)     // N >> 3
+           | ((uint32_t)(M >> 4) << 24);    // M >> 4
+}
+
+// D[tmem] (+)= A[smem] * B[smem]^T with BF16 operands (K = 16 per MMA, 32 bytes
+// of K per operand row as for E4M3), issued by one thread.
+__device__ __forceinline__ void mma_bf16(uint32_t tmem_d, uint64_t adesc, uint64_t bdesc,
+                                         uint32_t idesc, uint32_t accumulate) {
+    asm volatile(
+        "{\n"
+        ".reg .pred p;\n"
+        "setp.ne.b32 p, %4, 0;\n"
+        "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n"
+        "}\n" ::"r"(tmem_d),
+        "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate)
+        : "memory");
+}
+
 // The same MMA with the A operand kept in the tensor core's collector buffer:
 // A_FILL reads A from shared memory and keeps it, A_LASTUSE takes A from the
 // collector (the descriptor must name the same A as the filling MMA) and then

@@ -10,7 +10,8 @@ from __future__ import annotations
 import ctypes
 
 from . import _lib
-from ._lib import GB_PREC_EMULATED, GB_PREC_NATIVE, KERNELS, EmulatedLayout, Workdiv, check
+from ._lib import (GB_PREC_NATIVE, KERNELS, EmulatedLayout, Workdiv, check,
+                   precision_code)
 
 
 class Device:
@@ -94,7 +95,7 @@ def workdiv_suggest(kernel: str, m: int, n: int, k: int, device: Device | None =
 
 def workspace_size(precision: str, slices: int, m: int, n: int, k: int) -> int:
     out = ctypes.c_size_t()
-    prec = GB_PREC_EMULATED if precision == "emulated" else GB_PREC_NATIVE
+    prec = precision_code(precision)
     check(_lib.load().gb_dgemm_workspace_size(prec, slices, m, n, k, ctypes.byref(out)),
           "gb_dgemm_workspace_size")
     return out.value
@@ -131,8 +132,9 @@ def dgemm(A, B, C=None, alpha: float = 1.0, beta: float = 0.0, *, kernel: str = 
 
     A (m x k), B (k x n), C (m x n) are float64 CUDA tensors, row-major, any
     leading dimension (a column slice of a wider tensor is fine).  C is created
-    (zeros) when None.  precision: "native" or "emulated"; kernel: "auto",
-    "naive", "tiled", "dfma", "dmma"; slices: emulated digit slices (0 = default).
+    (zeros) when None.  precision: "native", "emulated" (E4M3 digits) or
+    "emulated_bf16" (BF16 digits); kernel: "auto", "naive", "tiled", "dfma",
+    "dmma"; slices: emulated digit slices (0 = the precision's default).
     """
     import torch
     m, k = A.shape
@@ -149,10 +151,10 @@ def dgemm(A, B, C=None, alpha: float = 1.0, beta: float = 0.0, *, kernel: str = 
     pb, ldb = _matrix_args(B, "B")
     pc, ldc = _matrix_args(C, "C")
     lda, ldb, ldc = max(lda, k, 1), max(ldb, n, 1), max(ldc, n, 1)
-    prec = GB_PREC_EMULATED if precision == "emulated" else GB_PREC_NATIVE
+    prec = precision_code(precision)
     ws_ptr, ws_bytes = None, 0
-    if prec == GB_PREC_EMULATED:
-        need = workspace_size("emulated", slices, m, n, k)
+    if prec != GB_PREC_NATIVE:
+        need = workspace_size(precision, slices, m, n, k)
         if workspace is None:
             workspace = alloc_workspace(need, A.device)
         ws_ptr, ws_bytes = ctypes.c_void_p(workspace.data_ptr()), workspace.numel() * workspace.element_size()
@@ -165,7 +167,7 @@ def dgemm(A, B, C=None, alpha: float = 1.0, beta: float = 0.0, *, kernel: str = 
 def host_workspace_size(precision: str, slices: int, m: int, n: int, k: int) -> int:
     """Device workspace bytes of dgemm_host for these sizes."""
     out = ctypes.c_size_t()
-    prec = GB_PREC_EMULATED if precision == "emulated" else GB_PREC_NATIVE
+    prec = precision_code(precision)
     check(_lib.load().gb_dgemm_host_workspace_size(prec, slices, m, n, k, ctypes.byref(out)),
           "gb_dgemm_host_workspace_size")
     return out.value
@@ -207,7 +209,7 @@ def dgemm_host(A, B, C, alpha: float = 1.0, beta: float = 0.0, *, precision: str
     pb, ldb = _host_matrix_args(B, "B")
     pc, ldc = _host_matrix_args(C, "C")
     lda, ldb, ldc = max(lda, k, 1), max(ldb, n, 1), max(ldc, n, 1)
-    prec = GB_PREC_EMULATED if precision == "emulated" else GB_PREC_NATIVE
+    prec = precision_code(precision)
     need = host_workspace_size(precision, slices, m, n, k)
     if workspace is None:
         workspace = alloc_workspace(need)

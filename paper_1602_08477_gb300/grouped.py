@@ -8,7 +8,7 @@ from __future__ import annotations
 import ctypes
 
 from . import _lib
-from ._lib import check
+from ._lib import check, precision_code
 
 TILES = {"auto": 0, "64x64": 1, "32x32": 2, "64x32": 3, "32x64": 4,
          "emu_rows": 5, "emu_cols": 6}
@@ -67,7 +67,7 @@ def make_descs(problems):
         d.A, d.lda = A.data_ptr(), _ld(A, k)
         d.B, d.ldb = B.data_ptr(), _ld(B, n)
         d.C, d.ldc = C.data_ptr(), _ld(C, n)
-        d.precision = 1 if p.get("precision", "native") == "emulated" else 0
+        d.precision = precision_code(p.get("precision", "native"))
         d.slices = p.get("slices", 0)
         d.tile = TILES[p.get("tile", "auto")] if isinstance(p.get("tile", "auto"), str) else p["tile"]
         d.reserved = 0

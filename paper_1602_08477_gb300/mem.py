@@ -11,7 +11,7 @@ import ctypes
 import numpy as np
 
 from . import _lib
-from ._lib import GB_PREC_EMULATED, GB_PREC_NATIVE, KERNELS, check
+from ._lib import KERNELS, check, precision_code
 
 
 class GbBuf(ctypes.Structure):
@@ -133,7 +133,7 @@ def dgemm_buffers(queue, A: Buffer, B: Buffer, C: Buffer, alpha: float = 1.0, be
     (m, k), (k2, n) = A.shape, B.shape
     if k2 != k or C.shape != (m, n):
         raise ValueError(f"shapes {A.shape} x {B.shape} -> {C.shape} do not match")
-    prec = GB_PREC_EMULATED if precision == "emulated" else GB_PREC_NATIVE
+    prec = precision_code(precision)
     ws = ctypes.c_void_p(workspace.ptr) if workspace is not None else None
     wbytes = workspace.shape[0] * workspace.dtype.itemsize if workspace is not None else 0
     check(_lib.load().gb_dgemm(queue.handle, None, KERNELS[kernel], prec, slices, m, n, k, alpha,

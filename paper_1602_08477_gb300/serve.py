@@ -4,7 +4,7 @@ from __future__ import annotations
 import ctypes
 
 from . import _lib
-from ._lib import check
+from ._lib import check, precision_code
 
 
 class Request(ctypes.Structure):
@@ -75,7 +75,7 @@ class Server:
                C=None, out=None, seed=0):
         """A, B, C, out: C-contiguous float64 host arrays (numpy) or None (device-
         generated operands from `seed`).  Returns the request id."""
-        r = Request(m, n, k, alpha, beta, 1 if precision == "emulated" else 0, slices,
+        r = Request(m, n, k, alpha, beta, precision_code(precision), slices,
                     _ptr(A), _ptr(B), _ptr(C), _ptr(out), seed)
         rid = ctypes.c_uint64()
         check(_lib.load().gb_server_submit(self.handle, ctypes.byref(r), ctypes.byref(rid)),

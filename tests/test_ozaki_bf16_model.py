@@ -14,6 +14,8 @@ import pytest
 from oracle import cgemm, exact, ozaki
 from synth import generators as g
 
+from gpu_util import inputs, within_bound
+
 B1, B, DMAX = ozaki.FORMATS["bf16"]
 
 
@@ -189,3 +191,13 @@ def test_e4m3_digits_unchanged_by_the_format_parameter():
     D2, _ = ozaki.slice_digits(A, e, 10, "e4m3", axis=1)
     assert D.dtype == np.int8 and np.array_equal(D, D2)
     assert np.abs(D).max() <= 16
+
+
+def test_short_k_hard_set_needs_eight_digits():
+    # the FP64 bound shrinks with k faster than the truncation error does: on the
+    # 16-decade hard set at n = k = 256 (C = 1.5 A B + 0.5 C) 7 BF16 digits miss
+    # it, 8 meet it (E4M3 digits: 12 miss, 13 meet)
+    A, Bm, C0 = inputs("hard", 256, 256, 256, g.BASE_SEED + 3)
+    r = {s: within_bound(ozaki.emulated_gemm(1.5, A, Bm, 0.5, C0, s=s, fmt="bf16"),
+                         1.5, A, Bm, 0.5, C0) for s in (7, 8)}
+    assert r[7] > 1.0 and r[8] <= 1.0
