@@ -7,7 +7,8 @@ path whose result is checked against the FP64 error bound; the native FP64 path
 inputs.  Inputs (8 n^2 bytes each) are larger than the 129 MB L2 at the default
 n, so no flush is needed.  At one GPU the same JSON line also carries, as
 sub-records: the accuracy of both paths against a double-double reference on
-sampled rows (`parity`), the 16-decade hard set at its slice count (`hard`),
+sampled rows (`parity`), the same inputs through the BF16 digit format
+(`bf16_digits`), the 16-decade hard set at its slice count (`hard`),
 the 2048-problem grouped workload against one launch per GEMM (`grouped`) and
 two short serving runs, at the specified and at a sustainable arrival rate
 (`serve`).  Other workloads print their own line (--workload).
@@ -71,6 +72,7 @@ def parse():
     p.add_argument("--no-serve-baseline", action="store_true",
                    help="skip the one-GEMM-per-launch run of the same serving trace")
     p.add_argument("--hard-slices", type=int, default=11)
+    p.add_argument("--bf16-slices", type=int, default=7)
     p.add_argument("--sub-serve-seconds", type=float, default=10.0)
     p.add_argument("--no-sub-records", action="store_true",
                    help="default workload only: skip the hard, grouped and serving sub-records")
@@ -885,6 +887,36 @@ def hard_record(args, gb, g, np, torch, A, B, C, q):
             "rows_checked": len(rows), "steps": 5, "warmup": 2, "clocks": clk}
 
 
+def bf16_record(args, gb, np, torch, A, B, C, q, A_h, B_h):
+    """The same uniform GEMM through the second digit format (8-bit digits in
+    BF16, kind::f16 MMAs) at the slice count that meets the FP64 bound there
+    (--bf16-slices), the whole path per step; rho against the double-double
+    reference on sampled rows."""
+    n, s = args.n, args.bf16_slices
+    ws = gb.alloc_workspace(gb.workspace_size("emulated_bf16", s, n, n, n))
+    clocks = ClockSampler(0)
+    clocks.start()
+    step = lambda: gb.dgemm(A, B, C, precision="emulated_bf16", slices=s, queue=q, workspace=ws)
+    ms = _time_stream(torch, step, 5, 2)
+    clk = clocks.stop()
+    q.wait()
+    rows = np.random.default_rng(n + 100 * s).choice(n, 4, replace=False)
+    got = C[torch.from_numpy(rows).cuda()].cpu().numpy()
+    from oracle import cgemm
+    hilo = cgemm.dgemm_dd_rows(A_h, B_h, rows)
+    del ws
+    torch.cuda.empty_cache()
+    pairs = s * (s + 1) / 2 * 2.0 * n ** 3
+    return {"workload": f"square DGEMM C = A B, n = {n}, uniform[-1,1] (the main line's inputs)",
+            "digits": "8-bit signed digits in BF16, kind::f16 MMAs, FP32 level sums read out "
+                      "every 1024 / s K indices",
+            "slices": s, "ms_per_step": round(ms, 3),
+            "tflops": round(2.0 * n ** 3 / (ms * 1e-3) / 1e12, 3),
+            "bf16_pair_tflops_whole_path": round(pairs / (ms * 1e-3) / 1e12, 1),
+            "rho_emulated": rho_rows(got, A_h, B_h, rows, hilo),
+            "rows_checked": len(rows), "steps": 5, "warmup": 2, "clocks": clk}
+
+
 def grouped_sub_record(args):
     """The grouped workload, summarised for the default line."""
     r = grouped_measure(args, 5, 2, baselines=True, e2e=False)
@@ -1096,6 +1128,7 @@ def main():
     if rank == 0 and world == 1 and not args.no_sub_records:
         del A_p, B_p, C_p, hws
         torch.cuda.empty_cache()
+        out["bf16_digits"] = bf16_record(args, gb, np, torch, A, B, C, q, A_h, B_h)
         out["hard"] = hard_record(args, gb, g, np, torch, A, B, C, q)
         out["grouped"] = grouped_sub_record(args)
         out["serve"] = serve_sub_record(args, gb, g, np)
