@@ -6,8 +6,10 @@
  * the work division (Section 3.2) becomes persistent: a fixed grid of CTAs
  * (SM count x resident CTAs per SM) takes tiles of all problems from a device
  * counter, expensive tiles first; emulated problems run each split-precision
- * step in one launch per distinct slice count (four launches per slice count).
- * A plan records the launches in a CUDA graph once and replays it.
+ * step in one launch per distinct slice count (three launches per slice count:
+ * the split of A's rows, the column maxima and split of B's columns, the
+ * products).  A plan records the launches in a CUDA graph once and replays it,
+ * the two splits as parallel branches.
  *
  * Ownership: descriptors are read during the call only; A, B, C and the
  * workspace are the caller's device buffers and must stay valid while a plan

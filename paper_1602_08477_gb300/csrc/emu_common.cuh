@@ -81,18 +81,26 @@ __device__ __forceinline__ double i128_to_double_subnormal(uint64_t hi, uint64_t
     return __longlong_as_double((long long)(M | (neg ? 0x8000000000000000ull : 0ull)));
 }
 
-__device__ __forceinline__ double i128_to_double_scaled(I128 x, int E) {
-    const bool neg = x.hi < 0;
-    uint64_t hi = (uint64_t)x.hi, lo = x.lo;
-    // |T| (two's complement negation of the 128-bit value when negative)
+// |T| as (hi, lo), its sign and the position p of its leading one (p = -1 for
+// T = 0).
+__device__ __forceinline__ void i128_magnitude(I128 x, uint64_t& hi, uint64_t& lo, bool& neg,
+                                               int& p) {
+    neg = x.hi < 0;
+    hi = (uint64_t)x.hi;
+    lo = x.lo;
+    // two's complement negation of the 128-bit value when negative
     lo = neg ? ~lo + 1 : lo;
     hi = neg ? ~hi + (lo == 0 ? 1 : 0) : hi;
-    if ((hi | lo) == 0) return 0.0;
-    const int p = hi ? 127 - __clzll((long long)hi) : 63 - __clzll((long long)lo);
+    p = hi ? 127 - __clzll((long long)hi) : 63 - __clzll((long long)lo);
+}
+
+// The normal-range rounding of |T| 2^E (T != 0, p + E + 1023 >= 1), branch-free
+// so that the outputs of a thread round as independent instruction streams.
+__device__ __forceinline__ double i128_round_normal(uint64_t hi, uint64_t lo, int p, int E,
+                                                    bool neg) {
     const int eb = p + E + 1023;  // biased exponent before a rounding carry
-    if (eb < 1) return i128_to_double_subnormal(hi, lo, p, E, neg);
     // leading one to bit 127: by 64 first when the high word is empty
-    const int c = 127 - p;                    // 0 .. 127
+    const int c = (127 - p) & 127;            // 0 .. 127
     const uint64_t h1 = c >= 64 ? lo : hi;
     const uint64_t l1 = c >= 64 ? 0 : lo;
     const int c1 = c & 63;
@@ -109,6 +117,16 @@ __device__ __forceinline__ double i128_to_double_scaled(I128 x, int E) {
                                     : (((uint64_t)e << 52) | (M & 0xFFFFFFFFFFFFFull));
     // sign by bit manipulation: GB300's FP64 pipe is slow even for negation
     return __longlong_as_double((long long)(bits | (neg ? 0x8000000000000000ull : 0ull)));
+}
+
+__device__ __forceinline__ double i128_to_double_scaled(I128 x, int E) {
+    uint64_t hi, lo;
+    bool neg;
+    int p;
+    i128_magnitude(x, hi, lo, neg, p);
+    if ((hi | lo) == 0) return 0.0;
+    if (p + E + 1023 < 1) return i128_to_double_subnormal(hi, lo, p, E, neg);
+    return i128_round_normal(hi, lo, p, E, neg);
 }
 
 // x += v * 2^sh exactly (0 <= sh <= 127 - 63).
@@ -150,40 +168,66 @@ __host__ __device__ constexpr int epi_col(int g, int j) {
     return j < 8 ? 8 * g + j : 32 + 4 * g + (j - 8);
 }
 
-// Columns J0 .. J0+W-1 of this thread (see epi_col) of one output row: all column
-// exponents loaded first (L1 hits), all outputs RN(T 2^E) formed, alpha / beta
-// applied, then the stores; `crow` is the row (stride `cstride` between columns).
-template <int S, int J0, int W, int N>
+// Columns J0 .. J0+W-1 of this thread (see epi_col) of one output row, in groups
+// of G: the group's column exponents loaded (L1 hits), its outputs RN(T 2^E)
+// formed, alpha / beta applied, then its stores; `crow` is the row (stride
+// `cstride` between columns).  G = 4 rounds four outputs as independent
+// instruction streams; G = 1 where the registers for that are not free.
+template <int S, int J0, int W, int N, int G = 4>
 __device__ __forceinline__ void store_part(const I128 (&T)[N], int32_t ei, int Ebase,
                                            const int32_t* fB, int64_t col0, int64_t n, int cg,
                                            bool plain, bool beta0, double alpha, double beta,
                                            double* crow, int64_t cstride) {
+    static_assert(W % G == 0, "whole groups of columns");
     const bool bad_row = ei == GB_BAD_LINE_DEV;
-    int32_t fj[W];
 #pragma unroll
-    for (int j = 0; j < W; ++j) {
-        const int64_t col = col0 + epi_col(cg, J0 + j);
-        fj[j] = col < n ? fB[col] : 0;
-    }
-    double out[W];
+    for (int g0 = 0; g0 < W; g0 += G) {
+        int32_t fj[G];
 #pragma unroll
-    for (int j = 0; j < W; ++j) {
-        const bool bad = bad_row || fj[j] == GB_BAD_LINE_DEV;
-        out[j] = bad ? __longlong_as_double(0x7FF8000000000000ll)
-                     : i128_to_double_scaled(T[J0 + j], ei + fj[j] + Ebase);
-        if (!plain && !bad) {
-            const int64_t col = col0 + epi_col(cg, J0 + j);
-            if (col < n) {
+        for (int j = 0; j < G; ++j) {
+            const int64_t col = col0 + epi_col(cg, J0 + g0 + j);
+            fj[j] = col < n ? fB[col] : 0;
+        }
+        // the group's outputs through the branch-free normal-range rounding
+        // (independent instruction streams; T = 0 by a select), subnormal results
+        // again in a second pass that is rarely taken
+        double out[G];
+        uint32_t special = 0;
+#pragma unroll
+        for (int j = 0; j < G; ++j) {
+            const bool bad = bad_row || fj[j] == GB_BAD_LINE_DEV;
+            uint64_t hi, lo;
+            bool neg;
+            int p;
+            i128_magnitude(T[J0 + g0 + j], hi, lo, neg, p);
+            const int E = ei + fj[j] + Ebase;
+            const bool zero = (hi | lo) == 0;
+            const bool in_c = col0 + epi_col(cg, J0 + g0 + j) < n;
+            special |= (in_c && !bad && !zero && p + E + 1023 < 1) ? (1u << j) : 0u;
+            out[j] = bad ? __longlong_as_double(0x7FF8000000000000ll)
+                         : zero ? 0.0 : i128_round_normal(hi, lo, p, E, neg);
+        }
+        if (special) {
+#pragma unroll
+            for (int j = 0; j < G; ++j)
+                if ((special >> j) & 1u)
+                    out[j] = i128_to_double_scaled(T[J0 + g0 + j], ei + fj[j] + Ebase);
+        }
+#pragma unroll
+        for (int j = 0; j < G; ++j) {
+            const bool bad = bad_row || fj[j] == GB_BAD_LINE_DEV;
+            const int64_t col = col0 + epi_col(cg, J0 + g0 + j);
+            if (!plain && !bad && col < n) {
                 double o = __dmul_rn(alpha, out[j]);
                 if (!beta0) o = __dadd_rn(o, __dmul_rn(beta, crow[col * cstride]));
                 out[j] = o;
             }
         }
-    }
 #pragma unroll
-    for (int j = 0; j < W; ++j) {
-        const int64_t col = col0 + epi_col(cg, J0 + j);
-        if (col < n) crow[col * cstride] = out[j];
+        for (int j = 0; j < G; ++j) {
+            const int64_t col = col0 + epi_col(cg, J0 + g0 + j);
+            if (col < n) crow[col * cstride] = out[j];
+        }
     }
 }
 

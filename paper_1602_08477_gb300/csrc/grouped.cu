@@ -218,10 +218,9 @@ gb_status build_layout(const gb_gemm_desc* d, int64_t count, Layout& L) {
         L.keys[1].push_back(colblks);
         L.keys[2].push_back(tblks);
         L.keys[3].push_back(tiles);
-        const int64_t ncb = (e.n + 31) / 32;                                 // real columns
         const int64_t ncbp = ((e.n + e.rb - 1) / e.rb * e.rb + 31) / 32;     // padded to tiles
         rows += (e.m + kEmuBM - 1) / kEmuBM * kEmuBM;  // 128-row blocks of the split of A
-        colblks += ncb;
+        colblks += ncbp;
         tblks += ncbp * ((w.kp + 63) / 64);
         const int64_t row_side = e.trans ? e.n : e.m;
         const int64_t nt = ((row_side + kEmuBM - 1) / kEmuBM) * e.tiles_n;
@@ -301,7 +300,7 @@ gb_status grouped_enqueue_async(const Launch& L, const gb_gemm_desc* descs, int6
         for (size_t r = 0; r < lay.s_ranges.size() && e == cudaSuccess; ++r) {
             e = launch_grouped_split(L, d, keys, lay.s_ranges[r]);
             if (e == cudaSuccess) e = launch_grouped_products(L, d, keys, lay.s_ranges[r]);
-            nl += 4;
+            nl += 3;
         }
     }
     if (launches) *launches = nl;
@@ -373,7 +372,8 @@ gb_status gb_grouped_workspace_size(const gb_gemm_desc* descs, int64_t count, si
     return GB_OK;
 }
 
-static gb_status enqueue_plan(gb_grouped_plan* p, cudaStream_t stream) {
+static gb_status enqueue_plan(gb_grouped_plan* p, cudaStream_t stream,
+                              const SplitFork* fk = nullptr) {
     const Launch L{stream, p->q->status, p->q->dev->sm_count};
     cudaError_t e = cudaSuccess;
     if (p->native_tiles > 0) {
@@ -383,7 +383,7 @@ static gb_status enqueue_plan(gb_grouped_plan* p, cudaStream_t stream) {
                                       p->grid_native);
     }
     for (size_t r = 0; r < p->s_ranges.size() && e == cudaSuccess; ++r) {
-        e = launch_grouped_split(L, p->d_emu, p->d_keys, p->s_ranges[r]);
+        e = launch_grouped_split(L, p->d_emu, p->d_keys, p->s_ranges[r], fk);
         if (e == cudaSuccess) e = launch_grouped_products(L, p->d_emu, p->d_keys, p->s_ranges[r]);
     }
     if (e != cudaSuccess) return cuda_fail(e, "grouped launch");
@@ -441,7 +441,7 @@ gb_status gb_grouped_plan_create(gb_queue* q, const gb_gemm_desc* descs, int64_t
     if (grid > p->native_tiles) grid = p->native_tiles;
     p->grid_native = (int)(grid > 0 ? grid : 1);
     p->launches = (p->native_tiles > 0 ? 1 : 0) +
-                  4 * (int)L.s_ranges.size();
+                  3 * (int)L.s_ranges.size();
 
     cudaError_t e = cudaSuccess;
     if (!L.native.empty())
@@ -459,11 +459,17 @@ gb_status gb_grouped_plan_create(gb_queue* q, const gb_gemm_desc* descs, int64_t
         return cuda_fail(e, "uploading the grouped tables");
     }
     if (use_graph) {
+        // captured with the split of A on a second stream beside that of B: in the
+        // graph the two are parallel branches that join before the products
         cudaStream_t cs = nullptr;
+        SplitFork fk{nullptr, nullptr, nullptr};
         e = cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking);
+        if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&fk.side, cudaStreamNonBlocking);
+        if (e == cudaSuccess) e = cudaEventCreateWithFlags(&fk.fork, cudaEventDisableTiming);
+        if (e == cudaSuccess) e = cudaEventCreateWithFlags(&fk.join, cudaEventDisableTiming);
         if (e == cudaSuccess) e = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal);
         if (e == cudaSuccess) {
-            st = enqueue_plan(p, cs);
+            st = enqueue_plan(p, cs, &fk);
             cudaGraph_t g = nullptr;
             cudaError_t e2 = cudaStreamEndCapture(cs, &g);
             if (st == GB_OK && e2 == cudaSuccess) {
@@ -475,6 +481,9 @@ gb_status gb_grouped_plan_create(gb_queue* q, const gb_gemm_desc* descs, int64_t
             }
         }
         if (cs) cudaStreamDestroy(cs);
+        if (fk.side) cudaStreamDestroy(fk.side);
+        if (fk.fork) cudaEventDestroy(fk.fork);
+        if (fk.join) cudaEventDestroy(fk.join);
         if (st != GB_OK || e != cudaSuccess) {
             if (p->exec) cudaGraphExecDestroy(p->exec);
             if (p->graph) cudaGraphDestroy(p->graph);

@@ -151,9 +151,18 @@ struct EmuSRange {
     int64_t kp_max;  // longest padded K of the range's problems
 };
 
-// Grouped e1 + e2 over the problems of one slice-count range (three launches).
+// A second stream and two events for running the split of A beside that of B:
+// the A rows go to `side` after `fork` is recorded on the launch stream, which
+// waits for `join` (recorded on `side` after them) before the products.
+struct SplitFork {
+    cudaStream_t side;
+    cudaEvent_t fork, join;
+};
+
+// Grouped e1 + e2 over the problems of one slice-count range (three launches;
+// with `fk`, the split of A on fk->side beside the two launches for B).
 cudaError_t launch_grouped_split(const Launch& L, const EmuProb* probs, const EmuKeys& keys,
-                                 const EmuSRange& r);
+                                 const EmuSRange& r, const SplitFork* fk = nullptr);
 // Grouped e3 + e4: persistent CTAs over the 128 x emu_bn(s) output tiles of the
 // problems of one slice-count range.
 cudaError_t launch_grouped_products(const Launch& L, const EmuProb* probs, const EmuKeys& keys,

@@ -570,8 +570,9 @@ __device__ __forceinline__ void bf16_products_persistent(const Walk& walk, uint8
                 const long long ab = __double_as_longlong(alpha), bb = __double_as_longlong(beta);
                 const bool beta0 = (bb & 0x7FFFFFFFFFFFFFFFll) == 0;
                 const bool plain = ab == 0x3FF0000000000000ll && beta0;
-                store_part<S, 0, 8>(T, ei, Ebase, a.fB, col0, n, cgroup, plain, beta0, alpha, beta,
-                                    crow, 1);
+                // one output at a time: the unit sums HI / MID / LO hold the registers
+                store_part<S, 0, 8, 8, 1>(T, ei, Ebase, a.fB, col0, n, cgroup, plain, beta0, alpha,
+                                          beta, crow, 1);
             }
             __syncwarp();
             if (lane == 0) ptx::mbar_arrive(&tail->args_empty[as]);

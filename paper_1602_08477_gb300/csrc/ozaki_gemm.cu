@@ -496,11 +496,13 @@ __device__ __forceinline__ void products_persistent(const Walk& walk, int chunk_
                 // 32 lanes then store 32 consecutive doubles of one row of C); the
                 // thread's columns in the parts of add_levels (8, then 4 for
                 // 48-column tiles) to stay within the registers
-                store_part<S, 0, 8>(T, ei, Ebase, fB, col0, n, cgroup, plain, beta0, alpha, beta,
-                                    crow, cstride);
+                // 48-column tiles hold 12 128-bit sums per thread: one output at a time
+                constexpr int G = CW > 8 ? 1 : 4;
+                store_part<S, 0, 8, CW, G>(T, ei, Ebase, fB, col0, n, cgroup, plain, beta0, alpha,
+                                           beta, crow, cstride);
                 if constexpr (CW > 8)
-                    store_part<S, 8, 4>(T, ei, Ebase, fB, col0, n, cgroup, plain, beta0, alpha,
-                                        beta, crow, cstride);
+                    store_part<S, 8, 4, CW, G>(T, ei, Ebase, fB, col0, n, cgroup, plain, beta0,
+                                               alpha, beta, crow, cstride);
             }
             __syncwarp();
             if (lane == 0) ptx::mbar_arrive(&tail->args_empty[as]);

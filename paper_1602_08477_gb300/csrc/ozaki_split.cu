@@ -549,6 +549,38 @@ __global__ void __launch_bounds__(256) grouped_split_cols_kernel(const EmuProb* 
     }
 }
 
+// Column maxima and digits of B in one pass per 32-column strip: a CTA takes one
+// strip of a problem's padded columns (strips past the real columns get zero
+// digits), finds the strip's column maxima over all K rows, then splits its
+// 64-row tiles, which it re-reads while they are still in L2.
+template <int S>
+__global__ void __launch_bounds__(256) grouped_split_strips_kernel(const EmuProb* __restrict__ P,
+                                                                   const int64_t* __restrict__ key,
+                                                                   int q_begin, int q_end,
+                                                                   int64_t cb_begin,
+                                                                   int64_t cb_end,
+                                                                   unsigned* status) {
+    fill_e4m3_table();
+    __shared__ uint64_t T[64][33];
+    __shared__ uint64_t mx_sh[8][32];
+    __shared__ int bad_sh[8][32];
+    for (int64_t b = cb_begin + blockIdx.x; b < cb_end; b += gridDim.x) {
+        const EmuProb& q = P[find_prob(key, q_begin, q_end - 1, b)];
+        const int64_t jb = b - q.first_colblk;
+        // the exponents of the strip's real columns, visible to the whole CTA after
+        // colmax_block's closing barrier
+        colmax_block<8>(jb, q.n, q.k, q.B, q.ldb, q.b_exp, status, mx_sh, bad_sh);
+        const int32_t* b_exp = q.b_exp;
+        const int64_t qn = q.n;
+        const int64_t nlb = (q.kp + 63) / 64;
+        for (int64_t lb = 0; lb < nlb; ++lb)
+            split_cols_tile<S>(jb, lb, q.n, q.k, q.B, q.ldb, S, q.b_digits, q.kp, T, q.rb,
+                               [] {}, [=](int, int64_t j) {
+                                   return j < qn ? (int)b_exp[j] : (int)GB_BAD_LINE_DEV;
+                               });
+    }
+}
+
 }  // namespace
 
 cudaError_t launch_split_rows(const Launch& L, int s, int64_t m, int64_t k, const double* A,
@@ -566,28 +598,37 @@ cudaError_t launch_split_rows(const Launch& L, int s, int64_t m, int64_t k, cons
 }
 
 cudaError_t launch_grouped_split(const Launch& L, const EmuProb* probs, const EmuKeys& keys,
-                                 const EmuSRange& r) {
+                                 const EmuSRange& r, const SplitFork* fk) {
     if (r.q_end <= r.q_begin) return cudaSuccess;
     const int64_t cap = (int64_t)L.sm_count * 16;
     auto g = [&](int64_t x) { return (unsigned)(x < cap ? (x > 0 ? x : 1) : cap); };
     const unsigned g_rows = g((r.row_end - r.row_begin) / kEmuBM);
+    // A's rows and B's columns are independent inputs of the products: with a
+    // fork the split of A runs on the side stream, beside the launches for B
+    cudaError_t err = cudaSuccess;
+    cudaStream_t rows_stream = L.stream;
+    if (fk) {
+        err = cudaEventRecord(fk->fork, L.stream);
+        if (err == cudaSuccess) err = cudaStreamWaitEvent(fk->side, fk->fork, 0);
+        if (err != cudaSuccess) return err;
+        rows_stream = fk->side;
+    }
 #define GB_LAUNCH_GROWS(SS)                                                                   \
-    grouped_split_rows_kernel<SS><<<g_rows, 256, 0, L.stream>>>(                              \
+    grouped_split_rows_kernel<SS><<<g_rows, 256, 0, rows_stream>>>(                           \
         probs, keys.row, r.q_begin, r.q_end, r.row_begin, r.row_end, L.status)
     GB_SWITCH_S(r.s, GB_LAUNCH_GROWS)
 #undef GB_LAUNCH_GROWS
-    cudaError_t err = cudaGetLastError();
-    if (err != cudaSuccess) return err;
-    grouped_colmax_kernel<<<g(r.cb_end - r.cb_begin), 256, 0, L.stream>>>(
-        probs, keys.colblk, r.q_begin, r.q_end, r.cb_begin, r.cb_end, L.status);
     err = cudaGetLastError();
+    if (err == cudaSuccess && fk) err = cudaEventRecord(fk->join, fk->side);
     if (err != cudaSuccess) return err;
-#define GB_LAUNCH_GCOLS(SS)                                                                   \
-    grouped_split_cols_kernel<SS><<<g(r.tb_end - r.tb_begin), 256, 0, L.stream>>>(            \
-        probs, keys.tblk, r.q_begin, r.q_end, r.tb_begin, r.tb_end)
-    GB_SWITCH_S(r.s, GB_LAUNCH_GCOLS)
-#undef GB_LAUNCH_GCOLS
-    return cudaGetLastError();
+#define GB_LAUNCH_GSTRIPS(SS)                                                                 \
+    grouped_split_strips_kernel<SS><<<g(r.cb_end - r.cb_begin), 256, 0, L.stream>>>(          \
+        probs, keys.colblk, r.q_begin, r.q_end, r.cb_begin, r.cb_end, L.status)
+    GB_SWITCH_S(r.s, GB_LAUNCH_GSTRIPS)
+#undef GB_LAUNCH_GSTRIPS
+    err = cudaGetLastError();
+    if (err == cudaSuccess && fk) err = cudaStreamWaitEvent(L.stream, fk->join, 0);
+    return err;
 }
 
 cudaError_t launch_colmax_part(const Launch& L, int64_t n, int64_t k, const double* B,
