@@ -172,8 +172,9 @@ __host__ __device__ constexpr int epi_col(int g, int j) {
 // of G: the group's column exponents loaded (L1 hits), its outputs RN(T 2^E)
 // formed, alpha / beta applied, then its stores; `crow` is the row (stride
 // `cstride` between columns).  G = 4 rounds four outputs as independent
-// instruction streams; G = 1 where the registers for that are not free.
-template <int S, int J0, int W, int N, int G = 4>
+// instruction streams; G = 1 where the registers for that are not free.  The
+// sums of these columns are T[TJ .. TJ+W-1].
+template <int S, int J0, int W, int N, int G = 4, int TJ = J0>
 __device__ __forceinline__ void store_part(const I128 (&T)[N], int32_t ei, int Ebase,
                                            const int32_t* fB, int64_t col0, int64_t n, int cg,
                                            bool plain, bool beta0, double alpha, double beta,
@@ -199,7 +200,7 @@ __device__ __forceinline__ void store_part(const I128 (&T)[N], int32_t ei, int E
             uint64_t hi, lo;
             bool neg;
             int p;
-            i128_magnitude(T[J0 + g0 + j], hi, lo, neg, p);
+            i128_magnitude(T[TJ + g0 + j], hi, lo, neg, p);
             const int E = ei + fj[j] + Ebase;
             const bool zero = (hi | lo) == 0;
             const bool in_c = col0 + epi_col(cg, J0 + g0 + j) < n;
@@ -211,7 +212,7 @@ __device__ __forceinline__ void store_part(const I128 (&T)[N], int32_t ei, int E
 #pragma unroll
             for (int j = 0; j < G; ++j)
                 if ((special >> j) & 1u)
-                    out[j] = i128_to_double_scaled(T[J0 + g0 + j], ei + fj[j] + Ebase);
+                    out[j] = i128_to_double_scaled(T[TJ + g0 + j], ei + fj[j] + Ebase);
         }
 #pragma unroll
         for (int j = 0; j < G; ++j) {

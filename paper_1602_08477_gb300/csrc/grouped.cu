@@ -83,8 +83,8 @@ struct Layout {
     std::vector<EmuLayout> emu_ws;
     std::vector<int64_t> emu_idx;   // descriptor index of each emulated problem
     std::vector<EmuSRange> s_ranges;  // one per distinct slice count
-    std::vector<int64_t> keys[4];     // compact prefixes: rows, column blocks, tblks, tiles
-    size_t off_counter = 0, off_native = 0, off_emu = 0, off_keys[4] = {0, 0, 0, 0};
+    std::vector<int64_t> keys[kEmuKeys];  // compact prefixes: rows, column strips, tiles
+    size_t off_counter = 0, off_native = 0, off_emu = 0, off_keys[kEmuKeys] = {0, 0, 0};
     size_t off_data = 0, total = 0;
     int max_s = 0;
     double flops = 0;
@@ -198,13 +198,13 @@ gb_status build_layout(const gb_gemm_desc* d, int64_t count, Layout& L) {
     L.off_native = 256;
     L.off_emu = up256(L.off_native + sizeof(GroupProb) * L.native.size());
     size_t kend = up256(L.off_emu + sizeof(EmuProb) * L.emu.size());
-    for (int a = 0; a < 4; ++a) {
+    for (int a = 0; a < kEmuKeys; ++a) {
         L.off_keys[a] = kend;
         kend = up256(kend + sizeof(int64_t) * L.emu.size());
     }
     L.off_data = (kend + 1023) & ~(size_t)1023;
     size_t off = L.off_data;
-    int64_t rows = 0, colblks = 0, tblks = 0, tiles = 0;
+    int64_t rows = 0, colblks = 0, tiles = 0;
     for (size_t i = 0; i < L.emu.size(); ++i) {
         EmuProb& e = L.emu[i];
         const EmuLayout& w = L.emu_ws[i];
@@ -212,28 +212,24 @@ gb_status build_layout(const gb_gemm_desc* d, int64_t count, Layout& L) {
         // device pointers are filled in once the workspace base is known
         e.first_row = rows;
         e.first_colblk = colblks;
-        e.first_tblk = tblks;
         e.first_tile = tiles;
         L.keys[0].push_back(rows);
         L.keys[1].push_back(colblks);
-        L.keys[2].push_back(tblks);
-        L.keys[3].push_back(tiles);
+        L.keys[2].push_back(tiles);
         const int64_t ncbp = ((e.n + e.rb - 1) / e.rb * e.rb + 31) / 32;     // padded to tiles
         rows += (e.m + kEmuBM - 1) / kEmuBM * kEmuBM;  // 128-row blocks of the split of A
         colblks += ncbp;
-        tblks += ncbp * ((w.kp + 63) / 64);
         const int64_t row_side = e.trans ? e.n : e.m;
         const int64_t nt = ((row_side + kEmuBM - 1) / kEmuBM) * e.tiles_n;
         tiles += nt;
         if (L.s_ranges.empty() || L.s_ranges.back().s != e.s)
             L.s_ranges.push_back(EmuSRange{e.s, (int)i, 0, e.first_row, 0, e.first_colblk, 0,
-                                           e.first_tblk, 0, e.first_tile, 0, 0});
+                                           e.first_tile, 0, 0});
         EmuSRange& r = L.s_ranges.back();
         r.q_end = (int)i + 1;
         r.kp_max = std::max(r.kp_max, w.kp);
         r.row_end = rows;
         r.cb_end = colblks;
-        r.tb_end = tblks;
         r.t_end = tiles;
         off += w.total;
     }
@@ -244,8 +240,7 @@ gb_status build_layout(const gb_gemm_desc* d, int64_t count, Layout& L) {
 EmuKeys keys_at(uint8_t* base, const Layout& L) {
     return EmuKeys{reinterpret_cast<const int64_t*>(base + L.off_keys[0]),
                    reinterpret_cast<const int64_t*>(base + L.off_keys[1]),
-                   reinterpret_cast<const int64_t*>(base + L.off_keys[2]),
-                   reinterpret_cast<const int64_t*>(base + L.off_keys[3])};
+                   reinterpret_cast<const int64_t*>(base + L.off_keys[2])};
 }
 
 }  // namespace
@@ -253,7 +248,7 @@ EmuKeys keys_at(uint8_t* base, const Layout& L) {
 size_t grouped_table_bytes(int64_t count) {
     const size_t c = (size_t)count;
     return 256 + up256(sizeof(GroupProb) * c) + up256(sizeof(EmuProb) * c) +
-           4 * up256(sizeof(int64_t) * c) + 1024;
+           kEmuKeys * up256(sizeof(int64_t) * c) + 1024;
 }
 
 gb_status grouped_enqueue_async(const Launch& L, const gb_gemm_desc* descs, int64_t count,
@@ -278,7 +273,7 @@ gb_status grouped_enqueue_async(const Launch& L, const gb_gemm_desc* descs, int6
         std::memcpy(stg + lay.off_native, lay.native.data(), sizeof(GroupProb) * lay.native.size());
     if (!lay.emu.empty()) {
         std::memcpy(stg + lay.off_emu, lay.emu.data(), sizeof(EmuProb) * lay.emu.size());
-        for (int a = 0; a < 4; ++a)
+        for (int a = 0; a < kEmuKeys; ++a)
             std::memcpy(stg + lay.off_keys[a], lay.keys[a].data(), sizeof(int64_t) * lay.emu.size());
     }
     cudaError_t e = cudaMemcpyAsync(dev, stg, lay.off_data, cudaMemcpyHostToDevice, L.stream);
@@ -450,7 +445,7 @@ gb_status gb_grouped_plan_create(gb_queue* q, const gb_gemm_desc* descs, int64_t
     if (e == cudaSuccess && !L.emu.empty())
         e = cudaMemcpyAsync(p->d_emu, L.emu.data(), sizeof(EmuProb) * L.emu.size(),
                             cudaMemcpyHostToDevice, q->stream);
-    for (int a = 0; a < 4 && e == cudaSuccess && !L.emu.empty(); ++a)
+    for (int a = 0; a < kEmuKeys && e == cudaSuccess && !L.emu.empty(); ++a)
         e = cudaMemcpyAsync(ws + L.off_keys[a], L.keys[a].data(), sizeof(int64_t) * L.emu.size(),
                             cudaMemcpyHostToDevice, q->stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(q->stream);

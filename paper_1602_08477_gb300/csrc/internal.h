@@ -119,8 +119,7 @@ struct EmuProb {
     int32_t ra, rb;  // tile lines of A's and B's digits: 128 and emu_bn(s), swapped if trans
     int32_t pad_;
     int64_t first_row;     // exclusive prefixes over the table of: rows of A padded to 128,
-    int64_t first_colblk;  // 32-column blocks of B,
-    int64_t first_tblk;    // (32-column x 64-row) blocks of B's padded columns,
+    int64_t first_colblk;  // 32-column strips of B's columns padded to whole tiles,
     int64_t first_tile;    // 128 x emu_bn(s) output tiles
 };
 
@@ -134,19 +133,18 @@ void emu_group_assign(EmuProb& e, uint8_t* base, const EmuLayout& w);
 struct EmuKeys {
     const int64_t* row;
     const int64_t* colblk;
-    const int64_t* tblk;
     const int64_t* tile;
 };
+constexpr int kEmuKeys = 3;  // prefix arrays in EmuKeys
 
 // The emulated problems of one slice count s occupy consecutive table entries;
-// their rows, column blocks, transpose blocks and output tiles are the ranges
+// their rows, column strips and output tiles are the ranges
 // [*_begin, *_end) of the table's prefixes.
 struct EmuSRange {
     int s;
     int q_begin, q_end;  // table entries
     int64_t row_begin, row_end;
     int64_t cb_begin, cb_end;
-    int64_t tb_begin, tb_end;
     int64_t t_begin, t_end;
     int64_t kp_max;  // longest padded K of the range's problems
 };

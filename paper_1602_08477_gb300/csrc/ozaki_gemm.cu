@@ -251,6 +251,51 @@ __device__ __forceinline__ void add_levels(uint32_t lane_addr, int cg, bool smal
 }
 
 
+// Tiles of one accumulation unit whose level sums are all below 2^22 (every
+// grouped problem of K * s < 16384) with 32-column tiles: the S levels of this
+// thread's 8 columns are read as ceil(S/2) 32-bit pairs x_L 32 + x_(L+1) (levels
+// L, L+1 of one batch; |pair| < 2^27.1), so the MMAs of the next tile get TMEM
+// back after the reads and two integer steps per value; the exact sums follow
+// from the pairs afterwards (pairs_to_sum).
+template <int S>
+__device__ __forceinline__ void read_level_pairs(uint32_t lane_addr, int cg,
+                                                 int32_t (&pr)[(S + 1) / 2][8]) {
+#pragma unroll
+    for (int L0 = 0; L0 < S; L0 += 2) {
+        uint32_t v0[8], v1[8];
+        ptx::tmem_ld_32x32b_x8(lane_addr + (uint32_t)(L0 * 32 + 8 * cg), v0);
+        if (L0 + 1 < S) ptx::tmem_ld_32x32b_x8(lane_addr + (uint32_t)((L0 + 1) * 32 + 8 * cg), v1);
+        ptx::tmem_ld_wait();
+#pragma unroll
+        for (int j = 0; j < 8; ++j) {
+            const int32_t x0 = f32_small_int_value(v0[j]);
+            pr[L0 / 2][j] = L0 + 1 < S ? x0 * 32 + f32_small_int_value(v1[j]) : x0;
+        }
+    }
+}
+
+// T = sum_L x_L 2^(5 (S-1-L)) of column j from its level pairs, exactly: Horner in
+// int64 over runs of three pairs (six levels; each run below 2^48), each run
+// added into the 128-bit T at the weight of its last level.
+template <int S>
+__device__ __forceinline__ I128 pairs_to_sum(const int32_t (&pr)[(S + 1) / 2][8], int j) {
+    constexpr int NP = (S + 1) / 2;
+    I128 T{0, 0};
+#pragma unroll
+    for (int r0 = 0; r0 < NP; r0 += 3) {
+        int64_t G = 0;
+        int last = 0;
+#pragma unroll
+        for (int i = r0; i < r0 + 3 && i < NP; ++i) {
+            const bool full = 2 * i + 1 < S;
+            G = G * (full ? 1024 : 32) + (int64_t)pr[i][j];
+            last = full ? 2 * i + 1 : 2 * i;
+        }
+        i128_add_shl(T, G, 5 * (S - 1 - last));
+    }
+    return T;
+}
+
 // How one launch keeps its level sums exact (see kchunk_stages): split
 // accumulators, or K chunks of chunk_stages pipeline stages (a huge value: none).
 struct AccPlan {
@@ -281,7 +326,7 @@ AccPlan acc_plan(int64_t kp, bool allow_split) {
 // of `slot_bytes` (>= KB * S * (128 + BN) * 32 bytes) plus a SmemTail.  A stage
 // holds KB consecutive K blocks: their A tiles (KB * S * 4 KiB, contiguous in the
 // workspace) then their B tiles (KB * S * BN * 32 bytes).
-template <int S, int BN, int KB, bool kSplit, class Walk>
+template <int S, int BN, int KB, bool kSplit, class Walk, bool kSmall = false>
 __device__ __forceinline__ void products_persistent(const Walk& walk, int chunk_stages,
                                                     uint8_t* smem, int stages,
                                                     uint32_t slot_bytes, unsigned* status) {
@@ -458,6 +503,57 @@ __device__ __forceinline__ void products_persistent(const Walk& walk, int chunk_
                     if (CW > 8) ptx::prefetch_l1(a.fB + a.col0 + 32 + 4 * cgroup);
                 }
             }
+            if constexpr (kSmall) {
+                static_assert(BN == 32 && !kSplit, "small-sum tiles: 32 columns, one set");
+                (void)nch;
+                (void)small;
+                {
+                    // one unit of small level sums: TMEM goes back right after the
+                    // level pairs are read (read_level_pairs)
+                    const bool ok = ptx::mbar_wait_bounded(tmem_full, chunk_iter & 1u, abort,
+                                                           status, kStatusTimeout,
+                                                           kWaitTimeoutNs);
+                    ptx::tc_fence_after();
+                    if (!ok || *abort) break;
+                    int32_t pr[(S + 1) / 2][8];
+                    if (live) read_level_pairs<S>(lane_addr, cgroup, pr);
+                    ptx::tc_fence_before();
+                    __syncwarp();
+                    if (lane == 0) ptx::mbar_arrive(tmem_empty);
+                    ++chunk_iter;
+                    if (row_ok) {
+                        const int64_t n = a.n, col0 = a.col0;
+                        const int32_t* fB = a.fB;
+                        const double alpha = a.alpha, beta = a.beta;
+                        const int64_t rstride = a.trans ? 1 : a.ldc, cstride = a.trans ? a.ldc : 1;
+                        double* crow = a.C + row * rstride;
+                        const int32_t ei = a.eA[row];
+                        const int Ebase = -8 - 5 * (S - 1);
+                        const long long ab = __double_as_longlong(alpha),
+                                        bb = __double_as_longlong(beta);
+                        const bool beta0 = (bb & 0x7FFFFFFFFFFFFFFFll) == 0;
+                        const bool plain = ab == 0x3FF0000000000000ll && beta0;
+                        // four columns at a time: their sums from the pairs, rounded
+                        // and stored one by one
+#pragma unroll
+                        for (int g0 = 0; g0 < 8; g0 += 4) {
+                            I128 T4[4];
+#pragma unroll
+                            for (int j = 0; j < 4; ++j) T4[j] = pairs_to_sum<S>(pr, g0 + j);
+                            if (g0 == 0)
+                                store_part<S, 0, 4, 4, 1, 0>(T4, ei, Ebase, fB, col0, n, cgroup,
+                                                             plain, beta0, alpha, beta, crow,
+                                                             cstride);
+                            else
+                                store_part<S, 4, 4, 4, 1, 0>(T4, ei, Ebase, fB, col0, n, cgroup,
+                                                             plain, beta0, alpha, beta, crow,
+                                                             cstride);
+                        }
+                    }
+                    __syncwarp();
+                    if (lane == 0) ptx::mbar_arrive(&tail->args_empty[as]);
+                }
+            } else {
             I128 T[CW];
 #pragma unroll
             for (int j = 0; j < CW; ++j) T[j] = I128{0, 0};
@@ -506,6 +602,7 @@ __device__ __forceinline__ void products_persistent(const Walk& walk, int chunk_
             }
             __syncwarp();
             if (lane == 0) ptx::mbar_arrive(&tail->args_empty[as]);
+            }
         }
     }
     ptx::tc_fence_before();
@@ -588,7 +685,7 @@ struct GroupWalk {
     }
 };
 
-template <int S>
+template <int S, bool kSmall>
 __global__ void __launch_bounds__(kThreads, 1)
     grouped_products_kernel(const EmuProb* __restrict__ P, const int64_t* __restrict__ key,
                             int q_begin, int q_end, int64_t t_begin, int64_t t_end,
@@ -598,8 +695,8 @@ __global__ void __launch_bounds__(kThreads, 1)
     uint8_t* smem = aligned_smem(smem_raw);
     constexpr int BN = emu_bn(S);
     const GroupWalk<BN> w{P, key, q_begin, q_end, t_begin, t_end, 0};
-    products_persistent<S, BN, kblocks_per_stage(S), false>(w, chunk_stages, smem, stages,
-                                                            slot_bytes, status);
+    products_persistent<S, BN, kblocks_per_stage(S), false, GroupWalk<BN>, kSmall>(
+        w, chunk_stages, smem, stages, slot_bytes, status);
 }
 
 struct RingShape {
@@ -663,14 +760,20 @@ cudaError_t launch_grouped_s(const Launch& L, const EmuProb* probs, const int64_
                              const EmuSRange& g) {
     const RingShape r = ring_for(S, kblocks_per_stage(S));
     if (r.stages < 2) return cudaErrorInvalidValue;
-    cudaError_t e = allow_smem(grouped_products_kernel<S>);
+    // every level sum of the range below 2^22 (K s < 16384 for its longest K) and
+    // 32-column tiles: the kernel whose epilogue hands TMEM back after reading
+    // the levels as pairs (read_level_pairs)
+    constexpr bool kPairs = emu_bn(S) == 32;
+    const bool small = kPairs && g.kp_max * S < 16384;
+    auto kern = small ? grouped_products_kernel<S, kPairs> : grouped_products_kernel<S, false>;
+    cudaError_t e = allow_smem(kern);
     if (e != cudaSuccess) return e;
     const int64_t tiles = g.t_end - g.t_begin;
     const int grid = (int)(tiles < L.sm_count ? tiles : L.sm_count);
     const AccPlan plan = acc_plan<S, kblocks_per_stage(S)>(g.kp_max, false);
-    grouped_products_kernel<S><<<grid, kThreads, r.smem, L.stream>>>(
-        probs, key, g.q_begin, g.q_end, g.t_begin, g.t_end, plan.chunk_stages, r.stages,
-        r.slot_bytes, L.status);
+    kern<<<grid, kThreads, r.smem, L.stream>>>(probs, key, g.q_begin, g.q_end, g.t_begin,
+                                               g.t_end, plan.chunk_stages, r.stages,
+                                               r.slot_bytes, L.status);
     return cudaGetLastError();
 }
 

@@ -515,40 +515,6 @@ __global__ void __launch_bounds__(256) grouped_split_rows_kernel(const EmuProb* 
     }
 }
 
-__global__ void __launch_bounds__(256) grouped_colmax_kernel(const EmuProb* __restrict__ P,
-                                                             const int64_t* __restrict__ key,
-                                                             int q_begin, int q_end,
-                                                             int64_t cb_begin, int64_t cb_end,
-                                                             unsigned* status) {
-    __shared__ uint64_t mx_sh[8][32];
-    __shared__ int bad_sh[8][32];
-    for (int64_t b = cb_begin + blockIdx.x; b < cb_end; b += gridDim.x) {
-        const EmuProb& q = P[find_prob(key, q_begin, q_end - 1, b)];
-        colmax_block<8>(b - q.first_colblk, q.n, q.k, q.B, q.ldb, q.b_exp, status, mx_sh, bad_sh);
-    }
-}
-
-template <int S>
-__global__ void __launch_bounds__(256) grouped_split_cols_kernel(const EmuProb* __restrict__ P,
-                                                                 const int64_t* __restrict__ key,
-                                                                 int q_begin, int q_end,
-                                                                 int64_t tb_begin,
-                                                                 int64_t tb_end) {
-    fill_e4m3_table();
-    __shared__ uint64_t T[64][33];
-    for (int64_t b = tb_begin + blockIdx.x; b < tb_end; b += gridDim.x) {
-        const EmuProb& q = P[find_prob(key, q_begin, q_end - 1, b)];
-        const int64_t local = b - q.first_tblk;
-        const int64_t ncb = ((q.n + q.rb - 1) / q.rb * q.rb + 31) / 32;  // padded columns
-        const int32_t* b_exp = q.b_exp;
-        const int64_t qn = q.n;
-        split_cols_tile<S>(local % ncb, local / ncb, q.n, q.k, q.B, q.ldb, S, q.b_digits, q.kp,
-                           T, q.rb, [] {}, [=](int, int64_t j) {
-                               return j < qn ? (int)b_exp[j] : (int)GB_BAD_LINE_DEV;
-                           });
-    }
-}
-
 // Column maxima and digits of B in one pass per 32-column strip: a CTA takes one
 // strip of a problem's padded columns (strips past the real columns get zero
 // digits), finds the strip's column maxima over all K rows, then splits its
