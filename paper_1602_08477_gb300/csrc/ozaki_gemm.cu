@@ -252,24 +252,36 @@ __device__ __forceinline__ void add_levels(uint32_t lane_addr, int cg, bool smal
 
 
 // Tiles of one accumulation unit whose level sums are all below 2^22 (every
-// grouped problem of K * s < 16384) with 32-column tiles: the S levels of this
-// thread's 8 columns are read as ceil(S/2) 32-bit pairs x_L 32 + x_(L+1) (levels
-// L, L+1 of one batch; |pair| < 2^27.1), so the MMAs of the next tile get TMEM
-// back after the reads and two integer steps per value; the exact sums follow
-// from the pairs afterwards (pairs_to_sum).
-template <int S>
+// grouped problem of K * s < 16384): the S levels of this thread's BN / 4 columns
+// (see epi_col) are read as ceil(S/2) 32-bit pairs x_L 32 + x_(L+1) (levels L,
+// L+1 of one batch; |pair| < 2^27.1), so the MMAs of the next tile get TMEM back
+// after the reads and two integer steps per value; the exact sums follow from
+// the pairs afterwards (pairs_to_sum).
+template <int S, int BN>
 __device__ __forceinline__ void read_level_pairs(uint32_t lane_addr, int cg,
-                                                 int32_t (&pr)[(S + 1) / 2][8]) {
+                                                 int32_t (&pr)[(S + 1) / 2][BN / 4]) {
 #pragma unroll
     for (int L0 = 0; L0 < S; L0 += 2) {
         uint32_t v0[8], v1[8];
-        ptx::tmem_ld_32x32b_x8(lane_addr + (uint32_t)(L0 * 32 + 8 * cg), v0);
-        if (L0 + 1 < S) ptx::tmem_ld_32x32b_x8(lane_addr + (uint32_t)((L0 + 1) * 32 + 8 * cg), v1);
+        ptx::tmem_ld_32x32b_x8(lane_addr + (uint32_t)(L0 * BN + 8 * cg), v0);
+        if (L0 + 1 < S) ptx::tmem_ld_32x32b_x8(lane_addr + (uint32_t)((L0 + 1) * BN + 8 * cg), v1);
         ptx::tmem_ld_wait();
 #pragma unroll
         for (int j = 0; j < 8; ++j) {
             const int32_t x0 = f32_small_int_value(v0[j]);
             pr[L0 / 2][j] = L0 + 1 < S ? x0 * 32 + f32_small_int_value(v1[j]) : x0;
+        }
+        if constexpr (BN == 48) {
+            uint32_t w0[4], w1[4];
+            ptx::tmem_ld_32x32b_x4(lane_addr + (uint32_t)(L0 * BN + 32 + 4 * cg), w0);
+            if (L0 + 1 < S)
+                ptx::tmem_ld_32x32b_x4(lane_addr + (uint32_t)((L0 + 1) * BN + 32 + 4 * cg), w1);
+            ptx::tmem_ld_wait();
+#pragma unroll
+            for (int j = 0; j < 4; ++j) {
+                const int32_t x0 = f32_small_int_value(w0[j]);
+                pr[L0 / 2][8 + j] = L0 + 1 < S ? x0 * 32 + f32_small_int_value(w1[j]) : x0;
+            }
         }
     }
 }
@@ -277,8 +289,8 @@ __device__ __forceinline__ void read_level_pairs(uint32_t lane_addr, int cg,
 // T = sum_L x_L 2^(5 (S-1-L)) of column j from its level pairs, exactly: Horner in
 // int64 over runs of three pairs (six levels; each run below 2^48), each run
 // added into the 128-bit T at the weight of its last level.
-template <int S>
-__device__ __forceinline__ I128 pairs_to_sum(const int32_t (&pr)[(S + 1) / 2][8], int j) {
+template <int S, int NC>
+__device__ __forceinline__ I128 pairs_to_sum(const int32_t (&pr)[(S + 1) / 2][NC], int j) {
     constexpr int NP = (S + 1) / 2;
     I128 T{0, 0};
 #pragma unroll
@@ -504,7 +516,7 @@ __device__ __forceinline__ void products_persistent(const Walk& walk, int chunk_
                 }
             }
             if constexpr (kSmall) {
-                static_assert(BN == 32 && !kSplit, "small-sum tiles: 32 columns, one set");
+                static_assert(!kSplit, "small-sum tiles: one accumulator set");
                 (void)nch;
                 (void)small;
                 {
@@ -515,8 +527,8 @@ __device__ __forceinline__ void products_persistent(const Walk& walk, int chunk_
                                                            kWaitTimeoutNs);
                     ptx::tc_fence_after();
                     if (!ok || *abort) break;
-                    int32_t pr[(S + 1) / 2][8];
-                    if (live) read_level_pairs<S>(lane_addr, cgroup, pr);
+                    int32_t pr[(S + 1) / 2][CW];
+                    if (live) read_level_pairs<S, BN>(lane_addr, cgroup, pr);
                     ptx::tc_fence_before();
                     __syncwarp();
                     if (lane == 0) ptx::mbar_arrive(tmem_empty);
@@ -536,16 +548,20 @@ __device__ __forceinline__ void products_persistent(const Walk& walk, int chunk_
                         // four columns at a time: their sums from the pairs, rounded
                         // and stored one by one
 #pragma unroll
-                        for (int g0 = 0; g0 < 8; g0 += 4) {
+                        for (int g0 = 0; g0 < CW; g0 += 4) {
                             I128 T4[4];
 #pragma unroll
-                            for (int j = 0; j < 4; ++j) T4[j] = pairs_to_sum<S>(pr, g0 + j);
+                            for (int j = 0; j < 4; ++j) T4[j] = pairs_to_sum<S, CW>(pr, g0 + j);
                             if (g0 == 0)
                                 store_part<S, 0, 4, 4, 1, 0>(T4, ei, Ebase, fB, col0, n, cgroup,
                                                              plain, beta0, alpha, beta, crow,
                                                              cstride);
-                            else
+                            else if (g0 == 4)
                                 store_part<S, 4, 4, 4, 1, 0>(T4, ei, Ebase, fB, col0, n, cgroup,
+                                                             plain, beta0, alpha, beta, crow,
+                                                             cstride);
+                            else
+                                store_part<S, 8, 4, 4, 1, 0>(T4, ei, Ebase, fB, col0, n, cgroup,
                                                              plain, beta0, alpha, beta, crow,
                                                              cstride);
                         }
@@ -760,12 +776,11 @@ cudaError_t launch_grouped_s(const Launch& L, const EmuProb* probs, const int64_
                              const EmuSRange& g) {
     const RingShape r = ring_for(S, kblocks_per_stage(S));
     if (r.stages < 2) return cudaErrorInvalidValue;
-    // every level sum of the range below 2^22 (K s < 16384 for its longest K) and
-    // 32-column tiles: the kernel whose epilogue hands TMEM back after reading
-    // the levels as pairs (read_level_pairs)
-    constexpr bool kPairs = emu_bn(S) == 32;
-    const bool small = kPairs && g.kp_max * S < 16384;
-    auto kern = small ? grouped_products_kernel<S, kPairs> : grouped_products_kernel<S, false>;
+    // every level sum of the range below 2^22 (K s < 16384 for its longest K): the
+    // kernel whose epilogue hands TMEM back after reading the levels as pairs
+    // (read_level_pairs)
+    const bool small = g.kp_max * S < 16384;
+    auto kern = small ? grouped_products_kernel<S, true> : grouped_products_kernel<S, false>;
     cudaError_t e = allow_smem(kern);
     if (e != cudaSuccess) return e;
     const int64_t tiles = g.t_end - g.t_begin;
