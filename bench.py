@@ -369,6 +369,28 @@ def grouped_measure(args, steps, warmup, baselines=True, e2e=True):
     eplan = gb.GroupedPlan(eprobs, use_graph=True)
     emu_ms = _time_stream(torch, eplan.run, steps, warmup)
     einfo = eplan.info()
+    # the same emulated group with each problem's slice count left to the tuning
+    # table (slices = 0), and its error against the group at 16 slices relative to
+    # the FP64 bound 2 (k + 2) u (|A||B|), |A||B| from the library's native GEMMs
+    tprobs = [dict(p, slices=0, C=torch.zeros_like(p["C"])) for p in eprobs]
+    tplan = gb.GroupedPlan(tprobs, use_graph=True)
+    tuned_ms = _time_stream(torch, tplan.run, steps, warmup)
+    tinfo = tplan.info()
+    tplan.close()
+    rprobs = [dict(p, slices=16, C=torch.zeros_like(p["C"])) for p in eprobs]
+    gb.dgemm_grouped(rprobs)
+    torch.cuda.synchronize()
+    u = 2.0 ** -53
+    rho_t = rho_f = 0.0
+    for p, fp, r, k in zip(tprobs, eprobs, rprobs, ks):
+        bound = 2.0 * (int(k) + 2) * u * gb.dgemm(p["A"].abs(), p["B"].abs())
+        rho_t = max(rho_t, float(((p["C"] - r["C"]).abs() / bound).max()))
+        rho_f = max(rho_f, float(((fp["C"] - r["C"]).abs() / bound).max()))
+    del rprobs
+    counts = {}
+    for m, n, k in zip(ms, ns, ks):
+        c = gb.tune_lookup_slices(int(m), int(n), int(k))
+        counts[c] = counts.get(c, 0) + 1
     rules = None
     if baselines and tuned == "shipped tuning table":
         # the same groups with the tuning table emptied: the native size rule and
@@ -414,7 +436,15 @@ def grouped_measure(args, steps, warmup, baselines=True, e2e=True):
         "emulated": {"slices": s, "ms": round(emu_ms, 3), "tflops_fp64_equiv": round(emu_tf, 3),
                      "tensor_frac": round(pair_flops / (emu_ms * 1e-3) / 1e12 /
                                           (2.0 * pk["bf16_tflops"]), 4),
-                     "launches": einfo["launches"]},
+                     "launches": einfo["launches"], "rho_max_vs_s16": rho_f},
+        "emulated_tuned_slices": {
+            "slices": "per problem from the tuning table (slices = 0)",
+            "problems_per_slice_count": {str(c): v for c, v in sorted(counts.items())},
+            "ms": round(tuned_ms, 3), "tflops_fp64_equiv": round(flops / tuned_ms / 1e9, 3),
+            "launches": tinfo["launches"], "tiles": tinfo["emulated_tiles"],
+            "rho_max_vs_s16": rho_t,
+            "note": "rho = max |C - C_16| / (2 (k+2) u |A||B|) over all outputs, C_16 the "
+                    "same group at 16 slices"},
         "tiles": {"native": info["native_tiles"], "emulated": einfo["emulated_tiles"]},
         "e2e": None, "clocks": clk,
     }
@@ -923,7 +953,8 @@ def grouped_sub_record(args):
     return {"workload": r["config"]["workload"], "tiles": r["config"]["tiles"],
             "native_tflops": r["value"], "native_ms": r["ms_per_step"],
             "native_frac_fp64_peak": r["roofline"]["frac"],
-            "emulated": r["emulated"], "one_launch_per_gemm": r["one_launch_per_gemm"],
+            "emulated": r["emulated"], "emulated_tuned_slices": r["emulated_tuned_slices"],
+            "one_launch_per_gemm": r["one_launch_per_gemm"],
             "untuned_rules": r.get("untuned_rules"),
             "launches_per_step": r["gpu_launches"] // 5, "clocks": r["clocks"]}
 

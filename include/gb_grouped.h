@@ -51,7 +51,8 @@ typedef struct {
     double* C;
     int64_t ldc;
     int32_t precision; /* gb_precision */
-    int32_t slices;    /* emulated: 1..16, 0 = default (11) */
+    int32_t slices;    /* emulated: 1..16, 0 = the tuning table's slice count for
+                          this shape (gb_tune_lookup_slices), else 11 */
     int32_t tile;      /* native: GB_TILE_AUTO .. GB_TILE_32x64; emulated: GB_TILE_AUTO,
                           GB_TILE_EMU_ROWS or GB_TILE_EMU_COLS */
     int32_t reserved;  /* must be 0 */
@@ -90,7 +91,13 @@ gb_status gb_dgemm_grouped(gb_queue* q, const gb_gemm_desc* descs, int64_t count
  * emulated ones) with m <= m_max, n <= n_max and k <= k_max gives its tile or
  * orientation.  Written by the autotuner; no matching entry = the size rule
  * (native) or the padding rule (emulated: the orientation with fewer padded
- * output slots).  GB_ERR_INVALID_ARG for a tile outside 1..6. */
+ * output slots).  A third kind, tile = GB_TUNE_SLICES + s (s = 1..16), gives an
+ * emulated problem with slices = 0 its slice count: the autotuner picks, per size
+ * cell, the fastest count whose error on its tuning batches stays a safe margin
+ * inside the FP64 bound of gb_gemm.h (a caller whose data spans a wider dynamic
+ * range than uniform[-1, 1] passes its own count); no matching entry = 11.
+ * GB_ERR_INVALID_ARG for any other tile. */
+#define GB_TUNE_SLICES 100
 typedef struct {
     int32_t m_max, n_max, k_max;
     int32_t tile;
@@ -103,9 +110,14 @@ gb_status gb_tune_get(gb_tune_entry* entries, int64_t capacity, int64_t* count);
 gb_status gb_tune_lookup(int64_t m, int64_t n, int64_t k, int32_t* tile);
 
 /* The orientation (GB_TILE_EMU_ROWS or GB_TILE_EMU_COLS) an emulated problem of
- * this shape and slice count (1..16, 0 = 11) would get with GB_TILE_AUTO.
- * Host only. */
+ * this shape and slice count (1..16, 0 = the table's, see gb_tune_lookup_slices)
+ * would get with GB_TILE_AUTO.  Host only. */
 gb_status gb_tune_lookup_emulated(int slices, int64_t m, int64_t n, int64_t k, int32_t* tile);
+
+/* The slice count an emulated problem of this shape submitted with slices = 0
+ * gets: the first matching slice-count entry (GB_TUNE_SLICES + s), else 11.
+ * Host only. */
+gb_status gb_tune_lookup_slices(int64_t m, int64_t n, int64_t k, int32_t* slices);
 
 #ifdef __cplusplus
 }

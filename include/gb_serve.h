@@ -45,7 +45,8 @@ typedef struct {
     int64_t m, n, k;
     double alpha, beta;
     int32_t precision;  /* gb_precision */
-    int32_t slices;     /* emulated: 1..16, 0 = default (11) */
+    int32_t slices;     /* emulated: 1..16, 0 = the tuning table's count for the
+                           request's shape, fixed at submit (else 11) */
     /* Operands: either host arrays (row-major, leading dimensions = k, n, n),
      * copied in when the request is batched and kept valid by the caller until
      * the request is done; or, with A_host == NULL, generated on the device

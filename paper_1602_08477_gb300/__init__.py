@@ -34,6 +34,7 @@ from .grouped import (  # noqa: E402,F401
     tune_get,
     tune_lookup,
     tune_lookup_emulated,
+    tune_lookup_slices,
     tune_set,
 )
 from .serve import Server, fill_uniform  # noqa: E402,F401

@@ -48,6 +48,7 @@ int default_tile(int64_t m, int64_t n) {
 
 bool native_tile(int t) { return t >= GB_TILE_64x64 && t <= GB_TILE_32x64; }
 bool emu_orientation(int t) { return t == GB_TILE_EMU_ROWS || t == GB_TILE_EMU_COLS; }
+bool slice_entry(int t) { return t >= GB_TUNE_SLICES + 1 && t <= GB_TUNE_SLICES + 16; }
 
 // First matching entry of the native kind, else the size rule.
 int lookup_tile(int64_t m, int64_t n, int64_t k) {
@@ -56,6 +57,20 @@ int lookup_tile(int64_t m, int64_t n, int64_t k) {
         if (native_tile(e.tile) && m <= e.m_max && n <= e.n_max && k <= e.k_max) return e.tile;
     return default_tile(m, n);
 }
+
+}  // namespace
+
+// Slice count of an emulated problem whose descriptor leaves it to the library
+// (slices = 0): the first matching slice-count entry, else 11.
+int default_emulated_slices(int64_t m, int64_t n, int64_t k) {
+    std::lock_guard<std::mutex> lock(g_tune_mu);
+    for (const auto& e : g_tune)
+        if (slice_entry(e.tile) && m <= e.m_max && n <= e.n_max && k <= e.k_max)
+            return e.tile - GB_TUNE_SLICES;
+    return 11;
+}
+
+namespace {
 
 // Orientation of an emulated problem: first matching entry of the emulated
 // kind, else the padding rule (emu_group_trans).
@@ -113,7 +128,7 @@ gb_status build_layout(const gb_gemm_desc* d, int64_t count, Layout& L) {
         if (x.precision == GB_PREC_EMULATED && x.tile != GB_TILE_AUTO && !emu_orientation(x.tile))
             return bad("problem %lld: an emulated problem's tile is AUTO, EMU_ROWS or EMU_COLS",
                        (long long)i);
-        const int s = x.slices == 0 ? 11 : x.slices;
+        const int s = x.slices == 0 ? default_emulated_slices(x.m, x.n, x.k) : x.slices;
         if (x.precision == GB_PREC_EMULATED && (s < 1 || s > 16))
             return bad("problem %lld: slices must be in [1, 16] (or 0)", (long long)i);
         if (x.m == 0 || x.n == 0) continue;
@@ -315,8 +330,10 @@ gb_status gb_tune_set(const gb_tune_entry* entries, int64_t count) {
         return GB_ERR_INVALID_ARG;
     }
     for (int64_t i = 0; i < count; ++i) {
-        if (!native_tile(entries[i].tile) && !emu_orientation(entries[i].tile)) {
-            set_error("tuning entry %lld: tile must be a concrete variant (1..6)", (long long)i);
+        if (!native_tile(entries[i].tile) && !emu_orientation(entries[i].tile) &&
+            !slice_entry(entries[i].tile)) {
+            set_error("tuning entry %lld: tile must be a concrete variant (1..6) or a slice "
+                      "count (GB_TUNE_SLICES + 1..16)", (long long)i);
             return GB_ERR_INVALID_ARG;
         }
     }
@@ -345,8 +362,21 @@ gb_status gb_tune_lookup(int64_t m, int64_t n, int64_t k, int32_t* tile) {
     return GB_OK;
 }
 
+gb_status gb_tune_lookup_slices(int64_t m, int64_t n, int64_t k, int32_t* slices) {
+    if (!slices || m < 0 || n < 0 || k < 0) {
+        set_error("slices is NULL or a size is negative");
+        return GB_ERR_INVALID_ARG;
+    }
+    *slices = default_emulated_slices(m, n, k);
+    return GB_OK;
+}
+
 gb_status gb_tune_lookup_emulated(int slices, int64_t m, int64_t n, int64_t k, int32_t* tile) {
-    const int s = slices == 0 ? 11 : slices;
+    if (m < 0 || n < 0 || k < 0) {
+        set_error("a size is negative");
+        return GB_ERR_INVALID_ARG;
+    }
+    const int s = slices == 0 ? default_emulated_slices(m, n, k) : slices;
     if (!tile || m < 0 || n < 0 || k < 0 || s < 1 || s > 16) {
         set_error("tile is NULL, a size is negative or slices is outside [0, 16]");
         return GB_ERR_INVALID_ARG;

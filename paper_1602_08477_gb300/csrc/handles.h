@@ -56,6 +56,9 @@ gb_status finish_call(gb_queue* q, cudaError_t e, const char* what);
 // Bytes of device (and pinned staging) space the tables of `count` grouped
 // problems need.
 size_t grouped_table_bytes(int64_t count);
+// Slice count of an emulated grouped problem (or request) submitted with
+// slices = 0: the tuning table's slice-count entry for its shape, else 11.
+int default_emulated_slices(int64_t m, int64_t n, int64_t k);
 
 // Enqueues a group on L.stream without any host synchronisation: the tables are
 // packed into `staging` (pinned host memory of grouped_table_bytes(count) bytes,

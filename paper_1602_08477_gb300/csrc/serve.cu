@@ -152,7 +152,7 @@ size_t footprint(const gb_request& r) {
     if (r.precision == GB_PREC_EMULATED) {
         // either orientation (the tuning table may pick the one the padding rule
         // does not): the larger workspace
-        const int s = r.slices == 0 ? 11 : r.slices;
+        const int s = r.slices;  // resolved at submit
         b += std::max(emu_group_layout(s, r.m, r.n, r.k, false).total,
                       emu_group_layout(s, r.m, r.n, r.k, true).total) +
              1024;
@@ -531,7 +531,11 @@ gb_status gb_server_submit(gb_server* S, const gb_request* req, uint64_t* reques
         return GB_ERR_INVALID_ARG;
     }
     r->r = q;
-    r->bytes = footprint(q);
+    // the slice count the request runs with, fixed now: its footprint and its
+    // grouped launch then agree whatever the tuning table holds later
+    if (q.precision == GB_PREC_EMULATED && q.slices == 0)
+        r->r.slices = default_emulated_slices(q.m, q.n, q.k);
+    r->bytes = footprint(r->r);
     r->flops = 2.0 * (double)q.m * (double)q.n * (double)q.k;
     r->cost = q.precision == GB_PREC_EMULATED ? r->flops / 16.0 : r->flops;
     r->lane = (S->policy == GB_SERVE_LANES && q.precision == GB_PREC_NATIVE &&
@@ -539,9 +543,10 @@ gb_status gb_server_submit(gb_server* S, const gb_request* req, uint64_t* reques
     r->t_submit = Clock::now();
     std::lock_guard<std::mutex> lock(S->mu);
     if (r->bytes > S->arena.total()) {
+        const size_t bytes = r->bytes;
         delete r;
         ++S->rejected;
-        set_error("request of %zu bytes can never fit the %zu-byte budget", footprint(q),
+        set_error("request of %zu bytes can never fit the %zu-byte budget", bytes,
                   S->arena.total());
         return GB_ERR_OUT_OF_BUDGET;
     }

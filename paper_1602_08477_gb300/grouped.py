@@ -10,8 +10,10 @@ import ctypes
 from . import _lib
 from ._lib import check, precision_code
 
+TUNE_SLICES = 100  # GB_TUNE_SLICES: a table entry of tile TUNE_SLICES + s gives slice count s
 TILES = {"auto": 0, "64x64": 1, "32x32": 2, "64x32": 3, "32x64": 4,
          "emu_rows": 5, "emu_cols": 6}
+TILES.update({f"emu_s{s}": TUNE_SLICES + s for s in range(1, 17)})
 TILE_NAMES = {v: k for k, v in TILES.items()}
 
 
@@ -44,6 +46,7 @@ _lib.extra_signatures({
     "gb_tune_get": (_st, [ctypes.POINTER(TuneEntry), _i64, ctypes.POINTER(_i64)]),
     "gb_tune_lookup": (_st, [_i64, _i64, _i64, ctypes.POINTER(ctypes.c_int32)]),
     "gb_tune_lookup_emulated": (_st, [_int, _i64, _i64, _i64, ctypes.POINTER(ctypes.c_int32)]),
+    "gb_tune_lookup_slices": (_st, [_i64, _i64, _i64, ctypes.POINTER(ctypes.c_int32)]),
 })
 
 
@@ -157,6 +160,13 @@ def tune_lookup(m, n, k) -> str:
     t = ctypes.c_int32()
     check(_lib.load().gb_tune_lookup(m, n, k, ctypes.byref(t)), "gb_tune_lookup")
     return TILE_NAMES[t.value]
+
+
+def tune_lookup_slices(m, n, k) -> int:
+    """Slice count of an emulated problem of this shape given slices = 0."""
+    t = ctypes.c_int32()
+    check(_lib.load().gb_tune_lookup_slices(m, n, k, ctypes.byref(t)), "gb_tune_lookup_slices")
+    return t.value
 
 
 def tune_lookup_emulated(m, n, k, slices=11) -> str:

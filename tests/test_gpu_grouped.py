@@ -119,7 +119,7 @@ def test_emulated_and_mixed_group(gb):
 
 def test_emulated_group_with_several_slice_counts(gb):
     """Problems of different s run in one launch set per slice count (split rows,
-    column maxima, split columns, products); each equals its single launch."""
+    column strips, products); each equals its single launch."""
     import torch
     ms, ns, ks = g.grouped_problems(5519, 24)
     slices = [3, 16, 8, 12]
@@ -165,6 +165,42 @@ def test_emulated_group_at_the_tuned_slice_count_meets_the_fp64_bound(gb):
     torch.cuda.synchronize()
     for p, (A, B) in zip(probs, host):
         assert within_bound(p["C"].cpu().numpy(), 1.0, A, B, 0.0, np.zeros_like(p["C"].cpu().numpy())) <= 1.0
+
+
+def test_slices_zero_takes_the_tables_count(gb):
+    """A problem submitted with slices = 0 runs at the slice count of the tuning
+    table's entry for its K (else 11): bit-identical to the same group with the
+    counts given explicitly, and within the FP64 bound against the oracle."""
+    import torch
+    big = (1 << 31) - 1
+    ms, ns, ks = g.grouped_problems(8821, 30)
+    table = [(big, big, 64, "emu_s12"), (big, big, 256, "emu_s10")]
+    want = [12 if k <= 64 else 10 if k <= 256 else 11 for k in ks]
+    probs, explicit, host = [], [], []
+    for i, (m, n, k) in enumerate(zip(ms, ns, ks)):
+        A = g.matrix("uniform", int(m), int(k), 8821 + i, 0)
+        B = g.matrix("uniform", int(k), int(n), 8821 + i, 1)
+        C0 = g.matrix("uniform", int(m), int(n), 8821 + i, 2)
+        base = dict(A=to_dev(A), B=to_dev(B), alpha=1.5, beta=0.5, precision="emulated")
+        probs.append(dict(base, C=to_dev(C0), slices=0))
+        explicit.append(dict(base, C=to_dev(C0), slices=want[i]))
+        host.append((A, B, C0))
+    saved = gb.tune_get()
+    gb.tune_set(table)
+    try:
+        assert [gb.tune_lookup_slices(int(m), int(n), int(k)) for m, n, k in zip(ms, ns, ks)] == want
+        plan = gb.GroupedPlan(probs, use_graph=True)
+        plan.run()
+        torch.cuda.synchronize()
+        assert plan.info()["launches"] == 3 * len(set(want))
+        plan.close()
+    finally:
+        gb.tune_set(saved)
+    gb.dgemm_grouped(explicit)
+    torch.cuda.synchronize()
+    for p, q in zip(probs, explicit):
+        assert torch.equal(p["C"], q["C"])
+    assert check_bound(probs, host) <= 2.0
 
 
 def test_edge_problems_in_a_group(gb):
