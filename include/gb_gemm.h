@@ -88,7 +88,8 @@ typedef struct {
 typedef enum {
     GB_PREC_NATIVE = 0,        /* FP64 arithmetic on the FP64 pipes */
     GB_PREC_EMULATED = 1,      /* FP64 result from E4M3 slices on the tcgen05 tensor cores */
-    GB_PREC_EMULATED_BF16 = 2  /* the same from BF16 slices (8-bit digits, kind::f16 MMAs) */
+    GB_PREC_EMULATED_BF16 = 2, /* the same from BF16 slices (8-bit digits, kind::f16 MMAs) */
+    GB_PREC_EMULATED_CRT = 3   /* the same from integer residues modulo N primes (kind::f16) */
 } gb_precision;
 
 typedef enum {
@@ -153,7 +154,8 @@ gb_status gb_workdiv_suggest(const gb_device* dev, gb_kernel kernel, int64_t m, 
  *   wd        work division, or NULL for the library's choice.  Native only;
  *             the emulated precision takes NULL.
  *   kernel    native variant (GB_KERNEL_AUTO for the library's choice).
- *   prec      GB_PREC_NATIVE, GB_PREC_EMULATED or GB_PREC_EMULATED_BF16.
+ *   prec      GB_PREC_NATIVE, GB_PREC_EMULATED, GB_PREC_EMULATED_BF16 or
+ *             GB_PREC_EMULATED_CRT.
  *   slices    emulated only: number s of digit slices per operand; E4M3:
  *             1 <= s <= 16 (the first slice carries 4 bits, each further one
  *             5; 0 selects the default of 11); BF16: 1 <= s <= 8 (7 bits, then
@@ -173,6 +175,22 @@ gb_status gb_workdiv_suggest(const gb_device* dev, gb_kernel kernel, int64_t m, 
  *             B's column exponents (n int32), scratch; the digits are BF16 codes
  *             tiled as in the E4M3 layout below, with R = 128 (A) and 32 (B)
  *             lines per tile and 16 digits per 32-byte K block.
+ *             Residues (GB_PREC_EMULATED_CRT; `slices` = N, the number of moduli,
+ *             1 <= N <= 14, 0 selects 13): each row of A and column of B is scaled
+ *             by a power of two to integers of b bits (round to nearest even; b
+ *             the largest count with k 2^(2b) <= M / 4, M the product of the
+ *             first N of the primes 509, 503, 499, 491, 487, 479, 467, 463, 461,
+ *             457, 449, 443, 439, 433; GB_ERR_UNSUPPORTED when k is too long for
+ *             b >= 1), the integer product is computed modulo each prime on the
+ *             tensor cores (BF16 residues |r| <= 254, FP32 sums of at most 256 K,
+ *             each exact) and recovered exactly by the Chinese remainder theorem,
+ *             then rounded once: the only approximation is the scaling to b
+ *             bits (13 moduli: b = 50 at k = 8192).  gb_dgemm is its only entry
+ *             point.  Workspace, each part 1024-byte aligned and in this order:
+ *             A's residues (2 N mp kp bytes, mp = m rounded up to 128, kp = k
+ *             rounded up to 16), B's residues (2 N np kp, np = n rounded up to
+ *             128), the residues of C (2 N mp np), A's row exponents (m int32),
+ *             B's column exponents (n int32), scratch.
  *   workspace device buffer of at least gb_dgemm_workspace_size() bytes,
  *             256-byte aligned (emulated only; native takes NULL, 0).
  * Errors: GB_ERR_INVALID_ARG (sizes, pointers, leading dimensions, slices),

@@ -92,8 +92,15 @@ def scale_to_integers(X: np.ndarray, e: np.ndarray, b: int, axis: int = 1,
 
 def sym_mod(X, m: int):
     """c3: the symmetric residue of integers X (numpy int64 or object arrays, or
-    Python ints) modulo odd m, with the sign of X."""
-    X = np.asarray(X, dtype=object)
+    Python ints) modulo odd m, with the sign of X: sign(X) sym(|X| mod m).
+    int64 arrays (|X| < 2^63) are reduced with numpy's integer operations, other
+    integers one by one; both are exact."""
+    X = np.asarray(X)
+    if X.dtype == np.int64:
+        u = np.abs(X) % m
+        s = np.where(2 * u <= m, u, u - m)
+        return np.where(X < 0, -s, s).astype(np.int64)
+    X = X.astype(object)
     u = np.vectorize(lambda x: abs(int(x)) % m, otypes=[object])(X) if X.size else X
     s = np.vectorize(lambda v: v if 2 * v <= m else v - m, otypes=[object])(u) if X.size else u
     sign = np.vectorize(lambda x: -1 if int(x) < 0 else 1, otypes=[object])(X) if X.size else X
@@ -106,11 +113,18 @@ def residues(Xi: np.ndarray, N: int) -> np.ndarray:
 
 
 def residue_products(RA: np.ndarray, RB: np.ndarray, N: int) -> np.ndarray:
-    """c4: c_t = sym(R^A_t R^B_t mod m_t), int64 (N, m, n).  Each product sum is an
-    exact int64 (k * 256^2 stays far below 2^63 for any k this model sees)."""
+    """c4: c_t = sym(R^A_t R^B_t mod m_t), int64 (N, m, n).  The products are
+    integers of magnitude at most k 256^2: below 2^53 (k < 2^37) every partial sum
+    of an FP64 matrix product is an exactly representable integer, whatever its
+    order, so the FP64 product is exact; longer K takes the int64 product."""
+    k = RA.shape[-1]
+    exact_fp64 = k * 256 * 256 < 2 ** 53
     out = []
     for t, m in enumerate(moduli(N)):
-        P = RA[t].astype(np.int64) @ RB[t].astype(np.int64)
+        if exact_fp64:
+            P = (RA[t].astype(np.float64) @ RB[t].astype(np.float64)).astype(np.int64)
+        else:
+            P = RA[t].astype(np.int64) @ RB[t].astype(np.int64)
         out.append(sym_mod(P, m))
     return np.stack(out)
 
@@ -148,17 +162,19 @@ def finish(Cp: np.ndarray, e: np.ndarray, f: np.ndarray, b: int, alpha: float, b
 
 
 def crt_gemm(alpha: float, A: np.ndarray, B: np.ndarray, beta: float = 0.0,
-             C0: np.ndarray | None = None, N: int = DEFAULT_N, rows=None,
+             C0: np.ndarray | None = None, N: int = DEFAULT_N, rows=None, cols=None,
              details: bool = False):
-    """alpha*A*B + beta*C0 by steps c1-c6.  ``rows`` restricts the output rows (C0
-    then holds only those rows; b still follows from the full k)."""
+    """alpha*A*B + beta*C0 by steps c1-c6.  ``rows`` / ``cols`` restrict the output
+    rows / columns (C0 then holds only those; each line's scaling depends on that
+    line alone and b on k, so the selected outputs are those of the full product)."""
     A = np.asarray(A, dtype=np.float64)
     B = np.asarray(B, dtype=np.float64)
-    m, k = A.shape
-    n = B.shape[1]
     if rows is not None:
         A = A[np.asarray(rows)]
-        m = A.shape[0]
+    if cols is not None:
+        B = B[:, np.asarray(cols)]
+    m, k = A.shape
+    n = B.shape[1]
     if m == 0 or n == 0:
         return np.zeros((m, n))
     if alpha == 0.0 or k == 0:

@@ -19,14 +19,15 @@ STATUS_NAMES = {
     8: "GB_ERR_NONFINITE", 9: "GB_ERR_BUSY", 10: "GB_ERR_WORKSPACE",
 }
 
-GB_PREC_NATIVE, GB_PREC_EMULATED, GB_PREC_EMULATED_BF16 = 0, 1, 2
+GB_PREC_NATIVE, GB_PREC_EMULATED, GB_PREC_EMULATED_BF16, GB_PREC_EMULATED_CRT = 0, 1, 2, 3
 #: precision names of the Python API -> gb_precision
 PRECISIONS = {"native": GB_PREC_NATIVE, "emulated": GB_PREC_EMULATED,
-              "emulated_bf16": GB_PREC_EMULATED_BF16}
+              "emulated_bf16": GB_PREC_EMULATED_BF16, "emulated_crt": GB_PREC_EMULATED_CRT}
 
 
 def precision_code(name: str) -> int:
-    """gb_precision value of a precision name ("native", "emulated", "emulated_bf16")."""
+    """gb_precision value of a precision name ("native", "emulated", "emulated_bf16",
+    "emulated_crt")."""
     try:
         return PRECISIONS[name]
     except KeyError:

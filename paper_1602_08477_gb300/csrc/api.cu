@@ -276,6 +276,8 @@ using namespace gb;
 
 // Slice count of the BF16-digit precision: 0 selects 7 (55 bits of each line).
 static int resolve_bf16_slices(int slices) { return slices == 0 ? 7 : slices; }
+// Moduli of the residue precision: 0 selects 13.
+static int resolve_crt_moduli(int slices) { return slices == 0 ? kCrtDefaultModuli : slices; }
 
 extern "C" {
 
@@ -397,6 +399,14 @@ gb_status gb_dgemm_workspace_size(gb_precision prec, int slices, int64_t m, int6
         *out = emu_layout_bf16(s, m, n, k).total;
         return GB_OK;
     }
+    if (prec == GB_PREC_EMULATED_CRT) {
+        const int N = resolve_crt_moduli(slices);
+        if (N < 1 || N > kCrtMaxModuli)
+            return invalid("the number of moduli must be in [1, %d] (or 0 for the default), got %d",
+                           kCrtMaxModuli, slices);
+        *out = crt_layout(N, m, n, k).total;
+        return GB_OK;
+    }
     if (prec != GB_PREC_EMULATED) return invalid("unknown precision %d", (int)prec);
     const int s = resolve_slices(slices);
     if (s < 1 || s > 16) return invalid("slices must be in [1, 16] (or 0 for the default), got %d", slices);
@@ -509,7 +519,8 @@ gb_status gb_dgemm(gb_queue* q, const gb_workdiv* wd, gb_kernel kernel, gb_preci
     if (!q) return invalid("q is NULL");
     gb_status st = check_gemm_args(m, n, k, alpha, A, lda, B, ldb, beta, C, ldc);
     if (st != GB_OK) return st;
-    if (prec != GB_PREC_NATIVE && prec != GB_PREC_EMULATED && prec != GB_PREC_EMULATED_BF16)
+    if (prec != GB_PREC_NATIVE && prec != GB_PREC_EMULATED && prec != GB_PREC_EMULATED_BF16 &&
+        prec != GB_PREC_EMULATED_CRT)
         return invalid("unknown precision %d", (int)prec);
     if (kernel < GB_KERNEL_AUTO || kernel > GB_KERNEL_DMMA) return invalid("unknown kernel %d", (int)kernel);
     int s = 0;
@@ -524,6 +535,16 @@ gb_status gb_dgemm(gb_queue* q, const gb_workdiv* wd, gb_kernel kernel, gb_preci
         if (k > kBf16MaxK) {
             set_error("the BF16-digit precision supports k <= %lld, got %lld",
                       (long long)kBf16MaxK, (long long)k);
+            return GB_ERR_UNSUPPORTED;
+        }
+    } else if (prec == GB_PREC_EMULATED_CRT) {
+        s = resolve_crt_moduli(slices);
+        if (s < 1 || s > kCrtMaxModuli)
+            return invalid("the number of moduli must be in [1, %d] (or 0), got %d", kCrtMaxModuli,
+                           slices);
+        if (crt_scale_bits(s, k) < 1) {
+            set_error("k = %lld is too long for %d moduli (the exact product would not fit)",
+                      (long long)k, s);
             return GB_ERR_UNSUPPORTED;
         }
     }
@@ -586,6 +607,23 @@ gb_status gb_dgemm(gb_queue* q, const gb_workdiv* wd, gb_kernel kernel, gb_preci
             e = launch_bf16_products(L, s, m, n, alpha, beta, C, ldc, ws + lay.a_digits,
                                      ws + lay.b_digits, lay.kp, ea, fb);
         return finish_call(q, e, "emulated (BF16 digits) dgemm");
+    }
+    if (prec == GB_PREC_EMULATED_CRT) {
+        const CrtLayout lay = crt_layout(s, m, n, k);
+        if (!workspace) {
+            set_error("the emulated path needs a workspace of %zu bytes", lay.total);
+            return GB_ERR_WORKSPACE;
+        }
+        if (!aligned(workspace, 256)) {
+            set_error("workspace must be 256-byte aligned");
+            return GB_ERR_WORKSPACE;
+        }
+        if (workspace_bytes < lay.total) {
+            set_error("workspace of %zu bytes < required %zu", workspace_bytes, lay.total);
+            return GB_ERR_WORKSPACE;
+        }
+        const cudaError_t e = launch_crt_gemm(L, g, static_cast<uint8_t*>(workspace), lay);
+        return finish_call(q, e, "emulated (residues) dgemm");
     }
 
     cudaError_t e = cudaSuccess;

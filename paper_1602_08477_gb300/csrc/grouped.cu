@@ -116,7 +116,7 @@ gb_status build_layout(const gb_gemm_desc* d, int64_t count, Layout& L) {
             set_error("%s", msg);
             return (gb_status)v;
         }
-        if (x.precision == GB_PREC_EMULATED_BF16) {
+        if (x.precision == GB_PREC_EMULATED_BF16 || x.precision == GB_PREC_EMULATED_CRT) {
             set_error("problem %lld: a group takes native or E4M3-digit precision", (long long)i);
             return GB_ERR_UNSUPPORTED;
         }

@@ -257,7 +257,7 @@ gb_status gb_dgemm_host_workspace_size(gb_precision prec, int slices, int64_t m,
         set_error("m, n, k must be >= 0");
         return GB_ERR_INVALID_ARG;
     }
-    if (prec == GB_PREC_EMULATED_BF16) {
+    if (prec == GB_PREC_EMULATED_BF16 || prec == GB_PREC_EMULATED_CRT) {
         set_error("the host-buffer GEMM takes native or E4M3-digit precision");
         return GB_ERR_UNSUPPORTED;
     }
@@ -316,7 +316,7 @@ gb_status gb_dgemm_host(gb_queue* q, gb_precision prec, int slices, int64_t m, i
     }
     const int v = validate_gemm(m, n, k, alpha, A, lda, B, ldb, beta, C, ldc);
     if (v != GB_OK) return (gb_status)v;
-    if (prec == GB_PREC_EMULATED_BF16) {
+    if (prec == GB_PREC_EMULATED_BF16 || prec == GB_PREC_EMULATED_CRT) {
         set_error("the host-buffer GEMM takes native or E4M3-digit precision");
         return GB_ERR_UNSUPPORTED;
     }

@@ -172,6 +172,25 @@ constexpr int kEmuBM = 128;  // output tile rows of the products kernel (A digit
 // 48 s <= 512 (s <= 10) and 32 above.
 __host__ __device__ constexpr int emu_bn(int s) { return s <= 10 ? 48 : 32; }
 
+// ---- emulated FP64 by residue arithmetic (ozaki_crt.cu) ----
+// Integers of b bits per line, multiplied modulo N primes (BF16 residues,
+// kind::f16 MMAs into FP32 sums of at most 256 K), recovered by the Chinese
+// remainder theorem and rounded once.
+constexpr int kCrtMaxModuli = 14;      // the product of the moduli stays below 2^125
+constexpr int kCrtDefaultModuli = 13;
+struct CrtLayout {
+    int N;       // moduli
+    int b;       // bits of the scaled integers (0: k too long for N moduli)
+    int64_t kp, mp, np;  // K padded to 16, m and n padded to 128
+    size_t a_res, b_res, c_res, a_exp, b_exp, b_part, total;
+};
+// The largest b in [1, 62] with 4 k 2^(2b) <= M (M the product of the first N
+// moduli), 0 when none.
+int crt_scale_bits(int N, int64_t k);
+CrtLayout crt_layout(int N, int64_t m, int64_t n, int64_t k);
+// Split of A and B, residue products, reconstruction (m, n > 0, k > 0, alpha != 0).
+cudaError_t launch_crt_gemm(const Launch& L, const Gemm& g, uint8_t* ws, const CrtLayout& lay);
+
 // ---- emulated FP64 with BF16 digits (ozaki_bf16.cu) ----
 // 8-bit signed digits (|d| <= 128) in BF16, kind::f16 MMAs.  Output tiles of
 // 128 x kBf16BN; digits stored pre-tiled as for E4M3 with 16 digits (32 bytes)

@@ -515,7 +515,7 @@ gb_status gb_server_submit(gb_server* S, const gb_request* req, uint64_t* reques
         return GB_ERR_INVALID_ARG;
     }
     const gb_request& q = *req;
-    if (q.precision == GB_PREC_EMULATED_BF16) {
+    if (q.precision == GB_PREC_EMULATED_BF16 || q.precision == GB_PREC_EMULATED_CRT) {
         set_error("gb_server_submit: requests take native or E4M3-digit precision");
         return GB_ERR_UNSUPPORTED;
     }

@@ -133,7 +133,8 @@ def dgemm(A, B, C=None, alpha: float = 1.0, beta: float = 0.0, *, kernel: str = 
     A (m x k), B (k x n), C (m x n) are float64 CUDA tensors, row-major, any
     leading dimension (a column slice of a wider tensor is fine).  C is created
     (zeros) when None.  precision: "native", "emulated" (E4M3 digits) or
-    "emulated_bf16" (BF16 digits); kernel: "auto", "naive", "tiled", "dfma",
+    "emulated_bf16" (BF16 digits) or "emulated_crt" (residues modulo `slices`
+    primes, 0 = 13); kernel: "auto", "naive", "tiled", "dfma",
     "dmma"; slices: emulated digit slices (0 = the precision's default).
     """
     import torch
