@@ -346,7 +346,7 @@ __device__ __forceinline__ int modulus_of(int t) {
 }
 
 // The items t = blockIdx.x, + gridDim.x, ...: modulus-major; within a modulus
-// rasterised like RasterWalk (groups of 8 tile rows sweep the tile columns).
+// rasterised (groups of 16 tile rows sweep the tile columns).
 struct CrtWalk {
     const uint8_t* ares;
     const uint8_t* bres;
@@ -361,9 +361,12 @@ struct CrtWalk {
         const int64_t per = (int64_t)tiles_m * tiles_n;
         const int mod = (int)(t / per);
         const int bid = (int)(t - (int64_t)mod * per);
-        const int group_size = 8 * tiles_n;
-        const int first_m = (bid / group_size) * 8;
-        const int gm = min(tiles_m - first_m, 8);
+        // 16 tile rows per group: a wave of 152 tiles then spans ~16 x 10 tiles,
+        // near the shape that minimises the re-reads of 128-row A strips and
+        // 256-column B strips from DRAM
+        const int group_size = 16 * tiles_n;
+        const int first_m = (bid / group_size) * 16;
+        const int gm = min(tiles_m - first_m, 16);
         const int tm = first_m + (bid % group_size) % gm;
         const int tn = (bid % group_size) / gm;
         ItemArgs a;
@@ -607,16 +610,42 @@ __global__ void __launch_bounds__(kThreads, 1)
 
 // ---- c5 + c6: reconstruction and the single rounding -------------------------------
 
+// The reconstruction's constants in 26-bit limbs (every product of a residue
+// and a limb then fits a 32 x 32 -> 64-bit multiply and the limb sums stay far
+// below 2^63): w_t = sum_i wl[t][i] 2^(26 i), M = sum_i Ml[i] 2^(26 i).
+constexpr int kLimbs = 5;  // 130 bits > the 125 of M
 struct CrtConsts {
-    uint64_t w_lo[kCrtMaxModuli], w_hi[kCrtMaxModuli];  // w_t < M < 2^125
-    float frac[kCrtMaxModuli];                          // w_t / M
-    uint64_t M_lo, M_hi;
+    int32_t wl[kCrtMaxModuli][kLimbs];
+    int32_t Ml[kLimbs];
+    float frac[kCrtMaxModuli];  // w_t / M
 };
 
-// One output per thread (consecutive threads along a row of C): the N residues,
-// q = nearest integer to sum_t c_t w_t / M (FP32 is ample: the sum lies within
-// 1/4 of an integer because |C'| <= M / 4), C' = sum_t c_t w_t - q M in wrapping
-// 128-bit arithmetic (the true C' fits), then RN(C' 2^E) and alpha / beta.
+// The reconstruction of one output from its N residues r: q = nearest integer
+// to sum_t r_t w_t / M (FP32 is ample: the sum lies within 1/4 of an integer
+// because |C'| <= M / 4), then C' = sum_t r_t w_t - q M limb by limb (each limb
+// sum |L_i| < 2^39) and the limbs joined in 128 bits (|C'| < 2^123).
+template <int N>
+__device__ __forceinline__ I128 reconstruct(const int32_t (&r)[N], const CrtConsts& K) {
+    float qf = 0.0f;
+#pragma unroll
+    for (int t = 0; t < N; ++t) qf = __fmaf_rn((float)r[t], K.frac[t], qf);
+    const int32_t q = __float2int_rn(qf);
+    int64_t L[kLimbs];
+#pragma unroll
+    for (int i = 0; i < kLimbs; ++i) L[i] = -(int64_t)q * (int64_t)K.Ml[i];
+#pragma unroll
+    for (int t = 0; t < N; ++t)
+#pragma unroll
+        for (int i = 0; i < kLimbs; ++i) L[i] += (int64_t)r[t] * (int64_t)K.wl[t][i];
+    __int128 acc = L[kLimbs - 1];
+#pragma unroll
+    for (int i = kLimbs - 2; i >= 0; --i) acc = acc * ((__int128)1 << 26) + L[i];
+    return I128{(int64_t)(acc >> 64), (uint64_t)acc};
+}
+
+// Two consecutive outputs per thread (the residues of a pair are one 32-bit word
+// per modulus), threads along a row of C, rows across grid.y: reconstruction,
+// RN(C' 2^E) and alpha / beta.
 template <int N>
 __global__ void __launch_bounds__(256) crt_combine_kernel(int64_t m, int64_t n,
                                                           const int16_t* __restrict__ cres,
@@ -629,40 +658,38 @@ __global__ void __launch_bounds__(256) crt_combine_kernel(int64_t m, int64_t n,
     const long long ab = __double_as_longlong(alpha), bb = __double_as_longlong(beta);
     const bool beta0 = (bb & 0x7FFFFFFFFFFFFFFFll) == 0;
     const bool plain = ab == 0x3FF0000000000000ll && beta0;
-    const int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (j >= n) return;
-    const int32_t fj = fB[j];
+    const int64_t j0 = 2 * ((int64_t)blockIdx.x * blockDim.x + threadIdx.x);
+    if (j0 >= n) return;
+    const bool two = j0 + 1 < n;
+    const int32_t f0 = fB[j0], f1 = two ? fB[j0 + 1] : 0;
     for (int64_t i = blockIdx.y; i < m; i += gridDim.y) {
-        const int16_t* src = cres + i * ldr + j;
-        int32_t r[N];
+        // ldr is a multiple of 256 and j0 even: one aligned 32-bit load per modulus
+        const uint32_t* src = reinterpret_cast<const uint32_t*>(cres + i * ldr + j0);
+        int32_t r0[N], r1[N];
 #pragma unroll
-        for (int t = 0; t < N; ++t) r[t] = src[(int64_t)t * plane];
-        const int32_t ei = eA[i];
-        double out;
-        if (ei == GB_BAD_LINE_DEV || fj == GB_BAD_LINE_DEV) {
-            out = __longlong_as_double(0x7FF8000000000000ll);
-        } else {
-            float qf = 0.0f;
-#pragma unroll
-            for (int t = 0; t < N; ++t) qf = __fmaf_rn((float)r[t], K.frac[t], qf);
-            const int q = __float2int_rn(qf);
-            unsigned __int128 S = 0;
-#pragma unroll
-            for (int t = 0; t < N; ++t) {
-                const unsigned __int128 wt = ((unsigned __int128)K.w_hi[t] << 64) | K.w_lo[t];
-                S += (unsigned __int128)(__int128)r[t] * wt;
-            }
-            const unsigned __int128 Mv = ((unsigned __int128)K.M_hi << 64) | K.M_lo;
-            S -= (unsigned __int128)(__int128)q * Mv;
-            const I128 x{(int64_t)(uint64_t)(S >> 64), (uint64_t)S};
-            out = i128_to_double_scaled(x, ei + fj - 2 * b);
-            if (!plain) {
-                double o = __dmul_rn(alpha, out);
-                if (!beta0) o = __dadd_rn(o, __dmul_rn(beta, C[i * ldc + j]));
-                out = o;
-            }
+        for (int t = 0; t < N; ++t) {
+            const uint32_t w = src[(int64_t)t * (plane >> 1)];
+            r0[t] = (int32_t)(int16_t)(w & 0xFFFFu);
+            r1[t] = (int32_t)(int16_t)(w >> 16);
         }
-        C[i * ldc + j] = out;
+        const int32_t ei = eA[i];
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+            if (h == 1 && !two) break;
+            const int32_t fj = h ? f1 : f0;
+            double out;
+            if (ei == GB_BAD_LINE_DEV || fj == GB_BAD_LINE_DEV) {
+                out = __longlong_as_double(0x7FF8000000000000ll);
+            } else {
+                out = i128_to_double_scaled(reconstruct<N>(h ? r1 : r0, K), ei + fj - 2 * b);
+                if (!plain) {
+                    double o = __dmul_rn(alpha, out);
+                    if (!beta0) o = __dadd_rn(o, __dmul_rn(beta, C[i * ldc + j0 + h]));
+                    out = o;
+                }
+            }
+            C[i * ldc + j0 + h] = out;
+        }
     }
 }
 
@@ -710,16 +737,15 @@ int64_t inverse_mod(int64_t x, int64_t p) {
 CrtConsts crt_consts(int N) {
     CrtConsts K{};
     const unsigned __int128 M = modulus_product(N);
+    const unsigned __int128 mask = ((unsigned __int128)1 << 26) - 1;
     for (int t = 0; t < N; ++t) {
         const unsigned __int128 Mt = M / (unsigned __int128)kModuli[t];
         const int64_t inv = inverse_mod((int64_t)(Mt % (unsigned __int128)kModuli[t]), kModuli[t]);
         const unsigned __int128 w = Mt * (unsigned __int128)inv;  // < M
-        K.w_lo[t] = (uint64_t)w;
-        K.w_hi[t] = (uint64_t)(w >> 64);
+        for (int i = 0; i < kLimbs; ++i) K.wl[t][i] = (int32_t)((w >> (26 * i)) & mask);
         K.frac[t] = (float)((double)w / (double)M);
     }
-    K.M_lo = (uint64_t)M;
-    K.M_hi = (uint64_t)(M >> 64);
+    for (int i = 0; i < kLimbs; ++i) K.Ml[i] = (int32_t)((M >> (26 * i)) & mask);
     return K;
 }
 
@@ -827,8 +853,8 @@ cudaError_t launch_crt_gemm(const Launch& L, const Gemm& g, uint8_t* ws, const C
     // c5 + c6
     {
         const CrtConsts K = crt_consts(N);
-        // columns across the threads of a CTA (coalesced), rows across grid.y
-        const int64_t bx = (g.n + 255) / 256;
+        // column pairs across the threads of a CTA (coalesced), rows across grid.y
+        const int64_t bx = (g.n + 511) / 512;
         int64_t by = ((int64_t)L.sm_count * 8 + bx - 1) / bx;
         if (by > g.m) by = g.m;
         if (by > 65535) by = 65535;
