@@ -1,14 +1,18 @@
 """Benchmark of the FP64 GEMM C = A B (square, uniform[-1, 1], alpha = 1, beta = 0).
 
 One step = one FP64-accurate GEMM at the configured n through the emulated path
-(split of A, split of B, tensor-core slice products + FP64 recombination), the
-path whose result is checked against the FP64 error bound; the native FP64 path
+(--path crt, the default: residues of A and of B, the residue products as BF16
+GEMMs on the tensor cores, Chinese-remainder reconstruction and one FP64
+rounding; --path e4m3: split of A, split of B, tensor-core slice products + FP64
+recombination), the path whose result is checked against the FP64 error bound;
+the native FP64 path
 (the library's default kernel at that size) is timed beside it on the same
 inputs.  Inputs (8 n^2 bytes each) are larger than the 129 MB L2 at the default
 n, so no flush is needed.  At one GPU the same JSON line also carries, as
 sub-records: the accuracy of both paths against a double-double reference on
-sampled rows (`parity`), the same inputs through the BF16 digit format
-(`bf16_digits`), the 16-decade hard set at its slice count (`hard`),
+sampled rows (`parity`), the same inputs through the emulated path the line does
+not time (`other_path`: E4M3 digit slices beside the default residues) and the
+BF16 digit format (`bf16_digits`), the 16-decade hard set at its slice count (`hard`),
 the 2048-problem grouped workload against one launch per GEMM (`grouped`) and
 two short serving runs, at the specified and at a sustainable arrival rate
 (`serve`).  Other workloads print their own line (--workload).
@@ -52,6 +56,10 @@ def parse():
     p.add_argument("--steps", type=int, default=10)
     p.add_argument("--warmup", type=int, default=3)
     p.add_argument("--n", type=int, default=8192)
+    p.add_argument("--path", default="crt", choices=["crt", "e4m3"],
+                   help="emulated path of the main line: residues modulo --moduli primes, or "
+                        "--slices E4M3 digit slices (the other one is a sub-record)")
+    p.add_argument("--moduli", type=int, default=13)
     p.add_argument("--slices", type=int, default=10)
     p.add_argument("--group-slices", type=int, default=11)
     p.add_argument("--native-steps", type=int, default=2)
@@ -72,6 +80,7 @@ def parse():
     p.add_argument("--no-serve-baseline", action="store_true",
                    help="skip the one-GEMM-per-launch run of the same serving trace")
     p.add_argument("--hard-slices", type=int, default=11)
+    p.add_argument("--hard-moduli", type=int, default=14)
     p.add_argument("--bf16-slices", type=int, default=7)
     p.add_argument("--sub-serve-seconds", type=float, default=10.0)
     p.add_argument("--no-sub-records", action="store_true",
@@ -186,19 +195,23 @@ def cpu_baseline(n, seed, seconds, A=None, B=None):
     return rec, sel, C
 
 
-def dgemm_metric_config(n, s, world):
+def dgemm_metric_config(n, world):
     """Metric name and config of the square-DGEMM workload, shared by both arms."""
     metric = "FP64-accurate GEMM TFLOP/s (emulated path; native FP64 beside it)"
     config = {"workload": f"square DGEMM C = A B, m = n = k = {n}, uniform[-1,1], "
                           f"alpha = 1, beta = 0 (sweep point n = {n})",
-              "slices": s, "flush": "inputs larger than L2 (no flush needed)",
+              "flush": "inputs larger than L2 (no flush needed)",
               "parallelism": f"replicas x{world}"}
     return metric, config
 
 
-def gpu_path(s):
-    return (f"GPU: emulated FP64, {s} E4M3 slices, tcgen05 FP32 accumulation, exact integer "
-            "recombination, one FP64 rounding")
+def gpu_path(kind, count):
+    if kind == "crt":
+        return (f"GPU: emulated FP64 by residues, b-bit integers modulo {count} primes as BF16 "
+                "GEMMs on tcgen05 (FP32 sums of 256 K, exact), Chinese-remainder "
+                "reconstruction, one FP64 rounding")
+    return (f"GPU: emulated FP64, {count} E4M3 slices, tcgen05 FP32 accumulation, exact "
+            "integer recombination, one FP64 rounding")
 
 
 CPU_PATH = ("CPU oracle: plain C definition loops (-O2, no FMA contraction), OpenMP over "
@@ -257,7 +270,7 @@ def run_reference(args):
     value = 2.0 * rows * n * n * args.steps / dt / 1e12
     rec = dict(rec, value=value, sample=f"{rows} of {n} rows of C = A B per step "
                                          f"(n = {n}), plain C oracle")
-    metric, config = dgemm_metric_config(n, args.slices, args.gpus)
+    metric, config = dgemm_metric_config(n, args.gpus)
     out = {"impl": "reference", "path": CPU_PATH, "metric": metric, "value": value,
            "unit": "TFLOP/s", "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
            "ms_per_step": dt / args.steps * 1e3, "higher_is_better": True, "scaling": "weak",
@@ -883,19 +896,23 @@ def run_daxpy(args):
 
 
 def hard_record(args, gb, g, np, torch, A, B, C, q):
-    """The 16-decade hard set at n, emulated with the slice count it needs
-    (--hard-slices), the whole path (split + products) per step; rho of both
-    paths against the double-double reference on sampled rows."""
+    """The 16-decade hard set at n through the main line's emulated path with the
+    count it needs there (--hard-moduli residues, or --hard-slices E4M3 slices), the
+    whole path per step; rho of both paths against the double-double reference on
+    sampled rows."""
     n, s = args.n, args.hard_slices
+    prec = "emulated_crt" if args.path == "crt" else "emulated"
+    if args.path == "crt":
+        s = args.hard_moduli
     seed = g.BASE_SEED + 3
     A_h = matrix_threads("hard", n, n, seed, g.STREAM_A)
     B_h = matrix_threads("hard", n, n, seed, g.STREAM_B)
     A.copy_(torch.from_numpy(A_h))
     B.copy_(torch.from_numpy(B_h))
-    ws = gb.alloc_workspace(gb.workspace_size("emulated", s, n, n, n))
+    ws = gb.alloc_workspace(gb.workspace_size(prec, s, n, n, n))
     clocks = ClockSampler(0)
     clocks.start()
-    step = lambda: gb.dgemm(A, B, C, precision="emulated", slices=s, queue=q, workspace=ws)
+    step = lambda: gb.dgemm(A, B, C, precision=prec, slices=s, queue=q, workspace=ws)
     ms = _time_stream(torch, step, 5, 2)
     clk = clocks.stop()
     q.wait()
@@ -910,11 +927,77 @@ def hard_record(args, gb, g, np, torch, A, B, C, q):
     torch.cuda.empty_cache()
     return {"workload": f"square DGEMM C = A B, n = {n}, entries +-(1+f) 2^E with E uniform in "
                         "[-27, 26] (16 decades), random signs",
-            "slices": s, "ms_per_step": round(ms, 3),
+            "path": prec, "slices" if prec == "emulated" else "moduli": s,
+            "ms_per_step": round(ms, 3),
             "tflops": round(2.0 * n ** 3 / (ms * 1e-3) / 1e12, 3),
             "rho_emulated": rho_rows(got_e, A_h, B_h, rows, hilo),
             "rho_native": rho_rows(got_n, A_h, B_h, rows, hilo),
             "rows_checked": len(rows), "steps": 5, "warmup": 2, "clocks": clk}
+
+
+def other_path_record(args, gb, np, torch, A, B, C, q, A_h, B_h):
+    """The main line's inputs through the emulated path it does not time: the E4M3
+    digit slices beside residues, or the other way round; whole path per step,
+    its dominant kernel's time and rho against the double-double reference."""
+    n = args.n
+    crt = args.path != "crt"  # the other path
+    N, s = args.moduli, args.slices
+    ws = gb.alloc_workspace(gb.workspace_size("emulated_crt", N, n, n, n) if crt
+                            else gb.workspace_size("emulated", s, n, n, n))
+    stream = torch.cuda.current_stream()
+
+    def run(ev=None):
+        if crt:
+            gb.emulated_crt_steps(A, B, C, 1.0, 0.0, N, ws, queue=q, steps=("split_a", "split_b"))
+        else:
+            gb.emulated_steps(A, B, C, 1.0, 0.0, s, ws, queue=q, steps=("split_a", "split_b"))
+        if ev is not None:
+            ev[0].record(stream)
+        if crt:
+            gb.emulated_crt_steps(A, B, C, 1.0, 0.0, N, ws, queue=q, steps=("products",))
+        else:
+            gb.emulated_steps(A, B, C, 1.0, 0.0, s, ws, queue=q, steps=("products",))
+        if ev is not None:
+            ev[1].record(stream)
+        if crt:
+            gb.emulated_crt_steps(A, B, C, 1.0, 0.0, N, ws, queue=q, steps=("combine",))
+
+    for _ in range(2):
+        run()
+    torch.cuda.synchronize()
+    evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+           for _ in range(5)]
+    t0, t1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    t0.record(stream)
+    for e in evs:
+        run(e)
+    t1.record(stream)
+    torch.cuda.synchronize()
+    ms = t0.elapsed_time(t1) / 5
+    prod_ms = statistics.mean(a.elapsed_time(b) for a, b in evs)
+    q.wait()
+    rows = np.random.default_rng(n + 7).choice(n, 4, replace=False)
+    got = C[torch.from_numpy(rows).cuda()].cpu().numpy()
+    from oracle import cgemm
+    hilo = cgemm.dgemm_dd_rows(A_h, B_h, rows)
+    del ws
+    torch.cuda.empty_cache()
+    pk, pk_kind = peaks()
+    flops = 2.0 * n ** 3
+    if crt:
+        work, peak, kernel = N * flops, pk["bf16_tflops"], "crt_products_kernel"
+        desc = f"{N} moduli (residues, BF16 GEMMs)"
+    else:
+        work, peak, kernel = s * (s + 1) / 2 * flops, 2.0 * pk["bf16_tflops"], "emu_products_kernel"
+        desc = f"{s} E4M3 digit slices"
+    achieved = work / (prod_ms * 1e-3) / 1e12
+    return {"path": desc, "ms_per_step": round(ms, 3),
+            "tflops": round(flops / (ms * 1e-3) / 1e12, 3),
+            "products": {"kernel": kernel, "launch_ms": round(prod_ms, 3),
+                         "achieved": round(achieved, 1), "peak": round(peak, 1),
+                         "frac": round(achieved / peak, 4)},
+            "rho_emulated": rho_rows(got, A_h, B_h, rows, hilo), "rows_checked": len(rows),
+            "steps": 5, "warmup": 2}
 
 
 def bf16_record(args, gb, np, torch, A, B, C, q, A_h, B_h):
@@ -940,7 +1023,8 @@ def bf16_record(args, gb, np, torch, A, B, C, q, A_h, B_h):
     return {"workload": f"square DGEMM C = A B, n = {n}, uniform[-1,1] (the main line's inputs)",
             "digits": "8-bit signed digits in BF16, kind::f16 MMAs, FP32 level sums read out "
                       "every 1024 / s K indices",
-            "slices": s, "ms_per_step": round(ms, 3),
+            "path": prec, "slices" if prec == "emulated" else "moduli": s,
+            "ms_per_step": round(ms, 3),
             "tflops": round(2.0 * n ** 3 / (ms * 1e-3) / 1e12, 3),
             "bf16_pair_tflops_whole_path": round(pairs / (ms * 1e-3) / 1e12, 1),
             "rho_emulated": rho_rows(got, A_h, B_h, rows, hilo),
@@ -1018,23 +1102,36 @@ def main():
         return max_over_ranks(x, world)
 
     n, s = args.n, args.slices
+    N = args.moduli
+    crt = args.path == "crt"
     seed = g.BASE_SEED + 1
     A_h = matrix_threads("uniform", n, n, seed, g.STREAM_A)
     B_h = matrix_threads("uniform", n, n, seed, g.STREAM_B)
     A = torch.from_numpy(A_h).cuda()
     B = torch.from_numpy(B_h).cuda()
     C = torch.zeros((n, n), dtype=torch.float64, device="cuda")
-    ws = gb.alloc_workspace(gb.workspace_size("emulated", s, n, n, n))
+    ws = gb.alloc_workspace(gb.workspace_size("emulated_crt", N, n, n, n) if crt
+                            else gb.workspace_size("emulated", s, n, n, n))
     flops = 2.0 * n * n * n
-    pair_flops = s * (s + 1) / 2 * flops
+    # the dominant kernel's algorithmic work per launch: the residue products (N BF16
+    # GEMMs of the whole K) or the slice-pair products (s (s+1) / 2 FP8 GEMMs)
+    pair_flops = N * flops if crt else s * (s + 1) / 2 * flops
 
     def step(ev=None):
-        gb.emulated_steps(A, B, C, 1.0, 0.0, s, ws, queue=q, steps=("split_a", "split_b"))
+        if crt:
+            gb.emulated_crt_steps(A, B, C, 1.0, 0.0, N, ws, queue=q, steps=("split_a", "split_b"))
+        else:
+            gb.emulated_steps(A, B, C, 1.0, 0.0, s, ws, queue=q, steps=("split_a", "split_b"))
         if ev is not None:
             ev[0].record(stream)
-        gb.emulated_steps(A, B, C, 1.0, 0.0, s, ws, queue=q, steps=("products",))
+        if crt:
+            gb.emulated_crt_steps(A, B, C, 1.0, 0.0, N, ws, queue=q, steps=("products",))
+        else:
+            gb.emulated_steps(A, B, C, 1.0, 0.0, s, ws, queue=q, steps=("products",))
         if ev is not None:
             ev[1].record(stream)
+        if crt:
+            gb.emulated_crt_steps(A, B, C, 1.0, 0.0, N, ws, queue=q, steps=("combine",))
 
     for _ in range(args.warmup):
         step()
@@ -1059,6 +1156,8 @@ def main():
     prod_ms = statistics.mean(a.elapsed_time(b) for a, b in evs)
     q.wait()
     emu_C = C.clone()
+    del ws
+    torch.cuda.empty_cache()
 
     # native FP64 leg on the same inputs (the library's default kernel at this size)
     Cn = torch.zeros_like(C)
@@ -1075,16 +1174,17 @@ def main():
     clk = clocks.stop()
 
     # end to end through the public API with pinned host buffers: gb_dgemm_host
-    # copies A and B in (B whole, A in row bands), splits and multiplies each band
-    # as it arrives and copies each band of C back while the next ones compute
+    # copies A and B in (A in row bands, B in column blocks), computes each piece as
+    # its operands arrive and copies each piece of C back while the next ones compute
     A_p = torch.from_numpy(A_h).pin_memory()
     B_p = torch.from_numpy(B_h).pin_memory()
     C_p = torch.empty((n, n), dtype=torch.float64).pin_memory()
     e2e_steps = max(3, args.steps)
-    hws = gb.alloc_workspace(gb.host_workspace_size("emulated", s, n, n, n))
+    e2e_prec, e2e_count = ("emulated_crt", N) if crt else ("emulated", s)
+    hws = gb.alloc_workspace(gb.host_workspace_size(e2e_prec, e2e_count, n, n, n))
 
     def e2e_step():
-        gb.dgemm_host(A_p, B_p, C_p, 1.0, 0.0, precision="emulated", slices=s, queue=q,
+        gb.dgemm_host(A_p, B_p, C_p, 1.0, 0.0, precision=e2e_prec, slices=e2e_count, queue=q,
                       workspace=hws)
 
     e2e_step()
@@ -1107,24 +1207,35 @@ def main():
     achieved = pair_flops / (prod_ms * 1e-3) / 1e12
     fp64_peak = SMS * FP64_FLOP_PER_CLK_SM * SM_MAX_MHZ * 1e6 / 1e12
     native_tflops = flops / (native_ms * 1e-3) / 1e12
+    if crt:
+        roof = {"bound": "tensor", "kernel": "crt_products_kernel",
+                "achieved": round(achieved, 1), "peak": round(pk["bf16_tflops"], 1),
+                "unit": "TFLOP/s", "frac": round(achieved / pk["bf16_tflops"], 4),
+                "peak_kind": f"{pk_kind} bf16 burst",
+                "traffic": MEASURED_TRAFFIC.get(("crt_products_kernel", n, N)),
+                "launch_ms": round(prod_ms, 4),
+                "algorithmic": f"N * 2 n^3 = {pair_flops:.4g} BF16 flop per launch "
+                               f"(N = {N} moduli)"}
+    else:
+        roof = {"bound": "tensor", "kernel": "emu_products_kernel",
+                "achieved": round(achieved, 1), "peak": round(fp8_peak, 1),
+                "unit": "TFLOP/s", "frac": round(achieved / fp8_peak, 4),
+                "peak_kind": f"{pk_kind} bf16 burst x 2 (FP8 nominal ratio)",
+                "traffic": MEASURED_TRAFFIC.get(("emu_products_kernel", n, s)),
+                "launch_ms": round(prod_ms, 4),
+                "algorithmic": f"s(s+1)/2 * 2 n^3 = {pair_flops:.4g} FP8 flop per launch"}
 
-    metric, config = dgemm_metric_config(n, s, world)
+    metric, config = dgemm_metric_config(n, world)
     out = {
-        "path": gpu_path(s),
+        "path": gpu_path("crt", N) if crt else gpu_path("e4m3", s),
         "metric": metric,
         "value": round(value, 3), "unit": "TFLOP/s", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": round(ms_step, 4), "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f64",
         "data": "synthetic (seeded splitmix64, uniform[-1,1])",
         "config": config,
-        "gpu_launches": 4 * args.steps,
-        "roofline": {"bound": "tensor", "kernel": "emu_products_kernel",
-                     "achieved": round(achieved, 1), "peak": round(fp8_peak, 1),
-                     "unit": "TFLOP/s", "frac": round(achieved / fp8_peak, 4),
-                     "peak_kind": f"{pk_kind} bf16 burst x 2 (FP8 nominal ratio)",
-                     "traffic": MEASURED_TRAFFIC.get(("emu_products_kernel", n, s)),
-                     "launch_ms": round(prod_ms, 4),
-                     "algorithmic": f"s(s+1)/2 * 2 n^3 = {pair_flops:.4g} FP8 flop per launch"},
+        "gpu_launches": (5 if crt else 4) * args.steps,
+        "roofline": roof,
         "native": {"kernel": "dfma" if n > 2048 else "tiled", "value": round(native_tflops, 4),
                    "unit": "TFLOP/s",
                    "ms_per_call": round(native_ms, 2),
@@ -1159,6 +1270,7 @@ def main():
     if rank == 0 and world == 1 and not args.no_sub_records:
         del A_p, B_p, C_p, hws
         torch.cuda.empty_cache()
+        out["other_path"] = other_path_record(args, gb, np, torch, A, B, C, q, A_h, B_h)
         out["bf16_digits"] = bf16_record(args, gb, np, torch, A, B, C, q, A_h, B_h)
         out["hard"] = hard_record(args, gb, g, np, torch, A, B, C, q)
         out["grouped"] = grouped_sub_record(args)

@@ -185,12 +185,12 @@ gb_status gb_workdiv_suggest(const gb_device* dev, gb_kernel kernel, int64_t m, 
  *             tensor cores (BF16 residues |r| <= 254, FP32 sums of at most 256 K,
  *             each exact) and recovered exactly by the Chinese remainder theorem,
  *             then rounded once: the only approximation is the scaling to b
- *             bits (13 moduli: b = 50 at k = 8192).  gb_dgemm is its only entry
- *             point.  Workspace, each part 1024-byte aligned and in this order:
- *             A's residues (2 N mp kp bytes, mp = m rounded up to 128, kp = k
- *             rounded up to 16), B's residues (2 N np kp, np = n rounded up to
- *             128), the residues of C (2 N mp np), A's row exponents (m int32),
- *             B's column exponents (n int32), scratch.
+ *             bits (13 moduli: b = 50 at k = 8192).  Entry points: gb_dgemm and
+ *             gb_dgemm_host.  Workspace, each part 1024-byte aligned and in this
+ *             order: A's residues (2 N mp kp bytes, mp = m rounded up to 128,
+ *             kp = k rounded up to 16), B's residues (2 N np kp, np = n rounded
+ *             up to 256), the residues of C (2 N mp np), A's row exponents (m
+ *             int32), B's column exponents (n int32), scratch.
  *   workspace device buffer of at least gb_dgemm_workspace_size() bytes,
  *             256-byte aligned (emulated only; native takes NULL, 0).
  * Errors: GB_ERR_INVALID_ARG (sizes, pointers, leading dimensions, slices),
@@ -249,6 +249,21 @@ gb_status gb_emulated_split_b(gb_queue* q, int slices, int64_t m, int64_t n, int
                               const double* B, int64_t ldb, void* workspace,
                               size_t workspace_bytes);
 
+/* The residue precision (GB_PREC_EMULATED_CRT, `moduli` as its `slices`) one
+ * step at a time, on a workspace laid out as gb_dgemm documents for it:
+ *   step 0  scaled integers, residues and exponents of A's rows (m x k, lda);
+ *   step 1  the same for B's columns (k x n, ldb);
+ *   step 2  the residue products on the tensor cores, into the workspace's
+ *           residues of C;
+ *   step 3  the reconstruction, rounding and alpha / beta into C (m x n, ldc).
+ * Steps 0 - 3 in order on one queue compute what gb_dgemm computes (alpha != 0,
+ * k > 0); each step reads only the operands it names (the others may be NULL).
+ * Errors as gb_dgemm; GB_ERR_INVALID_ARG for a step outside 0 - 3. */
+gb_status gb_emulated_crt_step(gb_queue* q, int step, int moduli, int64_t m, int64_t n,
+                               int64_t k, double alpha, const double* A, int64_t lda,
+                               const double* B, int64_t ldb, double beta, double* C,
+                               int64_t ldc, void* workspace, size_t workspace_bytes);
+
 /* Emulated steps e3+e4 from a workspace filled by the two split calls: the
  * slice-pair products on the tensor cores and the recombination into C. */
 gb_status gb_emulated_products(gb_queue* q, int slices, int64_t m, int64_t n, int64_t k,
@@ -273,9 +288,14 @@ gb_status gb_emulated_products(gb_queue* q, int slices, int64_t m, int64_t n, in
  * the first band's products start on the first block while the others arrive;
  * the last band runs in two launches so that only a small last block of C is
  * copied back after the products end; each block of C is copied back while the
- * next launches compute (gb_dgemm_host_schedule lists the launches).  Native
- * precision: A, B (and C) are copied, multiplied by the default native kernel,
- * C copied back.
+ * next launches compute (gb_dgemm_host_schedule lists the launches).  Residue
+ * precision (GB_PREC_EMULATED_CRT): A's first band of whole 128-row tiles, then B
+ * in up to 4 blocks of whole 256-column tiles, then A's other bands (up to 4
+ * bands, each at least two waves of products); the first band is multiplied with
+ * each block of B as it arrives, the other bands with all of B as they arrive,
+ * each piece's residues reconstructed into C and copied back while the next
+ * piece computes.  BF16 digits: GB_ERR_UNSUPPORTED.  Native precision: A, B (and
+ * C) are copied, multiplied by the default native kernel, C copied back.
  * The copies run on two streams the queue creates on the first call (one per
  * direction), ordered after all work already on the queue; the queue's stream
  * passes the end of this call once C is back in host memory.  The caller must

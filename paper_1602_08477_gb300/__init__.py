@@ -17,6 +17,7 @@ from .gemm import (  # noqa: F401
     emulated_layout,
     host_schedule,
     host_workspace_size,
+    emulated_crt_steps,
     emulated_steps,
     workdiv_suggest,
     workspace_size,

@@ -99,6 +99,8 @@ SIGNATURES = {
     "gb_emulated_split_a": (_st, [_vp, _int, _i64, _i64, _i64, _vp, _i64, _vp, _sz]),
     "gb_emulated_split_b": (_st, [_vp, _int, _i64, _i64, _i64, _vp, _i64, _vp, _sz]),
     "gb_emulated_products": (_st, [_vp, _int, _i64, _i64, _i64, _dbl, _dbl, _vp, _i64, _vp, _sz]),
+    "gb_emulated_crt_step": (_st, [_vp, _int, _int, _i64, _i64, _i64, _dbl, _vp, _i64, _vp, _i64,
+                                   _dbl, _vp, _i64, _vp, _sz]),
     "gb_selftest_wait_timeout": (_st, [_vp, ctypes.c_uint32]),
     "gb_dgemm_emulated_noalloc": (_st, [_vp, _int, _i64, _i64, _i64, _dbl, _vp, _i64, _vp, _i64,
                                         _dbl, _vp, _i64]),

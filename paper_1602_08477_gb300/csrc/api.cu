@@ -512,6 +512,53 @@ gb_status gb_emulated_products(gb_queue* q, int slices, int64_t m, int64_t n, in
     return finish_call(q, e, "emulated products");
 }
 
+gb_status gb_emulated_crt_step(gb_queue* q, int step, int moduli, int64_t m, int64_t n,
+                               int64_t k, double alpha, const double* A, int64_t lda,
+                               const double* B, int64_t ldb, double beta, double* C,
+                               int64_t ldc, void* workspace, size_t workspace_bytes) {
+    if (!q) return invalid("q is NULL");
+    if (step < 0 || step > 3) return invalid("step must be 0 - 3, got %d", step);
+    if (m < 0 || n < 0 || k < 1) return invalid("m, n >= 0 and k >= 1 for the steps");
+    const int N = resolve_crt_moduli(moduli);
+    if (N < 1 || N > kCrtMaxModuli)
+        return invalid("the number of moduli must be in [1, %d] (or 0), got %d", kCrtMaxModuli,
+                       moduli);
+    if (crt_scale_bits(N, k) < 1) {
+        set_error("k = %lld is too long for %d moduli", (long long)k, N);
+        return GB_ERR_UNSUPPORTED;
+    }
+    if (step == 0 && (!A || lda < k || !aligned(A, 8)))
+        return invalid("A missing, misaligned or lda < k");
+    if (step == 1 && (!B || ldb < (n > 1 ? n : 1) || !aligned(B, 8)))
+        return invalid("B missing, misaligned or ldb < n");
+    if (step == 3 && (!C || ldc < (n > 1 ? n : 1) || !aligned(C, 8)))
+        return invalid("C missing, misaligned or ldc < n");
+    const CrtLayout lay = crt_layout(N, m, n, k);
+    if (!workspace || !aligned(workspace, 256) || workspace_bytes < lay.total) {
+        set_error("the residue steps need a 256-byte aligned workspace of %zu bytes", lay.total);
+        return GB_ERR_WORKSPACE;
+    }
+    if (m == 0 || n == 0) return GB_OK;
+    DeviceScope scope(q->dev->idx);
+    if (!scope.ok) return cuda_fail(cudaGetLastError(), "cudaSetDevice");
+    const Launch L = launch_of(q);
+    uint8_t* ws = static_cast<uint8_t*>(workspace);
+    int32_t* ea = reinterpret_cast<int32_t*>(ws + lay.a_exp);
+    int32_t* fb = reinterpret_cast<int32_t*>(ws + lay.b_exp);
+    int16_t* cres = reinterpret_cast<int16_t*>(ws + lay.c_res);
+    cudaError_t e = cudaSuccess;
+    switch (step) {
+        case 0: e = crt_split_a(L, N, lay.b, m, k, A, lda, ws + lay.a_res, lay.kp, ea); break;
+        case 1:
+            e = crt_split_b(L, N, lay.b, n, k, B, ldb, ws + lay.b_res, lay.kp, fb,
+                            reinterpret_cast<uint64_t*>(ws + lay.b_part));
+            break;
+        case 2: e = crt_residue_products(L, N, m, n, lay.kp, ws + lay.a_res, ws + lay.b_res, cres); break;
+        default: e = crt_combine(L, N, lay.b, m, n, alpha, beta, C, ldc, cres, ea, fb); break;
+    }
+    return finish_call(q, e, "emulated (residues) step");
+}
+
 gb_status gb_dgemm(gb_queue* q, const gb_workdiv* wd, gb_kernel kernel, gb_precision prec,
                    int slices, int64_t m, int64_t n, int64_t k, double alpha, const double* A,
                    int64_t lda, const double* B, int64_t ldb, double beta, double* C,

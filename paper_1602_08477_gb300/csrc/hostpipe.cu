@@ -15,8 +15,9 @@
 //                in two launches
 //   d2h stream : each block of C as soon as its products are done
 //
-// so the first products start once a small first block of B and the first band
-// of A have arrived, the blocks of B grow as fast as the link keeps ahead of the
+// (the residue precision follows the same plan with its own steps and pieces,
+// crt_host_pipeline), so the first products start once a small first block of B
+// and the first band of A have arrived, the blocks of B grow as fast as the link keeps ahead of the
 // products, the other copies run under the tensor-core products, and only a small
 // last block of C is copied back after the last launch.  Launch sizes are chosen
 // so that each fills whole waves of the SMs where possible.  The native
@@ -46,6 +47,7 @@ HostLayout host_layout(gb_precision prec, int s, int64_t m, int64_t n, int64_t k
     HostLayout h;
     size_t off = 0;
     if (prec == GB_PREC_EMULATED) off = up256(emu_layout(s, m, n, k).total);
+    if (prec == GB_PREC_EMULATED_CRT) off = up256(crt_layout(s, m, n, k).total);
     h.emu = off;
     h.a = off;
     off = up256(off + 8 * (size_t)m * (size_t)k);
@@ -218,6 +220,121 @@ cudaError_t copy_rows(void* dst, size_t dpitch, const void* src, size_t spitch,
     return cudaMemcpy2DAsync(dst, dpitch, src, spitch, 8 * (size_t)cols, (size_t)rows, kind, s);
 }
 
+// Residue precision on host buffers: A in row bands of whole 128-row tiles (at
+// most 4, each with at least two waves of (modulus, tile) products), B in column
+// blocks of whole 256-column tiles (at most 4) for the first band.  h2d: A's first
+// band, B's blocks, A's other bands (each with C's rows when beta != 0); queue: the
+// first band's residues, then per block of B its residues, the products of the
+// first band with it and their reconstruction into C, then per further band its
+// residues, its products with all of B and their reconstruction; d2h: each piece
+// of C as soon as it is reconstructed.
+struct CrtPiece {
+    int64_t r0, r1, c0, c1;
+    int band, bblock;
+};
+
+cudaError_t crt_host_pipeline(const Launch& L, cudaStream_t hs, cudaStream_t ds, cudaEvent_t* ev,
+                              int N, int64_t m, int64_t n, int64_t k, double alpha,
+                              const double* A, int64_t lda, const double* B, int64_t ldb,
+                              double beta, double* C, int64_t ldc, uint8_t* ws,
+                              const CrtLayout& lay, double* dA, double* dB, double* dC) {
+    const int64_t tiles_m = (m + kCrtTileRows - 1) / kCrtTileRows;
+    const int64_t tiles_n = (n + kCrtTileCols - 1) / kCrtTileCols;
+    int64_t nb = (int64_t)N * tiles_m * tiles_n / (2 * (int64_t)L.sm_count);
+    if (nb > 4) nb = 4;
+    if (nb > tiles_m) nb = tiles_m;
+    if (nb < 1) nb = 1;
+    int64_t nbb = tiles_n < 4 ? tiles_n : 4;
+    if (nbb < 1) nbb = 1;
+    auto band = [&](int64_t i, int64_t* r0, int64_t* r1) {
+        *r0 = tiles_m * i / nb * kCrtTileRows;
+        const int64_t e = tiles_m * (i + 1) / nb * kCrtTileRows;
+        *r1 = e < m ? e : m;
+    };
+    auto block = [&](int64_t j, int64_t* c0, int64_t* c1) {
+        *c0 = tiles_n * j / nbb * kCrtTileCols;
+        const int64_t e = tiles_n * (j + 1) / nbb * kCrtTileCols;
+        *c1 = e < n ? e : n;
+    };
+    const bool reads_c = beta != 0.0;
+    int32_t* ea = reinterpret_cast<int32_t*>(ws + lay.a_exp);
+    int32_t* fb = reinterpret_cast<int32_t*>(ws + lay.b_exp);
+    uint8_t* ares = ws + lay.a_res;
+    uint8_t* bres = ws + lay.b_res;
+    int16_t* cres = reinterpret_cast<int16_t*>(ws + lay.c_res);
+    uint64_t* part = reinterpret_cast<uint64_t*>(ws + lay.b_part);
+    const size_t row_bytes = 2 * (size_t)N * (size_t)lay.kp;  // residues of one row or column
+    cudaEvent_t* ev_b = ev + 1;  // blocks of B in
+    cudaEvent_t* ev_a = ev + 5;  // bands of A (and C) in
+    cudaEvent_t* ev_p = ev + 9;  // pieces reconstructed
+    auto copy_b = [&](int64_t j) {
+        int64_t c0, c1;
+        block(j, &c0, &c1);
+        cudaError_t r = copy_rows(dB + c0, 8 * (size_t)n, B + c0, 8 * (size_t)ldb, c1 - c0, k,
+                                  cudaMemcpyHostToDevice, hs);
+        return r == cudaSuccess ? cudaEventRecord(ev_b[j], hs) : r;
+    };
+    auto copy_a = [&](int64_t i) {
+        int64_t r0, r1;
+        band(i, &r0, &r1);
+        cudaError_t r = copy_rows(dA + r0 * k, 8 * (size_t)k, A + r0 * lda, 8 * (size_t)lda, k,
+                                  r1 - r0, cudaMemcpyHostToDevice, hs);
+        if (r == cudaSuccess && reads_c)
+            r = copy_rows(dC + r0 * n, 8 * (size_t)n, C + r0 * ldc, 8 * (size_t)ldc, n, r1 - r0,
+                          cudaMemcpyHostToDevice, hs);
+        return r == cudaSuccess ? cudaEventRecord(ev_a[i], hs) : r;
+    };
+    auto split_a = [&](int64_t i) {
+        int64_t r0, r1;
+        band(i, &r0, &r1);
+        cudaError_t r = cudaStreamWaitEvent(L.stream, ev_a[i], 0);
+        if (r == cudaSuccess)
+            r = crt_split_a(L, N, lay.b, r1 - r0, k, dA + r0 * k, k, ares + (size_t)r0 * row_bytes,
+                            lay.kp, ea + r0);
+        return r;
+    };
+    auto split_b = [&](int64_t j) {
+        int64_t c0, c1;
+        block(j, &c0, &c1);
+        cudaError_t r = cudaStreamWaitEvent(L.stream, ev_b[j], 0);
+        if (r == cudaSuccess)
+            r = crt_split_b(L, N, lay.b, c1 - c0, k, dB + c0, n, bres + (size_t)c0 * row_bytes,
+                            lay.kp, fb + c0, part);
+        return r;
+    };
+    int np = 0;
+    auto piece = [&](int64_t r0, int64_t r1, int64_t c0, int64_t c1) {
+        cudaError_t r = crt_products(L, N, lay.b, r1 - r0, c1 - c0, lay.kp, alpha, beta,
+                                     dC + r0 * n + c0, n, ares + (size_t)r0 * row_bytes,
+                                     bres + (size_t)c0 * row_bytes, cres, ea + r0, fb + c0);
+        if (r == cudaSuccess) r = cudaEventRecord(ev_p[np], L.stream);
+        if (r == cudaSuccess) r = cudaStreamWaitEvent(ds, ev_p[np], 0);
+        if (r == cudaSuccess)
+            r = copy_rows(C + r0 * ldc + c0, 8 * (size_t)ldc, dC + r0 * n + c0, 8 * (size_t)n,
+                          c1 - c0, r1 - r0, cudaMemcpyDeviceToHost, ds);
+        ++np;
+        return r;
+    };
+    cudaError_t e = copy_a(0);
+    for (int64_t j = 0; j < nbb && e == cudaSuccess; ++j) e = copy_b(j);
+    for (int64_t i = 1; i < nb && e == cudaSuccess; ++i) e = copy_a(i);
+    if (e == cudaSuccess) e = split_a(0);
+    for (int64_t j = 0; j < nbb && e == cudaSuccess; ++j) {
+        int64_t r0, r1, c0, c1;
+        band(0, &r0, &r1);
+        block(j, &c0, &c1);
+        e = split_b(j);
+        if (e == cudaSuccess) e = piece(r0, r1, c0, c1);
+    }
+    for (int64_t i = 1; i < nb && e == cudaSuccess; ++i) {
+        int64_t r0, r1;
+        band(i, &r0, &r1);
+        e = split_a(i);
+        if (e == cudaSuccess) e = piece(r0, r1, 0, n);
+    }
+    return e;
+}
+
 // The queue's copy streams and events, created on first use.
 cudaError_t ensure_aux(gb_queue* q) {
     if (q->aux_h2d) return cudaSuccess;
@@ -257,17 +374,21 @@ gb_status gb_dgemm_host_workspace_size(gb_precision prec, int slices, int64_t m,
         set_error("m, n, k must be >= 0");
         return GB_ERR_INVALID_ARG;
     }
-    if (prec == GB_PREC_EMULATED_BF16 || prec == GB_PREC_EMULATED_CRT) {
-        set_error("the host-buffer GEMM takes native or E4M3-digit precision");
+    if (prec == GB_PREC_EMULATED_BF16) {
+        set_error("the host-buffer GEMM takes native, E4M3-digit or residue precision");
         return GB_ERR_UNSUPPORTED;
     }
-    if (prec != GB_PREC_NATIVE && prec != GB_PREC_EMULATED) {
+    if (prec != GB_PREC_NATIVE && prec != GB_PREC_EMULATED && prec != GB_PREC_EMULATED_CRT) {
         set_error("unknown precision %d", (int)prec);
         return GB_ERR_INVALID_ARG;
     }
-    const int s = slices == 0 ? 11 : slices;
+    const int s = slices == 0 ? (prec == GB_PREC_EMULATED_CRT ? kCrtDefaultModuli : 11) : slices;
     if (prec == GB_PREC_EMULATED && (s < 1 || s > 16)) {
         set_error("slices must be in [1, 16] (or 0 for the default), got %d", slices);
+        return GB_ERR_INVALID_ARG;
+    }
+    if (prec == GB_PREC_EMULATED_CRT && (s < 1 || s > kCrtMaxModuli)) {
+        set_error("the number of moduli must be in [1, %d] (or 0), got %d", kCrtMaxModuli, slices);
         return GB_ERR_INVALID_ARG;
     }
     *out = host_layout(prec, s, m, n, k).total;
@@ -316,18 +437,27 @@ gb_status gb_dgemm_host(gb_queue* q, gb_precision prec, int slices, int64_t m, i
     }
     const int v = validate_gemm(m, n, k, alpha, A, lda, B, ldb, beta, C, ldc);
     if (v != GB_OK) return (gb_status)v;
-    if (prec == GB_PREC_EMULATED_BF16 || prec == GB_PREC_EMULATED_CRT) {
-        set_error("the host-buffer GEMM takes native or E4M3-digit precision");
+    if (prec == GB_PREC_EMULATED_BF16) {
+        set_error("the host-buffer GEMM takes native, E4M3-digit or residue precision");
         return GB_ERR_UNSUPPORTED;
     }
-    if (prec != GB_PREC_NATIVE && prec != GB_PREC_EMULATED) {
+    if (prec != GB_PREC_NATIVE && prec != GB_PREC_EMULATED && prec != GB_PREC_EMULATED_CRT) {
         set_error("unknown precision %d", (int)prec);
         return GB_ERR_INVALID_ARG;
     }
-    const int s = slices == 0 ? 11 : slices;
+    const bool crt = prec == GB_PREC_EMULATED_CRT;
+    const int s = slices == 0 ? (crt ? kCrtDefaultModuli : 11) : slices;
     if (prec == GB_PREC_EMULATED && (s < 1 || s > 16)) {
         set_error("slices must be in [1, 16] (or 0 for the default), got %d", slices);
         return GB_ERR_INVALID_ARG;
+    }
+    if (crt && (s < 1 || s > kCrtMaxModuli)) {
+        set_error("the number of moduli must be in [1, %d] (or 0), got %d", kCrtMaxModuli, slices);
+        return GB_ERR_INVALID_ARG;
+    }
+    if (crt && k > 0 && crt_scale_bits(s, k) < 1) {
+        set_error("k = %lld is too long for %d moduli", (long long)k, s);
+        return GB_ERR_UNSUPPORTED;
     }
     if (m == 0 || n == 0) return GB_OK;
     const HostLayout h = host_layout(prec, s, m, n, k);
@@ -383,6 +513,14 @@ gb_status gb_dgemm_host(gb_queue* q, gb_precision prec, int slices, int64_t m, i
         return finish_call(q, e, "host-buffer dgemm: copy out");
     }
 
+    if (crt) {
+        e = crt_host_pipeline(L, hs, ds, ev, s, m, n, k, alpha, A, lda, B, ldb, beta, C, ldc, ws,
+                              crt_layout(s, m, n, k), dA, dB, dC);
+        // the queue completes when C is back in host memory
+        if (e == cudaSuccess) e = cudaEventRecord(ev[0], ds);
+        if (e == cudaSuccess) e = cudaStreamWaitEvent(qs, ev[0], 0);
+        return finish_call(q, e, "host-buffer emulated (residues) dgemm");
+    }
     const EmuLayout lay = emu_layout(s, m, n, k);
     int32_t* ea = reinterpret_cast<int32_t*>(ws + lay.a_exp);
     int32_t* fb = reinterpret_cast<int32_t*>(ws + lay.b_exp);

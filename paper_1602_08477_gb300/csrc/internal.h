@@ -190,6 +190,28 @@ int crt_scale_bits(int N, int64_t k);
 CrtLayout crt_layout(int N, int64_t m, int64_t n, int64_t k);
 // Split of A and B, residue products, reconstruction (m, n > 0, k > 0, alpha != 0).
 cudaError_t launch_crt_gemm(const Launch& L, const Gemm& g, uint8_t* ws, const CrtLayout& lay);
+// The steps one at a time, for a band of rows of A (whole 128-row tiles of the
+// full layout: its residues start band_row0 N kp 2 bytes into the A residues) or a
+// block of columns of B (whole 256-column tiles: band_col0 N kp 2 bytes in):
+// residues and exponents of A's rows / B's columns; the products of the tiles of
+// A (m rows) and B (n columns) given, their residues in cres (2 N pad(m, 128)
+// pad(n, 256) bytes) and the reconstruction into C.
+constexpr int kCrtTileRows = 128;  // row edges of bands of A
+constexpr int kCrtTileCols = 256;  // column edges of blocks of B
+cudaError_t crt_split_a(const Launch& L, int N, int b, int64_t m, int64_t k, const double* A,
+                        int64_t lda, uint8_t* ares, int64_t kp, int32_t* ea);
+cudaError_t crt_split_b(const Launch& L, int N, int b, int64_t n, int64_t k, const double* B,
+                        int64_t ldb, uint8_t* bres, int64_t kp, int32_t* fb, uint64_t* part);
+cudaError_t crt_products(const Launch& L, int N, int b, int64_t m, int64_t n, int64_t kp,
+                         double alpha, double beta, double* C, int64_t ldc, const uint8_t* ares,
+                         const uint8_t* bres, int16_t* cres, const int32_t* ea,
+                         const int32_t* fb);
+// crt_products in its two launches: the residue products, the reconstruction.
+cudaError_t crt_residue_products(const Launch& L, int N, int64_t m, int64_t n, int64_t kp,
+                                 const uint8_t* ares, const uint8_t* bres, int16_t* cres);
+cudaError_t crt_combine(const Launch& L, int N, int b, int64_t m, int64_t n, double alpha,
+                        double beta, double* C, int64_t ldc, const int16_t* cres,
+                        const int32_t* ea, const int32_t* fb);
 
 // ---- emulated FP64 with BF16 digits (ozaki_bf16.cu) ----
 // 8-bit signed digits (|d| <= 128) in BF16, kind::f16 MMAs.  Output tiles of

@@ -20,10 +20,12 @@
 // Compared with the digit-slice form (ozaki_gemm.cu), the tensor cores do N
 // products of the whole K instead of s (s + 1) / 2 pair products: 13 BF16
 // GEMMs (the work of 26 FP8 GEMMs) against 55 FP8 pair products at s = 10.
-// Residues are stored pre-tiled per modulus: for modulus t, each 128-line tile
-// and each K step of 16 elements is a 128 x 32-byte K-major block in the 32-byte
-// swizzle, the K steps of a tile one after another, so a pipeline stage is one
-// contiguous bulk copy per operand.
+// Residues are stored pre-tiled, tile by tile: for each tile of R lines (128 rows
+// of A, 256 columns of B), each modulus and each K step of 16 elements, an R x
+// 32-byte K-major block in the 32-byte swizzle, the K steps of a (tile, modulus)
+// one after another, so a pipeline stage is one contiguous bulk copy per operand,
+// and the residues of a band of tiles are one contiguous range (a band of rows or
+// a block of columns is computed like a GEMM of its own).
 #include <cuda_runtime.h>
 #include <cstdint>
 
@@ -108,15 +110,13 @@ __device__ __forceinline__ void residues_of(uint64_t mag, bool neg, int u, uint3
 }
 
 // Byte offset of the 16-byte chunk holding K indices l0 .. l0+7 (l0 % 8 == 0) of
-// line x of modulus t's residue tiles (`tiles` tiles of R lines, nks K steps).
+// line x for modulus t (N moduli, tiles of R lines, nks K steps).
 template <int R>
-__device__ __forceinline__ int64_t crt_offset(int64_t x, int64_t l0, int t, int64_t tiles,
-                                              int64_t nks) {
+__device__ __forceinline__ int64_t crt_offset(int64_t x, int64_t l0, int t, int N, int64_t nks) {
     const int64_t tile = x / R;
     const int r = (int)(x - tile * R);
     const int chunk = (int)((l0 >> 3) & 1) ^ ((r >> 2) & 1);
-    return (((int64_t)t * tiles + tile) * nks + (l0 >> 4)) * (int64_t)(R * 32) + r * 32 +
-           (chunk << 4);
+    return ((tile * N + t) * nks + (l0 >> 4)) * (int64_t)(R * 32) + r * 32 + (chunk << 4);
 }
 
 // Row i of A by a CTA of 128 threads: pass 1 max |a| and finiteness, pass 2 the
@@ -125,7 +125,7 @@ __device__ __forceinline__ int64_t crt_offset(int64_t x, int64_t l0, int t, int6
 template <int N>
 __device__ __forceinline__ void crt_split_row(int64_t i, int64_t m, int64_t k,
                                               const double* __restrict__ A, int64_t lda,
-                                              uint8_t* __restrict__ res, int64_t kp, int64_t tiles,
+                                              uint8_t* __restrict__ res, int64_t kp,
                                               int b, int32_t* __restrict__ exps, unsigned* status,
                                               uint64_t* red, int* bad_sh) {
     const int tid = threadIdx.x;
@@ -134,7 +134,7 @@ __device__ __forceinline__ void crt_split_row(int64_t i, int64_t m, int64_t k,
         for (int64_t l0 = (int64_t)tid * 8; l0 < kp; l0 += (int64_t)blockDim.x * 8)
 #pragma unroll
             for (int t = 0; t < N; ++t)
-                *reinterpret_cast<uint4*>(res + crt_offset<kTileLines>(i, l0, t, tiles, nks)) =
+                *reinterpret_cast<uint4*>(res + crt_offset<kTileLines>(i, l0, t, N, nks)) =
                     make_uint4(0u, 0u, 0u, 0u);
         return;
     }
@@ -188,7 +188,7 @@ __device__ __forceinline__ void crt_split_row(int64_t i, int64_t m, int64_t k,
         }
 #pragma unroll
         for (int t = 0; t < N; ++t)
-            *reinterpret_cast<uint4*>(res + crt_offset<kTileLines>(i, l0, t, tiles, nks)) =
+            *reinterpret_cast<uint4*>(res + crt_offset<kTileLines>(i, l0, t, N, nks)) =
                 make_uint4(w[t][0], w[t][1], w[t][2], w[t][3]);
     }
     __syncthreads();
@@ -205,8 +205,7 @@ __global__ void __launch_bounds__(128) crt_split_rows_kernel(int64_t m, int64_t 
     __shared__ int bad_sh;
     const int64_t mp = (m + kTileLines - 1) / kTileLines * kTileLines;
     for (int64_t i = blockIdx.x; i < mp; i += gridDim.x)
-        crt_split_row<N>(i, m, k, A, lda, res, kp, mp / kTileLines, b, exps, status, red,
-                         &bad_sh);
+        crt_split_row<N>(i, m, k, A, lda, res, kp, b, exps, status, red, &bad_sh);
 }
 
 // Columns of B: CTA (x, y) reduces the `ks` partial maxima of columns 32 x .. +31
@@ -279,10 +278,10 @@ __global__ void __launch_bounds__(256) crt_split_cols_kernel(int64_t n, int64_t 
                 }
             }
         }
-        const int64_t nks = kp / kStep, tiles = np / kTileLinesB;
+        const int64_t nks = kp / kStep;
 #pragma unroll
         for (int t = 0; t < N; ++t)
-            *reinterpret_cast<uint4*>(res + crt_offset<kTileLinesB>(j, lbase, t, tiles, nks)) =
+            *reinterpret_cast<uint4*>(res + crt_offset<kTileLinesB>(j, lbase, t, N, nks)) =
                 make_uint4(w[t][0], w[t][1], w[t][2], w[t][3]);
     }
 }
@@ -370,8 +369,8 @@ struct CrtWalk {
         const int tm = first_m + (bid % group_size) % gm;
         const int tn = (bid % group_size) / gm;
         ItemArgs a;
-        a.a_src = ares + (((int64_t)mod * tiles_m + tm) * nks) * kBlockBytes;
-        a.b_src = bres + (((int64_t)mod * tiles_n + tn) * nks) * kBlockBytesB;
+        a.a_src = ares + (((int64_t)tm * nmod + mod) * nks) * kBlockBytes;
+        a.b_src = bres + (((int64_t)tn * nmod + mod) * nks) * kBlockBytesB;
         a.cres = cres + (int64_t)mod * ((int64_t)tiles_m * kTileLines) * ldr +
                  (int64_t)tm * kTileLines * ldr + (int64_t)tn * kTileLinesB;
         a.modulus = modulus_of(mod);
@@ -790,47 +789,41 @@ CrtLayout crt_layout(int N, int64_t m, int64_t n, int64_t k) {
     return L;
 }
 
-cudaError_t launch_crt_gemm(const Launch& L, const Gemm& g, uint8_t* ws, const CrtLayout& lay) {
-    const int N = lay.N;
-    if (g.m == 0 || g.n == 0) return cudaSuccess;
-    if (N < 1 || N > kCrtMaxModuli || lay.b < 1) return cudaErrorInvalidValue;
-    int32_t* ea = reinterpret_cast<int32_t*>(ws + lay.a_exp);
-    int32_t* fb = reinterpret_cast<int32_t*>(ws + lay.b_exp);
-    uint8_t* ares = ws + lay.a_res;
-    uint8_t* bres = ws + lay.b_res;
-    int16_t* cres = reinterpret_cast<int16_t*>(ws + lay.c_res);
-    // c1 - c3 for A: one CTA per row
-    {
-        int64_t blocks = lay.mp;
-        const int64_t cap = (int64_t)L.sm_count * 16;
-        if (blocks > cap) blocks = cap;
+cudaError_t crt_split_a(const Launch& L, int N, int b, int64_t m, int64_t k, const double* A,
+                        int64_t lda, uint8_t* ares, int64_t kp, int32_t* ea) {
+    if (m == 0) return cudaSuccess;
+    int64_t blocks = (m + kTileLines - 1) / kTileLines * kTileLines;
+    const int64_t cap = (int64_t)L.sm_count * 16;
+    if (blocks > cap) blocks = cap;
+#define GB_LAUNCH(NN)                                                                          \
+    crt_split_rows_kernel<NN><<<(unsigned)blocks, 128, 0, L.stream>>>(m, k, A, lda, ares, kp, b, \
+                                                                      ea, L.status)
+    GB_SWITCH_N(N, GB_LAUNCH)
+#undef GB_LAUNCH
+    return cudaGetLastError();
+}
+
+cudaError_t crt_split_b(const Launch& L, int N, int b, int64_t n, int64_t k, const double* B,
+                        int64_t ldb, uint8_t* bres, int64_t kp, int32_t* fb, uint64_t* part) {
+    if (n == 0) return cudaSuccess;
+    int ks = 1;
+    cudaError_t e = launch_colmax_part(L, n, k, B, ldb, part, &ks);
+    if (e != cudaSuccess) return e;
+    const int64_t np = (n + kTileLinesB - 1) / kTileLinesB * kTileLinesB;
+    const dim3 grid((unsigned)(np / 32), (unsigned)((kp + 63) / 64));
 #define GB_LAUNCH(NN)                                                                        \
-    crt_split_rows_kernel<NN><<<(unsigned)blocks, 128, 0, L.stream>>>(g.m, g.k, g.A, g.lda, \
-                                                                      ares, lay.kp, lay.b, ea, \
-                                                                      L.status)
-        GB_SWITCH_N(N, GB_LAUNCH)
+    crt_split_cols_kernel<NN><<<grid, 256, 0, L.stream>>>(n, k, B, ldb, bres, kp, b, fb, part, \
+                                                          ks, L.status)
+    GB_SWITCH_N(N, GB_LAUNCH)
 #undef GB_LAUNCH
-        const cudaError_t e = cudaGetLastError();
-        if (e != cudaSuccess) return e;
-    }
-    // c1 - c3 for B: column maxima over K ranges, then tiles of 32 columns x 64 rows
-    {
-        int ks = 1;
-        cudaError_t e = launch_colmax_part(L, g.n, g.k, g.B, g.ldb,
-                                           reinterpret_cast<uint64_t*>(ws + lay.b_part), &ks);
-        if (e != cudaSuccess) return e;
-        const dim3 grid((unsigned)(lay.np / 32), (unsigned)((lay.kp + 63) / 64));
-        const uint64_t* part = reinterpret_cast<const uint64_t*>(ws + lay.b_part);
-#define GB_LAUNCH(NN)                                                                     \
-    crt_split_cols_kernel<NN><<<grid, 256, 0, L.stream>>>(g.n, g.k, g.B, g.ldb, bres,     \
-                                                          lay.kp, lay.b, fb, part, ks,    \
-                                                          L.status)
-        GB_SWITCH_N(N, GB_LAUNCH)
-#undef GB_LAUNCH
-        e = cudaGetLastError();
-        if (e != cudaSuccess) return e;
-    }
-    // c4: residue products
+    return cudaGetLastError();
+}
+
+cudaError_t crt_residue_products(const Launch& L, int N, int64_t m, int64_t n, int64_t kp,
+                                 const uint8_t* ares, const uint8_t* bres, int16_t* cres) {
+    if (m == 0 || n == 0) return cudaSuccess;
+    const int64_t mp = (m + kTileLines - 1) / kTileLines * kTileLines;
+    const int64_t np = (n + kTileLinesB - 1) / kTileLinesB * kTileLinesB;
     {
         const uint32_t slot = kKB * (kBlockBytes + kBlockBytesB);  // 48 KiB, 1024-aligned
         const int fixed = 1024 + (int)sizeof(SmemTailCrt) + 64;
@@ -838,37 +831,65 @@ cudaError_t launch_crt_gemm(const Launch& L, const Gemm& g, uint8_t* ws, const C
         if (stages > kMaxStages) stages = kMaxStages;
         if (stages < 2) return cudaErrorInvalidValue;
         const size_t smem = (size_t)stages * slot + fixed;
-        const int tiles_m = (int)(lay.mp / kTileLines), tiles_n = (int)(lay.np / kTileLinesB);
+        const int tiles_m = (int)(mp / kTileLines), tiles_n = (int)(np / kTileLinesB);
         const int64_t items = (int64_t)N * tiles_m * tiles_n;
         const int grid = (int)(items < L.sm_count ? items : L.sm_count);
         cudaError_t e = cudaFuncSetAttribute(crt_products_kernel,
                                              cudaFuncAttributeMaxDynamicSharedMemorySize,
                                              kSmemLimit);
         if (e != cudaSuccess) return e;
-        const CrtWalk w{ares, bres, cres, lay.np, lay.kp / kStep, tiles_m, tiles_n, N, 0};
+        const CrtWalk w{ares, bres, cres, np, kp / kStep, tiles_m, tiles_n, N, 0};
         crt_products_kernel<<<grid, kThreads, smem, L.stream>>>(w, stages, slot, L.status);
-        e = cudaGetLastError();
-        if (e != cudaSuccess) return e;
+        return cudaGetLastError();
     }
-    // c5 + c6
-    {
-        const CrtConsts K = crt_consts(N);
-        // column pairs across the threads of a CTA (coalesced), rows across grid.y
-        const int64_t bx = (g.n + 511) / 512;
-        int64_t by = ((int64_t)L.sm_count * 8 + bx - 1) / bx;
-        if (by > g.m) by = g.m;
-        if (by > 65535) by = 65535;
-        const dim3 grid((unsigned)bx, (unsigned)by);
-        const int64_t plane = lay.mp * lay.np;
-#define GB_LAUNCH(NN)                                                                          \
-    crt_combine_kernel<NN><<<grid, 256, 0, L.stream>>>(g.m, g.n, cres, lay.np,                \
-                                                                   plane, ea, fb, lay.b,       \
-                                                                   g.alpha, g.beta, g.C, g.ldc, \
-                                                                   K)
-        GB_SWITCH_N(N, GB_LAUNCH)
+}
+
+cudaError_t crt_combine(const Launch& L, int N, int b, int64_t m, int64_t n, double alpha,
+                        double beta, double* C, int64_t ldc, const int16_t* cres,
+                        const int32_t* ea, const int32_t* fb) {
+    if (m == 0 || n == 0) return cudaSuccess;
+    const int64_t mp = (m + kTileLines - 1) / kTileLines * kTileLines;
+    const int64_t np = (n + kTileLinesB - 1) / kTileLinesB * kTileLinesB;
+    const CrtConsts K = crt_consts(N);
+    // column pairs across the threads of a CTA (coalesced), rows across grid.y
+    const int64_t bx = (n + 511) / 512;
+    int64_t by = ((int64_t)L.sm_count * 8 + bx - 1) / bx;
+    if (by > m) by = m;
+    if (by > 65535) by = 65535;
+    const dim3 grid((unsigned)bx, (unsigned)by);
+    const int64_t plane = mp * np;
+#define GB_LAUNCH(NN)                                                                           \
+    crt_combine_kernel<NN><<<grid, 256, 0, L.stream>>>(m, n, cres, np, plane, ea, fb, b, alpha, \
+                                                       beta, C, ldc, K)
+    GB_SWITCH_N(N, GB_LAUNCH)
 #undef GB_LAUNCH
-    }
     return cudaGetLastError();
+}
+
+cudaError_t crt_products(const Launch& L, int N, int b, int64_t m, int64_t n, int64_t kp,
+                         double alpha, double beta, double* C, int64_t ldc, const uint8_t* ares,
+                         const uint8_t* bres, int16_t* cres, const int32_t* ea,
+                         const int32_t* fb) {
+    cudaError_t e = crt_residue_products(L, N, m, n, kp, ares, bres, cres);
+    if (e == cudaSuccess) e = crt_combine(L, N, b, m, n, alpha, beta, C, ldc, cres, ea, fb);
+    return e;
+}
+
+cudaError_t launch_crt_gemm(const Launch& L, const Gemm& g, uint8_t* ws, const CrtLayout& lay) {
+    const int N = lay.N;
+    if (g.m == 0 || g.n == 0) return cudaSuccess;
+    if (N < 1 || N > kCrtMaxModuli || lay.b < 1) return cudaErrorInvalidValue;
+    int32_t* ea = reinterpret_cast<int32_t*>(ws + lay.a_exp);
+    int32_t* fb = reinterpret_cast<int32_t*>(ws + lay.b_exp);
+    cudaError_t e = crt_split_a(L, N, lay.b, g.m, g.k, g.A, g.lda, ws + lay.a_res, lay.kp, ea);
+    if (e == cudaSuccess)
+        e = crt_split_b(L, N, lay.b, g.n, g.k, g.B, g.ldb, ws + lay.b_res, lay.kp, fb,
+                        reinterpret_cast<uint64_t*>(ws + lay.b_part));
+    if (e == cudaSuccess)
+        e = crt_products(L, N, lay.b, g.m, g.n, lay.kp, g.alpha, g.beta, g.C, g.ldc,
+                         ws + lay.a_res, ws + lay.b_res,
+                         reinterpret_cast<int16_t*>(ws + lay.c_res), ea, fb);
+    return e;
 }
 
 }  // namespace gb

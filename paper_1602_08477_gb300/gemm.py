@@ -242,3 +242,26 @@ def emulated_steps(A, B, C, alpha, beta, slices, workspace, queue: Queue | None 
         check(lib.gb_emulated_products(q.handle, slices, m, n, k, alpha, beta, pc,
                                        max(ldc, n, 1), ws, wsb), "gb_emulated_products")
     return C
+
+
+CRT_STEPS = ("split_a", "split_b", "products", "combine")
+
+
+def emulated_crt_steps(A, B, C, alpha, beta, moduli, workspace, queue: Queue | None = None,
+                       steps=CRT_STEPS):
+    """Run the residue precision's steps one by one (gb_emulated_crt_step): the
+    residues of A's rows, of B's columns, the residue products, the
+    reconstruction into C."""
+    m, k = A.shape
+    n = B.shape[1]
+    q = queue or default_queue(A.device.index)
+    lib = _lib.load()
+    ws, wsb = ctypes.c_void_p(workspace.data_ptr()), workspace.numel()
+    pa, lda = _matrix_args(A, "A")
+    pb, ldb = _matrix_args(B, "B")
+    pc, ldc = _matrix_args(C, "C")
+    for st in steps:
+        check(lib.gb_emulated_crt_step(q.handle, CRT_STEPS.index(st), moduli, m, n, k, alpha,
+                                       pa, max(lda, k, 1), pb, max(ldb, n, 1), beta, pc,
+                                       max(ldc, n, 1), ws, wsb), "gb_emulated_crt_step")
+    return C

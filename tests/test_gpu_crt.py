@@ -183,8 +183,8 @@ def test_argument_errors_and_other_entry_points(gb):
     with pytest.raises(gb.GbError, match="GB_ERR_UNSUPPORTED"):
         gb.dgemm(a, b, c, precision=PREC, slices=1,
                  workspace=torch.empty(1 << 20, dtype=torch.uint8, device="cuda"))
-    with pytest.raises(gb.GbError, match="GB_ERR_UNSUPPORTED"):
-        gb.host_workspace_size(PREC, 13, 16, 16, 16)
+    with pytest.raises(gb.GbError, match="GB_ERR_INVALID_ARG"):
+        gb.host_workspace_size(PREC, 15, 16, 16, 16)
     with pytest.raises(gb.GbError, match="GB_ERR_UNSUPPORTED"):
         gb.GroupedPlan([dict(A=dA, B=dB, C=dC, precision=PREC, slices=13)])
 
@@ -216,3 +216,49 @@ def test_full_size_sampled_rows(gb, n, kind, N):
     want = ozaki_crt.crt_gemm(1.0, A, B, N=N, rows=rows, cols=cols)
     assert np.array_equal(bits(got[np.ix_(rows, cols)]), bits(want))
     assert within_bound(got[rows], 1.0, A, B, 0.0, None, rows=rows) <= 1.0
+
+
+@pytest.mark.parametrize("m,n,k,beta", [(300, 700, 333, 0.0), (1100, 1300, 500, 0.5),
+                                        (129, 257, 17, 1.0)])
+def test_host_buffers_bit_identical_to_device_call(gb, m, n, k, beta):
+    # A, B, C in pinned host memory: bands of A, blocks of B and pieces of C
+    # pipelined with the copies; every piece's result is the device call's
+    import torch
+    A, B, C0 = inputs("uniform", m, n, k, 908)
+    want = run(gb, A, B, C0, 1.25, beta, 13)
+    hA = torch.from_numpy(A).pin_memory()
+    hB = torch.from_numpy(B).pin_memory()
+    hC = torch.from_numpy(C0.copy()).pin_memory()
+    gb.dgemm_host(hA, hB, hC, 1.25, beta, precision=PREC, slices=13)
+    torch.cuda.synchronize()
+    assert np.array_equal(bits(hC.numpy()), bits(want))
+
+
+def test_host_buffers_full_size_sampled(gb):
+    import torch
+    n = 8192
+    A, B, _ = inputs("uniform", n, n, n, g.BASE_SEED + 2, with_c=False)
+    hA = torch.from_numpy(A).pin_memory()
+    hB = torch.from_numpy(B).pin_memory()
+    hC = torch.empty((n, n), dtype=torch.float64).pin_memory()
+    gb.dgemm_host(hA, hB, hC, 1.0, 0.0, precision=PREC, slices=13)
+    torch.cuda.synchronize()
+    rng = np.random.default_rng(77)
+    rows = rng.choice(n, 4, replace=False)
+    cols = np.sort(rng.choice(n, 96, replace=False))
+    want = ozaki_crt.crt_gemm(1.0, A, B, N=13, rows=rows, cols=cols)
+    assert np.array_equal(bits(hC.numpy()[np.ix_(rows, cols)]), bits(want))
+
+
+def test_steps_one_at_a_time_equal_the_single_call(gb):
+    import torch
+    m, n, k = 300, 520, 700
+    A, B, C0 = inputs("uniform", m, n, k, 909)
+    want = run(gb, A, B, C0, -1.5, 0.25, 13)
+    ws = gb.alloc_workspace(gb.workspace_size(PREC, 13, m, n, k))
+    dC = to_dev(C0)
+    gb.emulated_crt_steps(to_dev(A), to_dev(B), dC, -1.5, 0.25, 13, ws)
+    torch.cuda.synchronize()
+    assert np.array_equal(bits(dC.cpu().numpy()), bits(want))
+    with pytest.raises(gb.GbError, match="GB_ERR_INVALID_ARG"):
+        gb.emulated_crt_steps(to_dev(A), to_dev(B), dC, 1.0, 0.0, 15, ws)
