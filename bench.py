@@ -1023,8 +1023,7 @@ def bf16_record(args, gb, np, torch, A, B, C, q, A_h, B_h):
     return {"workload": f"square DGEMM C = A B, n = {n}, uniform[-1,1] (the main line's inputs)",
             "digits": "8-bit signed digits in BF16, kind::f16 MMAs, FP32 level sums read out "
                       "every 1024 / s K indices",
-            "path": prec, "slices" if prec == "emulated" else "moduli": s,
-            "ms_per_step": round(ms, 3),
+            "slices": s, "ms_per_step": round(ms, 3),
             "tflops": round(2.0 * n ** 3 / (ms * 1e-3) / 1e12, 3),
             "bf16_pair_tflops_whole_path": round(pairs / (ms * 1e-3) / 1e12, 1),
             "rho_emulated": rho_rows(got, A_h, B_h, rows, hilo),
