@@ -7,7 +7,8 @@ through the C ABI twice in a row and checks each result against gb_dgemm with a
 caller workspace, bit for bit (the two run the same kernels on the same
 digits), and against the CPU model of the split-precision steps, also bit for
 bit; the cases include the default slice count (slices = 0) and operands that
-are views with leading dimensions wider than the matrix.  It lives in a file
+are views with leading dimensions wider than the matrix, and one call captured
+in a CUDA graph and replayed twice.  It lives in a file
 collected last so that a failure here leaves every other test already run.
 """
 import ctypes
@@ -61,6 +62,39 @@ def test_noalloc_matches_workspace_entry_point_twice():
             torch.cuda.synchronize()
             assert torch.equal(got, want)
             assert bool(torch.all(Cbuf[:, n:] == -7.0))   # nothing beyond the n columns
+
+
+def test_noalloc_call_captured_in_a_cuda_graph_and_replayed():
+    # the case the entry point exists for: a call recorded into a CUDA graph
+    # (no allocation may happen inside the capture) and replayed later
+    import torch
+    import paper_1602_08477_gb300 as gb
+    gb.build()
+    lib = gb.load()
+    m, n, k, s, alpha, beta = 257, 190, 300, 11, 1.25, 0.5
+    A = torch.from_numpy(g.matrix("uniform", m, k, 92, 0)).cuda()
+    B = torch.from_numpy(g.matrix("uniform", k, n, 92, 1)).cuda()
+    C0 = torch.from_numpy(g.matrix("uniform", m, n, 92, 2)).cuda()
+    want = C0.clone()
+    gb.dgemm(A, B, want, alpha, beta, precision="emulated", slices=s)
+    C = C0.clone()
+    # one plain call first: it loads the module that holds the static scratch
+    st = lib.gb_dgemm_emulated_noalloc(ctypes.c_void_p(torch.cuda.current_stream().cuda_stream),
+                                       s, m, n, k, alpha, _ptr(A), k, _ptr(B), n, beta, _ptr(C), n)
+    assert st == 0, gb._lib.last_error()
+    torch.cuda.synchronize()
+    assert torch.equal(C, want)
+    graph = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(graph):
+        st = lib.gb_dgemm_emulated_noalloc(
+            ctypes.c_void_p(torch.cuda.current_stream().cuda_stream), s, m, n, k, alpha, _ptr(A),
+            k, _ptr(B), n, beta, _ptr(C), n)
+    assert st == 0, gb._lib.last_error()
+    for _ in range(2):
+        C.copy_(C0)
+        graph.replay()
+        torch.cuda.synchronize()
+        assert torch.equal(C, want)
 
 
 def test_noalloc_rejects_sizes_beyond_the_static_scratch():
