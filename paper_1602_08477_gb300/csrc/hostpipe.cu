@@ -220,41 +220,103 @@ cudaError_t copy_rows(void* dst, size_t dpitch, const void* src, size_t spitch,
     return cudaMemcpy2DAsync(dst, dpitch, src, spitch, 8 * (size_t)cols, (size_t)rows, kind, s);
 }
 
-// Residue precision on host buffers: A in row bands of whole 128-row tiles (at
-// most 4, each with at least two waves of (modulus, tile) products), B in column
-// blocks of whole 256-column tiles (at most 4) for the first band.  h2d: A's first
-// band, B's blocks, A's other bands (each with C's rows when beta != 0); queue: the
+// Residue precision: the launches of one host-buffer GEMM.  A in nb equal row
+// bands of whole 128-row tiles (at most kMaxBands, each with at least two waves
+// of (modulus, tile) products).  The first band runs one launch per column block
+// of B, kCrtBBlocks equal blocks of whole 256-column tiles: narrower blocks would
+// start the products sooner, but a column block is a strided copy whose rows are
+// the block's width, and the host link moves rows narrower than 16 KiB far below
+// its rate (measured pinned -> device: 75 GB/s at 2 KiB, 109 at 8 KiB, 188 at
+// 16 KiB, 210 at 32 KiB).  The last band runs two launches when that shortens the
+// time after its products: the first part's copy back then runs under the second
+// part's products (planning estimates below; the result does not depend on them).
+constexpr int kCrtBBlocks = 4;
+constexpr double kPlanItemFlopsPerSm = 8.8e12;  // BF16 residue products, per SM and second
+constexpr double kPlanLinkBack = 190e9;         // device -> host bytes per second
+
+HostSchedule crt_host_schedule(int N, int64_t m, int64_t n, int64_t kp, int sms) {
+    HostSchedule h;
+    const int64_t tiles_m = (m + kCrtTileRows - 1) / kCrtTileRows;
+    const int64_t tiles_n = (n + kCrtTileCols - 1) / kCrtTileCols;
+    int64_t nb = (int64_t)N * tiles_m * tiles_n / (2 * (int64_t)sms);
+    if (nb > kMaxBands) nb = kMaxBands;
+    if (nb > tiles_m) nb = tiles_m;
+    if (nb < 1) nb = 1;
+    h.nb = (int)nb;
+    auto band = [&](int64_t i, int64_t* r0, int64_t* r1) {
+        *r0 = tiles_m * i / nb * kCrtTileRows;
+        const int64_t e = tiles_m * (i + 1) / nb * kCrtTileRows;
+        *r1 = e < m ? e : m;
+    };
+    // column blocks of B for the first band, in tile columns
+    int64_t cut[kMaxBBlocks + 1];
+    int nbb = 0;
+    cut[0] = 0;
+    {
+        const int64_t q = tiles_n < kCrtBBlocks ? tiles_n : kCrtBBlocks;
+        for (int64_t j = 1; j < q; ++j) cut[++nbb] = tiles_n * j / q;
+    }
+    cut[++nbb] = tiles_n;
+    h.nbb = nbb;
+    for (int j = 0; j <= nbb; ++j) h.bcut[j] = cut[j] * kCrtTileCols < n ? cut[j] * kCrtTileCols : n;
+    int64_t r0, r1;
+    band(0, &r0, &r1);
+    for (int j = 0; j < nbb; ++j) h.piece[h.np++] = Piece{r0, r1, h.bcut[j], h.bcut[j + 1], 0, j};
+    const double t_item = 2.0 * kCrtTileRows * kCrtTileCols * (double)kp / kPlanItemFlopsPerSm;
+    for (int64_t i = 1; i < nb; ++i) {
+        band(i, &r0, &r1);
+        int64_t split = tiles_n;
+        if (i + 1 == nb && tiles_n >= 4) {
+            // time from the band's start to the end of its copy back, one launch or two
+            const int64_t R = (r1 - r0 + kCrtTileRows - 1) / kCrtTileRows;
+            const double row_back = 8.0 * (double)(r1 - r0) / kPlanLinkBack;  // per column of C
+            const double whole = (double)waves(N * R * tiles_n, sms) * t_item +
+                                 row_back * (double)n;
+            double best = whole;
+            for (int64_t c = tiles_n - 1; 2 * c >= tiles_n; --c) {
+                const int64_t c_cols = c * kCrtTileCols < n ? c * kCrtTileCols : n;
+                const double t1 = (double)waves(N * R * c, sms) * t_item;
+                const double t2 = t1 + (double)waves(N * R * (tiles_n - c), sms) * t_item;
+                const double back1 = t1 + row_back * (double)c_cols;
+                const double end = (t2 > back1 ? t2 : back1) + row_back * (double)(n - c_cols);
+                if (end < best) {
+                    best = end;
+                    split = c;
+                }
+            }
+        }
+        if (split < tiles_n) {
+            h.piece[h.np++] = Piece{r0, r1, 0, split * kCrtTileCols, (int)i, -1};
+            h.piece[h.np++] = Piece{r0, r1, split * kCrtTileCols, n, (int)i, -1};
+        } else {
+            h.piece[h.np++] = Piece{r0, r1, 0, n, (int)i, -1};
+        }
+    }
+    return h;
+}
+
+// Residue precision on host buffers, on the schedule above.  h2d: A's first band,
+// B's blocks, A's other bands (each with C's rows when beta != 0); queue: the
 // first band's residues, then per block of B its residues, the products of the
 // first band with it and their reconstruction into C, then per further band its
-// residues, its products with all of B and their reconstruction; d2h: each piece
-// of C as soon as it is reconstructed.
-struct CrtPiece {
-    int64_t r0, r1, c0, c1;
-    int band, bblock;
-};
-
+// residues and its launches with all of B; d2h: each piece of C as soon as it is
+// reconstructed.
 cudaError_t crt_host_pipeline(const Launch& L, cudaStream_t hs, cudaStream_t ds, cudaEvent_t* ev,
                               int N, int64_t m, int64_t n, int64_t k, double alpha,
                               const double* A, int64_t lda, const double* B, int64_t ldb,
                               double beta, double* C, int64_t ldc, uint8_t* ws,
                               const CrtLayout& lay, double* dA, double* dB, double* dC) {
+    const HostSchedule sch = crt_host_schedule(N, m, n, lay.kp, L.sm_count);
     const int64_t tiles_m = (m + kCrtTileRows - 1) / kCrtTileRows;
-    const int64_t tiles_n = (n + kCrtTileCols - 1) / kCrtTileCols;
-    int64_t nb = (int64_t)N * tiles_m * tiles_n / (2 * (int64_t)L.sm_count);
-    if (nb > 4) nb = 4;
-    if (nb > tiles_m) nb = tiles_m;
-    if (nb < 1) nb = 1;
-    int64_t nbb = tiles_n < 4 ? tiles_n : 4;
-    if (nbb < 1) nbb = 1;
+    const int64_t nb = sch.nb, nbb = sch.nbb;
     auto band = [&](int64_t i, int64_t* r0, int64_t* r1) {
         *r0 = tiles_m * i / nb * kCrtTileRows;
         const int64_t e = tiles_m * (i + 1) / nb * kCrtTileRows;
         *r1 = e < m ? e : m;
     };
     auto block = [&](int64_t j, int64_t* c0, int64_t* c1) {
-        *c0 = tiles_n * j / nbb * kCrtTileCols;
-        const int64_t e = tiles_n * (j + 1) / nbb * kCrtTileCols;
-        *c1 = e < n ? e : n;
+        *c0 = sch.bcut[j];
+        *c1 = sch.bcut[j + 1];
     };
     const bool reads_c = beta != 0.0;
     int32_t* ea = reinterpret_cast<int32_t*>(ws + lay.a_exp);
@@ -264,9 +326,9 @@ cudaError_t crt_host_pipeline(const Launch& L, cudaStream_t hs, cudaStream_t ds,
     int16_t* cres = reinterpret_cast<int16_t*>(ws + lay.c_res);
     uint64_t* part = reinterpret_cast<uint64_t*>(ws + lay.b_part);
     const size_t row_bytes = 2 * (size_t)N * (size_t)lay.kp;  // residues of one row or column
-    cudaEvent_t* ev_b = ev + 1;  // blocks of B in
-    cudaEvent_t* ev_a = ev + 5;  // bands of A (and C) in
-    cudaEvent_t* ev_p = ev + 9;  // pieces reconstructed
+    cudaEvent_t* ev_b = ev + 1;                // column blocks of B in
+    cudaEvent_t* ev_a = ev + 1 + kMaxBBlocks;  // row bands of A (and C) in
+    cudaEvent_t* ev_p = ev_a + kMaxBands;      // pieces reconstructed
     auto copy_b = [&](int64_t j) {
         int64_t c0, c1;
         block(j, &c0, &c1);
@@ -318,19 +380,15 @@ cudaError_t crt_host_pipeline(const Launch& L, cudaStream_t hs, cudaStream_t ds,
     cudaError_t e = copy_a(0);
     for (int64_t j = 0; j < nbb && e == cudaSuccess; ++j) e = copy_b(j);
     for (int64_t i = 1; i < nb && e == cudaSuccess; ++i) e = copy_a(i);
-    if (e == cudaSuccess) e = split_a(0);
-    for (int64_t j = 0; j < nbb && e == cudaSuccess; ++j) {
-        int64_t r0, r1, c0, c1;
-        band(0, &r0, &r1);
-        block(j, &c0, &c1);
-        e = split_b(j);
-        if (e == cudaSuccess) e = piece(r0, r1, c0, c1);
-    }
-    for (int64_t i = 1; i < nb && e == cudaSuccess; ++i) {
-        int64_t r0, r1;
-        band(i, &r0, &r1);
-        e = split_a(i);
-        if (e == cudaSuccess) e = piece(r0, r1, 0, n);
+    int split_band = -1;
+    for (int p = 0; p < sch.np && e == cudaSuccess; ++p) {
+        const Piece& pc = sch.piece[p];
+        if (pc.band != split_band) {
+            e = split_a(pc.band);
+            split_band = pc.band;
+        }
+        if (e == cudaSuccess && pc.bblock >= 0) e = split_b(pc.bblock);
+        if (e == cudaSuccess) e = piece(pc.r0, pc.r1, pc.c0, pc.c1);
     }
     return e;
 }

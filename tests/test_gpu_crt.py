@@ -219,10 +219,11 @@ def test_full_size_sampled_rows(gb, n, kind, N):
 
 
 @pytest.mark.parametrize("m,n,k,beta", [(300, 700, 333, 0.0), (1100, 1300, 500, 0.5),
-                                        (129, 257, 17, 1.0)])
+                                        (129, 257, 17, 1.0), (2048, 3000, 256, 0.5)])
 def test_host_buffers_bit_identical_to_device_call(gb, m, n, k, beta):
     # A, B, C in pinned host memory: bands of A, blocks of B and pieces of C
-    # pipelined with the copies; every piece's result is the device call's
+    # pipelined with the copies; every piece's result is the device call's (the
+    # last case runs four bands, four blocks of B and a last band in two launches)
     import torch
     A, B, C0 = inputs("uniform", m, n, k, 908)
     want = run(gb, A, B, C0, 1.25, beta, 13)
