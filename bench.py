@@ -1187,8 +1187,23 @@ def main():
         gb.dgemm_host(A_p, B_p, C_p, 1.0, 0.0, precision=e2e_prec, slices=e2e_count, queue=q,
                       workspace=hws)
 
+    # the host link's rate just before and just after the timed steps (one plain
+    # pinned -> device copy of A each): the end-to-end figure moves with it, and
+    # the link is shared with the other GPUs of the machine
+    link_dst = torch.empty((n, n), dtype=torch.float64, device="cuda")
+
+    def link_gbs():
+        l0 = torch.cuda.Event(enable_timing=True)
+        l1 = torch.cuda.Event(enable_timing=True)
+        l0.record(stream)
+        link_dst.copy_(A_p, non_blocking=True)
+        l1.record(stream)
+        torch.cuda.synchronize()
+        return round(8 * n * n / l0.elapsed_time(l1) / 1e6, 1)
+
     e2e_step()
     torch.cuda.synchronize()
+    link_before = link_gbs()
     barrier()
     e0 = torch.cuda.Event(enable_timing=True)
     e1 = torch.cuda.Event(enable_timing=True)
@@ -1199,6 +1214,8 @@ def main():
     torch.cuda.synchronize()
     e2e_ms = slowest(e0.elapsed_time(e1)) / e2e_steps
     q.wait()
+    link_after = link_gbs()
+    del link_dst
 
     ms_step = ms_total / args.steps
     value = replica_value(flops, world, ms_step) / 1e12
@@ -1244,7 +1261,9 @@ def main():
                                 "frac": round(native_tflops / fp64_peak, 4),
                                 "peak_kind": "derived: 152 SM x 4 flop/clk x 2070 MHz"}},
         "e2e": {"value": round(replica_value(flops, world, e2e_ms) / 1e12, 3), "unit": "TFLOP/s",
-                "h2d_bytes_per_step": 2 * 8 * n * n, "d2h_bytes_per_step": 8 * n * n},
+                "h2d_bytes_per_step": 2 * 8 * n * n, "d2h_bytes_per_step": 8 * n * n,
+                "ms_per_step": round(e2e_ms, 4),
+                "link_h2d_gbs_before_after": [link_before, link_after]},
         "clocks": clk,
     }
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
