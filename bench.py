@@ -738,8 +738,9 @@ def run_serve_sweep(args):
 def run_sweep(args):
     """Native square DGEMM sweep n in {1024, ..., 10240}: naive vs tiled vs DFMA vs
     DMMA kernels, TFLOP/s and fraction of the FP64 peak; the vendor library's FP64
-    GEMM (cuBLAS via torch.matmul) beside them as context, and the emulated path
-    (FP64-accurate, --slices digit slices) at the same sizes."""
+    GEMM (cuBLAS via torch.matmul) beside them as context, and the two emulated
+    paths (FP64-accurate: --slices E4M3 digit slices, --moduli residues) at the same
+    sizes."""
     import torch
 
     import paper_1602_08477_gb300 as gb
@@ -754,7 +755,8 @@ def run_sweep(args):
         gb.fill_uniform(A, 1602084771, 0)
         gb.fill_uniform(B, 1602084771, 1)
         ws = gb.alloc_workspace(gb.workspace_size("emulated", args.slices, n, n, n))
-        for kernel in ("naive", "tiled", "dfma", "dmma", "cublas", "emulated"):
+        ws_crt = gb.alloc_workspace(gb.workspace_size("emulated_crt", args.moduli, n, n, n))
+        for kernel in ("naive", "tiled", "dfma", "dmma", "cublas", "emulated", "emulated_crt"):
             if kernel == "cublas":
                 # context only: the vendor library's FP64 GEMM through torch.matmul
                 f = lambda: torch.matmul(A, B, out=C)
@@ -762,14 +764,18 @@ def run_sweep(args):
                 # the FP64-accurate split-precision path at the bench's slice count
                 f = lambda: gb.dgemm(A, B, C, precision="emulated", slices=args.slices,
                                      workspace=ws)
+            elif kernel == "emulated_crt":
+                # the FP64-accurate residue path at the bench's number of moduli
+                f = lambda: gb.dgemm(A, B, C, precision="emulated_crt", slices=args.moduli,
+                                     workspace=ws_crt)
             else:
                 f = lambda: gb.dgemm(A, B, C, kernel=kernel)
-            steps = 10 if kernel == "emulated" else (1 if n >= 4096 else 3)
+            steps = 10 if kernel.startswith("emulated") else (1 if n >= 4096 else 3)
             ms = _time_stream(torch, f, steps, 1)
             tf = 2.0 * n ** 3 / ms / 1e9
             res.append(dict(n=n, kernel=kernel, ms=round(ms, 3), tflops=round(tf, 4),
                             frac_fp64_peak=round(tf / fp64_peak, 4)))
-        del A, B, C, ws
+        del A, B, C, ws, ws_crt
         torch.cuda.empty_cache()
     print(json.dumps({"metric": "native FP64 DGEMM TFLOP/s per kernel", "unit": "TFLOP/s",
                       "peak": round(fp64_peak, 4), "sweep": res}), flush=True)
