@@ -47,8 +47,7 @@ FP64_FLOP_PER_CLK_SM = 4.0
 # DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) of one launch of the
 # dominant kernel, from one ncu capture of the kernel as it is now:
 # (kernel, n, slices) -> bytes.  Reported only for that exact workload.
-MEASURED_TRAFFIC = {("emu_products_kernel", 8192, 10): int(9.80e9 + 559.31e6),
-                    ("crt_products_kernel", 8192, 13): int(16.84e9 + 2.09e9)}
+MEASURED_TRAFFIC = {("emu_products_kernel", 8192, 10): int(9.80e9 + 559.31e6)}
 
 
 def parse():

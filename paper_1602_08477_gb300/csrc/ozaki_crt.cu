@@ -315,6 +315,7 @@ constexpr int kKB = 4;                        // K steps per pipeline stage
 constexpr int kUnitStages = 4;                // stages per exact unit: 256 K
 constexpr int kMaxStages = 4;
 constexpr int kEpiCols = kTileLinesB / 4;     // columns of one epilogue warp
+constexpr int64_t kUnitK = (int64_t)kKB * kStep * kUnitStages;  // K of one exact unit
 
 struct ItemArgs {
     const uint8_t* a_src;  // A residue tiles of this item's tile row, K step 0
@@ -463,6 +464,8 @@ __global__ void __launch_bounds__(kThreads, 1)
     } else if (warp == 1 && lane == 0) {
         // ---- MMA issuer ----
         constexpr uint32_t idesc = ptx::idesc_bf16_f32(kTileLines, kTileLinesB);
+        const uint64_t adesc0 = ptx::umma_desc_sw32(ptx::smem_u32(smem));
+        const uint32_t slot16 = slot_bytes >> 4;  // descriptor address step of one slot
         int st = 0;
         uint32_t ph = 0;
         uint32_t unit = 0;  // units issued by this CTA so far: accumulator unit % kBufs
@@ -475,6 +478,50 @@ __global__ void __launch_bounds__(kThreads, 1)
                                         kStatusTimeout, kWaitTimeoutNs))
                 break;
             ptx::mbar_arrive(&tail->args_empty[as]);
+            if (stages == kUnitStages) {
+                // K is a whole number of units (the layout pads it), so every unit is
+                // kUnitStages full stages starting at slot 0: slots, descriptors and
+                // MMAs at compile-time offsets.  The issuing thread's own instructions
+                // per MMA are what bound this kernel's tensor pipe, so this loop keeps
+                // them to the barrier waits, the MMAs and the commits.
+                for (int u = 0; u < nst / kUnitStages; ++u) {
+                    const uint32_t b = unit % kBufs;
+                    if (unit >= (uint32_t)kBufs) {
+                        // the epilogue has read this accumulator's previous unit
+                        if (!ptx::mbar_wait_bounded(&tmem_empty[b], ((unit / kBufs) - 1) & 1u,
+                                                    abort, status, kStatusTimeout,
+                                                    kWaitTimeoutNs)) {
+                            stop = true;
+                            break;
+                        }
+                        ptx::tc_fence_after();
+                    }
+                    const uint32_t acc = tmem_base + b * (uint32_t)kTileLinesB;
+#pragma unroll
+                    for (int s2 = 0; s2 < kUnitStages; ++s2) {
+                        if (!ptx::mbar_wait_bounded(&full[s2], ph, abort, status, kStatusTimeout,
+                                                    kWaitTimeoutNs)) {
+                            stop = true;
+                            break;
+                        }
+                        ptx::tc_fence_after();
+                        const uint64_t adesc = adesc0 + (uint64_t)(s2 * slot16);
+                        const uint64_t bdesc = adesc + (uint64_t)((kKB * kBlockBytes) >> 4);
+#pragma unroll
+                        for (int kk = 0; kk < kKB; ++kk)
+                            ptx::mma_bf16(acc, adesc + (uint64_t)((kk * kBlockBytes) >> 4),
+                                          bdesc + (uint64_t)((kk * kBlockBytesB) >> 4), idesc,
+                                          (s2 == 0 && kk == 0) ? 0u : 1u);
+                        ptx::mma_commit(&empty[s2]);
+                    }
+                    if (stop) break;
+                    ph ^= 1u;
+                    ptx::mma_commit(&tmem_full[b]);
+                    ++unit;
+                }
+                continue;
+            }
+            // fewer ring slots than stages per unit: slot by slot
             int in_unit = 0;
             uint32_t acc = tmem_base;
             for (int j = 0; j < nst; ++j) {
@@ -766,8 +813,10 @@ int crt_scale_bits(int N, int64_t k) {
 CrtLayout crt_layout(int N, int64_t m, int64_t n, int64_t k) {
     CrtLayout L{};
     L.N = N;
-    L.kp = ((k + kStep - 1) / kStep) * kStep;
-    if (L.kp == 0) L.kp = kStep;
+    // K padded to whole exact units (the split kernels write zero residues there):
+    // every unit of the products kernel is kUnitStages full stages
+    L.kp = ((k + kUnitK - 1) / kUnitK) * kUnitK;
+    if (L.kp == 0) L.kp = kUnitK;
     L.mp = (m + kTileLines - 1) / kTileLines * kTileLines;
     L.np = (n + kTileLinesB - 1) / kTileLinesB * kTileLinesB;
     L.b = crt_scale_bits(N, k);
