@@ -47,7 +47,8 @@ FP64_FLOP_PER_CLK_SM = 4.0
 # DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) of one launch of the
 # dominant kernel, from one ncu capture of the kernel as it is now:
 # (kernel, n, slices) -> bytes.  Reported only for that exact workload.
-MEASURED_TRAFFIC = {("emu_products_kernel", 8192, 10): int(9.80e9 + 559.31e6)}
+MEASURED_TRAFFIC = {("emu_products_kernel", 8192, 10): int(9.80e9 + 559.31e6),
+                    ("crt_products_kernel", 8192, 13): int(13.08e9 + 2.05e9)}
 
 
 def parse():
@@ -1212,12 +1213,17 @@ def main():
     barrier()
     e0 = torch.cuda.Event(enable_timing=True)
     e1 = torch.cuda.Event(enable_timing=True)
+    marks = [torch.cuda.Event(enable_timing=True) for _ in range(e2e_steps - 1)]
     e0.record(stream)
-    for _ in range(e2e_steps):
+    for i in range(e2e_steps):
         e2e_step()
+        if i + 1 < e2e_steps:
+            marks[i].record(stream)
     e1.record(stream)
     torch.cuda.synchronize()
     e2e_ms = slowest(e0.elapsed_time(e1)) / e2e_steps
+    bounds = [e0] + marks + [e1]
+    e2e_each = sorted(bounds[i].elapsed_time(bounds[i + 1]) for i in range(e2e_steps))
     q.wait()
     link_after = link_gbs()
     del link_dst
@@ -1268,6 +1274,9 @@ def main():
         "e2e": {"value": round(replica_value(flops, world, e2e_ms) / 1e12, 3), "unit": "TFLOP/s",
                 "h2d_bytes_per_step": 2 * 8 * n * n, "d2h_bytes_per_step": 8 * n * n,
                 "ms_per_step": round(e2e_ms, 4),
+                "step_ms_min_median_max": [round(e2e_each[0], 3),
+                                           round(e2e_each[len(e2e_each) // 2], 3),
+                                           round(e2e_each[-1], 3)],
                 "link_h2d_gbs_before_after": [link_before, link_after]},
         "clocks": clk,
     }
