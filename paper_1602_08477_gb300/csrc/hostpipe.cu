@@ -231,7 +231,7 @@ cudaError_t copy_rows(void* dst, size_t dpitch, const void* src, size_t spitch,
 // time after its products: the first part's copy back then runs under the second
 // part's products (planning estimates below; the result does not depend on them).
 constexpr int kCrtBBlocks = 4;
-constexpr double kPlanItemFlopsPerSm = 8.8e12;  // BF16 residue products, per SM and second
+constexpr double kPlanItemFlopsPerSm = 10.5e12;  // BF16 residue products, per SM and second
 constexpr double kPlanLinkBack = 190e9;         // device -> host bytes per second
 
 HostSchedule crt_host_schedule(int N, int64_t m, int64_t n, int64_t kp, int sms) {

@@ -871,6 +871,9 @@ cudaError_t crt_split_b(const Launch& L, int N, int b, int64_t n, int64_t k, con
 cudaError_t crt_residue_products(const Launch& L, int N, int64_t m, int64_t n, int64_t kp,
                                  const uint8_t* ares, const uint8_t* bres, int16_t* cres) {
     if (m == 0 || n == 0) return cudaSuccess;
+    // the residues' K extent is whole exact units (crt_layout pads it so): the
+    // kernel's unit loop has no partial stages
+    if (kp <= 0 || kp % kUnitK != 0) return cudaErrorInvalidValue;
     const int64_t mp = (m + kTileLines - 1) / kTileLines * kTileLines;
     const int64_t np = (n + kTileLinesB - 1) / kTileLinesB * kTileLinesB;
     {
