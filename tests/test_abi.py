@@ -161,3 +161,19 @@ def test_library_binds_the_shared_cuda_runtime(lib):
     r = subprocess.run([sys.executable, "-c", code, _lib.LIB_PATH], capture_output=True,
                        text=True, check=True)
     assert r.stdout.strip() == "True"
+
+
+def test_residue_workspace_pads_k_to_whole_exact_units(lib):
+    # the residue precision stores its residues over K padded to whole units of
+    # 256 (the products kernel's exact FP32 units, four full pipeline stages
+    # each): the workspace is constant within a unit and grows by the residue
+    # planes of A and B (2 bytes x 13 moduli x padded lines) per unit
+    from paper_1602_08477_gb300 import workspace_size
+    m, n, N = 300, 260, 13
+    size = {k: workspace_size("emulated_crt", N, m, n, k) for k in (1, 17, 255, 256, 257, 511,
+                                                                     512, 513)}
+    assert size[1] == size[17] == size[255] == size[256]
+    assert size[257] == size[511] == size[512] > size[256]
+    mp, np_ = 384, 512  # rows of A padded to 128-row tiles, columns of B to 256
+    assert size[257] - size[256] == 2 * N * (mp + np_) * 256
+    assert size[513] - size[512] == 2 * N * (mp + np_) * 256
