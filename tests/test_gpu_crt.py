@@ -51,6 +51,17 @@ def test_bit_exact_against_model(gb, N, k):
     assert np.array_equal(bits(got), bits(want))
 
 
+@pytest.mark.parametrize("m,n,k", [(1, 1, 1000), (1, 513, 33), (257, 1, 300), (2, 3, 1),
+                                   (129, 255, 513)])
+def test_degenerate_and_single_line_shapes(gb, m, n, k):
+    # one row and/or one column (a single partly filled tile), K of one element,
+    # and K one past a whole unit of 256 (the padded K extent then holds a second,
+    # almost empty unit of zero residues)
+    A, B, C0 = inputs("uniform", m, n, k, 903 + m + n)
+    want = ozaki_crt.crt_gemm(0.5, A, B, -1.0, C0, N=13)
+    assert np.array_equal(bits(run(gb, A, B, C0, 0.5, -1.0, 13)), bits(want))
+
+
 @pytest.mark.parametrize("k", [256, 257, 4000, 17000])
 def test_long_k_exact_units(gb, k):
     # K in units of 256 (FP32 sums exact), the int32 totals reduced every 64 units
